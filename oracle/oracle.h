@@ -1,0 +1,101 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle of the hybrid stochastic-particle Shakhov /
+ * DSMC time step (Jin, Liu, Yang, Cao, Zhuo, Zhong, "A hybrid numerical
+ * algorithm based on the stochastic particle Shakhov and DSMC method",
+ * arXiv:2506.23917).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library; it
+ * is slow on purpose, single threaded, and written as a direct restatement
+ * of the paper's steps (Sec. III.B, Steps 1-6).  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares
+ * no code, header or constant table with the CUDA library.
+ *
+ * One context = one flow instance on a uniform Cartesian grid.
+ */
+#ifndef SP_ORACLE_H
+#define SP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_CAPACITY = -3 };
+enum { OR_BC_SPECULAR = 0, OR_BC_DIFFUSE = 1, OR_BC_OUTFLOW = 2, OR_BC_INFLOW = 3 };
+enum { OR_BODY_NONE = 0, OR_BODY_CIRCLE = 1, OR_BODY_SPHERE = 2 };
+enum { OR_MODE_HYBRID = 0, OR_MODE_DSMC = 1, OR_MODE_SHAKHOV = 2 };
+
+typedef struct or_config {
+  int32_t dim;            /* spatial dimensions 1..3; velocities are always 3-D */
+  int32_t n[3];           /* cells per axis (1 on unused axes)                    */
+  double lo[3], hi[3];    /* domain box (unused axes: a unit extent)              */
+  double m;               /* molecular mass                                       */
+  double R;               /* specific gas constant k/m                            */
+  double gamma;           /* ratio of specific heats                              */
+  double Pr;              /* Prandtl number of the Shakhov target                 */
+  double omega;           /* VHS viscosity-temperature exponent                   */
+  double T_ref, mu_ref;   /* mu = mu_ref (T/T_ref)^omega                          */
+  double d_ref;           /* VHS reference diameter                               */
+  double Fn;              /* real molecules per simulated particle                */
+  double cfl;             /* Delta t_G = cfl * min_k Delta t_c,k                  */
+  double dt_fixed;        /* > 0: constant step                                   */
+  int32_t face_bc[6];     /* face 2*axis+side (side 0 = lo)                       */
+  double face_T[6];       /* wall / reservoir temperature                         */
+  double face_n[6];       /* reservoir number density (inflow)                    */
+  double face_u[6][3];    /* reservoir drift velocity (inflow)                    */
+  int32_t ghost_layers;   /* reservoir layers outside each inflow face            */
+  int32_t body;           /* OR_BODY_*                                            */
+  double body_c[3], body_r, body_Tw;
+  const double* cell_volume; /* [ncells] or NULL (uniform)                        */
+  double sigc_T0;         /* temperature that seeds (sigma_T c_r)_max             */
+  int32_t n_steady;       /* first sampled step                                   */
+  uint64_t seed;
+  int32_t mode;           /* OR_MODE_*                                            */
+  int32_t ar_max;         /* Shakhov acceptance-rejection attempt cap             */
+} or_config;
+
+typedef struct or_ctx or_ctx;
+
+/* Moment fields, [field][cell]: */
+enum {
+  OR_F_N = 0, OR_F_n, OR_F_ux, OR_F_uy, OR_F_uz, OR_F_T, OR_F_qx, OR_F_qy, OR_F_qz,
+  OR_F_tau, OR_F_dtc, OR_F_ratio, OR_NFIELDS
+};
+
+int or_init(const or_config* cfg, or_ctx** out);
+/* pos: [dim][M] SoA, vel: [3][M] SoA.  Indexes and sorts the particles
+ * (state S_0) and sets Delta t^0 from the moments of S_0. */
+int or_set_particles(or_ctx* c, const double* pos, const double* vel, int64_t M);
+int or_step(or_ctx* c, int nsteps);
+int64_t or_num_particles(const or_ctx* c);
+int or_get_particles(const or_ctx* c, double* pos, double* vel, uint32_t* cell);
+/* kind 0: moments of the current state; kind 1: time-averaged (Step 6). */
+int or_moments(const or_ctx* c, int kind, double* out, int nfields);
+/* Records of the last step: per cell of S_n (cand, acc, nres, ar_attempts),
+ * per particle of S_n the resample flag, and the stable-sort permutation
+ * that produced S_{n+1} (old index of each new slot). */
+int or_get_step_record(const or_ctx* c, int64_t* cell4, uint8_t* resampled,
+                       uint32_t* perm, int64_t* n_old);
+int or_get_cell_start(const or_ctx* c, uint32_t* start);
+int or_get_sigc_max(const or_ctx* c, double* out);
+int or_get_sample(const or_ctx* c, double* out /* [8][ncells] */, int64_t* nsamp);
+double or_dt(const or_ctx* c);
+int64_t or_step_index(const or_ctx* c);
+/* counters over the whole run: removed, injected, move_capped, ar_capped */
+int or_get_totals(const or_ctx* c, int64_t* out4);
+void or_free(or_ctx* c);
+
+/* Building blocks exported for the pin tests. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_u01_from_words(uint32_t a, uint32_t b);
+double or_sigc(const or_config* cfg, double cr);   /* sigma_T(c_r) * c_r */
+/* one homogeneous collision step on a single cell's velocities (no transport);
+ * vel is [3][N] SoA, updated in place; returns the cell record. */
+int or_collide_cell(const or_config* cfg, int64_t step, uint32_t cell, double volume,
+                    double dt_G, double* sigc_max, double* vel, int64_t N,
+                    int64_t rec[4], uint8_t* resampled);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,97 @@
+"""Pins of the oracle's building blocks against published values and closed forms.
+
+* Philox4x32-10 against the published known-answer vectors.
+* The uniform conversion against its exact definition at the extremes.
+* The gas-model relations against the numbers printed in the paper (Sec. IV,
+  Table I, Sec. IV.B).
+* The VHS collision kernel sigma_T c_r: its Maxwellian average must equal
+  cbar / (n lambda) with lambda the VHS mean free path printed in Sec. IV --
+  a plausible slip in the cross-section (reduced mass, Gamma function,
+  exponent) changes this average.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+import oracle
+from paper_2506_23917_gb300 import workloads as W
+from tests.conftest import golden, read_gas_values
+
+
+def test_philox_known_answers():
+    with open(golden("philox4x32_10_kat.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_uniform_conversion_exact_extremes():
+    assert oracle.u01(0, 0) == 2.0 ** -53
+    assert oracle.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    # 52 bits: the top 26 bits of each word, high word first
+    assert oracle.u01(1 << 6, 0) == (2.0 * (1 << 26) + 1.0) * 2.0 ** -53
+    assert oracle.u01(0, 1 << 6) == 3.0 * 2.0 ** -53
+    assert oracle.u01(0, 63) == 2.0 ** -53  # low 6 bits discarded
+    rng = np.random.default_rng(0)
+    a = rng.integers(0, 2 ** 32, 2000, dtype=np.uint64)
+    b = rng.integers(0, 2 ** 32, 2000, dtype=np.uint64)
+    u = np.array([oracle.u01(int(x), int(y)) for x, y in zip(a, b)])
+    assert np.all((u > 0) & (u < 1))
+    assert abs(u.mean() - 0.5) < 0.03
+
+
+def test_argon_viscosity_from_diameter_matches_paper():
+    g = read_gas_values()
+    mu = W.vhs_mu_ref(W.ARGON["m"], g["argon_d_ref"], g["argon_T_ref"], g["argon_omega"])
+    assert abs(mu / g["argon_mu_ref"] - 1.0) < 2e-3
+
+
+def test_number_density_from_kn_matches_paper():
+    g = read_gas_values()
+    for kn, key in ((1e-2, "cyl_kn1e-2_n"), (1e-1, "cyl_kn1e-1_n")):
+        n = W.n_for_kn(kn, 1.0, g["argon_d_ref"], g["argon_T_ref"], g["cyl_T"], g["argon_omega"])
+        assert abs(n / g[key] - 1.0) < 1e-4
+    # Table I: rho_up = n m at Kn = 1e-2 and 1e-3 (L = 1 m), downstream 1/8
+    for kn, key in ((1e-2, "sod_kn1e-2_rho_up"), (1e-3, "sod_kn1e-3_rho_up")):
+        n = W.n_for_kn(kn, 1.0, g["argon_d_ref"], g["argon_T_ref"], 273.0, g["argon_omega"])
+        assert abs(n * W.ARGON["m"] / g[key] - 1.0) < 1e-4
+    assert abs(g["sod_kn1e-2_rho_down"] / g["sod_kn1e-2_rho_up"] - 0.125) < 1e-5
+    assert abs(g["sod_T_down"] / 273.0 - 0.8) < 1e-12
+    # the cylinder's freestream speed is Mach 5 in argon at 273 K (to the
+    # 0.5 % the paper's rounding of the gas constants allows)
+    a = math.sqrt(5.0 / 3.0 * W.KB / W.ARGON["m"] * 273.0)
+    assert abs(g["cyl_U"] / a - 5.0) < 3e-2
+
+
+def _argon_cfg(omega=0.81):
+    cfg = W.base_config(1, [1], [0.0], [1.0])
+    m = W.ARGON["m"]
+    cfg.update(m=m, R=W.KB / m, omega=omega, T_ref=273.0, d_ref=W.ARGON["d_ref"])
+    return cfg
+
+
+@pytest.mark.parametrize("omega", [0.5, 0.81, 1.0])
+@pytest.mark.parametrize("T", [273.0, 700.0])
+def test_vhs_kernel_maxwell_average_matches_mean_free_path(omega, T):
+    cfg = _argon_cfg(omega)
+    R = cfg["R"]
+    # relative speed of two Maxwellian molecules: 3-D Gaussian with variance 2RT
+    def pdf(cr):
+        return 4.0 * math.pi * cr * cr * (4.0 * math.pi * R * T) ** -1.5 * math.exp(-cr * cr / (4.0 * R * T))
+    s = math.sqrt(R * T)
+    avg = quad(lambda cr: oracle.sigc(cfg, cr) * pdf(cr), 0.0, 40.0 * s, epsrel=1e-11, limit=400)[0]
+    n = 1.0e20
+    lam = W.vhs_mfp(n, cfg["d_ref"], cfg["T_ref"], T, omega)
+    cbar = math.sqrt(8.0 * R * T / math.pi)
+    assert abs(avg / (cbar / (n * lam)) - 1.0) < 1e-6
+
+
+def test_hard_sphere_kernel_is_pi_d_squared_cr():
+    cfg = _argon_cfg(0.5)
+    for cr in (1.0, 250.0, 1234.5):
+        assert abs(oracle.sigc(cfg, cr) / (math.pi * cfg["d_ref"] ** 2 * cr) - 1.0) < 1e-14
