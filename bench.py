@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Throughput of the hybrid SP-Shakhov / DSMC time step on GB300.
+
+Workload (default): 2-D hypersonic argon flow past a cylinder -- Ma 5,
+Kn = 0.01 on the radius, VHS omega = 0.81, diffuse wall at T_inf, 600 x 300
+cells with analytic circular cut cells, 40 particles per freestream cell
+(~6.6 M particles), FP32 particle state with FP64 per-cell moments.  The
+flow is developed for --develop untimed steps from a uniform freestream,
+then --warmup steps, then exactly --steps timed steps (one CUDA graph per
+step).  value = particle-updates/s = (mean particle count) x steps / time,
+summed over ranks; under torchrun each rank advances its own independent
+instance (seed = rank), so scaling is weak.
+
+Extra keys: roofline of the dominant kernel (collision + free flight),
+the same workload in plain FP64 mode, an end-to-end figure through the C
+ABI with host buffers, and the CPU oracle timed on a bounded sample.
+--impl reference times the CPU oracle itself as the reference arm.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s and % HBM roofline, FP32+batched vs plain FP64 on one GB300"
+UNIT = "particle-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--develop", type=int, default=600)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=float, default=1.0)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--profile-steps", type=int, default=40)
+    return p.parse_args()
+
+
+def workload_name(scale):
+    nx, ny = max(4, int(round(600 * scale))), max(2, int(round(300 * scale)))
+    return f"cylinder2d_{nx}x{ny}_ppc40_Ma5_Kn0.01_argon_vhs"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            P = json.load(f)
+        return float(P["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def collide_traffic(src_hash):
+    """Per-particle DRAM traffic of the collision kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "collide_cylinder_traffic.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != src_hash:
+            return None
+        return float(kv["bytes_per_particle"])
+    except Exception:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sp_device.cuh", "sp_kern_f32.cu", "sp_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2506_23917_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def crop_config(cfg, x0, x1, y1):
+    """A sub-window of the cylinder grid (same cells) with open faces, used to
+    time the CPU oracle on a bounded sample of the workload."""
+    from paper_2506_23917_gb300 import workloads as W
+
+    dl = W.cell_size(cfg)
+    i0 = int(round((x0 - cfg["lo"][0]) / dl[0]))
+    i1 = int(round((x1 - cfg["lo"][0]) / dl[0]))
+    j1 = int(round((y1 - cfg["lo"][1]) / dl[1]))
+    c = dict(cfg)
+    c["n"] = [i1 - i0, j1, 1]
+    c["lo"] = [cfg["lo"][0] + i0 * dl[0], cfg["lo"][1], 0.0]
+    c["hi"] = [cfg["lo"][0] + i1 * dl[0], cfg["lo"][1] + j1 * dl[1], 1.0]
+    vol = np.asarray(cfg["cell_volume"]).reshape(cfg["n"][1], cfg["n"][0])
+    c["cell_volume"] = np.ascontiguousarray(vol[:j1, i0:i1]).ravel()
+    c["face_bc"] = [W.BC_OUTFLOW, W.BC_OUTFLOW, W.BC_SPECULAR, W.BC_OUTFLOW, W.BC_SPECULAR, W.BC_SPECULAR]
+    c["face_n"] = [0.0] * 6
+    return c
+
+
+def time_oracle(cfg, pos, vel, budget_s, max_steps, min_steps=1):
+    """Step the oracle on (cfg, pos, vel) for up to budget_s seconds."""
+    import oracle
+
+    o = oracle.Oracle(cfg)
+    o.set_particles(pos, vel)
+    upd, t, n = 0, 0.0, 0
+    while n < max_steps and (n < min_steps or t < budget_s):
+        m = o.M
+        t0 = time.perf_counter()
+        o.step(1)
+        t += time.perf_counter() - t0
+        upd += m
+        n += 1
+    return upd, t, n
+
+
+def cpu_sample(cfg, pos, vel, budget_s=15.0):
+    x0, x1, y1 = -1.8, 0.4, 1.5
+    c = crop_config(cfg, x0, x1, y1)
+    m = (pos[0] >= c["lo"][0]) & (pos[0] < c["hi"][0]) & (pos[1] < c["hi"][1])
+    upd, t, n = time_oracle(c, pos[:, m], vel[:, m], budget_s, max_steps=10 ** 6, min_steps=2)
+    sample = (f"oracle (FP64, 1 thread) on a {c['n'][0]}x{c['n'][1]}-cell window "
+              f"[{x0},{x1}]x[0,{y1}] R of the developed state ({int(m.sum())} particles), {n} steps")
+    return upd / t, sample
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on a window of the same
+    workload (uniform freestream start), sized so the run ends in minutes."""
+    from paper_2506_23917_gb300 import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg, regions = W.cylinder(scale=args.scale, n_steady=0)
+    total = args.steps + args.warmup
+    per_step_s = max(0.02, min(1.0, 120.0 / max(total, 1)))
+    target = per_step_s * 3.0e6  # particles the oracle moves in per_step_s
+    ppc = 40.0
+    dl = W.cell_size(cfg)
+    w = max(8, int(math.sqrt(target / ppc)))
+    x1 = -1.0 + 0.3
+    x0 = max(cfg["lo"][0], x1 - w * dl[0])
+    y1 = min(cfg["hi"][1], w * dl[1])
+    c = crop_config(cfg, x0, x1, y1)
+    reg = [dict(lo=[c["lo"][0], 0.0], hi=[c["hi"][0], c["hi"][1]], n=cfg["face_n"][0], T=273.0,
+                u=cfg["face_u"][0])]
+    pos, vel = W.fill_regions(c, reg, 1)
+    import oracle
+
+    o = oracle.Oracle(c)
+    o.set_particles(pos, vel)
+    o.step(args.warmup)
+    upd, t = 0, 0.0
+    for _ in range(args.steps):
+        m = o.M
+        t0 = time.perf_counter()
+        o.step(1)
+        t += time.perf_counter() - t0
+        upd += m
+    value = upd / t if t > 0 else 0.0
+    sample = (f"oracle (FP64, 1 thread) on a {c['n'][0]}x{c['n'][1]}-cell window of the "
+              f"{workload_name(args.scale)} grid from a uniform freestream start, {len(vel[0])} particles")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(args.scale), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_2506_23917_gb300 as sp
+    from paper_2506_23917_gb300 import build as spbuild
+    from paper_2506_23917_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        spbuild.build()
+    if dist:
+        dist.barrier()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    cfg, regions = W.cylinder(scale=args.scale, seed=1 + rank, n_steady=0)
+    pos, vel = W.fill_regions(cfg, regions, 1 + rank)
+    M_init = vel.shape[1]
+    cap = int(1.5 * M_init) + 200000
+    stream = torch.cuda.current_stream()
+    prec = sp.FP32 if args.precision == "fp32" else sp.FP64
+    sim = sp.Sim(cfg, prec, capacity=cap)
+    sim.set_particles(0, pos, vel)
+    sim.step(args.develop)
+    sim.sync()
+    sim.step(args.warmup)
+    sim.sync()
+    M0 = sim.count(0)
+    launches = sim.launches_per_step()
+
+    clocks = Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    sim.sync()
+    ms = e0.elapsed_time(e1)
+    M1 = sim.count(0)
+    upd = args.steps * 0.5 * (M0 + M1)
+    t_max, upd_sum = ms, upd
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([upd], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        t_max, upd_sum = float(t.item()), float(u.item())
+    value = upd_sum / (t_max * 1e-3)
+    ms_per_step = t_max / args.steps
+
+    # --- roofline of the dominant kernel (collision + free flight), measured
+    # with CUDA events around each kernel group on the library's stream
+    prof = sim.step_profiled(args.profile_steps)
+    sim.sync()
+    Mp = sim.count(0)
+    S = 4 * (cfg["dim"] + 3) if prec == sp.FP32 else 8 * (cfg["dim"] + 3)
+    collide_ms = prof[0] / args.profile_steps
+    bytes_collide = (2 * S + 4) * Mp  # state read + state write + new key
+    peak, peak_kind = load_peaks()
+    achieved = bytes_collide / (collide_ms * 1e-3) / 1e9
+    src_hash = kernel_source_hash()
+    tpp = collide_traffic(src_hash)
+    step_ms = sum(prof) / args.profile_steps
+    step_bytes = (2 * S + 8) * Mp
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tpp * Mp) if tpp is not None else None,
+                "kernel": "k_collide (gather + moments + DSMC + Shakhov + rescale + sample + move + key)",
+                "bytes_per_particle": 2 * S + 4, "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel_ms": collide_ms,
+                "share_of_step": prof[0] / sum(prof),
+                "group_ms_per_step": {k: v / args.profile_steps for k, v in
+                                      zip(["collide", "inject", "scan", "scatter"], prof)},
+                "step_frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak,
+                "step_bytes_per_particle": 2 * S + 8}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == sp.FP32 else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.scale), "cells": int(np.prod(cfg["n"][:2])),
+                       "particles_per_rank": int(0.5 * (M0 + M1)), "developed_steps": args.develop,
+                       "state": "FP32 particles, FP64 per-cell moments" if prec == sp.FP32 else "FP64",
+                       "l2": "inputs larger than L2 (state 2 x %.0f MB)" % (S * M0 / 1e6),
+                       "graph": "one CUDA graph per step", "parallelism": f"replicas{world}"},
+            "clocks": clk, "gpu_launches": launches * args.steps, "roofline": roofline}
+
+    # --- plain FP64 form of the same workload
+    if not args.no_fp64 and prec == sp.FP32:
+        sim64 = sp.Sim(cfg, sp.FP64, capacity=cap)
+        sim64.set_particles(0, pos, vel)
+        sim64.step(args.develop)
+        sim64.sync()
+        sim64.step(args.warmup)
+        sim64.sync()
+        k64 = max(20, args.steps // 10)
+        m0 = sim64.count(0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim64.step(k64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sim64.sync()
+        t64 = e0.elapsed_time(e1)
+        m1 = sim64.count(0)
+        v64 = k64 * 0.5 * (m0 + m1) / (t64 * 1e-3)
+        p64 = sim64.step_profiled(10)
+        line["fp64_plain"] = {"value": v64 * world, "unit": UNIT, "ms_per_step": t64 / k64, "steps": k64,
+                              "collide_ms": p64[0] / 10, "fp32_over_fp64": value / (v64 * world)}
+        sim64.close()
+
+    # --- end to end through the C ABI with host buffers: per step, upload
+    # the state from pinned host memory, advance one step, read the moments
+    if not args.no_e2e:
+        po, vo, _ = sim.particles(0)
+        n_e2e = po.shape[1]
+        hp = torch.from_numpy(np.ascontiguousarray(po)).pin_memory()
+        hv = torch.from_numpy(np.ascontiguousarray(vo)).pin_memory()
+        out = torch.empty((len(sp.FIELDS), sim.ncells[0]), dtype=torch.float64).pin_memory()
+        K2 = 20
+        for it in range(K2 + 2):
+            if it == 2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            sim.set_particles_ptr(0, hp.data_ptr(), hv.data_ptr(), n_e2e)
+            sim.step(1)
+            sim.moments_into(0, 0, out.data_ptr())
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        line["e2e"] = {"value": world * K2 * n_e2e / te, "unit": UNIT,
+                       "h2d_bytes_per_step": 8 * (cfg["dim"] + 3) * n_e2e,
+                       "d2h_bytes_per_step": 8 * len(sp.FIELDS) * sim.ncells[0],
+                       "note": "per step: pinned host state -> device, one step, moments -> pinned host"}
+
+    # --- CPU oracle on a bounded sample of the same (developed) state
+    if rank == 0 and world >= 1 and not args.no_cpu:
+        po, vo, _ = sim.particles(0)
+        v_cpu, sample = cpu_sample(cfg, po, vo)
+        line["cpu_baseline"] = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

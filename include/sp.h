@@ -1,0 +1,179 @@
+/*
+ * sp.h -- C ABI of libsp, a GB300 (sm_103a) implementation of the per-time-
+ * step particle pipeline of the hybrid stochastic-particle Shakhov / DSMC
+ * method of Jin, Liu, Yang, Cao, Zhuo, Zhong, arXiv:2506.23917.
+ *
+ * One call of sp_step() advances every flow instance of a context by one
+ * global time step, following Sec. III.B of the paper:
+ *   Step 3  index particles into cells and form the per-cell moments
+ *           n, U, T, Q with the unbiased estimators of Step 3;
+ *   Step 4  local observation time dt_c (Eq. "local time step"), relaxation
+ *           time tau = mu/p, the split of the step into a DSMC part and a
+ *           Shakhov part (Eqs. "tDSMC", "tShakhov"), the NTC/VHS collisions
+ *           of Sec. II.A, the Shakhov resampling of Sec. II.B (Eqs.
+ *           "Ncol_SBGK", "Maxwell", "A_cal") and the conservation rescale;
+ *   Step 5  time-averaged sums after N_steady;
+ *   Step 2  free flight (Eq. "free transport") with specular / diffuse
+ *           walls, a diffuse circle (2-D) or sphere (3-D) body, removal at
+ *           open faces, and injection from ghost-cell reservoirs at inflow
+ *           faces; the global step of the next interval is
+ *           Delta t_G = cfl * min_k dt_c,k (Eq. "global time step").
+ * The state between calls is "indexed and sorted by cell, not yet
+ * collided".  All random numbers come from Philox4x32-10 streams keyed by
+ * (seed) and counted by (step, cell or reservoir cell, slot, purpose), so
+ * the FP64 mode reproduces the CPU oracle particle for particle.
+ *
+ * Conventions
+ *  - Every function returns an sp_status; no exception crosses the ABI.
+ *  - All pointers in this header are HOST pointers unless stated otherwise.
+ *    Caller buffers are read or written before the call returns (the call
+ *    synchronises the context's stream when it copies data to the host).
+ *  - The library owns all device memory of a context; it allocates it in
+ *    sp_init() and frees it in sp_free().
+ *  - Device work is enqueued on the CUDA stream given to sp_init() (NULL
+ *    selects the legacy default stream of the current device).
+ *  - A device-side failure (capacity overflow, a cell above the staging
+ *    capacity, a bounce or acceptance-rejection cap) sets a sticky flag that
+ *    the next synchronising call reports as SP_ERR_DEVICE or
+ *    SP_ERR_CAPACITY; sp_errors() reads the individual counters.
+ */
+#ifndef SP_H
+#define SP_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SP_OK = 0,
+  SP_ERR_ARG = -1,      /* invalid argument or configuration              */
+  SP_ERR_CUDA = -2,     /* a CUDA runtime call failed                      */
+  SP_ERR_CAPACITY = -3, /* particle capacity or per-cell capacity exceeded */
+  SP_ERR_DEVICE = -4,   /* sticky device error flag set                    */
+  SP_ERR_STATE = -5     /* call out of order (e.g. sp_step before particles) */
+} sp_status;
+
+typedef enum { SP_FP64 = 0, SP_FP32 = 1 } sp_precision;
+typedef enum { SP_BC_SPECULAR = 0, SP_BC_DIFFUSE = 1, SP_BC_OUTFLOW = 2, SP_BC_INFLOW = 3 } sp_bc;
+typedef enum { SP_BODY_NONE = 0, SP_BODY_CIRCLE = 1, SP_BODY_SPHERE = 2 } sp_body;
+typedef enum { SP_MODE_HYBRID = 0, SP_MODE_DSMC = 1, SP_MODE_SHAKHOV = 2 } sp_mode;
+
+/* One flow instance on a uniform Cartesian grid.  Units are any consistent
+ * set (SI or nondimensional).  Faces are numbered 2*axis + side, side 0 is
+ * the lower face. */
+typedef struct sp_config {
+  int32_t dim;            /* spatial dimensions 1..3 (velocities are 3-D)    */
+  int32_t n[3];           /* cells per axis; unused axes are forced to 1     */
+  double lo[3], hi[3];    /* domain box; unused axes give the unit depth     */
+  double m;               /* molecular mass                                  */
+  double R;               /* specific gas constant k/m                       */
+  double gamma;           /* ratio of specific heats (local time step)       */
+  double Pr;              /* Prandtl number of the Shakhov target g^S        */
+  double omega;           /* VHS exponent: mu = mu_ref (T/T_ref)^omega       */
+  double T_ref, mu_ref;   /* VHS reference temperature and viscosity         */
+  double d_ref;           /* VHS reference diameter (cross-section)          */
+  double Fn;              /* real molecules per simulated particle           */
+  double cfl;             /* Delta t_G = cfl * min_k dt_c,k                  */
+  double dt_fixed;        /* > 0: constant Delta t_G                         */
+  int32_t face_bc[6];     /* sp_bc per face                                  */
+  double face_T[6];       /* wall temperature (diffuse) / reservoir T (inflow) */
+  double face_n[6];       /* reservoir number density (inflow)               */
+  double face_u[6][3];    /* reservoir drift velocity (inflow)               */
+  int32_t ghost_layers;   /* reservoir cell layers outside each inflow face  */
+  int32_t body;           /* sp_body; diffuse at body_Tw                     */
+  double body_c[3], body_r, body_Tw;
+  const double* cell_volume; /* host [ncells] fluid volume per cell, or NULL
+                                (uniform); read during sp_init only        */
+  double sigc_T0;         /* (sigma_T c_r)_max starts at 2 sigma_T(cbar) cbar,
+                             cbar = 4 sqrt(R sigc_T0 / pi)                   */
+  int32_t n_steady;       /* first step index that is time-averaged          */
+  uint64_t seed;          /* Philox key of this instance                     */
+  int32_t mode;           /* sp_mode: hybrid, or one sub-step forced         */
+  int32_t ar_max;         /* cap on Shakhov acceptance-rejection attempts    */
+} sp_config;
+
+typedef struct sp_ctx sp_ctx;
+
+/* Moment fields, laid out [field][cell] in sp_moments() output. */
+enum {
+  SP_F_N = 0, SP_F_n, SP_F_ux, SP_F_uy, SP_F_uz, SP_F_T, SP_F_qx, SP_F_qy, SP_F_qz,
+  SP_F_tau, SP_F_dtc, SP_F_ratio, SP_NFIELDS
+};
+
+/* Create a context holding n_instances independent flows (cfgs[0..n)), all
+ * with the same dim, stored and advanced in one set of kernels.
+ * precision: SP_FP64 (state and arithmetic in FP64) or SP_FP32 (particle
+ * state and per-particle arithmetic in FP32; per-cell moments, relaxation
+ * weights, rescale factors and time averages in FP64).
+ * capacity: device particle slots over all instances (<= 2^31).
+ * stream: a cudaStream_t or NULL.  Errors: SP_ERR_ARG for an invalid
+ * config, SP_ERR_CUDA if device memory cannot be had. */
+sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t capacity,
+                  void* stream, sp_ctx** out);
+
+/* Step 1 of the paper: give instance `inst` its particles.  pos is
+ * [dim][n] (SoA, row d holds coordinate d), vel is [3][n]; both host FP64.
+ * The data is copied to a device staging area on the context's stream
+ * (asynchronously when the host memory is page-locked: keep it unchanged
+ * until the next synchronising call).  At the next sp_step / query every
+ * instance's staged particles are converted to the context's precision,
+ * indexed and stably sorted by cell (input order within a cell), and
+ * Delta t of the next step is set to cfl * min dt_c of that state.  Calling
+ * it again restarts every instance from its staged particles; sampling sums
+ * and the step counter are kept.  Errors: SP_ERR_CAPACITY if n exceeds the
+ * capacity. */
+sp_status sp_set_particles(sp_ctx* ctx, int inst, const double* pos, const double* vel, int64_t n);
+
+/* Advance all instances by n_steps global steps (asynchronous). */
+sp_status sp_step(sp_ctx* ctx, int n_steps);
+
+/* kind 0: moments of the current state (fields SP_F_*); kind 1: time-
+ * averaged fields of Step 6 (N, n, ux, uy, uz, T and the mean DSMC ratio in
+ * SP_F_ratio; the other fields are 0).  out: host [n_fields][ncells(inst)]. */
+sp_status sp_moments(sp_ctx* ctx, int inst, int kind, double* out, int n_fields);
+
+/* Current particles of instance inst in sorted order (host FP64, SoA).
+ * Any pointer may be NULL.  *n receives the count; with pos == vel == cell
+ * == NULL only the count is returned. */
+sp_status sp_get_particles(sp_ctx* ctx, int inst, double* pos, double* vel, uint32_t* cell,
+                           int64_t* n);
+
+/* Record of the last step of instance inst, for parity checks: cell4 host
+ * int64 [4][ncells] = (candidates, accepted, resampled, AR attempts) per cell
+ * of the collided state; resampled host uint8 [n_old] per particle of that
+ * state; perm host uint32 [n] = source index (in the moved sequence, injected
+ * particles appended) of each slot of the new state.  Recording must be
+ * enabled with sp_set_record(ctx, 1) before the step. */
+sp_status sp_set_record(sp_ctx* ctx, int on);
+sp_status sp_get_step_record(sp_ctx* ctx, int inst, int64_t* cell4, uint8_t* resampled,
+                             uint32_t* perm, int64_t* n_old);
+
+/* Cell offsets of the current state of instance inst: host uint32
+ * [ncells+1], relative to the instance's first particle. */
+sp_status sp_get_cell_start(sp_ctx* ctx, int inst, uint32_t* start);
+/* Per-cell (sigma_T c_r)_max of instance inst: host double [ncells]. */
+sp_status sp_get_sigc_max(sp_ctx* ctx, int inst, double* out);
+/* Delta t of the next step of instance inst, and the global step index. */
+sp_status sp_get_dt(sp_ctx* ctx, int inst, double* dt, int64_t* step);
+/* Device error counters: [0] capacity overflow, [1] cell above staging
+ * capacity, [2] bounce cap, [3] AR cap, [4] NTC candidate cap.
+ * Clears nothing. */
+sp_status sp_errors(sp_ctx* ctx, int64_t* out5);
+/* Advance n_steps steps launched one kernel at a time (no CUDA graph) with
+ * CUDA events around the kernel groups; ms[0..min(n_slots,4)) receives the
+ * summed device time of (0) the collision + free-flight kernels, (1) the
+ * reservoir injection, (2) the histogram scan and bookkeeping, (3) the
+ * scatter.  Synchronises after every step (for measurement only). */
+sp_status sp_step_profiled(sp_ctx* ctx, int n_steps, double* ms, int n_slots);
+/* Wait for the context's stream. */
+sp_status sp_sync(sp_ctx* ctx);
+/* Number of kernel launches one sp_step() issues (for launch accounting). */
+int sp_launches_per_step(sp_ctx* ctx);
+sp_status sp_free(sp_ctx* ctx);
+const char* sp_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

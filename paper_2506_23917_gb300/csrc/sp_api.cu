@@ -1,0 +1,800 @@
+// sp_api.cu -- host driver and C ABI of libsp (see include/sp.h).
+//
+// Per step the driver enqueues, on the context's stream:
+//   1. k_collide (warp per cell, cells up to kCapSmall particles) and its
+//      big-cell launch (one warp per cell with a large staging area):
+//      gather through perm in stable order -> Step 3 moments -> Step 4
+//      DSMC / Shakhov / rescale -> Step 5 sums -> Step 2 free flight of the
+//      next interval, new key and histogram;
+//   2. reservoir injection at inflow faces (count, scan, write);
+//   3. exclusive scan of the histogram -> cell offsets of the new state;
+//   4. bookkeeping (particle count, Delta t of the next step, step index);
+//   5. scatter of source indices into the new cell order.
+// The sequence is captured once per buffer parity as a CUDA graph and
+// replayed by sp_step().
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/sp.h"
+#include "sp_internal.h"
+
+using namespace sp;
+
+namespace {
+constexpr int kBigCap = 8192;
+constexpr double kPiHost = 3.14159265358979323846;
+}  // namespace
+
+struct sp_ctx {
+  int n_inst = 0, dim = 0, prec = 0;
+  size_t tsize = 8;
+  std::vector<InstParams> hP;
+  std::vector<sp_config> cfg;
+  InstParams* dP = nullptr;
+  int64_t NC = 0, cap = 0;
+  // device buffers
+  void* pos[2][3] = {{nullptr}};
+  void* vel[2][3] = {{nullptr}};
+  uint32_t *key = nullptr, *perm = nullptr, *count = nullptr, *fill = nullptr, *start = nullptr;
+  uint32_t *cell_inst = nullptr, *scan_part = nullptr, *big_list = nullptr, *big_count = nullptr;
+  double *vol = nullptr, *smax = nullptr, *samp = nullptr;
+  int32_t* rec = nullptr;
+  uint8_t* resamp = nullptr;
+  double* dt_cur = nullptr;
+  unsigned long long* dt_min = nullptr;
+  uint32_t *step_d = nullptr, *Mcur = nullptr, *Mtot = nullptr;
+  unsigned long long* err = nullptr;
+  GhostCell* ghosts = nullptr;
+  int64_t n_ghost = 0;
+  uint32_t *gcount = nullptr, *goff = nullptr, *gscan_part = nullptr;
+  cudaStream_t stream = nullptr;
+  int cur = 0;
+  int64_t step_host = 0;
+  bool uploaded = false, dirty = false, record = false;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_ok = false;
+  int launches = 0;
+  std::vector<double*> dstage;    // per instance: FP64 [dim][n] then [3][n], device
+  std::vector<int64_t> stage_n, stage_cap;
+  uint32_t* part_inst = nullptr;  // [cap] instance of each uploaded particle
+  std::vector<uint32_t> prev_start;  // [NC+1] of the state before the last step (record mode)
+  std::vector<unsigned long long> hinf, hmin;  // host mirrors used by upload()
+  std::vector<double> hdt;
+  uint32_t hM = 0;
+};
+
+namespace {
+
+sp_status cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return SP_OK;
+  fprintf(stderr, "libsp: CUDA error %s\n", cudaGetErrorString(e));
+  return SP_ERR_CUDA;
+}
+#define CK(x)                                     \
+  do {                                            \
+    cudaError_t e_ = (x);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_);  \
+  } while (0)
+
+template <class P>
+cudaError_t dalloc(P** p, size_t bytes) {
+  return cudaMalloc((void**)p, bytes ? bytes : 16);
+}
+
+void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
+  memset(P, 0, sizeof *P);
+  P->dim = c.dim;
+  for (int d = 0; d < 3; ++d) {
+    P->n[d] = d < c.dim ? c.n[d] : 1;
+    P->lo[d] = c.lo[d];
+    P->hi[d] = c.hi[d];
+    P->dl[d] = (c.hi[d] - c.lo[d]) / (double)P->n[d];
+    P->inv_d[d] = (double)P->n[d] / (c.hi[d] - c.lo[d]);
+  }
+  P->Lmin = INFINITY;
+  for (int d = 0; d < c.dim; ++d) P->Lmin = std::min(P->Lmin, P->dl[d]);
+  P->m = c.m;
+  P->R = c.R;
+  P->gamma = c.gamma;
+  P->Pr = c.Pr;
+  P->omega = c.omega;
+  P->T_ref = c.T_ref;
+  P->mu_ref = c.mu_ref;
+  P->Fn = c.Fn;
+  P->cfl = c.cfl;
+  P->dt_fixed = c.dt_fixed;
+  // VHS (Bird): sigma_T c_r = pi d^2 (4 R T_ref)^(w - 1/2) / Gamma(5/2 - w) c_r^(2 - 2w)
+  P->sigc_coef = kPiHost * c.d_ref * c.d_ref * pow(4.0 * c.R * c.T_ref, c.omega - 0.5) /
+                 tgamma(2.5 - c.omega);
+  P->sigc_exp = 2.0 - 2.0 * c.omega;
+  for (int f = 0; f < 6; ++f) {
+    P->face_bc[f] = c.face_bc[f];
+    P->face_T[f] = c.face_T[f];
+  }
+  P->body = c.body;
+  for (int d = 0; d < 3; ++d) P->body_c[d] = c.body_c[d];
+  P->body_r = c.body_r;
+  P->body_Tw = c.body_Tw;
+  P->n_steady = c.n_steady;
+  P->key0 = (uint32_t)c.seed;
+  P->key1 = (uint32_t)(c.seed >> 32);
+  P->mode = c.mode;
+  P->ar_max = c.ar_max < 1 ? 1 : c.ar_max;
+  P->cell_off = cell_off;
+  P->ncells = (int64_t)P->n[0] * P->n[1] * P->n[2];
+}
+
+bool valid(const sp_config& c, int dim) {
+  if (c.dim != dim || c.dim < 1 || c.dim > 3) return false;
+  for (int d = 0; d < 3; ++d) {
+    if (d < c.dim && c.n[d] < 1) return false;
+    if (!(c.hi[d] > c.lo[d])) return false;
+  }
+  if (!(c.R > 0) || !(c.m > 0) || !(c.Fn > 0) || !(c.mu_ref > 0) || !(c.T_ref > 0)) return false;
+  if (c.body == SP_BODY_CIRCLE && c.dim != 2) return false;
+  if (c.body == SP_BODY_SPHERE && c.dim != 3) return false;
+  return true;
+}
+
+// Reservoir cells in (face, layer-major, tangential) order with the same
+// arithmetic as the reference definition of their boxes.
+void build_ghosts(const sp_config& c, const InstParams& P, int inst, std::vector<GhostCell>& out) {
+  for (int f = 0; f < 6; ++f) {
+    const int ax = f / 2, side = f % 2;
+    if (ax >= c.dim || c.face_bc[f] != SP_BC_INFLOW) continue;
+    int ta[2], nt = 0;
+    for (int d = 0; d < c.dim; ++d)
+      if (d != ax) ta[nt++] = d;
+    int64_t ntan = 1;
+    for (int i = 0; i < nt; ++i) ntan *= P.n[ta[i]];
+    const int64_t ng = ntan * c.ghost_layers;
+    const double RT = c.R * c.face_T[f];
+    const double s2RT = sqrt(2.0 * RT);
+    for (int64_t gc = 0; gc < ng; ++gc) {
+      const int64_t layer = gc / ntan, t = gc % ntan;
+      GhostCell G;
+      memset(&G, 0, sizeof G);
+      G.inst = inst;
+      G.face = f;
+      G.gc = (uint32_t)gc;
+      for (int d = 0; d < 3; ++d) {
+        G.blo[d] = c.lo[d];
+        G.bhi[d] = c.hi[d];
+      }
+      int64_t tt = t;
+      for (int i = 0; i < nt; ++i) {
+        const int d = ta[i];
+        const int64_t id = tt % P.n[d];
+        tt /= P.n[d];
+        G.blo[d] = c.lo[d] + (double)id * P.dl[d];
+        G.bhi[d] = c.lo[d] + (double)(id + 1) * P.dl[d];
+      }
+      if (side == 0) {
+        G.blo[ax] = c.lo[ax] - (double)(layer + 1) * P.dl[ax];
+        G.bhi[ax] = c.lo[ax] - (double)layer * P.dl[ax];
+      } else {
+        G.blo[ax] = c.hi[ax] + (double)layer * P.dl[ax];
+        G.bhi[ax] = c.hi[ax] + (double)(layer + 1) * P.dl[ax];
+      }
+      const double Vg = (G.bhi[0] - G.blo[0]) * (G.bhi[1] - G.blo[1]) * (G.bhi[2] - G.blo[2]);
+      G.lam = c.face_n[f] * Vg / c.Fn;
+      G.s2RT = s2RT;
+      for (int d = 0; d < 3; ++d) G.u[d] = c.face_u[f][d];
+      out.push_back(G);
+    }
+  }
+}
+
+StepArgs make_step_args(sp_ctx* c, int par) {
+  StepArgs a;
+  memset(&a, 0, sizeof a);
+  for (int d = 0; d < 3; ++d) {
+    a.Apos[d] = c->pos[par][d];
+    a.Bpos[d] = c->pos[1 - par][d];
+    a.Avel[d] = c->vel[par][d];
+    a.Bvel[d] = c->vel[1 - par][d];
+  }
+  a.key = c->key;
+  a.perm = c->perm;
+  a.start = c->start;
+  a.count = c->count;
+  a.cell_inst = c->cell_inst;
+  a.vol = c->vol;
+  a.smax = c->smax;
+  a.samp = c->samp;
+  a.rec = c->record ? c->rec : nullptr;
+  a.resamp = c->record ? c->resamp : nullptr;
+  a.P = c->dP;
+  a.dt_cur = c->dt_cur;
+  a.dt_min = c->dt_min;
+  a.step = c->step_d;
+  a.big_list = c->big_list;
+  a.big_count = c->big_count;
+  a.err = c->err;
+  a.NC = c->NC;
+  a.cap = c->cap;
+  a.big_cap = kBigCap;
+  return a;
+}
+
+InjectArgs make_inject_args(sp_ctx* c, int par) {
+  InjectArgs a;
+  memset(&a, 0, sizeof a);
+  a.ghosts = c->ghosts;
+  a.n_ghost = c->n_ghost;
+  a.gcount = c->gcount;
+  a.goff = c->goff;
+  for (int d = 0; d < 3; ++d) {
+    a.Bpos[d] = c->pos[1 - par][d];
+    a.Bvel[d] = c->vel[1 - par][d];
+  }
+  a.key = c->key;
+  a.count = c->count;
+  a.P = c->dP;
+  a.dt_cur = c->dt_cur;
+  a.step = c->step_d;
+  a.Mcur = c->Mcur;
+  a.err = c->err;
+  a.cap = c->cap;
+  return a;
+}
+
+int small_grid(const sp_ctx* c) {
+  int64_t g = (c->NC + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+void launch_collide_p(sp_ctx* c, const StepArgs& a, bool big, int grid) {
+  if (c->prec == SP_FP64) launch_collide_f64(c->dim, a, big, grid, c->stream);
+  else launch_collide_f32(c->dim, a, big, grid, c->stream);
+}
+
+// Enqueue one step reading buffer `par` and writing buffer 1 - par.  With
+// ev != nullptr, events ev[0..4] bracket the four kernel groups (collide,
+// inject, scan + bookkeeping, scatter).
+int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
+  int n = 0;
+  const StepArgs a = make_step_args(c, par);
+  if (ev) cudaEventRecord(ev[0], c->stream);
+  launch_collide_p(c, a, false, small_grid(c)); ++n;
+  launch_collide_p(c, a, true, 2 * 152); ++n;
+  if (ev) cudaEventRecord(ev[1], c->stream);
+  if (c->n_ghost > 0) {
+    const InjectArgs ia = make_inject_args(c, par);
+    if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 0, c->stream);
+    else launch_inject_f32(c->dim, ia, 0, c->stream);
+    launch_scan(c->gcount, c->goff, c->n_ghost, c->gscan_part, c->stream);
+    if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 1, c->stream);
+    else launch_inject_f32(c->dim, ia, 1, c->stream);
+    n += 5;
+  }
+  if (ev) cudaEventRecord(ev[2], c->stream);
+  launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream); n += 3;
+  launch_cell_finalize(c->count, c->fill, c->NC, c->stream); ++n;
+  launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
+                       c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->stream); ++n;
+  if (ev) cudaEventRecord(ev[3], c->stream);
+  launch_scatter(c->key, c->start, c->fill, c->perm, c->Mtot, c->cap, c->stream); ++n;
+  if (ev) cudaEventRecord(ev[4], c->stream);
+  return n;
+}
+
+void destroy_graphs(sp_ctx* c) {
+  for (int i = 0; i < 2; ++i)
+    if (c->graph[i]) {
+      cudaGraphExecDestroy(c->graph[i]);
+      c->graph[i] = nullptr;
+    }
+  c->graph_ok = false;
+}
+
+sp_status build_graphs(sp_ctx* c) {
+  destroy_graphs(c);
+  for (int par = 0; par < 2; ++par) {
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = c->stream;
+    c->stream = cs;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      c->launches = enqueue_step(c, par);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    c->stream = saved;
+    cudaStreamDestroy(cs);
+    CK(e);
+    e = cudaGraphInstantiate(&c->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+  }
+  c->graph_ok = true;
+  return SP_OK;
+}
+
+sp_status check_errors(sp_ctx* c) {
+  unsigned long long h[kNumErr];
+  CK(cudaMemcpyAsync(h, c->err, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h[kErrCapacity] || h[kErrCellCap]) return SP_ERR_CAPACITY;
+  return SP_OK;
+}
+
+// Convert the staged particles of every instance into the state buffers,
+// index and sort them, and set Delta t of the next step from their moments.
+sp_status upload(sp_ctx* c) {
+  int64_t M = 0;
+  for (int i = 0; i < c->n_inst; ++i) M += c->stage_n[i];
+  if (M > c->cap) return SP_ERR_CAPACITY;
+  const int dim = c->dim;
+  int64_t off = 0;
+  for (int i = 0; i < c->n_inst; ++i) {
+    const int64_t n = c->stage_n[i];
+    if (n > 0) {
+      const double* sp = c->dstage[i];
+      if (c->prec == SP_FP64)
+        launch_stage_in_f64(dim, sp, sp + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
+                            (uint32_t)i, c->stream);
+      else
+        launch_stage_in_f32(dim, sp, sp + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
+                            (uint32_t)i, c->stream);
+    }
+    off += n;
+  }
+  CK(cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * c->NC, c->stream));
+  CK(cudaMemsetAsync(c->fill, 0, sizeof(uint32_t) * c->NC, c->stream));
+  const void* P3[3] = {c->pos[c->cur][0], c->pos[c->cur][1], c->pos[c->cur][2]};
+  if (c->prec == SP_FP64) launch_keys_f64(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
+  else launch_keys_f32(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
+  launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream);
+  launch_cell_finalize(c->count, c->fill, c->NC, c->stream);
+  c->hM = (uint32_t)M;
+  CK(cudaMemcpyAsync(c->Mtot, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->Mcur, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
+  launch_scatter(c->key, c->start, c->fill, c->perm, c->Mtot, c->cap, c->stream);
+  CK(cudaMemsetAsync(c->fill, 0, sizeof(uint32_t) * c->NC, c->stream));
+  // Delta t from the moments of this state
+  for (int i = 0; i < c->n_inst; ++i) c->hinf[i] = 0x7FF0000000000000ull;
+  CK(cudaMemcpyAsync(c->dt_min, c->hinf.data(), 8 * c->n_inst, cudaMemcpyHostToDevice, c->stream));
+  StepArgs a = make_step_args(c, c->cur);
+  if (c->prec == SP_FP64) launch_moments_f64(a, 0, c->NC, nullptr, c->stream);
+  else launch_moments_f32(a, 0, c->NC, nullptr, c->stream);
+  CK(cudaMemcpyAsync(c->hmin.data(), c->dt_min, 8 * c->n_inst, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (c->hP[i].dt_fixed > 0) c->hdt[i] = c->hP[i].dt_fixed;
+    else if (c->hmin[i] != 0x7FF0000000000000ull) {
+      double v;
+      memcpy(&v, &c->hmin[i], 8);
+      c->hdt[i] = c->hP[i].cfl * v;
+    } else {
+      return SP_ERR_ARG;  // no cell with two particles and no fixed step
+    }
+  }
+  CK(cudaMemcpyAsync(c->dt_cur, c->hdt.data(), 8 * c->n_inst, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->dt_min, c->hinf.data(), 8 * c->n_inst, cudaMemcpyHostToDevice, c->stream));
+  c->uploaded = true;
+  c->dirty = false;
+  return SP_OK;
+}
+
+sp_status ensure_ready(sp_ctx* c) {
+  if (c->dirty) {
+    sp_status s = upload(c);
+    if (s != SP_OK) return s;
+  }
+  if (!c->uploaded) return SP_ERR_STATE;
+  return SP_OK;
+}
+
+// host copy of start[] over an instance's cell range
+sp_status host_starts(sp_ctx* c, int inst, std::vector<uint32_t>& st) {
+  const InstParams& P = c->hP[inst];
+  st.resize(P.ncells + 1);
+  CK(cudaMemcpyAsync(st.data(), c->start + P.cell_off, sizeof(uint32_t) * (P.ncells + 1),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SP_OK;
+}
+
+// perm over an instance's range, each cell's entries in ascending order
+// (the stable order the collision kernel restores).
+sp_status host_perm_sorted(sp_ctx* c, const std::vector<uint32_t>& st, std::vector<uint32_t>& pm) {
+  const int64_t s0 = st[0], n = (int64_t)st.back() - s0;
+  pm.resize(std::max<int64_t>(n, 1));
+  if (n > 0)
+    CK(cudaMemcpyAsync(pm.data(), c->perm + s0, 4 * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (size_t k = 0; k + 1 < st.size(); ++k) std::sort(pm.begin() + (st[k] - s0), pm.begin() + (st[k + 1] - s0));
+  pm.resize(n);
+  return SP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sp_status_str(int s) {
+  switch (s) {
+    case SP_OK: return "ok";
+    case SP_ERR_ARG: return "invalid argument";
+    case SP_ERR_CUDA: return "CUDA runtime error";
+    case SP_ERR_CAPACITY: return "capacity exceeded";
+    case SP_ERR_DEVICE: return "device error flag set";
+    case SP_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t capacity,
+                  void* stream, sp_ctx** out) {
+  if (!cfgs || n_instances < 1 || !out || capacity < 1 || capacity > (int64_t(1) << 31)) return SP_ERR_ARG;
+  if (precision != SP_FP64 && precision != SP_FP32) return SP_ERR_ARG;
+  const int dim = cfgs[0].dim;
+  for (int i = 0; i < n_instances; ++i)
+    if (!valid(cfgs[i], dim)) return SP_ERR_ARG;
+  sp_ctx* c = new (std::nothrow) sp_ctx;
+  if (!c) return SP_ERR_ARG;
+  c->n_inst = n_instances;
+  c->dim = dim;
+  c->prec = precision;
+  c->tsize = precision == SP_FP64 ? 8 : 4;
+  c->stream = (cudaStream_t)stream;
+  c->cap = capacity;
+  c->cfg.assign(cfgs, cfgs + n_instances);
+  c->hP.resize(n_instances);
+  int64_t off = 0;
+  for (int i = 0; i < n_instances; ++i) {
+    fill_params(cfgs[i], &c->hP[i], off);
+    off += c->hP[i].ncells;
+  }
+  c->NC = off;
+  if (c->NC >= (int64_t)0xFFFFFFF0) { delete c; return SP_ERR_ARG; }
+  c->dstage.assign(n_instances, nullptr);
+  c->stage_n.assign(n_instances, 0);
+  c->stage_cap.assign(n_instances, 0);
+  c->hinf.assign(n_instances, 0x7FF0000000000000ull);
+  c->hmin.assign(n_instances, 0);
+  c->hdt.assign(n_instances, 0.0);
+  std::vector<GhostCell> gh;
+  for (int i = 0; i < n_instances; ++i) build_ghosts(cfgs[i], c->hP[i], i, gh);
+  c->n_ghost = (int64_t)gh.size();
+
+  sp_status st = [&]() -> sp_status {
+    CK(precision == SP_FP64 ? configure_f64(kBigCap) : configure_f32(kBigCap));
+    const int64_t NC = c->NC, cap = c->cap;
+    for (int b = 0; b < 2; ++b)
+      for (int d = 0; d < 3; ++d) {
+        if (d < dim) CK(dalloc(&c->pos[b][d], cap * c->tsize));
+        CK(dalloc(&c->vel[b][d], cap * c->tsize));
+      }
+    CK(dalloc(&c->key, 4 * cap));
+    CK(dalloc(&c->part_inst, 4 * cap));
+    CK(dalloc(&c->perm, 4 * cap));
+    CK(dalloc(&c->count, 4 * NC));
+    CK(dalloc(&c->fill, 4 * NC));
+    CK(dalloc(&c->start, 4 * (NC + 1)));
+    CK(dalloc(&c->cell_inst, 4 * NC));
+    CK(dalloc(&c->scan_part, 4 * scan_partial_size(NC)));
+    CK(dalloc(&c->big_list, 4 * NC));
+    CK(dalloc(&c->big_count, 4));
+    CK(dalloc(&c->vol, 8 * NC));
+    CK(dalloc(&c->smax, 8 * NC));
+    CK(dalloc(&c->samp, 8 * 8 * NC));
+    CK(dalloc(&c->dP, sizeof(InstParams) * n_instances));
+    CK(dalloc(&c->dt_cur, 8 * n_instances));
+    CK(dalloc(&c->dt_min, 8 * n_instances));
+    CK(dalloc(&c->step_d, 4));
+    CK(dalloc(&c->Mcur, 4));
+    CK(dalloc(&c->Mtot, 4));
+    CK(dalloc(&c->err, 8 * kNumErr));
+    CK(dalloc(&c->ghosts, sizeof(GhostCell) * std::max<int64_t>(c->n_ghost, 1)));
+    CK(dalloc(&c->gcount, 4 * std::max<int64_t>(c->n_ghost, 1)));
+    CK(dalloc(&c->goff, 4 * (std::max<int64_t>(c->n_ghost, 1) + 1)));
+    CK(dalloc(&c->gscan_part, 4 * scan_partial_size(std::max<int64_t>(c->n_ghost, 1))));
+    cudaStream_t s = c->stream;
+    CK(cudaMemcpyAsync(c->dP, c->hP.data(), sizeof(InstParams) * n_instances, cudaMemcpyHostToDevice, s));
+    if (c->n_ghost)
+      CK(cudaMemcpyAsync(c->ghosts, gh.data(), sizeof(GhostCell) * c->n_ghost, cudaMemcpyHostToDevice, s));
+    std::vector<uint32_t> ci(NC);
+    std::vector<double> vol(NC), sm(NC);
+    for (int i = 0; i < n_instances; ++i) {
+      const InstParams& P = c->hP[i];
+      const sp_config& g = cfgs[i];
+      const double v0 = P.dl[0] * P.dl[1] * P.dl[2];
+      const double crb = 4.0 * sqrt(g.R * g.sigc_T0 / kPiHost);
+      const double s0 = 2.0 * (P.sigc_coef * pow(crb, P.sigc_exp));
+      for (int64_t k = 0; k < P.ncells; ++k) {
+        ci[P.cell_off + k] = (uint32_t)i;
+        vol[P.cell_off + k] = g.cell_volume ? g.cell_volume[k] : v0;
+        sm[P.cell_off + k] = s0;
+      }
+    }
+    CK(cudaMemcpyAsync(c->cell_inst, ci.data(), 4 * NC, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->vol, vol.data(), 8 * NC, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->smax, sm.data(), 8 * NC, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->samp, 0, 8 * 8 * NC, s));
+    CK(cudaMemsetAsync(c->step_d, 0, 4, s));
+    CK(cudaMemsetAsync(c->big_count, 0, 4, s));
+    CK(cudaMemsetAsync(c->err, 0, 8 * kNumErr, s));
+    CK(cudaMemsetAsync(c->count, 0, 4 * NC, s));
+    CK(cudaMemsetAsync(c->fill, 0, 4 * NC, s));
+    CK(cudaStreamSynchronize(s));
+    return SP_OK;
+  }();
+  if (st != SP_OK) {
+    sp_free(c);
+    return st;
+  }
+  *out = c;
+  return SP_OK;
+}
+
+sp_status sp_set_particles(sp_ctx* c, int inst, const double* pos, const double* vel, int64_t n) {
+  if (!c || inst < 0 || inst >= c->n_inst || n < 0 || (n > 0 && (!pos || !vel))) return SP_ERR_ARG;
+  if (n > c->cap) return SP_ERR_CAPACITY;
+  const int64_t need = (int64_t)(c->dim + 3) * n;
+  if (need > c->stage_cap[inst]) {
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->dstage[inst]) CK(cudaFree(c->dstage[inst]));
+    c->dstage[inst] = nullptr;
+    CK(dalloc(&c->dstage[inst], 8 * need));
+    c->stage_cap[inst] = need;
+  }
+  if (n > 0) {
+    CK(cudaMemcpyAsync(c->dstage[inst], pos, 8 * c->dim * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->dstage[inst] + c->dim * n, vel, 8 * 3 * n, cudaMemcpyHostToDevice, c->stream));
+  }
+  c->stage_n[inst] = n;
+  c->dirty = true;
+  return SP_OK;
+}
+
+sp_status sp_set_record(sp_ctx* c, int on) {
+  if (!c) return SP_ERR_ARG;
+  const bool want = on != 0;
+  if (want && !c->rec) {
+    CK(dalloc(&c->rec, 4 * 4 * c->NC));
+    CK(dalloc(&c->resamp, c->cap));
+  }
+  if (want != c->record) {
+    c->record = want;
+    destroy_graphs(c);
+  }
+  return SP_OK;
+}
+
+sp_status sp_step(sp_ctx* c, int n_steps) {
+  if (!c || n_steps < 0) return SP_ERR_ARG;
+  sp_status s = ensure_ready(c);
+  if (s != SP_OK) return s;
+  if (!c->graph_ok) {
+    s = build_graphs(c);
+    if (s != SP_OK) return s;
+  }
+  for (int i = 0; i < n_steps; ++i) {
+    if (c->record) {
+      c->prev_start.resize(c->NC + 1);
+      CK(cudaMemcpyAsync(c->prev_start.data(), c->start, 4 * (c->NC + 1), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemsetAsync(c->resamp, 0, c->cap, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+    c->cur ^= 1;
+    c->step_host += 1;
+  }
+  return SP_OK;
+}
+
+sp_status sp_step_profiled(sp_ctx* c, int n_steps, double* ms, int n_slots) {
+  if (!c || n_steps < 0 || !ms || n_slots < 1) return SP_ERR_ARG;
+  sp_status s = ensure_ready(c);
+  if (s != SP_OK) return s;
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
+  double acc[4] = {0, 0, 0, 0};
+  for (int it = 0; it < n_steps; ++it) {
+    enqueue_step(c, c->cur, ev);
+    CK(cudaEventSynchronize(ev[4]));
+    for (int k = 0; k < 4; ++k) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      acc[k] += t;
+    }
+    c->cur ^= 1;
+    c->step_host += 1;
+  }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  for (int k = 0; k < n_slots && k < 4; ++k) ms[k] = acc[k];
+  CK(cudaGetLastError());
+  return SP_OK;
+}
+
+sp_status sp_sync(sp_ctx* c) {
+  if (!c) return SP_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  return check_errors(c);
+}
+
+int sp_launches_per_step(sp_ctx* c) {
+  if (!c) return 0;
+  if (!c->graph_ok && c->uploaded) build_graphs(c);
+  return c->launches;
+}
+
+sp_status sp_moments(sp_ctx* c, int inst, int kind, double* out, int n_fields) {
+  if (!c || inst < 0 || inst >= c->n_inst || !out || n_fields < 1) return SP_ERR_ARG;
+  sp_status s = ensure_ready(c);
+  if (s != SP_OK) return s;
+  const InstParams& P = c->hP[inst];
+  const int64_t nc = P.ncells;
+  const int nf = std::min(n_fields, (int)SP_NFIELDS);
+  if (kind == 0) {
+    double* d = nullptr;
+    CK(dalloc(&d, 8 * SP_NFIELDS * nc));
+    StepArgs a = make_step_args(c, c->cur);
+    if (c->prec == SP_FP64) launch_moments_f64(a, P.cell_off, P.cell_off + nc, d, c->stream);
+    else launch_moments_f32(a, P.cell_off, P.cell_off + nc, d, c->stream);
+    CK(cudaMemcpyAsync(out, d, 8 * nf * nc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaFree(d));
+  } else {
+    std::vector<double> S(8 * nc), vol(nc);
+    for (int f = 0; f < 8; ++f)
+      CK(cudaMemcpyAsync(S.data() + f * nc, c->samp + f * c->NC + P.cell_off, 8 * nc, cudaMemcpyDeviceToHost,
+                         c->stream));
+    CK(cudaMemcpyAsync(vol.data(), c->vol + P.cell_off, 8 * nc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t nsamp = std::max<int64_t>(0, c->step_host - (int64_t)P.n_steady);
+    for (int64_t k = 0; k < nc; ++k) {
+      double f[SP_NFIELDS] = {0};
+      const double sN = S[k];
+      if (nsamp > 0) {
+        f[SP_F_N] = sN / (double)nsamp;
+        f[SP_F_n] = vol[k] > 0 ? f[SP_F_N] * P.Fn / vol[k] : 0.0;
+        f[SP_F_ratio] = S[7 * nc + k] / (double)nsamp;
+      }
+      if (sN > 0) {
+        double U[3], e = 0;
+        for (int d = 0; d < 3; ++d) {
+          U[d] = S[(1 + d) * nc + k] / sN;
+          e += S[(4 + d) * nc + k] / sN - U[d] * U[d];
+        }
+        f[SP_F_ux] = U[0];
+        f[SP_F_uy] = U[1];
+        f[SP_F_uz] = U[2];
+        f[SP_F_T] = e / (3.0 * P.R);
+      }
+      for (int i = 0; i < nf; ++i) out[(int64_t)i * nc + k] = f[i];
+    }
+  }
+  return check_errors(c);
+}
+
+sp_status sp_get_particles(sp_ctx* c, int inst, double* pos, double* vel, uint32_t* cell, int64_t* n) {
+  if (!c || inst < 0 || inst >= c->n_inst) return SP_ERR_ARG;
+  sp_status s = ensure_ready(c);
+  if (s != SP_OK) return s;
+  std::vector<uint32_t> st;
+  s = host_starts(c, inst, st);
+  if (s != SP_OK) return s;
+  const int64_t M = (int64_t)st.back() - st[0];
+  if (n) *n = M;
+  if (!pos && !vel && !cell) return SP_OK;
+  if (cell)
+    for (size_t k = 0; k + 1 < st.size(); ++k)
+      for (uint32_t i = st[k]; i < st[k + 1]; ++i) cell[i - st[0]] = (uint32_t)k;
+  if (!pos && !vel) return SP_OK;
+  std::vector<uint32_t> pm;
+  s = host_perm_sorted(c, st, pm);
+  if (s != SP_OK) return s;
+  uint32_t* dperm = nullptr;
+  double *dpos = nullptr, *dvel = nullptr;
+  CK(dalloc(&dperm, 4 * std::max<int64_t>(M, 1)));
+  CK(dalloc(&dpos, 8 * 3 * std::max<int64_t>(M, 1)));
+  CK(dalloc(&dvel, 8 * 3 * std::max<int64_t>(M, 1)));
+  if (M > 0) CK(cudaMemcpyAsync(dperm, pm.data(), 4 * M, cudaMemcpyHostToDevice, c->stream));
+  const void* Ap[3] = {c->pos[c->cur][0], c->pos[c->cur][1], c->pos[c->cur][2]};
+  const void* Av[3] = {c->vel[c->cur][0], c->vel[c->cur][1], c->vel[c->cur][2]};
+  if (c->prec == SP_FP64) launch_gather_f64(c->dim, Ap, Av, dperm, 0, M, dpos, dvel, c->stream);
+  else launch_gather_f32(c->dim, Ap, Av, dperm, 0, M, dpos, dvel, c->stream);
+  if (pos && M > 0) CK(cudaMemcpyAsync(pos, dpos, 8 * c->dim * M, cudaMemcpyDeviceToHost, c->stream));
+  if (vel && M > 0) CK(cudaMemcpyAsync(vel, dvel, 8 * 3 * M, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  cudaFree(dperm);
+  cudaFree(dpos);
+  cudaFree(dvel);
+  return check_errors(c);
+}
+
+sp_status sp_get_step_record(sp_ctx* c, int inst, int64_t* cell4, uint8_t* resampled, uint32_t* perm,
+                             int64_t* n_old) {
+  if (!c || inst < 0 || inst >= c->n_inst || !c->record || !c->rec) return SP_ERR_STATE;
+  CK(cudaStreamSynchronize(c->stream));
+  const InstParams& P = c->hP[inst];
+  const int64_t nc = P.ncells;
+  if (cell4) {
+    std::vector<int32_t> r(4 * nc);
+    for (int f = 0; f < 4; ++f)
+      CK(cudaMemcpy(r.data() + f * nc, c->rec + f * c->NC + P.cell_off, 4 * nc, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < 4 * nc; ++i) cell4[i] = r[i];
+  }
+  const int64_t o0 = c->prev_start.empty() ? 0 : c->prev_start[P.cell_off];
+  const int64_t o1 = c->prev_start.empty() ? 0 : c->prev_start[P.cell_off + nc];
+  if (n_old) *n_old = o1 - o0;
+  if (resampled && o1 > o0) CK(cudaMemcpy(resampled, c->resamp + o0, o1 - o0, cudaMemcpyDeviceToHost));
+  if (perm) {
+    std::vector<uint32_t> st, pm;
+    sp_status s = host_starts(c, inst, st);
+    if (s != SP_OK) return s;
+    s = host_perm_sorted(c, st, pm);
+    if (s != SP_OK) return s;
+    std::copy(pm.begin(), pm.end(), perm);
+  }
+  return SP_OK;
+}
+
+sp_status sp_get_cell_start(sp_ctx* c, int inst, uint32_t* start) {
+  if (!c || inst < 0 || inst >= c->n_inst || !start) return SP_ERR_ARG;
+  sp_status s = ensure_ready(c);
+  if (s != SP_OK) return s;
+  std::vector<uint32_t> st;
+  s = host_starts(c, inst, st);
+  if (s != SP_OK) return s;
+  for (size_t i = 0; i < st.size(); ++i) start[i] = st[i] - st[0];
+  return SP_OK;
+}
+
+sp_status sp_get_sigc_max(sp_ctx* c, int inst, double* out) {
+  if (!c || inst < 0 || inst >= c->n_inst || !out) return SP_ERR_ARG;
+  const InstParams& P = c->hP[inst];
+  CK(cudaMemcpyAsync(out, c->smax + P.cell_off, 8 * P.ncells, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SP_OK;
+}
+
+sp_status sp_get_dt(sp_ctx* c, int inst, double* dt, int64_t* step) {
+  if (!c || inst < 0 || inst >= c->n_inst) return SP_ERR_ARG;
+  sp_status s = ensure_ready(c);
+  if (s != SP_OK) return s;
+  if (dt) {
+    CK(cudaMemcpyAsync(dt, c->dt_cur + inst, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (step) *step = c->step_host;
+  return SP_OK;
+}
+
+sp_status sp_errors(sp_ctx* c, int64_t* out5) {
+  if (!c || !out5) return SP_ERR_ARG;
+  unsigned long long h[kNumErr];
+  CK(cudaMemcpyAsync(h, c->err, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < kNumErr; ++i) out5[i] = (int64_t)h[i];
+  return SP_OK;
+}
+
+sp_status sp_free(sp_ctx* c) {
+  if (!c) return SP_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  destroy_graphs(c);
+  for (int b = 0; b < 2; ++b)
+    for (int d = 0; d < 3; ++d) {
+      cudaFree(c->pos[b][d]);
+      cudaFree(c->vel[b][d]);
+    }
+  for (double* p : c->dstage) cudaFree(p);
+  void* ptrs[] = {c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
+                  c->big_count, c->vol, c->smax, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
+                  c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
+  for (void* p : ptrs) cudaFree(p);
+  delete c;
+  return SP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// sp_common.cu -- precision-independent kernels of libsp: the exclusive
+// scan of the cell histogram (counting sort by cell), the scatter that
+// writes the slot -> source permutation, and the end-of-step bookkeeping.
+#include <cstdint>
+
+#include "sp_internal.h"
+
+namespace sp {
+
+namespace {
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = lane < kScanThreads / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanThreads / 32) wsum[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t before = w > 0 ? wsum[w - 1] : 0;
+  *total = wsum[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void k_scan_reduce(const uint32_t* in, int64_t n, uint32_t* partial) {
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  uint32_t s = 0;
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t j = base + (int64_t)i * kScanThreads + threadIdx.x;
+    if (j < n) s += in[j];
+  }
+  uint32_t tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block totals by one block (any count).
+__global__ void k_scan_top(uint32_t* partial, int64_t nb) {
+  uint32_t carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const int64_t j = b0 + threadIdx.x;
+    const uint32_t v = j < nb ? partial[j] : 0;
+    uint32_t tot;
+    const uint32_t e = block_excl_scan(v, &tot);
+    if (j < nb) partial[j] = carry + e;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) partial[nb] = carry;
+}
+
+// out[j] = sum of in[0..j), out[n] = total.  Each thread owns kScanItems
+// consecutive elements of the block's tile.
+__global__ void k_scan_down(const uint32_t* in, uint32_t* out, int64_t n, const uint32_t* partial,
+                            int64_t nb) {
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t j = base + i;
+    v[i] = j < n ? in[j] : 0;
+    s += v[i];
+  }
+  uint32_t tot;
+  uint32_t run = partial[blockIdx.x] + block_excl_scan(s, &tot);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t j = base + i;
+    if (j < n) out[j] = run;
+    run += v[i];
+  }
+  if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = partial[nb];
+}
+
+__global__ void k_zero2(uint32_t* a, uint32_t* b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    a[i] = 0;
+    b[i] = 0;
+  }
+}
+
+// perm[start[key] + rank] = source index; the rank within a cell comes from
+// warp-aggregated atomics, so the order inside a cell is arbitrary here and
+// restored to source order by the collision kernel (a stable sort overall).
+__global__ void k_scatter(const uint32_t* key, const uint32_t* start, uint32_t* fill, uint32_t* perm,
+                          const uint32_t* Mtot, int64_t cap) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t M = (int64_t)*Mtot;
+  const uint32_t k = (i < M && i < cap) ? key[i] : kSentinel;
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+  if (k == kSentinel) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&fill[k], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+  perm[start[k] + base + rank] = (uint32_t)i;
+}
+
+__global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
+                                unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
+                                uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
+                                const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
+                                uint32_t* big_count) {
+  if (threadIdx.x == 0) {
+    const uint32_t inj = n_ghost > 0 ? goff[n_ghost - 1] + gcount[n_ghost - 1] : 0u;
+    const uint32_t old = *Mcur;
+    *Mtot = old + inj;
+    *Mcur = start_new[NC];
+    *step = *step + 1u;
+    *big_count = 0u;
+  }
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+    const unsigned long long inf = 0x7FF0000000000000ull;
+    if (P[i].dt_fixed > 0) {
+      dt_cur[i] = P[i].dt_fixed;
+    } else if (dt_min[i] != inf) {
+      dt_cur[i] = P[i].cfl * __longlong_as_double((long long)dt_min[i]);
+    }
+    dt_min[i] = inf;
+  }
+}
+}  // namespace
+
+int64_t scan_partial_size(int64_t n) { return (n + kTile - 1) / kTile + 1; }
+
+void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s) {
+  const int64_t nb = (n + kTile - 1) / kTile;
+  if (nb == 0) {
+    cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+    return;
+  }
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
+  k_scan_top<<<1, kScanThreads, 0, s>>>(partial, nb);
+  k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partial, nb);
+}
+
+void launch_cell_finalize(uint32_t* count, uint32_t* fill, int64_t NC, cudaStream_t s) {
+  int64_t g = (NC + 255) / 256;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  k_zero2<<<(unsigned)g, 256, 0, s>>>(count, fill, NC);
+}
+
+void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* fill, uint32_t* perm,
+                    const uint32_t* Mtot, int64_t cap, cudaStream_t s) {
+  const int64_t g = (cap + 255) / 256;
+  k_scatter<<<(unsigned)(g > 0 ? g : 1), 256, 0, s>>>(key, start, fill, perm, Mtot, cap);
+}
+
+void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
+                          unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
+                          uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
+                          const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
+                          uint32_t* big_count, cudaStream_t s) {
+  k_step_finalize<<<1, 256, 0, s>>>(P, n_inst, dt_cur, dt_min, step, Mcur, Mtot, start_new, NC,
+                                    goff, gcount, n_ghost, big_count);
+}
+
+}  // namespace sp

@@ -1,0 +1,858 @@
+// sp_device.cuh -- device code of libsp: Philox streams, the per-cell
+// collision step and the free-flight / wall / reservoir step of the hybrid
+// stochastic-particle Shakhov / DSMC method (arXiv:2506.23917, Sec. III.B).
+//
+// Templated on the particle precision T (double: FP64 mode, float: FP32
+// mode) and the spatial dimension DIM.  Per-cell quantities (moments, tau,
+// dt_c, the DSMC/Shakhov split, exp(-dt/tau), rescale factors, time
+// averages) are always FP64; per-particle arithmetic runs in T.
+#pragma once
+#include <cstdint>
+
+#include "sp_internal.h"
+
+namespace sp {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64
+// multiplications with Weyl-bumped keys.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// FP64 uniform in (0,1): 52 bits from two words, (2k+1) 2^-53.
+__device__ __forceinline__ double u01d(uint32_t a, uint32_t b) {
+  const unsigned long long k = ((unsigned long long)(a >> 6) << 26) | (unsigned long long)(b >> 6);
+  return (double)(2ull * k + 1ull) * 1.1102230246251565404236316680908203125e-16;
+}
+// FP32 uniform in (0,1): 23 bits from one word, (2k+1) 2^-24.
+__device__ __forceinline__ float u01f(uint32_t a) {
+  return (float)(2u * (a >> 9) + 1u) * 5.9604644775390625e-8f;
+}
+
+// A uniform stream addressed by (step, a, b, purpose<<24 | sub); the q-th
+// uniform lives in block q/2 (FP64) or q/4 (FP32) of the counter word 3.
+template <class T>
+struct Uni;
+
+template <>
+struct Uni<double> {
+  uint32_t c0, c1, c2, c3, k0, k1;
+  int blk;
+  uint4 w;
+  __device__ Uni(uint32_t step, uint32_t a, uint32_t b, uint32_t c3base, uint32_t key0, uint32_t key1)
+      : c0(step), c1(a), c2(b), c3(c3base), k0(key0), k1(key1), blk(-1) {}
+  __device__ __forceinline__ double get(int q) {
+    const int bq = q >> 1;
+    if (bq != blk) {
+      w = philox10(c0, c1, c2, c3 + (uint32_t)bq, k0, k1);
+      blk = bq;
+    }
+    return (q & 1) ? u01d(w.z, w.w) : u01d(w.x, w.y);
+  }
+};
+
+template <>
+struct Uni<float> {
+  uint32_t c0, c1, c2, c3, k0, k1;
+  int blk;
+  uint4 w;
+  __device__ Uni(uint32_t step, uint32_t a, uint32_t b, uint32_t c3base, uint32_t key0, uint32_t key1)
+      : c0(step), c1(a), c2(b), c3(c3base), k0(key0), k1(key1), blk(-1) {}
+  __device__ __forceinline__ float get(int q) {
+    const int bq = q >> 2;
+    if (bq != blk) {
+      w = philox10(c0, c1, c2, c3 + (uint32_t)bq, k0, k1);
+      blk = bq;
+    }
+    const int r = q & 3;
+    return u01f(r == 0 ? w.x : r == 1 ? w.y : r == 2 ? w.z : w.w);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Precision helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tlog(double x) { return log(x); }
+__device__ __forceinline__ float tlog(float x) { return logf(x); }
+__device__ __forceinline__ double tpow(double x, double e) { return pow(x, e); }
+__device__ __forceinline__ float tpow(float x, float e) { return powf(x, e); }
+__device__ __forceinline__ double tfloor(double x) { return floor(x); }
+__device__ __forceinline__ float tfloor(float x) { return floorf(x); }
+__device__ __forceinline__ double tfabs(double x) { return fabs(x); }
+__device__ __forceinline__ float tfabs(float x) { return fabsf(x); }
+// cos / sin of 2 pi u
+__device__ __forceinline__ void sincos2pi(double u, double* s, double* c) {
+  const double th = 2.0 * kPi * u;
+  *s = sin(th);
+  *c = cos(th);
+}
+__device__ __forceinline__ void sincos2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
+__device__ __forceinline__ double cos2pi(double u) { return cos(2.0 * kPi * u); }
+__device__ __forceinline__ float cos2pi(float u) { return cospif(2.0f * u); }
+
+template <class T>
+__device__ __forceinline__ T tinf();
+template <>
+__device__ __forceinline__ double tinf<double>() { return __longlong_as_double(0x7FF0000000000000ll); }
+template <>
+__device__ __forceinline__ float tinf<float>() { return __int_as_float(0x7F800000); }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry: cell index, free flight with walls and body (Step 2).
+// ---------------------------------------------------------------------------
+template <class T, int DIM>
+__device__ __forceinline__ uint32_t cell_of(const InstParams& P, const T* x) {
+  uint32_t idx[3] = {0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const T f = tfloor((x[d] - (T)P.lo[d]) * (T)P.inv_d[d]);
+    int i = (int)f;
+    if (f < (T)0) i = 0;
+    if (i > P.n[d] - 1) i = P.n[d] - 1;
+    idx[d] = (uint32_t)i;
+  }
+  return idx[0] + (uint32_t)P.n[0] * (idx[1] + (uint32_t)P.n[1] * idx[2]);
+}
+
+// Diffuse re-emission at wall temperature Tw: normal speed from
+// c_n = sqrt(-2 R Tw ln R1), tangential Box-Muller pair (R3, R4).
+template <class T>
+__device__ __forceinline__ void diffuse_sample(const InstParams& P, double Tw, Uni<T>& r, T* cn,
+                                               T* t1, T* t2) {
+  const T R1 = r.get(0), R3 = r.get(1), R4 = r.get(2);
+  const T RTw = (T)(P.R * Tw);
+  *cn = tsqrt((T)-2.0 * RTw * tlog(R1));
+  const T r4 = tsqrt(-tlog(R4));
+  const T s = tsqrt((T)2.0 * RTw);
+  T sn, cs;
+  sincos2pi(R3, &sn, &cs);
+  *t1 = s * cs * r4;
+  *t2 = s * sn * r4;
+}
+
+// Moves one particle for time trem.  Returns true when it left the domain.
+// Draw stream of bounce b: (step, a, b_idx, purpose<<24 | subbase + 2b).
+template <class T, int DIM>
+__device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t step,
+                              uint32_t purpose, uint32_t sa, uint32_t sb, uint32_t subbase,
+                              unsigned long long* err) {
+  for (int bounce = 0;; ++bounce) {
+    if (bounce >= kMaxBounce) {
+      atomicAdd(&err[kErrBounce], 1ull);
+      return false;
+    }
+    T tf = tinf<T>();
+    int fa = -1, fs = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      if (v[d] > (T)0) {
+        const T t = ((T)P.hi[d] - x[d]) / v[d];
+        if (t < tf) { tf = t; fa = d; fs = 1; }
+      } else if (v[d] < (T)0) {
+        const T t = ((T)P.lo[d] - x[d]) / v[d];
+        if (t < tf) { tf = t; fa = d; fs = 0; }
+      }
+    }
+    T tb = tinf<T>();
+    if (P.body != 0) {
+      const int D = P.body == 1 ? 2 : 3;
+      T bb = 0, aa = 0, cc = 0;
+      for (int d = 0; d < D; ++d) {
+        const T dx = x[d] - (T)P.body_c[d];
+        bb += v[d] * dx;
+        aa += v[d] * v[d];
+        cc += dx * dx;
+      }
+      cc -= (T)P.body_r * (T)P.body_r;
+      if (bb < (T)0 && aa > (T)0) {
+        const T disc = bb * bb - aa * cc;
+        if (disc >= (T)0) {
+          const T t = (-bb - tsqrt(disc)) / aa;
+          tb = t < (T)0 ? (T)0 : t;
+        }
+      }
+    }
+    const T th = tf < tb ? tf : tb;
+    if (!(th < trem)) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) x[d] += v[d] * trem;
+      return false;
+    }
+    const uint32_t c3 = (purpose << 24) | (subbase + 2u * (uint32_t)bounce);
+    if (tb <= tf) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) x[d] += v[d] * tb;
+      trem -= tb;
+      T nv[3] = {0, 0, 0};
+      const int D = P.body == 1 ? 2 : 3;
+      for (int d = 0; d < D; ++d) nv[d] = (x[d] - (T)P.body_c[d]) / (T)P.body_r;
+      T e1[3], e2[3];
+      if (P.body == 1) {
+        e1[0] = -nv[1]; e1[1] = nv[0]; e1[2] = 0;
+        e2[0] = 0; e2[1] = 0; e2[2] = 1;
+      } else {
+        T ax[3] = {0, 0, 0};
+        if (tfabs(nv[0]) < (T)0.9) ax[0] = 1; else ax[1] = 1;
+        const T cx = nv[1] * ax[2] - nv[2] * ax[1];
+        const T cy = nv[2] * ax[0] - nv[0] * ax[2];
+        const T cz = nv[0] * ax[1] - nv[1] * ax[0];
+        const T cn = tsqrt(cx * cx + cy * cy + cz * cz);
+        e1[0] = cx / cn; e1[1] = cy / cn; e1[2] = cz / cn;
+        e2[0] = nv[1] * e1[2] - nv[2] * e1[1];
+        e2[1] = nv[2] * e1[0] - nv[0] * e1[2];
+        e2[2] = nv[0] * e1[1] - nv[1] * e1[0];
+      }
+      Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
+      T cn, t1, t2;
+      diffuse_sample<T>(P, P.body_Tw, r, &cn, &t1, &t2);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
+      continue;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+      if (d != fa) x[d] += v[d] * tf;
+    x[fa] = fs ? (T)P.hi[fa] : (T)P.lo[fa];
+    trem -= tf;
+    const int f = 2 * fa + fs;
+    const int bc = P.face_bc[f];
+    if (bc == 0) {
+      v[fa] = -v[fa];
+    } else if (bc == 1) {
+      Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
+      T cn, t1, t2;
+      diffuse_sample<T>(P, P.face_T[f], r, &cn, &t1, &t2);
+      v[fa] = fs ? -cn : cn;
+      v[(fa + 1) % 3] = t1;
+      v[(fa + 2) % 3] = t2;
+    } else {
+      return true;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative pieces of the per-cell step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int next_pow2(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+// Ascending bitonic sort of s[0..n2) by one warp (n2 a power of two).
+__device__ inline void warp_bitonic(uint32_t* s, int n2) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < n2; t += 32) {
+        const int p = t ^ j;
+        if (p > t) {
+          const uint32_t a = s[t], b = s[p];
+          const bool up = (t & k) == 0;
+          if ((a > b) == up) {
+            s[t] = b;
+            s[p] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Warp-aggregated histogram increment (key == kSentinel is skipped).
+__device__ __forceinline__ void warp_count(uint32_t key, uint32_t* count) {
+  const unsigned peers = __match_any_sync(kFull, key);
+  const int lane = threadIdx.x & 31;
+  if (key != kSentinel && lane == __ffs(peers) - 1) atomicAdd(&count[key], (uint32_t)__popc(peers));
+}
+
+struct CellMoments {
+  double U[3], T, q[3], n, tau, dtc;
+};
+
+// Step 3 moments of the staged velocities of one cell (all lanes get them).
+template <class T>
+__device__ CellMoments cell_moments(const InstParams& P, double V, int N, const T* vx, const T* vy,
+                                    const T* vz) {
+  const int lane = threadIdx.x & 31;
+  CellMoments m;
+  T s0 = 0, s1 = 0, s2 = 0;
+  for (int s = lane; s < N; s += 32) {
+    s0 += vx[s];
+    s1 += vy[s];
+    s2 += vz[s];
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  m.U[0] = (double)s0 / (double)N;
+  m.U[1] = (double)s1 / (double)N;
+  m.U[2] = (double)s2 / (double)N;
+  m.n = (double)N * P.Fn / V;
+  m.T = 0;
+  m.q[0] = m.q[1] = m.q[2] = 0;
+  m.tau = __longlong_as_double(0x7FF0000000000000ll);
+  m.dtc = m.tau;
+  if (N < 2) return m;
+  const T U0 = (T)m.U[0], U1 = (T)m.U[1], U2 = (T)m.U[2];
+  T S2 = 0, S3x = 0, S3y = 0, S3z = 0;
+  for (int s = lane; s < N; s += 32) {
+    const T C0 = vx[s] - U0, C1 = vy[s] - U1, C2 = vz[s] - U2;
+    const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+    S2 += c2;
+    S3x += c2 * C0;
+    S3y += c2 * C1;
+    S3z += c2 * C2;
+  }
+  S2 = warp_sum(S2);
+  S3x = warp_sum(S3x);
+  S3y = warp_sum(S3y);
+  S3z = warp_sum(S3z);
+  m.T = (double)S2 / (3.0 * P.R * (double)(N - 1));
+  if (N >= 3) {
+    const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
+    m.q[0] = f * (double)S3x;
+    m.q[1] = f * (double)S3y;
+    m.q[2] = f * (double)S3z;
+  }
+  const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
+  if (m.T > 0) {
+    const double p = m.n * P.m * P.R * m.T;
+    const double mu = P.mu_ref * pow(m.T / P.T_ref, P.omega);
+    m.tau = mu / p;
+    m.dtc = P.Lmin / (umag + sqrt(P.gamma * P.R * m.T));
+  } else if (umag > 0) {
+    m.dtc = P.Lmin / umag;
+  }
+  return m;
+}
+
+__device__ __forceinline__ double dsmc_ratio(const InstParams& P, int N, const CellMoments& m) {
+  if (P.mode == 1) return 1.0;
+  if (P.mode == 2) return 0.0;
+  if (N < 2 || !(m.T > 0) || m.dtc <= m.tau) return 1.0;
+  return m.tau / m.dtc;
+}
+
+// ---------------------------------------------------------------------------
+// One cell of the fused step: gather -> moments -> DSMC -> Shakhov ->
+// rescale -> sample -> free flight + key + histogram.  Called by a whole
+// warp; sidx/svx/svy/svz are the warp's staging arrays of capacity cap.
+// ---------------------------------------------------------------------------
+template <class T, int DIM>
+__device__ void process_cell(const StepArgs& a, int64_t k, uint32_t* sidx, T* svx, T* svy, T* svz,
+                             int cap) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t s0 = a.start[k];
+  const int N = (int)(a.start[k + 1] - s0);
+  const uint32_t inst = a.cell_inst[k];
+  const InstParams& P = a.P[inst];
+  const uint32_t kl = (uint32_t)(k - P.cell_off);
+  const uint32_t step = *a.step;
+  const double dtG = a.dt_cur[inst];
+  const double V = a.vol[k];
+  const int64_t NC = a.NC;
+  const bool sample = (int64_t)step >= (int64_t)P.n_steady;
+  if (a.rec && lane < 4) a.rec[lane * NC + k] = 0;
+  if (N == 0) {
+    if (sample && lane == 0) {
+      CellMoments m0;
+      m0.T = 0;
+      m0.tau = m0.dtc = 0;
+      a.samp[7 * NC + k] += dsmc_ratio(P, 0, m0);
+    }
+    return;
+  }
+  T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
+  T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
+  if (N > cap) {
+    // no room to stage this cell: its particles are dropped and flagged
+    if (lane == 0) atomicAdd(&a.err[kErrCellCap], 1ull);
+    for (int s = lane; s < N; s += 32) a.key[s0 + s] = kSentinel;
+    return;
+  }
+  // 1. the cell's source indices in stable (ascending) order
+  const int n2 = next_pow2(N);
+  for (int s = lane; s < n2; s += 32) sidx[s] = s < N ? a.perm[s0 + s] : kSentinel;
+  __syncwarp();
+  warp_bitonic(sidx, n2);
+  // 2. gather velocities
+  const T* Av0 = (const T*)a.Avel[0];
+  const T* Av1 = (const T*)a.Avel[1];
+  const T* Av2 = (const T*)a.Avel[2];
+  for (int s = lane; s < N; s += 32) {
+    const uint32_t o = sidx[s];
+    svx[s] = Av0[o];
+    svy[s] = Av1[o];
+    svz[s] = Av2[o];
+  }
+  __syncwarp();
+  // 3. moments (Step 3) and the local time step (Eq. "local time step")
+  const CellMoments m = cell_moments<T>(P, V, N, svx, svy, svz);
+  if (N >= 2 && lane == 0 && m.dtc < __longlong_as_double(0x7FF0000000000000ll))
+    atomicMin(&a.dt_min[inst], (unsigned long long)__double_as_longlong(m.dtc));
+  int ncand = 0, nacc = 0, nres = 0, nar = 0;
+  if (N >= 2 && m.T > 0) {
+    // 4. split of the step (Eqs. tDSMC, tShakhov)
+    double dsmc, sbgk;
+    if (P.mode == 1) { dsmc = dtG; sbgk = 0; }
+    else if (P.mode == 2) { dsmc = 0; sbgk = dtG; }
+    else if (m.dtc <= m.tau) { dsmc = dtG; sbgk = 0; }
+    else {
+      const double r = m.tau / m.dtc;
+      dsmc = r * dtG;
+      sbgk = (1.0 - r) * dtG;
+    }
+    // 5. DSMC sub-step: NTC candidates, VHS acceptance, isotropic scattering
+    if (dsmc > 0) {
+      const double smax0 = a.smax[k];
+      const double ncr = 0.5 * (double)N * (double)(N - 1) * P.Fn * smax0 * dsmc / V;
+      Uni<T> rr(step, kl, kSentinel, kPurpNtc << 24, P.key0, P.key1);
+      int64_t ncol = (int64_t)floor(ncr + (double)rr.get(0));
+      if (ncol > kNcolCap) {
+        ncol = kNcolCap;
+        if (lane == 0) atomicAdd(&a.err[kErrNcol], 1ull);
+      }
+      T smax = (T)smax0;
+      const T coef = (T)P.sigc_coef, ex = (T)P.sigc_exp;
+      for (int64_t base = 0; base < ncol; base += 32) {
+        const int64_t kk = base + lane;
+        int ci = 0, cj = 0;
+        T u3 = 0, u4 = 0, u5 = 0;
+        if (kk < ncol) {
+          Uni<T> r(step, kl, (uint32_t)kk, kPurpNtc << 24, P.key0, P.key1);
+          const T u1 = r.get(0), u2 = r.get(1);
+          u3 = r.get(2);
+          u4 = r.get(3);
+          u5 = r.get(4);
+          ci = (int)(u1 * (T)N);
+          if (ci > N - 1) ci = N - 1;
+          cj = (int)(u2 * (T)(N - 1));
+          if (cj > N - 2) cj = N - 2;
+          if (cj >= ci) cj += 1;
+        }
+        const int nb = (int)((ncol - base) < 32 ? (ncol - base) : 32);
+        for (int L = 0; L < nb; ++L) {
+          const int i = __shfl_sync(kFull, ci, L), j = __shfl_sync(kFull, cj, L);
+          const T v3 = __shfl_sync(kFull, u3, L), v4 = __shfl_sync(kFull, u4, L),
+                  v5 = __shfl_sync(kFull, u5, L);
+          const T ax = svx[i], ay = svy[i], az = svz[i];
+          const T bx = svx[j], by = svy[j], bz = svz[j];
+          const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
+          const T cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
+          const T sc = coef * tpow(cr, ex);
+          if (sc > smax) smax = sc;
+          __syncwarp();
+          if (v3 < sc / smax) {
+            ++nacc;
+            const T cchi = (T)2.0 * v4 - (T)1.0;
+            const T schi = tsqrt((T)1.0 - cchi * cchi);
+            T sn, cs;
+            sincos2pi(v5, &sn, &cs);
+            const T w0 = cchi, w1 = schi * cs, w2 = schi * sn;
+            const T m0 = ax + bx, m1 = ay + by, m2 = az + bz;
+            if (lane == 0) {
+              svx[i] = (T)0.5 * (m0 - cr * w0);
+              svy[i] = (T)0.5 * (m1 - cr * w1);
+              svz[i] = (T)0.5 * (m2 - cr * w2);
+              svx[j] = (T)0.5 * (m0 + cr * w0);
+              svy[j] = (T)0.5 * (m1 + cr * w1);
+              svz[j] = (T)0.5 * (m2 + cr * w2);
+            }
+            __syncwarp();
+          }
+        }
+      }
+      ncand = (int)ncol;
+      if (lane == 0) a.smax[k] = (double)smax;
+    }
+    // 6. Shakhov sub-step: Bernoulli(1 - exp(-dt/tau)), Box-Muller + A test
+    if (sbgk > 0 && N >= 3) {
+      const double Pd = 1.0 - exp(-sbgk / m.tau);
+      const double RTd = P.R * m.T;
+      const double qn = sqrt(m.q[0] * m.q[0] + m.q[1] * m.q[1] + m.q[2] * m.q[2]);
+      const T Amax = (T)(1.0 + 20.0 * (1.0 - P.Pr) * qn / (RTd * sqrt(RTd)));
+      const T Pt = (T)Pd, RT = (T)RTd, s2RT = (T)sqrt(2.0 * RTd), omp = (T)(1.0 - P.Pr);
+      const T q0 = (T)m.q[0], q1 = (T)m.q[1], q2 = (T)m.q[2];
+      const T U0 = (T)m.U[0], U1 = (T)m.U[1], U2 = (T)m.U[2];
+      int myres = 0, myar = 0;
+      for (int s = lane; s < N; s += 32) {
+        Uni<T> r(step, kl, (uint32_t)s, kPurpShk << 24, P.key0, P.key1);
+        const T u0 = r.get(0);
+        if (!(u0 < Pt)) continue;
+        ++myres;
+        if (a.resamp) a.resamp[s0 + s] = 1;
+        T C0 = 0, C1 = 0, C2 = 0;
+        for (int t = 0; t < P.ar_max; ++t) {
+          const T R1 = r.get(1 + 5 * t), R2 = r.get(2 + 5 * t), R3 = r.get(3 + 5 * t);
+          const T R4 = r.get(4 + 5 * t), R5 = r.get(5 + 5 * t);
+          const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
+          T sn3, cs3;
+          sincos2pi(R3, &sn3, &cs3);
+          C0 = s2RT * cos2pi(R1) * r2;
+          C1 = s2RT * cs3 * r4;
+          C2 = s2RT * sn3 * r4;
+          const T qC = q0 * C0 + q1 * C1 + q2 * C2;
+          const T CC = C0 * C0 + C1 * C1 + C2 * C2;
+          const T A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
+          ++myar;
+          if (R5 * Amax < A) break;
+          if (t == P.ar_max - 1) atomicAdd(&a.err[kErrAr], 1ull);
+        }
+        svx[s] = U0 + C0;
+        svy[s] = U1 + C1;
+        svz[s] = U2 + C2;
+      }
+      nres = warp_sum(myres);
+      nar = warp_sum(myar);
+      __syncwarp();
+      // 7. conservation rescale c' = U + (c_p - U_p) sqrt(T/T_p)
+      if (nres > 0) {
+        T p0 = 0, p1 = 0, p2 = 0;
+        for (int s = lane; s < N; s += 32) {
+          p0 += svx[s];
+          p1 += svy[s];
+          p2 += svz[s];
+        }
+        const double Up0 = (double)warp_sum(p0) / (double)N;
+        const double Up1 = (double)warp_sum(p1) / (double)N;
+        const double Up2 = (double)warp_sum(p2) / (double)N;
+        const T Upt0 = (T)Up0, Upt1 = (T)Up1, Upt2 = (T)Up2;
+        T S2 = 0;
+        for (int s = lane; s < N; s += 32) {
+          const T C0 = svx[s] - Upt0, C1 = svy[s] - Upt1, C2 = svz[s] - Upt2;
+          S2 += C0 * C0 + C1 * C1 + C2 * C2;
+        }
+        const double Tp = (double)warp_sum(S2) / (3.0 * P.R * (double)(N - 1));
+        if (Tp > 0) {
+          const T f = (T)sqrt(m.T / Tp);
+          for (int s = lane; s < N; s += 32) {
+            svx[s] = U0 + (svx[s] - Upt0) * f;
+            svy[s] = U1 + (svy[s] - Upt1) * f;
+            svz[s] = U2 + (svz[s] - Upt2) * f;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (a.rec && lane == 0) {
+    a.rec[0 * NC + k] = ncand;
+    a.rec[1 * NC + k] = nacc;
+    a.rec[2 * NC + k] = nres;
+    a.rec[3 * NC + k] = nar;
+  }
+  // 8. time-averaged sums (Step 5)
+  if (sample) {
+    T sv0 = 0, sv1 = 0, sv2 = 0, sq0 = 0, sq1 = 0, sq2 = 0;
+    for (int s = lane; s < N; s += 32) {
+      const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
+      sv0 += x0; sv1 += x1; sv2 += x2;
+      sq0 += x0 * x0; sq1 += x1 * x1; sq2 += x2 * x2;
+    }
+    sv0 = warp_sum(sv0); sv1 = warp_sum(sv1); sv2 = warp_sum(sv2);
+    sq0 = warp_sum(sq0); sq1 = warp_sum(sq1); sq2 = warp_sum(sq2);
+    if (lane == 0) {
+      double* S = a.samp;
+      S[0 * NC + k] += (double)N;
+      S[1 * NC + k] += (double)sv0;
+      S[2 * NC + k] += (double)sv1;
+      S[3 * NC + k] += (double)sv2;
+      S[4 * NC + k] += (double)sq0;
+      S[5 * NC + k] += (double)sq1;
+      S[6 * NC + k] += (double)sq2;
+      S[7 * NC + k] += dsmc_ratio(P, N, m);
+    }
+  }
+  // 9. free flight of the next interval (Step 2), key and histogram
+  const T dt = (T)dtG;
+  for (int sb = 0; sb < N; sb += 32) {
+    const int s = sb + lane;
+    uint32_t key = kSentinel;
+    if (s < N) {
+      const uint32_t o = sidx[s];
+      T x[3] = {0, 0, 0};
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) x[d] = ((const T*)a.Apos[d])[o];
+      T v[3] = {svx[s], svy[s], svz[s]};
+      const bool gone = move_particle<T, DIM>(P, x, v, dt, step, kPurpWall, kl, (uint32_t)s, 0u, a.err);
+      if (!gone) key = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) Bx[d][s0 + s] = x[d];
+      Bv[0][s0 + s] = v[0];
+      Bv[1][s0 + s] = v[1];
+      Bv[2][s0 + s] = v[2];
+      a.key[s0 + s] = key;
+    }
+    warp_count(key, a.count);
+  }
+}
+
+template <class T, int DIM>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_collide(StepArgs a, int big) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!big) {
+    const int cap = kCapSmall;
+    unsigned char* base = smem + (size_t)warp * cap * (4 + 3 * sizeof(T));
+    uint32_t* sidx = (uint32_t*)base;
+    T* svx = (T*)(base + (size_t)cap * 4);
+    T* svy = svx + cap;
+    T* svz = svy + cap;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < a.NC; k += nw) {
+      const int N = (int)(a.start[k + 1] - a.start[k]);
+      if (N > cap) {
+        if (lane == 0) {
+          const uint32_t i = atomicAdd(a.big_count, 1u);
+          a.big_list[i] = (uint32_t)k;
+        }
+        continue;
+      }
+      process_cell<T, DIM>(a, k, sidx, svx, svy, svz, cap);
+    }
+  } else {
+    if (warp != 0) return;
+    const int cap = a.big_cap;
+    uint32_t* sidx = (uint32_t*)smem;
+    T* svx = (T*)(smem + (size_t)cap * 4);
+    T* svy = svx + cap;
+    T* svz = svy + cap;
+    const uint32_t nbig = *a.big_count;
+    for (uint32_t i = blockIdx.x; i < nbig; i += gridDim.x)
+      process_cell<T, DIM>(a, (int64_t)a.big_list[i], sidx, svx, svy, svz, cap);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reservoir injection (ghost cells outside inflow faces), two passes:
+// pass 0 counts survivors per ghost cell, pass 1 writes them at
+// Mcur + goff[g] in (ghost cell, particle) order.
+// ---------------------------------------------------------------------------
+template <class T, int DIM>
+__global__ void k_inject(InjectArgs a, int pass) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_ghost) return;
+  const GhostCell G = a.ghosts[g];
+  const InstParams& P = a.P[G.inst];
+  const uint32_t step = *a.step;
+  const double dtd = a.dt_cur[G.inst];
+  const T dt = (T)dtd;
+  const int ax = G.face / 2, side = G.face % 2;
+  const T face = side ? (T)P.hi[ax] : (T)P.lo[ax];
+  const uint32_t sb = (uint32_t)G.face * 16u;
+  Uni<T> rc(step, G.gc, kSentinel, (kPurpInj << 24) | sb, P.key0, P.key1);
+  const int64_t ng = (int64_t)floor(G.lam + (double)rc.get(0));
+  uint32_t nsurv = 0;
+  const int64_t base = pass == 1 ? (int64_t)*a.Mcur + (int64_t)a.goff[g] : 0;
+  T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
+  T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
+  const T s2RT = (T)G.s2RT;
+  for (int64_t m = 0; m < ng; ++m) {
+    Uni<T> r(step, G.gc, (uint32_t)m, (kPurpInj << 24) | sb, P.key0, P.key1);
+    T x[3] = {0, 0, 0}, v[3];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) x[d] = (T)G.blo[d] + r.get(d) * ((T)G.bhi[d] - (T)G.blo[d]);
+    const T R1 = r.get(3), R2 = r.get(4), R3 = r.get(5), R4 = r.get(6);
+    const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
+    T sn3, cs3;
+    sincos2pi(R3, &sn3, &cs3);
+    v[0] = (T)G.u[0] + s2RT * cos2pi(R1) * r2;
+    v[1] = (T)G.u[1] + s2RT * cs3 * r4;
+    v[2] = (T)G.u[2] + s2RT * sn3 * r4;
+    const T vn = v[ax];
+    if (side == 0 ? !(vn > (T)0) : !(vn < (T)0)) continue;
+    const T te = (face - x[ax]) / vn;
+    if (!(te < dt)) continue;
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      if (d == ax) continue;
+      T y = x[d] + v[d] * te;
+      if (y < (T)P.lo[d]) {
+        if (P.face_bc[2 * d] != 0) { ok = false; break; }
+        y = (T)2.0 * (T)P.lo[d] - y;
+        v[d] = -v[d];
+      } else if (y > (T)P.hi[d]) {
+        if (P.face_bc[2 * d + 1] != 0) { ok = false; break; }
+        y = (T)2.0 * (T)P.hi[d] - y;
+        v[d] = -v[d];
+      }
+      if (y < (T)P.lo[d] || y > (T)P.hi[d]) { ok = false; break; }
+      x[d] = y;
+    }
+    if (!ok) continue;
+    x[ax] = face;
+    if (move_particle<T, DIM>(P, x, v, dt - te, step, kPurpInjWall, G.gc, (uint32_t)m,
+                              (uint32_t)G.face << 16, a.err))
+      continue;
+    if (pass == 1) {
+      const int64_t idx = base + nsurv;
+      if (idx >= a.cap) {
+        atomicAdd(&a.err[kErrCapacity], 1ull);
+      } else {
+        const uint32_t key = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) Bx[d][idx] = x[d];
+        Bv[0][idx] = v[0];
+        Bv[1][idx] = v[1];
+        Bv[2][idx] = v[2];
+        a.key[idx] = key;
+        atomicAdd(&a.count[key], 1u);
+      }
+    }
+    ++nsurv;
+  }
+  if (pass == 0) a.gcount[g] = nsurv;
+}
+
+// ---------------------------------------------------------------------------
+// Observability / initialisation kernels
+// ---------------------------------------------------------------------------
+// Moments of the current state for cells [c0, c1) (warp per cell, unsorted
+// sums).  With out == nullptr only dt_min is updated.
+template <class T>
+__global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nc = c1 - c0;
+  for (int64_t k = c0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c1; k += nw) {
+    const uint32_t s0 = a.start[k];
+    const int N = (int)(a.start[k + 1] - s0);
+    const InstParams& P = a.P[a.cell_inst[k]];
+    // two passes straight from global memory
+    const T* Av0 = (const T*)a.Avel[0];
+    const T* Av1 = (const T*)a.Avel[1];
+    const T* Av2 = (const T*)a.Avel[2];
+    double U[3] = {0, 0, 0};
+    {
+      T s0x = 0, s1x = 0, s2x = 0;
+      for (int s = lane; s < N; s += 32) {
+        const uint32_t o = a.perm[s0 + s];
+        s0x += Av0[o]; s1x += Av1[o]; s2x += Av2[o];
+      }
+      s0x = warp_sum(s0x); s1x = warp_sum(s1x); s2x = warp_sum(s2x);
+      if (N > 0) { U[0] = (double)s0x / N; U[1] = (double)s1x / N; U[2] = (double)s2x / N; }
+    }
+    CellMoments m;
+    m.U[0] = U[0]; m.U[1] = U[1]; m.U[2] = U[2];
+    m.n = N > 0 ? (double)N * P.Fn / a.vol[k] : 0.0;
+    m.T = 0; m.q[0] = m.q[1] = m.q[2] = 0;
+    m.tau = __longlong_as_double(0x7FF0000000000000ll);
+    m.dtc = m.tau;
+    if (N >= 2) {
+      const T Ux = (T)U[0], Uy = (T)U[1], Uz = (T)U[2];
+      T S2 = 0, S3x = 0, S3y = 0, S3z = 0;
+      for (int s = lane; s < N; s += 32) {
+        const uint32_t o = a.perm[s0 + s];
+        const T C0 = Av0[o] - Ux, C1 = Av1[o] - Uy, C2 = Av2[o] - Uz;
+        const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+        S2 += c2; S3x += c2 * C0; S3y += c2 * C1; S3z += c2 * C2;
+      }
+      S2 = warp_sum(S2); S3x = warp_sum(S3x); S3y = warp_sum(S3y); S3z = warp_sum(S3z);
+      m.T = (double)S2 / (3.0 * P.R * (double)(N - 1));
+      if (N >= 3) {
+        const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
+        m.q[0] = f * (double)S3x; m.q[1] = f * (double)S3y; m.q[2] = f * (double)S3z;
+      }
+      const double umag = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+      if (m.T > 0) {
+        const double p = m.n * P.m * P.R * m.T;
+        m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
+        m.dtc = P.Lmin / (umag + sqrt(P.gamma * P.R * m.T));
+      } else if (umag > 0) {
+        m.dtc = P.Lmin / umag;
+      }
+    }
+    if (lane == 0) {
+      if (out) {
+        const int64_t i = k - c0;
+        out[0 * nc + i] = (double)N;
+        out[1 * nc + i] = m.n;
+        out[2 * nc + i] = m.U[0];
+        out[3 * nc + i] = m.U[1];
+        out[4 * nc + i] = m.U[2];
+        out[5 * nc + i] = m.T;
+        out[6 * nc + i] = m.q[0];
+        out[7 * nc + i] = m.q[1];
+        out[8 * nc + i] = m.q[2];
+        out[9 * nc + i] = m.tau;
+        out[10 * nc + i] = m.dtc;
+        out[11 * nc + i] = dsmc_ratio(P, N, m);
+      } else if (N >= 2 && m.dtc < __longlong_as_double(0x7FF0000000000000ll)) {
+        atomicMin(&a.dt_min[a.cell_inst[k]], (unsigned long long)__double_as_longlong(m.dtc));
+      }
+    }
+  }
+}
+
+template <class T, int DIM>
+__global__ void k_keys(const T* x0, const T* x1, const T* x2, int64_t M, const uint32_t* part_inst,
+                       const InstParams* Ps, uint32_t* key, uint32_t* count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const InstParams& P = Ps[part_inst[i]];
+  T x[3] = {x0[i], DIM > 1 ? x1[i] : (T)0, DIM > 2 ? x2[i] : (T)0};
+  const uint32_t k = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
+  key[i] = k;
+  atomicAdd(&count[k], 1u);
+}
+
+// Host-provided FP64 particles of one instance -> state buffers at offset off.
+template <class T>
+__global__ void k_stage_in(const double* pos, const double* vel, int dim, int64_t n, T* p0, T* p1, T* p2,
+                           T* v0, T* v1, T* v2, int64_t off, uint32_t* part_inst, uint32_t inst) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  T* P3[3] = {p0, p1, p2};
+  for (int d = 0; d < dim; ++d) P3[d][off + j] = (T)pos[d * n + j];
+  v0[off + j] = (T)vel[j];
+  v1[off + j] = (T)vel[n + j];
+  v2[off + j] = (T)vel[2 * n + j];
+  part_inst[off + j] = inst;
+}
+
+template <class T>
+__global__ void k_gather(const T* p0, const T* p1, const T* p2, const T* v0, const T* v1, const T* v2,
+                         int dim, const uint32_t* perm, int64_t s0, int64_t n, double* out_pos,
+                         double* out_vel) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t o = perm[s0 + j];
+  const T* P3[3] = {p0, p1, p2};
+  for (int d = 0; d < dim; ++d) out_pos[d * n + j] = (double)P3[d][o];
+  out_vel[0 * n + j] = (double)v0[o];
+  out_vel[1 * n + j] = (double)v1[o];
+  out_vel[2 * n + j] = (double)v2[o];
+}
+
+}  // namespace sp

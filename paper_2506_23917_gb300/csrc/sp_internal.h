@@ -1,0 +1,126 @@
+// sp_internal.h -- data structures shared by the host driver and the kernels
+// of libsp (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sp {
+
+constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // key of a removed particle
+constexpr int kMaxBounce = 16;               // wall events per particle per step
+constexpr int64_t kNcolCap = int64_t(1) << 24;
+constexpr int kWarpsPerBlock = 4;            // collide kernel, small cells
+constexpr int kCapSmall = 512;               // per-warp staging capacity (particles)
+
+// Philox stream purposes (high byte of counter word 3).
+constexpr uint32_t kPurpNtc = 1, kPurpShk = 2, kPurpWall = 3, kPurpInj = 4, kPurpInjWall = 5;
+
+// Error counters (device, sticky).
+enum { kErrCapacity = 0, kErrCellCap = 1, kErrBounce = 2, kErrAr = 3, kErrNcol = 4, kNumErr = 5 };
+
+// Per-instance constants, precomputed on the host.
+struct InstParams {
+  int dim;
+  int n[3];
+  double lo[3], hi[3], inv_d[3], dl[3], Lmin;
+  double m, R, gamma, Pr, omega, T_ref, mu_ref, Fn, cfl, dt_fixed;
+  double sigc_coef, sigc_exp;  // sigma_T c_r = coef * c_r^exp
+  int face_bc[6];
+  double face_T[6];
+  int body;
+  double body_c[3], body_r, body_Tw;
+  int n_steady;
+  uint32_t key0, key1;
+  int mode;
+  int ar_max;
+  int64_t cell_off;  // first global cell of the instance
+  int64_t ncells;
+};
+
+// One reservoir (ghost) cell outside an inflow face.
+struct GhostCell {
+  int inst;
+  int face;
+  uint32_t gc;       // index within the face's reservoir (Philox counter)
+  int pad;
+  double blo[3], bhi[3];
+  double lam;        // expected particles = n_face * V / Fn
+  double s2RT;       // sqrt(2 R T_face)
+  double u[3];       // reservoir drift
+};
+
+struct StepArgs {
+  // particle buffers: A = current (read through perm), B = output
+  const void* Apos[3];
+  const void* Avel[3];
+  void* Bpos[3];
+  void* Bvel[3];
+  uint32_t* key;        // [cap]   key of each B slot
+  const uint32_t* perm; // [cap]   slot -> source index in A
+  const uint32_t* start;// [NC+1]  cell offsets of the current state
+  uint32_t* count;      // [NC]    next-state histogram (atomics)
+  const uint32_t* cell_inst;  // [NC]
+  const double* vol;    // [NC]
+  double* smax;         // [NC]
+  double* samp;         // [8][NC]
+  int32_t* rec;         // [4][NC] or null
+  uint8_t* resamp;      // [cap] or null
+  const InstParams* P;  // [n_inst]
+  const double* dt_cur; // [n_inst]
+  unsigned long long* dt_min;  // [n_inst] (double bits, atomicMin)
+  const uint32_t* step; // global step index
+  uint32_t* big_list;   // cells above kCapSmall
+  uint32_t* big_count;
+  unsigned long long* err;  // [kNumErr]
+  int64_t NC;
+  int64_t cap;
+  int big_cap;          // staging capacity of the big-cell launch
+};
+
+struct InjectArgs {
+  const GhostCell* ghosts;
+  int64_t n_ghost;
+  uint32_t* gcount;     // [n_ghost] survivors (pass 0)
+  const uint32_t* goff; // [n_ghost] exclusive offsets (pass 1)
+  void* Bpos[3];
+  void* Bvel[3];
+  uint32_t* key;
+  uint32_t* count;
+  const InstParams* P;
+  const double* dt_cur;
+  const uint32_t* step;
+  const uint32_t* Mcur; // particles of the current state (base of appends)
+  unsigned long long* err;
+  int64_t cap;
+};
+
+// Launch wrappers, one set per precision (sp_kern_f64.cu, sp_kern_f32.cu).
+#define SP_DECLARE_LAUNCHERS(tag)                                                                  \
+  void launch_collide_##tag(int dim, const StepArgs& a, bool big, int grid, cudaStream_t s);      \
+  void launch_inject_##tag(int dim, const InjectArgs& a, int pass, cudaStream_t s);               \
+  void launch_moments_##tag(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s); \
+  void launch_keys_##tag(int dim, const void* const pos[3], int64_t M, const uint32_t* part_inst, \
+                         const InstParams* P, uint32_t* key, uint32_t* count, cudaStream_t s);   \
+  void launch_gather_##tag(int dim, const void* const Apos[3], const void* const Avel[3],        \
+                           const uint32_t* perm, int64_t s0, int64_t n, double* out_pos,          \
+                           double* out_vel, cudaStream_t s);                                      \
+  void launch_stage_in_##tag(int dim, const double* pos, const double* vel, int64_t n,             \
+                             void* const dpos[3], void* const dvel[3], int64_t off,              \
+                             uint32_t* part_inst, uint32_t inst, cudaStream_t s);                \
+  cudaError_t configure_##tag(int big_cap);
+SP_DECLARE_LAUNCHERS(f64)
+SP_DECLARE_LAUNCHERS(f32)
+
+// Precision-independent kernels (sp_common.cu).
+void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s);
+void launch_cell_finalize(uint32_t* count, uint32_t* fill, int64_t NC, cudaStream_t s);
+void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* fill, uint32_t* perm,
+                    const uint32_t* Mtot, int64_t cap, cudaStream_t s);
+void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
+                          unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
+                          uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
+                          const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
+                          uint32_t* big_count, cudaStream_t s);
+int64_t scan_partial_size(int64_t n);
+
+}  // namespace sp

@@ -1,0 +1,98 @@
+// sp_kern_f32.cu -- FP32-mode instantiations of the libsp kernels.
+#include "sp_device.cuh"
+
+namespace sp {
+
+namespace {
+using T = float;
+
+template <int DIM>
+void collide_dim(const StepArgs& a, bool big, int grid, cudaStream_t s) {
+  if (!big) {
+    const size_t smem = (size_t)kWarpsPerBlock * kCapSmall * (4 + 3 * sizeof(T));
+    k_collide<T, DIM><<<grid, 32 * kWarpsPerBlock, smem, s>>>(a, 0);
+  } else {
+    const size_t smem = (size_t)a.big_cap * (4 + 3 * sizeof(T));
+    k_collide<T, DIM><<<grid, 32, smem, s>>>(a, 1);
+  }
+}
+
+template <int DIM>
+void inject_dim(const InjectArgs& a, int pass, cudaStream_t s) {
+  const int64_t g = (a.n_ghost + 127) / 128;
+  k_inject<T, DIM><<<(unsigned)g, 128, 0, s>>>(a, pass);
+}
+
+template <int DIM>
+void keys_dim(const void* const pos[3], int64_t M, const uint32_t* part_inst, const InstParams* P,
+              uint32_t* key, uint32_t* count, cudaStream_t s) {
+  const int64_t g = (M + 255) / 256;
+  k_keys<T, DIM><<<(unsigned)g, 256, 0, s>>>((const T*)pos[0], (const T*)pos[1], (const T*)pos[2], M,
+                                             part_inst, P, key, count);
+}
+
+template <int DIM>
+cudaError_t configure_dim(int big_cap) {
+  const size_t small = (size_t)kWarpsPerBlock * kCapSmall * (4 + 3 * sizeof(T));
+  const size_t big = (size_t)big_cap * (4 + 3 * sizeof(T));
+  const size_t mx = small > big ? small : big;
+  return cudaFuncSetAttribute(k_collide<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+}
+}  // namespace
+
+void launch_collide_f32(int dim, const StepArgs& a, bool big, int grid, cudaStream_t s) {
+  if (dim == 1) collide_dim<1>(a, big, grid, s);
+  else if (dim == 2) collide_dim<2>(a, big, grid, s);
+  else collide_dim<3>(a, big, grid, s);
+}
+
+void launch_inject_f32(int dim, const InjectArgs& a, int pass, cudaStream_t s) {
+  if (a.n_ghost == 0) return;
+  if (dim == 1) inject_dim<1>(a, pass, s);
+  else if (dim == 2) inject_dim<2>(a, pass, s);
+  else inject_dim<3>(a, pass, s);
+}
+
+void launch_moments_f32(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s) {
+  const int64_t nc = c1 - c0;
+  int64_t g = (nc + 7) / 8;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  k_moments<T><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, out);
+}
+
+void launch_keys_f32(int dim, const void* const pos[3], int64_t M, const uint32_t* part_inst,
+                       const InstParams* P, uint32_t* key, uint32_t* count, cudaStream_t s) {
+  if (M == 0) return;
+  if (dim == 1) keys_dim<1>(pos, M, part_inst, P, key, count, s);
+  else if (dim == 2) keys_dim<2>(pos, M, part_inst, P, key, count, s);
+  else keys_dim<3>(pos, M, part_inst, P, key, count, s);
+}
+
+void launch_gather_f32(int dim, const void* const Apos[3], const void* const Avel[3],
+                         const uint32_t* perm, int64_t s0, int64_t n, double* out_pos,
+                         double* out_vel, cudaStream_t s) {
+  if (n == 0) return;
+  const int64_t g = (n + 255) / 256;
+  k_gather<T><<<(unsigned)g, 256, 0, s>>>((const T*)Apos[0], (const T*)Apos[1], (const T*)Apos[2],
+                                          (const T*)Avel[0], (const T*)Avel[1], (const T*)Avel[2],
+                                          dim, perm, s0, n, out_pos, out_vel);
+}
+
+void launch_stage_in_f32(int dim, const double* pos, const double* vel, int64_t n, void* const dpos[3],
+                          void* const dvel[3], int64_t off, uint32_t* part_inst, uint32_t inst,
+                          cudaStream_t s) {
+  if (n == 0) return;
+  const int64_t g = (n + 255) / 256;
+  k_stage_in<T><<<(unsigned)g, 256, 0, s>>>(pos, vel, dim, n, (T*)dpos[0], (T*)dpos[1], (T*)dpos[2],
+                                            (T*)dvel[0], (T*)dvel[1], (T*)dvel[2], off, part_inst, inst);
+}
+
+cudaError_t configure_f32(int big_cap) {
+  cudaError_t e = configure_dim<1>(big_cap);
+  if (e == cudaSuccess) e = configure_dim<2>(big_cap);
+  if (e == cudaSuccess) e = configure_dim<3>(big_cap);
+  return e;
+}
+
+}  // namespace sp

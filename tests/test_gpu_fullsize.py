@@ -1,0 +1,92 @@
+"""The benchmark workload at full size (2-D cylinder, 600 x 300 cut-cell
+grid, ~6.6 M particles).
+
+* FP64 mode: two full steps checked against the oracle with the same bar
+  as the small parity cases (bit-exact integers, 1e-12 relative floats).
+* FP32 mode (the configuration the benchmark times, CUDA graph per step):
+  properties that hold at any size -- no capacity or staging overflow,
+  particle count and freestream state consistent with the FP64 run and
+  with the inflow state, wall-free far field unchanged.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_23917_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2506_23917_gb300 import build
+
+    build.build()
+    import paper_2506_23917_gb300 as sp
+
+    return sp
+
+
+@pytest.fixture(scope="module")
+def cyl():
+    cfg, regions = W.cylinder(scale=1.0, n_steady=0)
+    pos, vel = W.fill_regions(cfg, regions, 1)
+    return cfg, pos, vel
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def test_full_size_fp64_two_steps_match_oracle(sp, cyl):
+    cfg, pos, vel = cyl
+    o = oracle.Oracle(cfg)
+    o.set_particles(pos, vel)
+    s = sp.Sim(cfg, sp.FP64, capacity=int(1.3 * vel.shape[1]))
+    s.set_particles(0, pos, vel)
+    s.set_record(True)
+    for n in range(2):
+        o.step(1)
+        s.step(1)
+        c_o, r_o, p_o = o.record()
+        c_s, r_s, p_s = s.record(0)
+        assert np.array_equal(c_s, c_o), f"records differ at step {n}"
+        assert np.array_equal(r_s, r_o)
+        assert np.array_equal(p_s, p_o)
+        assert np.array_equal(s.cell_start(0), o.cell_start())
+        po, vo, _ = o.particles()
+        ps, vs, _ = s.particles(0)
+        assert _rel(vs, vo) <= 1e-12 and _rel(ps, po) <= 1e-12
+        assert abs(s.dt(0) / o.dt - 1) <= 1e-12
+    assert c_o[0].sum() > 0
+
+
+def test_full_size_fp32_graph_run_properties(sp, cyl):
+    cfg, pos, vel = cyl
+    M0 = vel.shape[1]
+    res = {}
+    for prec in (sp.FP32, sp.FP64):
+        s = sp.Sim(cfg, prec, capacity=int(1.5 * M0) + 200000)
+        s.set_particles(0, pos, vel)
+        s.step(150)
+        s.sync()
+        e = s.errors()
+        assert e["capacity"] == 0 and e["cell_cap"] == 0
+        m = s.moments(0, 0)
+        res[prec] = (s.count(0), m)
+        s.close()
+    n32, m32 = res[sp.FP32]
+    n64, m64 = res[sp.FP64]
+    assert abs(n32 / n64 - 1) < 5e-3
+    # upstream freestream block (x < -2.2 R): density and velocity at the inflow state
+    nx, ny = cfg["n"][0], cfg["n"][1]
+    xs = cfg["lo"][0] + (np.arange(nx) + 0.5) * (cfg["hi"][0] - cfg["lo"][0]) / nx
+    up = np.tile(xs < -2.2, ny)
+    n_inf, U = cfg["face_n"][0], cfg["face_u"][0][0]
+    for m in (m32, m64):
+        assert abs(np.mean(m[1][up]) / n_inf - 1) < 0.01
+        assert abs(np.mean(m[2][up]) / U - 1) < 0.01
+        assert abs(np.mean(m[5][up]) / 273.0 - 1) < 0.02

@@ -1,0 +1,195 @@
+"""GPU FP64 mode against the oracle, through the C ABI.
+
+The bar (FP64 mode): bit-exact cell offsets, stable-sort permutations,
+per-cell candidate / accepted / resampled / acceptance-rejection counts and
+resampled-particle sets after every step; positions, velocities, Delta t
+and (sigma c)_max within 1e-12 relative (velocities and positions relative
+to the largest magnitude in the state, since a particle's own component
+may be near zero).  Both sides draw the same Philox4x32-10 streams; they
+differ only in the order of floating-point sums and in the last bits of
+the transcendental functions (CUDA vs the C library), which is what the
+1e-12 tolerance absorbs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_23917_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def sp():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    from paper_2506_23917_gb300 import build
+
+    build.build()
+    import paper_2506_23917_gb300 as sp
+
+    return sp
+
+
+def _close(a, b, rtol=RTOL, what=""):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    if a.size == 0:
+        return
+    scale = max(np.max(np.abs(b)), 1e-300)
+    err = np.max(np.abs(a - b))
+    assert err <= rtol * scale, f"{what}: max abs err {err:.3e} vs scale {scale:.3e}"
+
+
+def compare_state(o, s, inst=0, what=""):
+    assert s.count(inst) == o.M, (what, s.count(inst), o.M)
+    np.testing.assert_array_equal(s.cell_start(inst), o.cell_start(), err_msg=what + " cell offsets")
+    po, vo, co = o.particles()
+    ps, vs, cs = s.particles(inst)
+    np.testing.assert_array_equal(cs, co, err_msg=what + " cells")
+    _close(vs, vo, what=what + " velocities")
+    _close(ps, po, what=what + " positions")
+    _close([s.dt(inst)], [o.dt], what=what + " dt")
+    _close(s.sigc_max(inst), o.sigc_max(), what=what + " sigc_max")
+
+
+def compare_record(o, s, inst=0, what=""):
+    c_o, r_o, p_o = o.record()
+    c_s, r_s, p_s = s.record(inst)
+    names = ["candidates", "accepted", "resampled", "AR attempts"]
+    for i in range(4):
+        np.testing.assert_array_equal(c_s[i], c_o[i], err_msg=f"{what} {names[i]}")
+    np.testing.assert_array_equal(r_s, r_o, err_msg=what + " resampled set")
+    if s.cfgs[inst] is s.cfgs[0] and len(s.cfgs) == 1:
+        np.testing.assert_array_equal(p_s, p_o, err_msg=what + " permutation")
+    return c_o
+
+
+def run_pair(sp, cfg, pos, vel, steps, capacity=None):
+    o = oracle.Oracle(cfg)
+    o.set_particles(pos, vel)
+    s = sp.Sim(cfg, sp.FP64, capacity=capacity or max(4 * vel.shape[1], 4096))
+    s.set_particles(0, pos, vel)
+    s.set_record(True)
+    compare_state(o, s, what="initial")
+    totals = np.zeros(4, dtype=np.int64)
+    for n in range(steps):
+        o.step(1)
+        s.step(1)
+        c = compare_record(o, s, what=f"step {n}")
+        totals += c.sum(axis=1)
+        compare_state(o, s, what=f"step {n}")
+    assert s.errors()["capacity"] == 0 and s.errors()["cell_cap"] == 0
+    return o, s, totals
+
+
+def test_sod_fp64_matches_oracle(sp):
+    cfg, regions = W.sod(ncell=200, ppc_left=100.0, lam_left=1e-3, n_steady=10)
+    pos, vel = W.fill_regions(cfg, regions, 1)
+    o, s, tot = run_pair(sp, cfg, pos, vel, steps=25)
+    assert tot[0] > 0 and tot[1] > 0 and tot[2] > 0  # both sub-steps ran
+    # Step 5/6 time averages and the instantaneous moments
+    _close(s.moments(0, 1), o.moments(1), what="averaged moments")
+    mi_s, mi_o = s.moments(0, 0), o.moments(0)
+    for f in range(mi_o.shape[0]):
+        fin = np.isfinite(mi_o[f])
+        np.testing.assert_array_equal(np.isfinite(mi_s[f]), fin)
+        _close(mi_s[f][fin], mi_o[f][fin], what=f"instant field {f}")
+
+
+def test_big_cell_hybrid_matches_oracle(sp):
+    """One cell above the per-warp staging capacity (big-cell launch), with
+    both the DSMC and the Shakhov sub-steps active."""
+    N = 1500
+    cfg = W.homogeneous(N=N, Kn=0.05, omega=0.81)
+    pos, vel = W.homogeneous_particles(cfg, N, Tx=2.0, skew=0.1, seed=3)
+    o, s, tot = run_pair(sp, cfg, pos, vel, steps=6)
+    assert tot[0] > 0 and tot[2] > 0
+
+
+def test_channel_with_body_inflow_outflow_matches_oracle(sp):
+    cfg, regions = W.box2d(nx=24, ny=12, ppc=30.0)
+    pos, vel = W.fill_regions(cfg, regions, 3)
+    o, s, tot = run_pair(sp, cfg, pos, vel, steps=12)
+    t = o.totals()
+    assert t["injected"] > 0 and t["removed"] > 0
+
+
+def test_sphere_box_matches_oracle(sp):
+    cfg, regions = W.box3d(n=(12, 8, 8), ppc=12.0)
+    pos, vel = W.fill_regions(cfg, regions, 5)
+    o, s, tot = run_pair(sp, cfg, pos, vel, steps=6)
+    assert o.totals()["injected"] > 0
+
+
+@pytest.mark.parametrize("mode", [W.MODE_DSMC, W.MODE_SHAKHOV])
+def test_forced_modes_match_oracle(sp, mode):
+    cfg, regions = W.sod(ncell=60, ppc_left=60.0, lam_left=1e-3, mode=mode)
+    pos, vel = W.fill_regions(cfg, regions, 2)
+    run_pair(sp, cfg, pos, vel, steps=8)
+
+
+def test_tiny_cells_edge_cases(sp):
+    """Cells with 0, 1, 2 (DSMC only) and 3 (Shakhov allowed) particles and
+    an empty tail of the domain."""
+    cfg = W.base_config(1, [12], [0.0], [1.2])
+    cfg.update(d_ref=0.3, mu_ref=0.02, Fn=0.05, dt_fixed=0.02, sigc_T0=1.0)
+    counts = [0, 1, 2, 3, 0, 5, 2, 1, 3, 0, 0, 0]
+    rng = np.random.default_rng(9)
+    xs, vs = [], []
+    for k, n in enumerate(counts):
+        xs.append(0.1 * k + 0.1 * rng.random(n))
+        vs.append(rng.normal(0, 1, (3, n)))
+    pos = np.concatenate(xs)[None, :]
+    vel = np.concatenate(vs, axis=1)
+    run_pair(sp, cfg, pos, vel, steps=10)
+
+
+def test_batch_instances_match_separate_oracles(sp):
+    insts = W.batch(n_inst=4, Nmin=300, Nmax=3000, Kn_min=1e-3, Kn_max=1e-1, n_steady=3)
+    cfgs = [c for c, _, _ in insts]
+    s = sp.Sim(cfgs, sp.FP64, capacity=40000)
+    s.set_record(True)
+    os_ = []
+    for i, (c, p, v) in enumerate(insts):
+        s.set_particles(i, p, v)
+        o = oracle.Oracle(c)
+        o.set_particles(p, v)
+        os_.append(o)
+    for n in range(6):
+        s.step(1)
+        for i, o in enumerate(os_):
+            o.step(1)
+            compare_record(o, s, inst=i, what=f"inst {i} step {n}")
+            compare_state(o, s, inst=i, what=f"inst {i} step {n}")
+    for i, o in enumerate(os_):
+        _close(s.moments(i, 1), o.moments(1), what=f"inst {i} averages")
+
+
+def test_empty_instance_with_fixed_step(sp):
+    cfg = W.base_config(1, [8], [0.0], [1.0])
+    cfg.update(dt_fixed=0.01)
+    s = sp.Sim(cfg, sp.FP64, capacity=64)
+    s.set_particles(0, np.zeros((1, 0)), np.zeros((3, 0)))
+    s.step(3)
+    s.sync()
+    assert s.count(0) == 0
+
+
+def test_capacity_overflow_is_reported(sp):
+    cfg, regions = W.box2d(nx=16, ny=8, ppc=20.0)
+    pos, vel = W.fill_regions(cfg, regions, 3)
+    s = sp.Sim(cfg, sp.FP64, capacity=vel.shape[1] + 5)
+    s.set_particles(0, pos, vel)
+    s.step(4)
+    with pytest.raises(sp.SpError) as e:
+        s.sync()
+    assert e.value.code == -3
+    assert s.errors()["capacity"] > 0
+    small = sp.Sim(cfg, sp.FP64, capacity=10)
+    with pytest.raises(sp.SpError) as e:
+        small.set_particles(0, pos, vel)
+    assert e.value.code == -3
