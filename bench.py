@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--profile-steps", type=int, default=40)
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-steps", type=int, default=200)
     return p.parse_args()
 
 
@@ -227,6 +229,60 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_batch(sp, torch, stream, steps):
+    from paper_2506_23917_gb300 import workloads as W
+
+    insts = W.batch(n_inst=256, seed=1, n_steady=0)
+    M = sum(v.shape[1] for _, _, v in insts)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sim = sp.Sim([c for c, _, _ in insts], sp.FP32, capacity=int(1.3 * M) + 10000)
+    for i, (c, p, v) in enumerate(insts):
+        sim.set_particles(i, p, v)
+    sim.step(5)
+    sim.sync()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    t32 = e0.elapsed_time(e1)
+    launches32 = sim.launches_per_step()
+    sim.close()
+    sims = []
+    for c, p, v in insts:
+        s = sp.Sim(c, sp.FP64, capacity=int(1.3 * v.shape[1]) + 1000)
+        s.set_particles(0, p, v)
+        s.step(5)
+        sims.append(s)
+    for s in sims:
+        s.sync()
+    k64 = max(5, steps // 10)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k64):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    for s in sims:
+        s.sync()
+    t64 = e0.elapsed_time(e1)
+    launches64 = sum(s.launches_per_step() for s in sims)
+    for s in sims:
+        s.close()
+    v32 = steps * M / (t32 * 1e-3)
+    v64 = k64 * M / (t64 * 1e-3)
+    return {"workload": "256 x 1-D (even: Sod, nx = 2N/112.5; odd: homogeneous relaxation), "
+                        "N log-uniform 1e3..5e5, Kn log-uniform 1e-4..1", "particles": M,
+            "fp32_batched": {"value": v32, "unit": UNIT, "ms_per_step": t32 / steps, "steps": steps,
+                             "launches_per_step": launches32},
+            "fp64_separate": {"value": v64, "unit": UNIT, "ms_per_step": t64 / k64, "steps": k64,
+                              "launches_per_step": launches64},
+            "speedup": v32 / v64}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -379,6 +435,12 @@ def main():
                        "h2d_bytes_per_step": 8 * (cfg["dim"] + 3) * n_e2e,
                        "d2h_bytes_per_step": 8 * len(sp.FIELDS) * sim.ncells[0],
                        "note": "per step: pinned host state -> device, one step, moments -> pinned host"}
+
+    # --- batched ensemble: 256 independent 1-D Sod / relaxation instances of
+    # uneven size, FP32 in one context (one set of launches per step) vs the
+    # plain FP64 form as 256 separate contexts stepped one after another
+    if not args.no_batch and rank == 0:
+        line["batch256"] = bench_batch(sp, torch, stream, args.batch_steps)
 
     # --- CPU oracle on a bounded sample of the same (developed) state
     if rank == 0 and world >= 1 and not args.no_cpu:

@@ -25,7 +25,9 @@
 using namespace sp;
 
 namespace {
-constexpr int kBigCap = 8192;
+// Staging capacity (particles) of the big-cell launch: one warp, 227 KB of
+// shared memory at 32 B (FP64) or 20 B (FP32) per particle, a power of two.
+constexpr int kBigCap64 = 4096, kBigCap32 = 8192;
 constexpr double kPiHost = 3.14159265358979323846;
 }  // namespace
 
@@ -217,7 +219,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.err = c->err;
   a.NC = c->NC;
   a.cap = c->cap;
-  a.big_cap = kBigCap;
+  a.big_cap = c->prec == SP_FP64 ? kBigCap64 : kBigCap32;
   return a;
 }
 
@@ -465,7 +467,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
   c->n_ghost = (int64_t)gh.size();
 
   sp_status st = [&]() -> sp_status {
-    CK(precision == SP_FP64 ? configure_f64(kBigCap) : configure_f32(kBigCap));
+    CK(precision == SP_FP64 ? configure_f64(kBigCap64) : configure_f32(kBigCap32));
     const int64_t NC = c->NC, cap = c->cap;
     for (int b = 0; b < 2; ++b)
       for (int d = 0; d < 3; ++d) {

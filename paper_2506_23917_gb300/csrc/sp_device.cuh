@@ -369,8 +369,8 @@ __device__ __forceinline__ double dsmc_ratio(const InstParams& P, int N, const C
 // warp; sidx/svx/svy/svz are the warp's staging arrays of capacity cap.
 // ---------------------------------------------------------------------------
 template <class T, int DIM>
-__device__ void process_cell(const StepArgs& a, int64_t k, uint32_t* sidx, T* svx, T* svy, T* svz,
-                             int cap) {
+__device__ void process_cell(const StepArgs& a, int64_t k, uint32_t* sidx, int* stag, T* svx, T* svy,
+                             T* svz, int cap) {
   const int lane = threadIdx.x & 31;
   const uint32_t s0 = a.start[k];
   const int N = (int)(a.start[k + 1] - s0);
@@ -414,6 +414,7 @@ __device__ void process_cell(const StepArgs& a, int64_t k, uint32_t* sidx, T* sv
     svx[s] = Av0[o];
     svy[s] = Av1[o];
     svz[s] = Av2[o];
+    stag[s] = 0x7FFFFFFF;
   }
   __syncwarp();
   // 3. moments (Step 3) and the local time step (Eq. "local time step")
@@ -444,6 +445,7 @@ __device__ void process_cell(const StepArgs& a, int64_t k, uint32_t* sidx, T* sv
       }
       T smax = (T)smax0;
       const T coef = (T)P.sigc_coef, ex = (T)P.sigc_exp;
+      int myacc = 0;
       for (int64_t base = 0; base < ncol; base += 32) {
         const int64_t kk = base + lane;
         int ci = 0, cj = 0;
@@ -461,37 +463,65 @@ __device__ void process_cell(const StepArgs& a, int64_t k, uint32_t* sidx, T* sv
           if (cj >= ci) cj += 1;
         }
         const int nb = (int)((ncol - base) < 32 ? (ncol - base) : 32);
-        for (int L = 0; L < nb; ++L) {
-          const int i = __shfl_sync(kFull, ci, L), j = __shfl_sync(kFull, cj, L);
-          const T v3 = __shfl_sync(kFull, u3, L), v4 = __shfl_sync(kFull, u4, L),
-                  v5 = __shfl_sync(kFull, u5, L);
-          const T ax = svx[i], ay = svy[i], az = svz[i];
-          const T bx = svx[j], by = svy[j], bz = svz[j];
-          const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
-          const T cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
-          const T sc = coef * tpow(cr, ex);
-          if (sc > smax) smax = sc;
+        unsigned pending = nb == 32 ? kFull : ((1u << nb) - 1u);
+        // Candidates are taken in order in runs that touch disjoint pairs:
+        // within a run every candidate sees the velocities left by all
+        // earlier candidates, and (sigma c)_max is an inclusive prefix
+        // maximum, so the outcome equals the one-by-one NTC loop.
+        while (pending) {
+          const bool mine = (pending >> lane) & 1u;
+          if (mine) {
+            atomicMin(&stag[ci], lane);
+            atomicMin(&stag[cj], lane);
+          }
           __syncwarp();
-          if (v3 < sc / smax) {
-            ++nacc;
-            const T cchi = (T)2.0 * v4 - (T)1.0;
+          const bool clash = mine && (stag[ci] != lane || stag[cj] != lane);
+          const unsigned cmask = __ballot_sync(kFull, clash);
+          const int F = cmask ? __ffs(cmask) - 1 : 32;
+          const unsigned run = pending & (F == 32 ? kFull : ((1u << F) - 1u));
+          __syncwarp();
+          if (mine) {
+            stag[ci] = 0x7FFFFFFF;
+            stag[cj] = 0x7FFFFFFF;
+          }
+          const bool act = (run >> lane) & 1u;
+          T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;
+          if (act) {
+            ax = svx[ci]; ay = svy[ci]; az = svz[ci];
+            bx = svx[cj]; by = svy[cj]; bz = svz[cj];
+            const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
+            cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
+            sc = coef * tpow(cr, ex);
+          }
+          T pm = sc;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(kFull, pm, o);
+            if (lane >= o && y > pm) pm = y;
+          }
+          const T smL = pm > smax ? pm : smax;
+          if (act && u3 < sc / smL) {
+            ++myacc;
+            const T cchi = (T)2.0 * u4 - (T)1.0;
             const T schi = tsqrt((T)1.0 - cchi * cchi);
             T sn, cs;
-            sincos2pi(v5, &sn, &cs);
+            sincos2pi(u5, &sn, &cs);
             const T w0 = cchi, w1 = schi * cs, w2 = schi * sn;
             const T m0 = ax + bx, m1 = ay + by, m2 = az + bz;
-            if (lane == 0) {
-              svx[i] = (T)0.5 * (m0 - cr * w0);
-              svy[i] = (T)0.5 * (m1 - cr * w1);
-              svz[i] = (T)0.5 * (m2 - cr * w2);
-              svx[j] = (T)0.5 * (m0 + cr * w0);
-              svy[j] = (T)0.5 * (m1 + cr * w1);
-              svz[j] = (T)0.5 * (m2 + cr * w2);
-            }
-            __syncwarp();
+            svx[ci] = (T)0.5 * (m0 - cr * w0);
+            svy[ci] = (T)0.5 * (m1 - cr * w1);
+            svz[ci] = (T)0.5 * (m2 - cr * w2);
+            svx[cj] = (T)0.5 * (m0 + cr * w0);
+            svy[cj] = (T)0.5 * (m1 + cr * w1);
+            svz[cj] = (T)0.5 * (m2 + cr * w2);
           }
+          const T top = __shfl_sync(kFull, pm, 31);
+          if (top > smax) smax = top;
+          pending &= ~run;
+          __syncwarp();
         }
       }
+      nacc = warp_sum(myacc);
       ncand = (int)ncol;
       if (lane == 0) a.smax[k] = (double)smax;
     }
@@ -617,17 +647,25 @@ __device__ void process_cell(const StepArgs& a, int64_t k, uint32_t* sidx, T* sv
   }
 }
 
+// Per-warp staging layout: sidx[cap] (u32), stag[cap] (i32), vx, vy, vz [cap] (T).
+template <class T>
+__host__ __device__ constexpr size_t stage_bytes_per_particle() {
+  return 4 + 4 + 3 * sizeof(T);
+}
+
 template <class T, int DIM>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_collide(StepArgs a, int big) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cap = big ? a.big_cap : kCapSmall;
+  if (big && warp != 0) return;
+  unsigned char* base = smem + (size_t)(big ? 0 : warp) * cap * stage_bytes_per_particle<T>();
+  uint32_t* sidx = (uint32_t*)base;
+  int* stag = (int*)(base + (size_t)cap * 4);
+  T* svx = (T*)(base + (size_t)cap * 8);
+  T* svy = svx + cap;
+  T* svz = svy + cap;
   if (!big) {
-    const int cap = kCapSmall;
-    unsigned char* base = smem + (size_t)warp * cap * (4 + 3 * sizeof(T));
-    uint32_t* sidx = (uint32_t*)base;
-    T* svx = (T*)(base + (size_t)cap * 4);
-    T* svy = svx + cap;
-    T* svz = svy + cap;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < a.NC; k += nw) {
       const int N = (int)(a.start[k + 1] - a.start[k]);
@@ -638,18 +676,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_collide(StepArgs a, int
         }
         continue;
       }
-      process_cell<T, DIM>(a, k, sidx, svx, svy, svz, cap);
+      process_cell<T, DIM>(a, k, sidx, stag, svx, svy, svz, cap);
     }
   } else {
-    if (warp != 0) return;
-    const int cap = a.big_cap;
-    uint32_t* sidx = (uint32_t*)smem;
-    T* svx = (T*)(smem + (size_t)cap * 4);
-    T* svy = svx + cap;
-    T* svz = svy + cap;
     const uint32_t nbig = *a.big_count;
     for (uint32_t i = blockIdx.x; i < nbig; i += gridDim.x)
-      process_cell<T, DIM>(a, (int64_t)a.big_list[i], sidx, svx, svy, svz, cap);
+      process_cell<T, DIM>(a, (int64_t)a.big_list[i], sidx, stag, svx, svy, svz, cap);
   }
 }
 

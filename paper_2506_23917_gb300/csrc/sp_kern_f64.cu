@@ -9,10 +9,10 @@ using T = double;
 template <int DIM>
 void collide_dim(const StepArgs& a, bool big, int grid, cudaStream_t s) {
   if (!big) {
-    const size_t smem = (size_t)kWarpsPerBlock * kCapSmall * (4 + 3 * sizeof(T));
+    const size_t smem = (size_t)kWarpsPerBlock * kCapSmall * stage_bytes_per_particle<T>();
     k_collide<T, DIM><<<grid, 32 * kWarpsPerBlock, smem, s>>>(a, 0);
   } else {
-    const size_t smem = (size_t)a.big_cap * (4 + 3 * sizeof(T));
+    const size_t smem = (size_t)a.big_cap * stage_bytes_per_particle<T>();
     k_collide<T, DIM><<<grid, 32, smem, s>>>(a, 1);
   }
 }
@@ -33,8 +33,8 @@ void keys_dim(const void* const pos[3], int64_t M, const uint32_t* part_inst, co
 
 template <int DIM>
 cudaError_t configure_dim(int big_cap) {
-  const size_t small = (size_t)kWarpsPerBlock * kCapSmall * (4 + 3 * sizeof(T));
-  const size_t big = (size_t)big_cap * (4 + 3 * sizeof(T));
+  const size_t small = (size_t)kWarpsPerBlock * kCapSmall * stage_bytes_per_particle<T>();
+  const size_t big = (size_t)big_cap * stage_bytes_per_particle<T>();
   const size_t mx = small > big ? small : big;
   return cudaFuncSetAttribute(k_collide<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }

@@ -26,6 +26,7 @@ Gas-model relations used to derive a config from (Kn, L, T):
 from __future__ import annotations
 
 import math
+import warnings
 
 import numpy as np
 
@@ -112,8 +113,10 @@ def _chord_area(x0, x1, y0, y1, cx, cy, r):
                     pts.append(xb)
     pts = sorted(set(pts))
     tot = 0.0
-    for p, q in zip(pts[:-1], pts[1:]):
-        tot += quad(L, p, q, epsabs=1e-14, epsrel=1e-12, limit=200)[0]
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        for p, q in zip(pts[:-1], pts[1:]):
+            tot += quad(L, p, q, epsabs=1e-14, epsrel=1e-12, limit=200)[0]
     return tot
 
 
@@ -217,18 +220,20 @@ def fill_regions(cfg, regions, seed):
             box *= hi[d] - lo[d]
         if "count" in reg:
             count = int(reg["count"])
+            pos = np.empty((dim, 0))
+            need = count
+            while need > 0:
+                m = int(need * 1.2) + 16
+                cand = np.stack([lo[d] + (hi[d] - lo[d]) * rng.random(m) for d in range(dim)])
+                cand = cand[:, ~_inside_body(cfg, cand)][:, :need]
+                pos = np.concatenate([pos, cand], axis=1)
+                need = count - pos.shape[1]
         else:
-            count = int(round(reg["n"] * box / cfg["Fn"]))
-        pos = np.empty((dim, 0))
-        need = count
-        # rejection against the body keeps the fluid density uniform
-        while need > 0:
-            m = int(need * 1.2) + 16
+            # uniform in the box at density n; those inside the body are dropped
+            m = int(round(reg["n"] * box / cfg["Fn"]))
             cand = np.stack([lo[d] + (hi[d] - lo[d]) * rng.random(m) for d in range(dim)])
-            keep = ~_inside_body(cfg, cand)
-            cand = cand[:, keep][:, :need]
-            pos = np.concatenate([pos, cand], axis=1)
-            need = count - pos.shape[1]
+            pos = cand[:, ~_inside_body(cfg, cand)]
+            count = pos.shape[1]
         s = math.sqrt(cfg["R"] * reg["T"])
         vel = rng.normal(0.0, s, size=(3, count)) + np.asarray(reg["u"], dtype=np.float64)[:, None]
         P.append(pos)
@@ -401,10 +406,25 @@ def box3d(n=(12, 8, 8), ppc=20.0, seed=5, T=1.0, U=3.0, Kn=0.05):
     return cfg, regions
 
 
+def homogeneous_box(N, Kn, seed=1, Tx=2.0, Tyz=1.0, skew=0.05, ppc=56.25, n_steady=10**9):
+    """Spatially homogeneous relaxation in a 1-D box of unit length with
+    specular walls: nx = round(N/ppc) cells, uniform positions, a
+    bi-Maxwellian (T_x != T_y = T_z) with a heat-flux-carrying skew."""
+    nx = max(1, int(round(N / ppc)))
+    cfg = base_config(1, [nx], [0.0], [1.0])
+    T = (Tx + 2 * Tyz) / 3.0
+    d = d_for_mfp(Kn, 1.0, 1.0, T, 0.5)
+    cfg.update(omega=0.5, T_ref=1.0, d_ref=d, mu_ref=vhs_mu_ref(1.0, d, 1.0, 0.5, kB=1.0),
+               Fn=1.0 / N, sigc_T0=T, seed=seed, n_steady=n_steady)
+    pos, vel = homogeneous_particles(cfg, N, Tx=Tx, Tyz=Tyz, skew=skew, seed=seed)
+    return cfg, pos, vel
+
+
 def batch(n_inst=256, seed=1, Nmin=1e3, Nmax=5e5, Kn_min=1e-4, Kn_max=1.0, n_steady=10**9):
     """Ensemble of independent 1-D instances: even i a Sod tube with
-    nx = round(2 N_i / 112.5) cells, odd i a homogeneous relaxation cell;
-    N_i and Kn log-uniform.  Returns a list of (cfg, pos, vel)."""
+    nx = round(2 N_i / 112.5) cells, odd i a spatially homogeneous
+    relaxation box (~56 particles per cell); N_i and Kn log-uniform.
+    Returns a list of (cfg, pos, vel)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     Ns = np.exp(rng.uniform(math.log(Nmin), math.log(Nmax), n_inst))
     Kns = np.exp(rng.uniform(math.log(Kn_min), math.log(Kn_max), n_inst))
@@ -417,8 +437,6 @@ def batch(n_inst=256, seed=1, Nmin=1e3, Nmax=5e5, Kn_min=1e-4, Kn_max=1.0, n_ste
                                n_steady=n_steady)
             pos, vel = fill_regions(cfg, regions, seed * 7919 + i)
         else:
-            cfg = homogeneous(N=N, Kn=float(Kns[i]), seed=seed * 1000 + i)
-            cfg["n_steady"] = n_steady
-            pos, vel = homogeneous_particles(cfg, N, skew=0.05, seed=seed * 7919 + i)
+            cfg, pos, vel = homogeneous_box(N, float(Kns[i]), seed=seed * 1000 + i, n_steady=n_steady)
         out.append((cfg, pos, vel))
     return out
