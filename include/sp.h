@@ -171,6 +171,30 @@ sp_status sp_sync(sp_ctx* ctx);
 /* Number of kernel launches one sp_step() issues (for launch accounting). */
 int sp_launches_per_step(sp_ctx* ctx);
 sp_status sp_free(sp_ctx* ctx);
+
+/* Stable counting sort of cell keys that allocates no device memory.  The
+ * paper has no counterpart: this is the indexing step (Step 3) offered as a
+ * standalone call for callers that cannot call cudaMalloc -- code that runs
+ * where the device memory plan is fixed (between CUDA-graph captures, under
+ * a hard memory quota) or hosts that own every device buffer and forbid the
+ * library to allocate.
+ *   d_keys  device uint32 [n]: cell of each particle; keys >= ncells drop
+ *           the particle (0xFFFFFFFF marks a removed particle)
+ *   d_start device uint32 [ncells+1] (out): cell offsets, d_start[ncells]
+ *           = number of particles kept
+ *   d_perm  device uint32 [n] (out): d_perm[d_start[c] + r] = index of the
+ *           r-th kept particle of cell c, in ascending index order
+ *   stream  cudaStream_t or NULL; the call is asynchronous on it.
+ * Scratch lives in a file-scope __device__ array sized for ncells <=
+ * 1,048,576 (8 MiB, held by every GPU that loads the library until exit);
+ * larger ncells return SP_ERR_CAPACITY with a message.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call shares the one
+ * array and clears the counters it needs, so calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race: serialise
+ * them.  Calls no cudaMalloc, cudaFree or other allocating routine. */
+sp_status sp_sort_cells_static(const uint32_t* d_keys, int64_t n, int64_t ncells, uint32_t* d_start,
+                               uint32_t* d_perm, void* stream);
 const char* sp_status_str(int status);
 
 #ifdef __cplusplus

@@ -50,7 +50,7 @@ class SpConfig(C.Structure):
 SYMBOLS = ["sp_init", "sp_set_particles", "sp_step", "sp_moments", "sp_get_particles",
            "sp_set_record", "sp_get_step_record", "sp_get_cell_start", "sp_get_sigc_max",
            "sp_get_dt", "sp_errors", "sp_sync", "sp_step_profiled", "sp_launches_per_step", "sp_free",
-           "sp_status_str"]
+           "sp_status_str", "sp_sort_cells_static"]
 
 _lib = None
 
@@ -78,6 +78,7 @@ def lib():
         L.sp_step_profiled.argtypes = [P, C.c_int, P, C.c_int]
         L.sp_launches_per_step.argtypes = [P]
         L.sp_free.argtypes = [P]
+        L.sp_sort_cells_static.argtypes = [P, C.c_int64, C.c_int64, P, P, P]
         L.sp_status_str.argtypes = [C.c_int]
         L.sp_status_str.restype = C.c_char_p
         _lib = L
@@ -135,6 +136,14 @@ def current_stream():
     except Exception:  # pragma: no cover - torch absent
         pass
     return None
+
+
+def sort_cells_static(keys_ptr, n, ncells, start_ptr, perm_ptr, stream=None):
+    """sp_sort_cells_static on caller-owned device buffers (raw pointers):
+    stable counting sort of cell keys with no device allocation."""
+    st = stream if stream is not None else current_stream()
+    _chk("sp_sort_cells_static", lib().sp_sort_cells_static(C.c_void_p(keys_ptr), n, ncells,
+                                                             C.c_void_p(start_ptr), C.c_void_p(perm_ptr), st))
 
 
 class Sim:

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsp.so")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["sp_api.cu", "sp_common.cu", "sp_kern_f64.cu", "sp_kern_f32.cu"]
+SOURCES = ["sp_api.cu", "sp_common.cu", "sp_kern_f64.cu", "sp_kern_f32.cu", "sp_noalloc.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
