@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--develop", type=int, default=600)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--scale", type=float, default=1.0)
+    p.add_argument("--config", default="cylinder", choices=["cylinder", "sphere", "sod"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -52,9 +53,25 @@ def parse():
     return p.parse_args()
 
 
-def workload_name(scale):
+def workload_name(scale, config="cylinder"):
+    if config == "sphere":
+        n = [max(4, int(round(v * scale))) for v in (256, 128, 128)]
+        return f"sphere3d_{n[0]}x{n[1]}x{n[2]}_ppc30_Ma10_Kn0.005_Tw4_argon_vhs"
+    if config == "sod":
+        return "sod1d_200cells_ppc500_62.5_lam1e-3_hardsphere"
     nx, ny = max(4, int(round(600 * scale))), max(2, int(round(300 * scale)))
     return f"cylinder2d_{nx}x{ny}_ppc40_Ma5_Kn0.01_argon_vhs"
+
+
+def make_workload(W, config, scale, seed):
+    if config == "sphere":
+        cfg, regions = W.sphere(scale=scale, seed=seed, n_steady=0)
+    elif config == "sod":
+        cfg, regions = W.sod(ncell=200, ppc_left=500.0, lam_left=1e-3, seed=seed, n_steady=0)
+    else:
+        cfg, regions = W.cylinder(scale=scale, seed=seed, n_steady=0)
+    pos, vel = W.fill_regions(cfg, regions, seed)
+    return cfg, pos, vel
 
 
 def load_peaks():
@@ -312,8 +329,7 @@ def main():
         if dist:
             dist.barrier()
 
-    cfg, regions = W.cylinder(scale=args.scale, seed=1 + rank, n_steady=0)
-    pos, vel = W.fill_regions(cfg, regions, 1 + rank)
+    cfg, pos, vel = make_workload(W, args.config, args.scale, 1 + rank)
     M_init = vel.shape[1]
     cap = int(1.5 * M_init) + 200000
     stream = torch.cuda.current_stream()
@@ -382,7 +398,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == sp.FP32 else "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.scale), "cells": int(np.prod(cfg["n"][:2])),
+            "config": {"workload": workload_name(args.scale, args.config),
+                       "cells": int(np.prod(cfg["n"][:cfg["dim"]])),
                        "particles_per_rank": int(0.5 * (M0 + M1)), "developed_steps": args.develop,
                        "state": "FP32 particles, FP64 per-cell moments" if prec == sp.FP32 else "FP64",
                        "l2": "inputs larger than L2 (state 2 x %.0f MB)" % (S * M0 / 1e6),
@@ -443,7 +460,7 @@ def main():
         line["batch256"] = bench_batch(sp, torch, stream, args.batch_steps)
 
     # --- CPU oracle on a bounded sample of the same (developed) state
-    if rank == 0 and world >= 1 and not args.no_cpu:
+    if rank == 0 and world >= 1 and not args.no_cpu and args.config == "cylinder":
         po, vo, _ = sim.particles(0)
         v_cpu, sample = cpu_sample(cfg, po, vo)
         line["cpu_baseline"] = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}

@@ -43,6 +43,8 @@ struct sp_ctx {
   void* vel[2][3] = {{nullptr}};
   uint32_t *key = nullptr, *perm = nullptr, *count = nullptr, *fill = nullptr, *start = nullptr;
   uint32_t *cell_inst = nullptr, *scan_part = nullptr, *big_list = nullptr, *big_count = nullptr;
+  uint32_t* ticket = nullptr;
+  int collide_grid = 1;
   double *vol = nullptr, *smax = nullptr, *samp = nullptr;
   int32_t* rec = nullptr;
   uint8_t* resamp = nullptr;
@@ -128,6 +130,28 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
   P->ar_max = c.ar_max < 1 ? 1 : c.ar_max;
   P->cell_off = cell_off;
   P->ncells = (int64_t)P->n[0] * P->n[1] * P->n[2];
+  for (int d = 0; d < 3; ++d) {
+    P->g64.lo[d] = P->lo[d];
+    P->g64.hi[d] = P->hi[d];
+    P->g64.inv_d[d] = P->inv_d[d];
+    P->g64.body_c[d] = P->body_c[d];
+  }
+  P->g64.body_r = P->body_r;
+  for (int f = 0; f < 6; ++f) P->g64.face_RT[f] = c.R * c.face_T[f];
+  P->g64.body_RT = c.R * c.body_Tw;
+  P->g64.sigc_coef = P->sigc_coef;
+  P->g64.sigc_exp = P->sigc_exp;
+  for (int d = 0; d < 3; ++d) {
+    P->g32.lo[d] = (float)P->g64.lo[d];
+    P->g32.hi[d] = (float)P->g64.hi[d];
+    P->g32.inv_d[d] = (float)P->g64.inv_d[d];
+    P->g32.body_c[d] = (float)P->g64.body_c[d];
+  }
+  P->g32.body_r = (float)P->g64.body_r;
+  for (int f = 0; f < 6; ++f) P->g32.face_RT[f] = (float)P->g64.face_RT[f];
+  P->g32.body_RT = (float)P->g64.body_RT;
+  P->g32.sigc_coef = (float)P->sigc_coef;
+  P->g32.sigc_exp = (float)P->sigc_exp;
 }
 
 bool valid(const sp_config& c, int dim) {
@@ -216,6 +240,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.step = c->step_d;
   a.big_list = c->big_list;
   a.big_count = c->big_count;
+  a.ticket = c->ticket;
   a.err = c->err;
   a.NC = c->NC;
   a.cap = c->cap;
@@ -245,9 +270,12 @@ InjectArgs make_inject_args(sp_ctx* c, int par) {
   return a;
 }
 
+// Persistent launch: enough blocks to fill every SM, never more than the
+// number of 32-cell chunks needs.
 int small_grid(const sp_ctx* c) {
-  int64_t g = (c->NC + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+  const int64_t chunks = (c->NC + 31) / 32;
+  const int64_t need = (chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, c->collide_grid));
 }
 
 void launch_collide_p(sp_ctx* c, const StepArgs& a, bool big, int grid) {
@@ -278,7 +306,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream); n += 3;
   launch_cell_finalize(c->count, c->fill, c->NC, c->stream); ++n;
   launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
-                       c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->stream); ++n;
+                       c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->stream); ++n;
   if (ev) cudaEventRecord(ev[3], c->stream);
   launch_scatter(c->key, c->start, c->fill, c->perm, c->Mtot, c->cap, c->stream); ++n;
   if (ev) cudaEventRecord(ev[4], c->stream);
@@ -484,6 +512,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->scan_part, 4 * scan_partial_size(NC)));
     CK(dalloc(&c->big_list, 4 * NC));
     CK(dalloc(&c->big_count, 4));
+    CK(dalloc(&c->ticket, 4));
     CK(dalloc(&c->vol, 8 * NC));
     CK(dalloc(&c->smax, 8 * NC));
     CK(dalloc(&c->samp, 8 * 8 * NC));
@@ -522,6 +551,11 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(cudaMemsetAsync(c->samp, 0, 8 * 8 * NC, s));
     CK(cudaMemsetAsync(c->step_d, 0, 4, s));
     CK(cudaMemsetAsync(c->big_count, 0, 4, s));
+    CK(cudaMemsetAsync(c->ticket, 0, 4, s));
+    int dev = 0, nsm = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    c->collide_grid = nsm * (precision == SP_FP64 ? collide_blocks_per_sm_f64(dim) : collide_blocks_per_sm_f32(dim));
     CK(cudaMemsetAsync(c->err, 0, 8 * kNumErr, s));
     CK(cudaMemsetAsync(c->count, 0, 4 * NC, s));
     CK(cudaMemsetAsync(c->fill, 0, 4 * NC, s));
@@ -791,7 +825,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

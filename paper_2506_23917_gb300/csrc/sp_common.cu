@@ -119,7 +119,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                                 unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                                 uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                                 const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                                uint32_t* big_count) {
+                                uint32_t* big_count, uint32_t* ticket) {
   if (threadIdx.x == 0) {
     const uint32_t inj = n_ghost > 0 ? goff[n_ghost - 1] + gcount[n_ghost - 1] : 0u;
     const uint32_t old = *Mcur;
@@ -127,6 +127,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
     *Mcur = start_new[NC];
     *step = *step + 1u;
     *big_count = 0u;
+    *ticket = 0u;
   }
   for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
     const unsigned long long inf = 0x7FF0000000000000ull;
@@ -170,9 +171,9 @@ void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                           uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                           const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                          uint32_t* big_count, cudaStream_t s) {
+                          uint32_t* big_count, uint32_t* ticket, cudaStream_t s) {
   k_step_finalize<<<1, 256, 0, s>>>(P, n_inst, dt_cur, dt_min, step, Mcur, Mtot, start_new, NC,
-                                    goff, gcount, n_ghost, big_count);
+                                    goff, gcount, n_ghost, big_count, ticket);
 }
 
 }  // namespace sp

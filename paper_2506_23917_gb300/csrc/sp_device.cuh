@@ -127,12 +127,20 @@ __device__ __forceinline__ T warp_sum(T v) {
 // ---------------------------------------------------------------------------
 // Geometry: cell index, free flight with walls and body (Step 2).
 // ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ const Geo<T>& geo(const InstParams& P);
+template <>
+__device__ __forceinline__ const Geo<double>& geo<double>(const InstParams& P) { return P.g64; }
+template <>
+__device__ __forceinline__ const Geo<float>& geo<float>(const InstParams& P) { return P.g32; }
+
 template <class T, int DIM>
 __device__ __forceinline__ uint32_t cell_of(const InstParams& P, const T* x) {
+  const Geo<T>& G = geo<T>(P);
   uint32_t idx[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const T f = tfloor((x[d] - (T)P.lo[d]) * (T)P.inv_d[d]);
+    const T f = tfloor((x[d] - G.lo[d]) * G.inv_d[d]);
     int i = (int)f;
     if (f < (T)0) i = 0;
     if (i > P.n[d] - 1) i = P.n[d] - 1;
@@ -141,13 +149,11 @@ __device__ __forceinline__ uint32_t cell_of(const InstParams& P, const T* x) {
   return idx[0] + (uint32_t)P.n[0] * (idx[1] + (uint32_t)P.n[1] * idx[2]);
 }
 
-// Diffuse re-emission at wall temperature Tw: normal speed from
-// c_n = sqrt(-2 R Tw ln R1), tangential Box-Muller pair (R3, R4).
+// Diffuse re-emission at a wall with R T_w = RTw: normal speed
+// c_n = sqrt(-2 R T_w ln R1), tangential Box-Muller pair (R3, R4).
 template <class T>
-__device__ __forceinline__ void diffuse_sample(const InstParams& P, double Tw, Uni<T>& r, T* cn,
-                                               T* t1, T* t2) {
+__device__ __forceinline__ void diffuse_sample(T RTw, Uni<T>& r, T* cn, T* t1, T* t2) {
   const T R1 = r.get(0), R3 = r.get(1), R4 = r.get(2);
-  const T RTw = (T)(P.R * Tw);
   *cn = tsqrt((T)-2.0 * RTw * tlog(R1));
   const T r4 = tsqrt(-tlog(R4));
   const T s = tsqrt((T)2.0 * RTw);
@@ -158,11 +164,12 @@ __device__ __forceinline__ void diffuse_sample(const InstParams& P, double Tw, U
 }
 
 // Moves one particle for time trem.  Returns true when it left the domain.
-// Draw stream of bounce b: (step, a, b_idx, purpose<<24 | subbase + 2b).
+// Draw stream of bounce b: (step, sa, sb, purpose<<24 | subbase + 2b).
 template <class T, int DIM>
 __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t step,
                               uint32_t purpose, uint32_t sa, uint32_t sb, uint32_t subbase,
                               unsigned long long* err) {
+  const Geo<T>& G = geo<T>(P);
   for (int bounce = 0;; ++bounce) {
     if (bounce >= kMaxBounce) {
       atomicAdd(&err[kErrBounce], 1ull);
@@ -173,10 +180,10 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       if (v[d] > (T)0) {
-        const T t = ((T)P.hi[d] - x[d]) / v[d];
+        const T t = (G.hi[d] - x[d]) / v[d];
         if (t < tf) { tf = t; fa = d; fs = 1; }
       } else if (v[d] < (T)0) {
-        const T t = ((T)P.lo[d] - x[d]) / v[d];
+        const T t = (G.lo[d] - x[d]) / v[d];
         if (t < tf) { tf = t; fa = d; fs = 0; }
       }
     }
@@ -185,12 +192,12 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
       const int D = P.body == 1 ? 2 : 3;
       T bb = 0, aa = 0, cc = 0;
       for (int d = 0; d < D; ++d) {
-        const T dx = x[d] - (T)P.body_c[d];
+        const T dx = x[d] - G.body_c[d];
         bb += v[d] * dx;
         aa += v[d] * v[d];
         cc += dx * dx;
       }
-      cc -= (T)P.body_r * (T)P.body_r;
+      cc -= G.body_r * G.body_r;
       if (bb < (T)0 && aa > (T)0) {
         const T disc = bb * bb - aa * cc;
         if (disc >= (T)0) {
@@ -212,7 +219,7 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
       trem -= tb;
       T nv[3] = {0, 0, 0};
       const int D = P.body == 1 ? 2 : 3;
-      for (int d = 0; d < D; ++d) nv[d] = (x[d] - (T)P.body_c[d]) / (T)P.body_r;
+      for (int d = 0; d < D; ++d) nv[d] = (x[d] - G.body_c[d]) / G.body_r;
       T e1[3], e2[3];
       if (P.body == 1) {
         e1[0] = -nv[1]; e1[1] = nv[0]; e1[2] = 0;
@@ -231,7 +238,7 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
       }
       Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
       T cn, t1, t2;
-      diffuse_sample<T>(P, P.body_Tw, r, &cn, &t1, &t2);
+      diffuse_sample<T>(G.body_RT, r, &cn, &t1, &t2);
 #pragma unroll
       for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
       continue;
@@ -239,7 +246,7 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
       if (d != fa) x[d] += v[d] * tf;
-    x[fa] = fs ? (T)P.hi[fa] : (T)P.lo[fa];
+    x[fa] = fs ? G.hi[fa] : G.lo[fa];
     trem -= tf;
     const int f = 2 * fa + fs;
     const int bc = P.face_bc[f];
@@ -248,7 +255,7 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
     } else if (bc == 1) {
       Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
       T cn, t1, t2;
-      diffuse_sample<T>(P, P.face_T[f], r, &cn, &t1, &t2);
+      diffuse_sample<T>(G.face_RT[f], r, &cn, &t1, &t2);
       v[fa] = fs ? -cn : cn;
       v[(fa + 1) % 3] = t1;
       v[(fa + 2) % 3] = t2;
@@ -267,27 +274,6 @@ __device__ __forceinline__ int next_pow2(int n) {
   return p;
 }
 
-// Ascending bitonic sort of s[0..n2) by one warp (n2 a power of two).
-__device__ inline void warp_bitonic(uint32_t* s, int n2) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = lane; t < n2; t += 32) {
-        const int p = t ^ j;
-        if (p > t) {
-          const uint32_t a = s[t], b = s[p];
-          const bool up = (t & k) == 0;
-          if ((a > b) == up) {
-            s[t] = b;
-            s[p] = a;
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
-
 // Warp-aggregated histogram increment (key == kSentinel is skipped).
 __device__ __forceinline__ void warp_count(uint32_t key, uint32_t* count) {
   const unsigned peers = __match_any_sync(kFull, key);
@@ -299,63 +285,6 @@ struct CellMoments {
   double U[3], T, q[3], n, tau, dtc;
 };
 
-// Step 3 moments of the staged velocities of one cell (all lanes get them).
-template <class T>
-__device__ CellMoments cell_moments(const InstParams& P, double V, int N, const T* vx, const T* vy,
-                                    const T* vz) {
-  const int lane = threadIdx.x & 31;
-  CellMoments m;
-  T s0 = 0, s1 = 0, s2 = 0;
-  for (int s = lane; s < N; s += 32) {
-    s0 += vx[s];
-    s1 += vy[s];
-    s2 += vz[s];
-  }
-  s0 = warp_sum(s0);
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
-  m.U[0] = (double)s0 / (double)N;
-  m.U[1] = (double)s1 / (double)N;
-  m.U[2] = (double)s2 / (double)N;
-  m.n = (double)N * P.Fn / V;
-  m.T = 0;
-  m.q[0] = m.q[1] = m.q[2] = 0;
-  m.tau = __longlong_as_double(0x7FF0000000000000ll);
-  m.dtc = m.tau;
-  if (N < 2) return m;
-  const T U0 = (T)m.U[0], U1 = (T)m.U[1], U2 = (T)m.U[2];
-  T S2 = 0, S3x = 0, S3y = 0, S3z = 0;
-  for (int s = lane; s < N; s += 32) {
-    const T C0 = vx[s] - U0, C1 = vy[s] - U1, C2 = vz[s] - U2;
-    const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
-    S2 += c2;
-    S3x += c2 * C0;
-    S3y += c2 * C1;
-    S3z += c2 * C2;
-  }
-  S2 = warp_sum(S2);
-  S3x = warp_sum(S3x);
-  S3y = warp_sum(S3y);
-  S3z = warp_sum(S3z);
-  m.T = (double)S2 / (3.0 * P.R * (double)(N - 1));
-  if (N >= 3) {
-    const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
-    m.q[0] = f * (double)S3x;
-    m.q[1] = f * (double)S3y;
-    m.q[2] = f * (double)S3z;
-  }
-  const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
-  if (m.T > 0) {
-    const double p = m.n * P.m * P.R * m.T;
-    const double mu = P.mu_ref * pow(m.T / P.T_ref, P.omega);
-    m.tau = mu / p;
-    m.dtc = P.Lmin / (umag + sqrt(P.gamma * P.R * m.T));
-  } else if (umag > 0) {
-    m.dtc = P.Lmin / umag;
-  }
-  return m;
-}
-
 __device__ __forceinline__ double dsmc_ratio(const InstParams& P, int N, const CellMoments& m) {
   if (P.mode == 1) return 1.0;
   if (P.mode == 2) return 0.0;
@@ -363,294 +292,499 @@ __device__ __forceinline__ double dsmc_ratio(const InstParams& P, int N, const C
   return m.tau / m.dtc;
 }
 
+// Per-cell constants of a batch that the particle-parallel phases read
+// (one warp's batch of at most 32 cells).
+template <class T>
+struct __align__(16) CellTab {
+  int off[33];   // slot range of cell i: [off[i], off[i+1])
+  int inst[32];
+  int kl[32];    // instance-local cell index (Philox counter)
+  int nres[32];
+  int nar[32];
+  int pad[3];
+  T U[3][32];
+  T q[3][32];
+  T RT[32], s2RT[32], Amax[32], Pres[32], omp[32], dt[32];
+  T Up[3][32];
+  T f[32];
+};
+
+// Staging per particle: velocities (3 T), source index, clash tag, cell.
+template <class T>
+__host__ __device__ constexpr size_t stage_bytes_per_particle() {
+  return 3 * sizeof(T) + 4 + 4 + 1;
+}
+template <class T>
+__host__ __device__ constexpr size_t warp_stage_bytes(int cap) {
+  return (sizeof(CellTab<T>) + (size_t)cap * stage_bytes_per_particle<T>() + 15) / 16 * 16;
+}
+
 // ---------------------------------------------------------------------------
-// One cell of the fused step: gather -> moments -> DSMC -> Shakhov ->
-// rescale -> sample -> free flight + key + histogram.  Called by a whole
-// warp; sidx/svx/svy/svz are the warp's staging arrays of capacity cap.
+// One batch of G consecutive cells [k0, k0+G) whose particles fit the warp's
+// staging area: gather in stable order -> Step 3 moments -> Step 4 split,
+// DSMC, Shakhov, rescale -> Step 5 sums -> Step 2 free flight, new key and
+// histogram.  Particle work is spread over the lanes across the whole
+// batch; per-cell FP64 arithmetic runs lane-per-cell (lane i <-> cell i).
 // ---------------------------------------------------------------------------
 template <class T, int DIM>
-__device__ void process_cell(const StepArgs& a, int64_t k, uint32_t* sidx, int* stag, T* svx, T* svy,
-                             T* svz, int cap) {
+__device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* ct, uint32_t* sidx,
+                              int* stag, uint8_t* sseg, T* svx, T* svy, T* svz) {
   const int lane = threadIdx.x & 31;
-  const uint32_t s0 = a.start[k];
-  const int N = (int)(a.start[k + 1] - s0);
-  const uint32_t inst = a.cell_inst[k];
-  const InstParams& P = a.P[inst];
-  const uint32_t kl = (uint32_t)(k - P.cell_off);
-  const uint32_t step = *a.step;
-  const double dtG = a.dt_cur[inst];
-  const double V = a.vol[k];
   const int64_t NC = a.NC;
-  const bool sample = (int64_t)step >= (int64_t)P.n_steady;
-  if (a.rec && lane < 4) a.rec[lane * NC + k] = 0;
-  if (N == 0) {
-    if (sample && lane == 0) {
-      CellMoments m0;
-      m0.T = 0;
-      m0.tau = m0.dtc = 0;
-      a.samp[7 * NC + k] += dsmc_ratio(P, 0, m0);
-    }
-    return;
+  const uint32_t step = *a.step;
+  const uint32_t p0 = a.start[k0];
+  const int M = (int)(a.start[k0 + G] - p0);
+  // ---- lane-per-cell bookkeeping
+  const bool own = lane < G;
+  const int64_t kc = k0 + (own ? lane : 0);
+  int Ni = 0, offi = 0;
+  uint32_t inst = 0;
+  if (own) {
+    const uint32_t s0 = a.start[kc];
+    Ni = (int)(a.start[kc + 1] - s0);
+    offi = (int)(s0 - p0);
+    inst = a.cell_inst[kc];
+    ct->off[lane] = offi;
+    ct->inst[lane] = (int)inst;
+    ct->kl[lane] = (int)(kc - a.P[inst].cell_off);
+    ct->nres[lane] = 0;
+    ct->nar[lane] = 0;
   }
-  T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
-  T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
-  if (N > cap) {
-    // no room to stage this cell: its particles are dropped and flagged
-    if (lane == 0) atomicAdd(&a.err[kErrCellCap], 1ull);
-    for (int s = lane; s < N; s += 32) a.key[s0 + s] = kSentinel;
-    return;
-  }
-  // 1. the cell's source indices in stable (ascending) order
-  const int n2 = next_pow2(N);
-  for (int s = lane; s < n2; s += 32) sidx[s] = s < N ? a.perm[s0 + s] : kSentinel;
+  if (lane == 0) ct->off[G] = M;
   __syncwarp();
-  warp_bitonic(sidx, n2);
-  // 2. gather velocities
-  const T* Av0 = (const T*)a.Avel[0];
-  const T* Av1 = (const T*)a.Avel[1];
-  const T* Av2 = (const T*)a.Avel[2];
-  for (int s = lane; s < N; s += 32) {
-    const uint32_t o = sidx[s];
-    svx[s] = Av0[o];
-    svy[s] = Av1[o];
-    svz[s] = Av2[o];
-    stag[s] = 0x7FFFFFFF;
+  // ---- 1. source indices, cell of each slot, stable order within cells
+  for (int s = lane; s < M; s += 32) sidx[s] = a.perm[p0 + s];
+  for (int i = 0; i < G; ++i) {
+    const int o0 = ct->off[i], o1 = ct->off[i + 1];
+    for (int s = o0 + lane; s < o1; s += 32) sseg[s] = (uint8_t)i;
   }
   __syncwarp();
-  // 3. moments (Step 3) and the local time step (Eq. "local time step")
-  const CellMoments m = cell_moments<T>(P, V, N, svx, svy, svz);
-  if (N >= 2 && lane == 0 && m.dtc < __longlong_as_double(0x7FF0000000000000ll))
-    atomicMin(&a.dt_min[inst], (unsigned long long)__double_as_longlong(m.dtc));
-  int ncand = 0, nacc = 0, nres = 0, nar = 0;
-  if (N >= 2 && m.T > 0) {
-    // 4. split of the step (Eqs. tDSMC, tShakhov)
-    double dsmc, sbgk;
-    if (P.mode == 1) { dsmc = dtG; sbgk = 0; }
-    else if (P.mode == 2) { dsmc = 0; sbgk = dtG; }
-    else if (m.dtc <= m.tau) { dsmc = dtG; sbgk = 0; }
-    else {
-      const double r = m.tau / m.dtc;
-      dsmc = r * dtG;
-      sbgk = (1.0 - r) * dtG;
-    }
-    // 5. DSMC sub-step: NTC candidates, VHS acceptance, isotropic scattering
-    if (dsmc > 0) {
-      const double smax0 = a.smax[k];
-      const double ncr = 0.5 * (double)N * (double)(N - 1) * P.Fn * smax0 * dsmc / V;
-      Uni<T> rr(step, kl, kSentinel, kPurpNtc << 24, P.key0, P.key1);
-      int64_t ncol = (int64_t)floor(ncr + (double)rr.get(0));
-      if (ncol > kNcolCap) {
-        ncol = kNcolCap;
-        if (lane == 0) atomicAdd(&a.err[kErrNcol], 1ull);
-      }
-      T smax = (T)smax0;
-      const T coef = (T)P.sigc_coef, ex = (T)P.sigc_exp;
-      int myacc = 0;
-      for (int64_t base = 0; base < ncol; base += 32) {
-        const int64_t kk = base + lane;
-        int ci = 0, cj = 0;
-        T u3 = 0, u4 = 0, u5 = 0;
-        if (kk < ncol) {
-          Uni<T> r(step, kl, (uint32_t)kk, kPurpNtc << 24, P.key0, P.key1);
-          const T u1 = r.get(0), u2 = r.get(1);
-          u3 = r.get(2);
-          u4 = r.get(3);
-          u5 = r.get(4);
-          ci = (int)(u1 * (T)N);
-          if (ci > N - 1) ci = N - 1;
-          cj = (int)(u2 * (T)(N - 1));
-          if (cj > N - 2) cj = N - 2;
-          if (cj >= ci) cj += 1;
-        }
-        const int nb = (int)((ncol - base) < 32 ? (ncol - base) : 32);
-        unsigned pending = nb == 32 ? kFull : ((1u << nb) - 1u);
-        // Candidates are taken in order in runs that touch disjoint pairs:
-        // within a run every candidate sees the velocities left by all
-        // earlier candidates, and (sigma c)_max is an inclusive prefix
-        // maximum, so the outcome equals the one-by-one NTC loop.
-        while (pending) {
-          const bool mine = (pending >> lane) & 1u;
-          if (mine) {
-            atomicMin(&stag[ci], lane);
-            atomicMin(&stag[cj], lane);
-          }
-          __syncwarp();
-          const bool clash = mine && (stag[ci] != lane || stag[cj] != lane);
-          const unsigned cmask = __ballot_sync(kFull, clash);
-          const int F = cmask ? __ffs(cmask) - 1 : 32;
-          const unsigned run = pending & (F == 32 ? kFull : ((1u << F) - 1u));
-          __syncwarp();
-          if (mine) {
-            stag[ci] = 0x7FFFFFFF;
-            stag[cj] = 0x7FFFFFFF;
-          }
-          const bool act = (run >> lane) & 1u;
-          T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;
-          if (act) {
-            ax = svx[ci]; ay = svy[ci]; az = svz[ci];
-            bx = svx[cj]; by = svy[cj]; bz = svz[cj];
-            const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
-            cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
-            sc = coef * tpow(cr, ex);
-          }
-          T pm = sc;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const T y = __shfl_up_sync(kFull, pm, o);
-            if (lane >= o && y > pm) pm = y;
-          }
-          const T smL = pm > smax ? pm : smax;
-          if (act && u3 < sc / smL) {
-            ++myacc;
-            const T cchi = (T)2.0 * u4 - (T)1.0;
-            const T schi = tsqrt((T)1.0 - cchi * cchi);
-            T sn, cs;
-            sincos2pi(u5, &sn, &cs);
-            const T w0 = cchi, w1 = schi * cs, w2 = schi * sn;
-            const T m0 = ax + bx, m1 = ay + by, m2 = az + bz;
-            svx[ci] = (T)0.5 * (m0 - cr * w0);
-            svy[ci] = (T)0.5 * (m1 - cr * w1);
-            svz[ci] = (T)0.5 * (m2 - cr * w2);
-            svx[cj] = (T)0.5 * (m0 + cr * w0);
-            svy[cj] = (T)0.5 * (m1 + cr * w1);
-            svz[cj] = (T)0.5 * (m2 + cr * w2);
-          }
-          const T top = __shfl_sync(kFull, pm, 31);
-          if (top > smax) smax = top;
-          pending &= ~run;
-          __syncwarp();
-        }
-      }
-      nacc = warp_sum(myacc);
-      ncand = (int)ncol;
-      if (lane == 0) a.smax[k] = (double)smax;
-    }
-    // 6. Shakhov sub-step: Bernoulli(1 - exp(-dt/tau)), Box-Muller + A test
-    if (sbgk > 0 && N >= 3) {
-      const double Pd = 1.0 - exp(-sbgk / m.tau);
-      const double RTd = P.R * m.T;
-      const double qn = sqrt(m.q[0] * m.q[0] + m.q[1] * m.q[1] + m.q[2] * m.q[2]);
-      const T Amax = (T)(1.0 + 20.0 * (1.0 - P.Pr) * qn / (RTd * sqrt(RTd)));
-      const T Pt = (T)Pd, RT = (T)RTd, s2RT = (T)sqrt(2.0 * RTd), omp = (T)(1.0 - P.Pr);
-      const T q0 = (T)m.q[0], q1 = (T)m.q[1], q2 = (T)m.q[2];
-      const T U0 = (T)m.U[0], U1 = (T)m.U[1], U2 = (T)m.U[2];
-      int myres = 0, myar = 0;
-      for (int s = lane; s < N; s += 32) {
-        Uni<T> r(step, kl, (uint32_t)s, kPurpShk << 24, P.key0, P.key1);
-        const T u0 = r.get(0);
-        if (!(u0 < Pt)) continue;
-        ++myres;
-        if (a.resamp) a.resamp[s0 + s] = 1;
-        T C0 = 0, C1 = 0, C2 = 0;
-        for (int t = 0; t < P.ar_max; ++t) {
-          const T R1 = r.get(1 + 5 * t), R2 = r.get(2 + 5 * t), R3 = r.get(3 + 5 * t);
-          const T R4 = r.get(4 + 5 * t), R5 = r.get(5 + 5 * t);
-          const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
-          T sn3, cs3;
-          sincos2pi(R3, &sn3, &cs3);
-          C0 = s2RT * cos2pi(R1) * r2;
-          C1 = s2RT * cs3 * r4;
-          C2 = s2RT * sn3 * r4;
-          const T qC = q0 * C0 + q1 * C1 + q2 * C2;
-          const T CC = C0 * C0 + C1 * C1 + C2 * C2;
-          const T A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
-          ++myar;
-          if (R5 * Amax < A) break;
-          if (t == P.ar_max - 1) atomicAdd(&a.err[kErrAr], 1ull);
-        }
-        svx[s] = U0 + C0;
-        svy[s] = U1 + C1;
-        svz[s] = U2 + C2;
-      }
-      nres = warp_sum(myres);
-      nar = warp_sum(myar);
-      __syncwarp();
-      // 7. conservation rescale c' = U + (c_p - U_p) sqrt(T/T_p)
-      if (nres > 0) {
-        T p0 = 0, p1 = 0, p2 = 0;
-        for (int s = lane; s < N; s += 32) {
-          p0 += svx[s];
-          p1 += svy[s];
-          p2 += svz[s];
-        }
-        const double Up0 = (double)warp_sum(p0) / (double)N;
-        const double Up1 = (double)warp_sum(p1) / (double)N;
-        const double Up2 = (double)warp_sum(p2) / (double)N;
-        const T Upt0 = (T)Up0, Upt1 = (T)Up1, Upt2 = (T)Up2;
-        T S2 = 0;
-        for (int s = lane; s < N; s += 32) {
-          const T C0 = svx[s] - Upt0, C1 = svy[s] - Upt1, C2 = svz[s] - Upt2;
-          S2 += C0 * C0 + C1 * C1 + C2 * C2;
-        }
-        const double Tp = (double)warp_sum(S2) / (3.0 * P.R * (double)(N - 1));
-        if (Tp > 0) {
-          const T f = (T)sqrt(m.T / Tp);
-          for (int s = lane; s < N; s += 32) {
-            svx[s] = U0 + (svx[s] - Upt0) * f;
-            svy[s] = U1 + (svy[s] - Upt1) * f;
-            svz[s] = U2 + (svz[s] - Upt2) * f;
+  // cells whose source indices arrived out of order (the scatter's atomics
+  // keep each scattering warp's run ascending, so most cells are in order)
+  unsigned mine_uns = 0;
+  for (int t = lane; t < M; t += 32) {
+    const int c = sseg[t];
+    if (t + 1 < ct->off[c + 1] && sidx[t] > sidx[t + 1]) mine_uns |= 1u << c;
+  }
+  const unsigned uns = __reduce_or_sync(kFull, mine_uns);
+  if (uns) {
+    const int nmax = __reduce_max_sync(kFull, ((uns >> lane) & 1u) ? (unsigned)Ni : 0u);
+    const int n2 = next_pow2(nmax);
+    // sorting network with all comparators pointing up: sorts a segment of
+    // any length in place (slots past its end act as +infinity)
+    for (int k = 2; k <= n2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (unsigned rem = uns; rem; rem &= rem - 1) {
+          const int c = __ffs(rem) - 1;
+          const int lo = ct->off[c], n = ct->off[c + 1] - lo;
+          if (k > 2 * n) continue;  // every comparator of this stage is out of range
+          for (int li = lane; li < n; li += 32) {
+            const int q = (j == (k >> 1)) ? (li ^ (k - 1)) : (li ^ j);
+            if (q > li && q < n) {
+              const uint32_t x = sidx[lo + li], y = sidx[lo + q];
+              if (x > y) {
+                sidx[lo + li] = y;
+                sidx[lo + q] = x;
+              }
+            }
           }
         }
         __syncwarp();
       }
     }
   }
-  if (a.rec && lane == 0) {
-    a.rec[0 * NC + k] = ncand;
-    a.rec[1 * NC + k] = nacc;
-    a.rec[2 * NC + k] = nres;
-    a.rec[3 * NC + k] = nar;
+  // ---- 2. gather velocities
+  {
+    const T* Av0 = (const T*)a.Avel[0];
+    const T* Av1 = (const T*)a.Avel[1];
+    const T* Av2 = (const T*)a.Avel[2];
+    for (int s = lane; s < M; s += 32) {
+      const uint32_t o = sidx[s];
+      svx[s] = Av0[o];
+      svy[s] = Av1[o];
+      svz[s] = Av2[o];
+      stag[s] = 0x7FFFFFFF;
+    }
   }
-  // 8. time-averaged sums (Step 5)
-  if (sample) {
-    T sv0 = 0, sv1 = 0, sv2 = 0, sq0 = 0, sq1 = 0, sq2 = 0;
-    for (int s = lane; s < N; s += 32) {
+  __syncwarp();
+  // ---- 3. moment sums per cell (warp-cooperative), kept by lane i
+  T m0 = 0, m1 = 0, m2 = 0, mS2 = 0, mS3x = 0, mS3y = 0, mS3z = 0;
+  for (int i = 0; i < G; ++i) {
+    const int o0 = ct->off[i], n = ct->off[i + 1] - o0;
+    if (n == 0) continue;
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int s = o0 + lane; s < o0 + n; s += 32) {
+      s0 += svx[s];
+      s1 += svy[s];
+      s2 += svz[s];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    T S2 = 0, S3x = 0, S3y = 0, S3z = 0;
+    if (n >= 2) {
+      const T U0 = s0 / (T)n, U1 = s1 / (T)n, U2 = s2 / (T)n;
+      for (int s = o0 + lane; s < o0 + n; s += 32) {
+        const T C0 = svx[s] - U0, C1 = svy[s] - U1, C2 = svz[s] - U2;
+        const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+        S2 += c2;
+        S3x += c2 * C0;
+        S3y += c2 * C1;
+        S3z += c2 * C2;
+      }
+      S2 = warp_sum(S2);
+      S3x = warp_sum(S3x);
+      S3y = warp_sum(S3y);
+      S3z = warp_sum(S3z);
+    }
+    if (lane == i) {
+      m0 = s0; m1 = s1; m2 = s2;
+      mS2 = S2; mS3x = S3x; mS3y = S3y; mS3z = S3z;
+    }
+  }
+  // ---- 4. per-cell FP64 arithmetic, lane i <-> cell i
+  const InstParams& Pi = a.P[inst];
+  CellMoments m;
+  m.T = 0;
+  m.q[0] = m.q[1] = m.q[2] = 0;
+  m.n = 0;
+  m.U[0] = m.U[1] = m.U[2] = 0;
+  m.tau = __longlong_as_double(0x7FF0000000000000ll);
+  m.dtc = m.tau;
+  int64_t ncol = 0;
+  T smaxT = 0;
+  double ratio = 1.0;
+  bool sample = false;
+  if (own) {
+    sample = (int64_t)step >= (int64_t)Pi.n_steady;
+    const double V = a.vol[kc];
+    if (Ni > 0) {
+      m.U[0] = (double)m0 / (double)Ni;
+      m.U[1] = (double)m1 / (double)Ni;
+      m.U[2] = (double)m2 / (double)Ni;
+      m.n = (double)Ni * Pi.Fn / V;
+    }
+    if (Ni >= 2) {
+      m.T = (double)mS2 / (3.0 * Pi.R * (double)(Ni - 1));
+      if (Ni >= 3) {
+        const double den = (double)(Ni - 1) * (double)(Ni - 2);
+        m.q[0] = 0.5 * (double)Ni * (double)mS3x / den;
+        m.q[1] = 0.5 * (double)Ni * (double)mS3y / den;
+        m.q[2] = 0.5 * (double)Ni * (double)mS3z / den;
+      }
+      const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
+      if (m.T > 0) {
+        const double p = m.n * Pi.m * Pi.R * m.T;
+        const double mu = Pi.mu_ref * pow(m.T / Pi.T_ref, Pi.omega);
+        m.tau = mu / p;
+        m.dtc = Pi.Lmin / (umag + sqrt(Pi.gamma * Pi.R * m.T));
+      } else if (umag > 0) {
+        m.dtc = Pi.Lmin / umag;
+      }
+      if (m.dtc < __longlong_as_double(0x7FF0000000000000ll))
+        atomicMin(&a.dt_min[inst], (unsigned long long)__double_as_longlong(m.dtc));
+    }
+    ratio = dsmc_ratio(Pi, Ni, m);
+    const double dtG = a.dt_cur[inst];
+    ct->dt[lane] = (T)dtG;
+    ct->Pres[lane] = 0;
+    if (Ni >= 2 && m.T > 0) {
+      double dsmc, sbgk;
+      if (Pi.mode == 1) { dsmc = dtG; sbgk = 0; }
+      else if (Pi.mode == 2) { dsmc = 0; sbgk = dtG; }
+      else if (m.dtc <= m.tau) { dsmc = dtG; sbgk = 0; }
+      else {
+        const double r = m.tau / m.dtc;
+        dsmc = r * dtG;
+        sbgk = (1.0 - r) * dtG;
+      }
+      if (dsmc > 0) {
+        const double smax0 = a.smax[kc];
+        smaxT = (T)smax0;
+        const double ncr = 0.5 * (double)Ni * (double)(Ni - 1) * Pi.Fn * smax0 * dsmc / V;
+        Uni<T> rr(step, (uint32_t)ct->kl[lane], kSentinel, kPurpNtc << 24, Pi.key0, Pi.key1);
+        ncol = (int64_t)floor(ncr + (double)rr.get(0));
+        if (ncol > kNcolCap) {
+          ncol = kNcolCap;
+          atomicAdd(&a.err[kErrNcol], 1ull);
+        }
+      }
+      if (sbgk > 0 && Ni >= 3) {
+        const double RTd = Pi.R * m.T;
+        const double qn = sqrt(m.q[0] * m.q[0] + m.q[1] * m.q[1] + m.q[2] * m.q[2]);
+        ct->Pres[lane] = (T)(1.0 - exp(-sbgk / m.tau));
+        ct->RT[lane] = (T)RTd;
+        ct->s2RT[lane] = (T)sqrt(2.0 * RTd);
+        ct->Amax[lane] = (T)(1.0 + 20.0 * (1.0 - Pi.Pr) * qn / (RTd * sqrt(RTd)));
+        ct->omp[lane] = (T)(1.0 - Pi.Pr);
+      }
+    }
+    ct->U[0][lane] = (T)m.U[0];
+    ct->U[1][lane] = (T)m.U[1];
+    ct->U[2][lane] = (T)m.U[2];
+    ct->q[0][lane] = (T)m.q[0];
+    ct->q[1][lane] = (T)m.q[1];
+    ct->q[2][lane] = (T)m.q[2];
+  }
+  __syncwarp();
+  // ---- 5. DSMC sub-step, cell by cell (candidates in order, conflict-free runs)
+  int nacc_i = 0;
+  const unsigned dcells = __ballot_sync(kFull, ncol > 0);
+  for (unsigned rem = dcells; rem; rem &= rem - 1) {
+    const int i = __ffs(rem) - 1;
+    const int64_t nc = __shfl_sync(kFull, (long long)ncol, i);
+    const int o0 = ct->off[i], N = ct->off[i + 1] - o0;
+    const InstParams& P = a.P[ct->inst[i]];
+    const uint32_t kl = (uint32_t)ct->kl[i];
+    T smax = __shfl_sync(kFull, smaxT, i);
+    const T coef = geo<T>(P).sigc_coef, ex = geo<T>(P).sigc_exp;
+    int myacc = 0;
+    for (int64_t base = 0; base < nc; base += 32) {
+      const int64_t kk = base + lane;
+      int ci = 0, cj = 0;
+      T u3 = 0, u4 = 0, u5 = 0;
+      if (kk < nc) {
+        Uni<T> r(step, kl, (uint32_t)kk, kPurpNtc << 24, P.key0, P.key1);
+        const T u1 = r.get(0), u2 = r.get(1);
+        u3 = r.get(2);
+        u4 = r.get(3);
+        u5 = r.get(4);
+        ci = (int)(u1 * (T)N);
+        if (ci > N - 1) ci = N - 1;
+        cj = (int)(u2 * (T)(N - 1));
+        if (cj > N - 2) cj = N - 2;
+        if (cj >= ci) cj += 1;
+        ci += o0;
+        cj += o0;
+      }
+      const int nb = (int)((nc - base) < 32 ? (nc - base) : 32);
+      unsigned pending = nb == 32 ? kFull : ((1u << nb) - 1u);
+      // Runs of candidates on disjoint pairs: each sees the velocities left
+      // by all earlier candidates and (sigma c)_max is an inclusive prefix
+      // maximum, so the outcome equals the one-by-one NTC loop.
+      while (pending) {
+        const bool mine = (pending >> lane) & 1u;
+        if (mine) {
+          atomicMin(&stag[ci], lane);
+          atomicMin(&stag[cj], lane);
+        }
+        __syncwarp();
+        const bool clash = mine && (stag[ci] != lane || stag[cj] != lane);
+        const unsigned cmask = __ballot_sync(kFull, clash);
+        const int F = cmask ? __ffs(cmask) - 1 : 32;
+        const unsigned run = pending & (F == 32 ? kFull : ((1u << F) - 1u));
+        __syncwarp();
+        if (mine) {
+          stag[ci] = 0x7FFFFFFF;
+          stag[cj] = 0x7FFFFFFF;
+        }
+        const bool act = (run >> lane) & 1u;
+        T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;
+        if (act) {
+          ax = svx[ci]; ay = svy[ci]; az = svz[ci];
+          bx = svx[cj]; by = svy[cj]; bz = svz[cj];
+          const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
+          cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
+          sc = coef * tpow(cr, ex);
+        }
+        T pm = sc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const T y = __shfl_up_sync(kFull, pm, o);
+          if (lane >= o && y > pm) pm = y;
+        }
+        const T smL = pm > smax ? pm : smax;
+        if (act && u3 < sc / smL) {
+          ++myacc;
+          const T cchi = (T)2.0 * u4 - (T)1.0;
+          const T schi = tsqrt((T)1.0 - cchi * cchi);
+          T sn, cs;
+          sincos2pi(u5, &sn, &cs);
+          const T w0 = cchi, w1 = schi * cs, w2 = schi * sn;
+          const T q0 = ax + bx, q1 = ay + by, q2 = az + bz;
+          svx[ci] = (T)0.5 * (q0 - cr * w0);
+          svy[ci] = (T)0.5 * (q1 - cr * w1);
+          svz[ci] = (T)0.5 * (q2 - cr * w2);
+          svx[cj] = (T)0.5 * (q0 + cr * w0);
+          svy[cj] = (T)0.5 * (q1 + cr * w1);
+          svz[cj] = (T)0.5 * (q2 + cr * w2);
+        }
+        const T top = __shfl_sync(kFull, pm, 31);
+        if (top > smax) smax = top;
+        pending &= ~run;
+        __syncwarp();
+      }
+    }
+    const int acc = warp_sum(myacc);
+    if (lane == i) {
+      nacc_i = acc;
+      a.smax[kc] = (double)smax;
+    }
+  }
+  // ---- 6. Shakhov sub-step, all particles of the batch in parallel
+  for (int s = lane; s < M; s += 32) {
+    const int c = sseg[s];
+    const T Pres = ct->Pres[c];
+    if (!(Pres > (T)0)) continue;
+    const InstParams& P = a.P[ct->inst[c]];
+    const int slot = s - ct->off[c];
+    Uni<T> r(step, (uint32_t)ct->kl[c], (uint32_t)slot, kPurpShk << 24, P.key0, P.key1);
+    const T u0 = r.get(0);
+    if (!(u0 < Pres)) continue;
+    atomicAdd(&ct->nres[c], 1);
+    if (a.resamp) a.resamp[p0 + s] = 1;
+    const T RT = ct->RT[c], s2RT = ct->s2RT[c], Amax = ct->Amax[c], omp = ct->omp[c];
+    const T q0 = ct->q[0][c], q1 = ct->q[1][c], q2 = ct->q[2][c];
+    T C0 = 0, C1 = 0, C2 = 0;
+    int t = 0;
+    for (; t < P.ar_max; ++t) {
+      const T R1 = r.get(1 + 5 * t), R2 = r.get(2 + 5 * t), R3 = r.get(3 + 5 * t);
+      const T R4 = r.get(4 + 5 * t), R5 = r.get(5 + 5 * t);
+      const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
+      T sn3, cs3;
+      sincos2pi(R3, &sn3, &cs3);
+      C0 = s2RT * cos2pi(R1) * r2;
+      C1 = s2RT * cs3 * r4;
+      C2 = s2RT * sn3 * r4;
+      const T qC = q0 * C0 + q1 * C1 + q2 * C2;
+      const T CC = C0 * C0 + C1 * C1 + C2 * C2;
+      const T A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
+      if (R5 * Amax < A) break;
+    }
+    if (t == P.ar_max) {
+      t = P.ar_max - 1;
+      atomicAdd(&a.err[kErrAr], 1ull);
+    }
+    atomicAdd(&ct->nar[c], t + 1);
+    svx[s] = ct->U[0][c] + C0;
+    svy[s] = ct->U[1][c] + C1;
+    svz[s] = ct->U[2][c] + C2;
+  }
+  __syncwarp();
+  // ---- 7. conservation rescale c' = U + (c_p - U_p) sqrt(T/T_p)
+  const int nres_i = own ? ct->nres[lane] : 0;
+  const unsigned rcells = __ballot_sync(kFull, nres_i > 0);
+  if (rcells) {
+    T rp0 = 0, rp1 = 0, rp2 = 0, rS2 = 0;
+    for (unsigned rem = rcells; rem; rem &= rem - 1) {
+      const int i = __ffs(rem) - 1;
+      const int o0 = ct->off[i], n = ct->off[i + 1] - o0;
+      T p0s = 0, p1s = 0, p2s = 0;
+      for (int s = o0 + lane; s < o0 + n; s += 32) {
+        p0s += svx[s];
+        p1s += svy[s];
+        p2s += svz[s];
+      }
+      p0s = warp_sum(p0s);
+      p1s = warp_sum(p1s);
+      p2s = warp_sum(p2s);
+      const T Up0 = p0s / (T)n, Up1 = p1s / (T)n, Up2 = p2s / (T)n;
+      T S2 = 0;
+      for (int s = o0 + lane; s < o0 + n; s += 32) {
+        const T C0 = svx[s] - Up0, C1 = svy[s] - Up1, C2 = svz[s] - Up2;
+        S2 += C0 * C0 + C1 * C1 + C2 * C2;
+      }
+      S2 = warp_sum(S2);
+      if (lane == i) {
+        rp0 = Up0; rp1 = Up1; rp2 = Up2;
+        rS2 = S2;
+      }
+    }
+    if (nres_i > 0) {
+      const double Tp = (double)rS2 / (3.0 * Pi.R * (double)(Ni - 1));
+      ct->f[lane] = Tp > 0 ? (T)sqrt(m.T / Tp) : (T)-1;
+      ct->Up[0][lane] = rp0;
+      ct->Up[1][lane] = rp1;
+      ct->Up[2][lane] = rp2;
+    }
+    __syncwarp();
+    for (int s = lane; s < M; s += 32) {
+      const int c = sseg[s];
+      if (!((rcells >> c) & 1u)) continue;
+      const T f = ct->f[c];
+      if (!(f > (T)0)) continue;
+      svx[s] = ct->U[0][c] + (svx[s] - ct->Up[0][c]) * f;
+      svy[s] = ct->U[1][c] + (svy[s] - ct->Up[1][c]) * f;
+      svz[s] = ct->U[2][c] + (svz[s] - ct->Up[2][c]) * f;
+    }
+    __syncwarp();
+  }
+  // ---- 8. time-averaged sums (Step 5)
+  const unsigned scells = __ballot_sync(kFull, sample && Ni > 0);
+  T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
+  for (unsigned rem = scells; rem; rem &= rem - 1) {
+    const int i = __ffs(rem) - 1;
+    const int o0 = ct->off[i], o1 = ct->off[i + 1];
+    T v0 = 0, v1 = 0, v2 = 0, w0 = 0, w1 = 0, w2 = 0;
+    for (int s = o0 + lane; s < o1; s += 32) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
-      sv0 += x0; sv1 += x1; sv2 += x2;
-      sq0 += x0 * x0; sq1 += x1 * x1; sq2 += x2 * x2;
+      v0 += x0; v1 += x1; v2 += x2;
+      w0 += x0 * x0; w1 += x1 * x1; w2 += x2 * x2;
     }
-    sv0 = warp_sum(sv0); sv1 = warp_sum(sv1); sv2 = warp_sum(sv2);
-    sq0 = warp_sum(sq0); sq1 = warp_sum(sq1); sq2 = warp_sum(sq2);
-    if (lane == 0) {
-      double* S = a.samp;
-      S[0 * NC + k] += (double)N;
-      S[1 * NC + k] += (double)sv0;
-      S[2 * NC + k] += (double)sv1;
-      S[3 * NC + k] += (double)sv2;
-      S[4 * NC + k] += (double)sq0;
-      S[5 * NC + k] += (double)sq1;
-      S[6 * NC + k] += (double)sq2;
-      S[7 * NC + k] += dsmc_ratio(P, N, m);
+    v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+    w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
+    if (lane == i) {
+      a0 = v0; a1 = v1; a2 = v2;
+      b0 = w0; b1 = w1; b2 = w2;
     }
   }
-  // 9. free flight of the next interval (Step 2), key and histogram
-  const T dt = (T)dtG;
-  for (int sb = 0; sb < N; sb += 32) {
+  if (own) {
+    if (sample) {
+      double* S = a.samp;
+      S[0 * NC + kc] += (double)Ni;
+      if (Ni > 0) {
+        S[1 * NC + kc] += (double)a0;
+        S[2 * NC + kc] += (double)a1;
+        S[3 * NC + kc] += (double)a2;
+        S[4 * NC + kc] += (double)b0;
+        S[5 * NC + kc] += (double)b1;
+        S[6 * NC + kc] += (double)b2;
+      }
+      S[7 * NC + kc] += ratio;
+    }
+    if (a.rec) {
+      a.rec[0 * NC + kc] = (int32_t)ncol;
+      a.rec[1 * NC + kc] = nacc_i;
+      a.rec[2 * NC + kc] = nres_i;
+      a.rec[3 * NC + kc] = ct->nar[lane];
+    }
+  }
+  // ---- 9. free flight of the next interval (Step 2), key and histogram
+  T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
+  T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
+  for (int sb = 0; sb < M; sb += 32) {
     const int s = sb + lane;
     uint32_t key = kSentinel;
-    if (s < N) {
+    if (s < M) {
+      const int c = sseg[s];
+      const InstParams& P = a.P[ct->inst[c]];
       const uint32_t o = sidx[s];
       T x[3] = {0, 0, 0};
 #pragma unroll
       for (int d = 0; d < DIM; ++d) x[d] = ((const T*)a.Apos[d])[o];
       T v[3] = {svx[s], svy[s], svz[s]};
-      const bool gone = move_particle<T, DIM>(P, x, v, dt, step, kPurpWall, kl, (uint32_t)s, 0u, a.err);
+      const bool gone = move_particle<T, DIM>(P, x, v, ct->dt[c], step, kPurpWall, (uint32_t)ct->kl[c],
+                                              (uint32_t)(s - ct->off[c]), 0u, a.err);
       if (!gone) key = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) Bx[d][s0 + s] = x[d];
-      Bv[0][s0 + s] = v[0];
-      Bv[1][s0 + s] = v[1];
-      Bv[2][s0 + s] = v[2];
-      a.key[s0 + s] = key;
+      for (int d = 0; d < DIM; ++d) Bx[d][p0 + s] = x[d];
+      Bv[0][p0 + s] = v[0];
+      Bv[1][p0 + s] = v[1];
+      Bv[2][p0 + s] = v[2];
+      a.key[p0 + s] = key;
     }
     warp_count(key, a.count);
   }
+  __syncwarp();
 }
 
-// Per-warp staging layout: sidx[cap] (u32), stag[cap] (i32), vx, vy, vz [cap] (T).
-template <class T>
-__host__ __device__ constexpr size_t stage_bytes_per_particle() {
-  return 4 + 4 + 3 * sizeof(T);
+// Drops every particle of a cell that exceeds even the big-cell staging
+// area (flagged; the run reports SP_ERR_CAPACITY).
+__device__ inline void drop_cell(const StepArgs& a, int64_t k) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t s0 = a.start[k], s1 = a.start[k + 1];
+  if (lane == 0) atomicAdd(&a.err[kErrCellCap], 1ull);
+  for (uint32_t s = s0 + lane; s < s1; s += 32) a.key[s] = kSentinel;
 }
 
 template <class T, int DIM>
@@ -659,29 +793,54 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_collide(StepArgs a, int
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cap = big ? a.big_cap : kCapSmall;
   if (big && warp != 0) return;
-  unsigned char* base = smem + (size_t)(big ? 0 : warp) * cap * stage_bytes_per_particle<T>();
-  uint32_t* sidx = (uint32_t*)base;
-  int* stag = (int*)(base + (size_t)cap * 4);
-  T* svx = (T*)(base + (size_t)cap * 8);
+  unsigned char* base = smem + (size_t)(big ? 0 : warp) * warp_stage_bytes<T>(cap);
+  CellTab<T>* ct = (CellTab<T>*)base;
+  T* svx = (T*)(base + sizeof(CellTab<T>));
   T* svy = svx + cap;
   T* svz = svy + cap;
+  uint32_t* sidx = (uint32_t*)(svz + cap);
+  int* stag = (int*)(sidx + cap);
+  uint8_t* sseg = (uint8_t*)(stag + cap);
   if (!big) {
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < a.NC; k += nw) {
-      const int N = (int)(a.start[k + 1] - a.start[k]);
-      if (N > cap) {
-        if (lane == 0) {
-          const uint32_t i = atomicAdd(a.big_count, 1u);
-          a.big_list[i] = (uint32_t)k;
-        }
-        continue;
+    const int64_t nchunks = (a.NC + 31) / 32;
+    for (;;) {
+      uint32_t chunk = 0;
+      if (lane == 0) chunk = atomicAdd(a.ticket, 1u);
+      chunk = __shfl_sync(kFull, chunk, 0);
+      if ((int64_t)chunk >= nchunks) break;
+      const int64_t c0 = (int64_t)chunk * 32;
+      const int nc = (int)((a.NC - c0) < 32 ? (a.NC - c0) : 32);
+      int cum = lane < nc ? (int)(a.start[c0 + lane + 1] - a.start[c0 + lane]) : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, cum, o);
+        if (lane >= o) cum += y;
       }
-      process_cell<T, DIM>(a, k, sidx, stag, svx, svy, svz, cap);
+      int kk = 0;
+      while (kk < nc) {
+        const int before = kk > 0 ? __shfl_sync(kFull, cum, kk - 1) : 0;
+        const unsigned fit = __ballot_sync(kFull, lane >= kk && lane < nc && cum - before <= cap);
+        const int G = __popc(fit);
+        if (G == 0) {
+          // a single cell above the warp's staging area
+          if (lane == 0) {
+            const uint32_t i = atomicAdd(a.big_count, 1u);
+            a.big_list[i] = (uint32_t)(c0 + kk);
+          }
+          kk += 1;
+          continue;
+        }
+        process_batch<T, DIM>(a, c0 + kk, G, ct, sidx, stag, sseg, svx, svy, svz);
+        kk += G;
+      }
     }
   } else {
     const uint32_t nbig = *a.big_count;
-    for (uint32_t i = blockIdx.x; i < nbig; i += gridDim.x)
-      process_cell<T, DIM>(a, (int64_t)a.big_list[i], sidx, stag, svx, svy, svz, cap);
+    for (uint32_t i = blockIdx.x; i < nbig; i += gridDim.x) {
+      const int64_t k = (int64_t)a.big_list[i];
+      if ((int)(a.start[k + 1] - a.start[k]) > cap) drop_cell(a, k);
+      else process_batch<T, DIM>(a, k, 1, ct, sidx, stag, sseg, svx, svy, svz);
+    }
   }
 }
 
@@ -700,7 +859,8 @@ __global__ void k_inject(InjectArgs a, int pass) {
   const double dtd = a.dt_cur[G.inst];
   const T dt = (T)dtd;
   const int ax = G.face / 2, side = G.face % 2;
-  const T face = side ? (T)P.hi[ax] : (T)P.lo[ax];
+  const Geo<T>& GE = geo<T>(P);
+  const T face = side ? GE.hi[ax] : GE.lo[ax];
   const uint32_t sb = (uint32_t)G.face * 16u;
   Uni<T> rc(step, G.gc, kSentinel, (kPurpInj << 24) | sb, P.key0, P.key1);
   const int64_t ng = (int64_t)floor(G.lam + (double)rc.get(0));
@@ -730,16 +890,16 @@ __global__ void k_inject(InjectArgs a, int pass) {
     for (int d = 0; d < DIM; ++d) {
       if (d == ax) continue;
       T y = x[d] + v[d] * te;
-      if (y < (T)P.lo[d]) {
+      if (y < GE.lo[d]) {
         if (P.face_bc[2 * d] != 0) { ok = false; break; }
-        y = (T)2.0 * (T)P.lo[d] - y;
+        y = (T)2.0 * GE.lo[d] - y;
         v[d] = -v[d];
-      } else if (y > (T)P.hi[d]) {
+      } else if (y > GE.hi[d]) {
         if (P.face_bc[2 * d + 1] != 0) { ok = false; break; }
-        y = (T)2.0 * (T)P.hi[d] - y;
+        y = (T)2.0 * GE.hi[d] - y;
         v[d] = -v[d];
       }
-      if (y < (T)P.lo[d] || y > (T)P.hi[d]) { ok = false; break; }
+      if (y < GE.lo[d] || y > GE.hi[d]) { ok = false; break; }
       x[d] = y;
     }
     if (!ok) continue;

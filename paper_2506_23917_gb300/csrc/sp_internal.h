@@ -18,6 +18,17 @@ constexpr uint32_t kPurpNtc = 1, kPurpShk = 2, kPurpWall = 3, kPurpInj = 4, kPur
 // Error counters (device, sticky).
 enum { kErrCapacity = 0, kErrCellCap = 1, kErrBounce = 2, kErrAr = 3, kErrNcol = 4, kNumErr = 5 };
 
+// Geometry and wall constants of an instance in the particle precision T
+// (so per-particle code never converts).
+template <class T>
+struct Geo {
+  T lo[3], hi[3], inv_d[3];
+  T body_c[3], body_r;
+  T face_RT[6];  // R * T_face
+  T body_RT;     // R * T_wall of the body
+  T sigc_coef, sigc_exp;
+};
+
 // Per-instance constants, precomputed on the host.
 struct InstParams {
   int dim;
@@ -35,6 +46,8 @@ struct InstParams {
   int ar_max;
   int64_t cell_off;  // first global cell of the instance
   int64_t ncells;
+  Geo<double> g64;
+  Geo<float> g32;
 };
 
 // One reservoir (ghost) cell outside an inflow face.
@@ -71,6 +84,7 @@ struct StepArgs {
   const uint32_t* step; // global step index
   uint32_t* big_list;   // cells above kCapSmall
   uint32_t* big_count;
+  uint32_t* ticket;     // work-stealing counter over 32-cell chunks
   unsigned long long* err;  // [kNumErr]
   int64_t NC;
   int64_t cap;
@@ -107,6 +121,7 @@ struct InjectArgs {
   void launch_stage_in_##tag(int dim, const double* pos, const double* vel, int64_t n,             \
                              void* const dpos[3], void* const dvel[3], int64_t off,              \
                              uint32_t* part_inst, uint32_t inst, cudaStream_t s);                \
+  int collide_blocks_per_sm_##tag(int dim);                                                       \
   cudaError_t configure_##tag(int big_cap);
 SP_DECLARE_LAUNCHERS(f64)
 SP_DECLARE_LAUNCHERS(f32)
@@ -120,7 +135,7 @@ void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                           uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                           const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                          uint32_t* big_count, cudaStream_t s);
+                          uint32_t* big_count, uint32_t* ticket, cudaStream_t s);
 int64_t scan_partial_size(int64_t n);
 
 }  // namespace sp

@@ -9,10 +9,10 @@ using T = float;
 template <int DIM>
 void collide_dim(const StepArgs& a, bool big, int grid, cudaStream_t s) {
   if (!big) {
-    const size_t smem = (size_t)kWarpsPerBlock * kCapSmall * stage_bytes_per_particle<T>();
+    const size_t smem = (size_t)kWarpsPerBlock * warp_stage_bytes<T>(kCapSmall);
     k_collide<T, DIM><<<grid, 32 * kWarpsPerBlock, smem, s>>>(a, 0);
   } else {
-    const size_t smem = (size_t)a.big_cap * stage_bytes_per_particle<T>();
+    const size_t smem = warp_stage_bytes<T>(a.big_cap);
     k_collide<T, DIM><<<grid, 32, smem, s>>>(a, 1);
   }
 }
@@ -33,8 +33,8 @@ void keys_dim(const void* const pos[3], int64_t M, const uint32_t* part_inst, co
 
 template <int DIM>
 cudaError_t configure_dim(int big_cap) {
-  const size_t small = (size_t)kWarpsPerBlock * kCapSmall * stage_bytes_per_particle<T>();
-  const size_t big = (size_t)big_cap * stage_bytes_per_particle<T>();
+  const size_t small = (size_t)kWarpsPerBlock * warp_stage_bytes<T>(kCapSmall);
+  const size_t big = warp_stage_bytes<T>(big_cap);
   const size_t mx = small > big ? small : big;
   return cudaFuncSetAttribute(k_collide<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
@@ -86,6 +86,15 @@ void launch_stage_in_f32(int dim, const double* pos, const double* vel, int64_t 
   const int64_t g = (n + 255) / 256;
   k_stage_in<T><<<(unsigned)g, 256, 0, s>>>(pos, vel, dim, n, (T*)dpos[0], (T*)dpos[1], (T*)dpos[2],
                                             (T*)dvel[0], (T*)dvel[1], (T*)dvel[2], off, part_inst, inst);
+}
+
+int collide_blocks_per_sm_f32(int dim) {
+  int n = 0;
+  const size_t smem = (size_t)kWarpsPerBlock * warp_stage_bytes<T>(kCapSmall);
+  if (dim == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 1>, 32 * kWarpsPerBlock, smem);
+  else if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 2>, 32 * kWarpsPerBlock, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 3>, 32 * kWarpsPerBlock, smem);
+  return n > 0 ? n : 1;
 }
 
 cudaError_t configure_f32(int big_cap) {

@@ -89,14 +89,40 @@ def test_fp32_channel_time_averages_match_fp64(sp):
     _compare(sp, cfg, pos, vel, warm=300, nbatch=20, per=100)
 
 
-def test_fp32_sod_early_profile_matches_fp64(sp):
-    """Unsteady flow: the ensemble over seeds is replaced by one long
-    realisation of a periodic-free quantity -- here the Sod tube with
-    specular ends relaxes to rest; the time average over the late window is
-    compared."""
-    cfg, regions = W.sod(ncell=100, ppc_left=400.0, lam_left=1e-3)
-    pos, vel = W.fill_regions(cfg, regions, 4)
-    _compare(sp, cfg, pos, vel, warm=1500, nbatch=20, per=50)
+def test_fp32_sod_ensemble_profile_matches_fp64(sp):
+    """Unsteady flow: 64 Sod tubes with different seeds run as one batched
+    context to t = 0.15 (fixed step), in FP64 and in FP32; the ensemble mean
+    density, velocity and temperature profiles must agree (relative L2 1e-2,
+    3 standard errors of the ensemble means for >= 95 % of the cells)."""
+    R = 64
+    cfgs, parts = [], []
+    for r in range(R):
+        cfg, regions = W.sod(ncell=100, ppc_left=1000.0, lam_left=1e-3, seed=100 + r)
+        cfg["dt_fixed"] = 1e-3
+        pos, vel = W.fill_regions(cfg, regions, 100 + r)
+        cfgs.append(cfg)
+        parts.append((pos, vel))
+    M = sum(v.shape[1] for _, v in parts)
+    prof = {}
+    for prec in (sp.FP64, sp.FP32):
+        s = sp.Sim(cfgs, prec, capacity=M + 1000)
+        for i, (p, v) in enumerate(parts):
+            s.set_particles(i, p, v)
+        s.step(150)
+        s.sync()
+        assert s.errors()["capacity"] == 0 and s.errors()["cell_cap"] == 0
+        prof[prec] = np.array([s.moments(i, 0)[[1, 2, 5]] for i in range(R)])  # (R, 3, cells)
+        s.close()
+    for fi, name in enumerate(("n", "ux", "T")):
+        a = prof[sp.FP64][:, fi]
+        b = prof[sp.FP32][:, fi]
+        ma, mb = a.mean(axis=0), b.mean(axis=0)
+        se = np.sqrt(a.var(axis=0, ddof=1) / R + b.var(axis=0, ddof=1) / R)
+        scale = np.linalg.norm(ma) if name != "ux" else np.linalg.norm(np.abs(ma) + np.sqrt(prof[sp.FP64][:, 2].mean(axis=0)))
+        l2 = np.linalg.norm(mb - ma) / scale
+        within = np.mean(np.abs(mb - ma) <= 3 * se)
+        assert l2 < 1e-2, (name, l2)
+        assert within >= 0.95, (name, within)
 
 
 def test_fp32_closed_box_conserves_energy(sp):
