@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--profile-steps", type=int, default=40)
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-tune", action="store_true")
     p.add_argument("--batch-steps", type=int, default=200)
     return p.parse_args()
 
@@ -246,6 +247,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def reduce_timing(ms, updates, dist, device):
+    """Whole-job figures: the slowest rank's time and the sum of the
+    particle updates of all ranks (each rank advances its own instance)."""
+    if dist is None:
+        return ms, updates
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def rank_seed(rank):
+    """Each rank's instance gets its own Philox key and initial particles."""
+    return 1 + rank
+
+
 def bench_batch(sp, torch, stream, steps):
     from paper_2506_23917_gb300 import workloads as W
 
@@ -329,7 +349,7 @@ def main():
         if dist:
             dist.barrier()
 
-    cfg, pos, vel = make_workload(W, args.config, args.scale, 1 + rank)
+    cfg, pos, vel = make_workload(W, args.config, args.scale, rank_seed(rank))
     M_init = vel.shape[1]
     cap = int(1.5 * M_init) + 200000
     stream = torch.cuda.current_stream()
@@ -338,6 +358,7 @@ def main():
     sim.set_particles(0, pos, vel)
     sim.step(args.develop)
     sim.sync()
+    sched = sim.autotune(steps_per_trial=3) if not args.no_tune else None
     sim.step(args.warmup)
     sim.sync()
     M0 = sim.count(0)
@@ -360,13 +381,7 @@ def main():
     ms = e0.elapsed_time(e1)
     M1 = sim.count(0)
     upd = args.steps * 0.5 * (M0 + M1)
-    t_max, upd_sum = ms, upd
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([upd], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        t_max, upd_sum = float(t.item()), float(u.item())
+    t_max, upd_sum = reduce_timing(ms, upd, dist, "cuda")
     value = upd_sum / (t_max * 1e-3)
     ms_per_step = t_max / args.steps
 
@@ -403,7 +418,8 @@ def main():
                        "particles_per_rank": int(0.5 * (M0 + M1)), "developed_steps": args.develop,
                        "state": "FP32 particles, FP64 per-cell moments" if prec == sp.FP32 else "FP64",
                        "l2": "inputs larger than L2 (state 2 x %.0f MB)" % (S * M0 / 1e6),
-                       "graph": "one CUDA graph per step", "parallelism": f"replicas{world}"},
+                       "graph": "one CUDA graph per step", "parallelism": f"replicas{world}",
+                       "schedule": {"cap": sched[0], "warps_per_block": sched[1]} if sched else "default"},
             "clocks": clk, "gpu_launches": launches * args.steps, "roofline": roofline}
 
     # --- plain FP64 form of the same workload

@@ -166,6 +166,18 @@ sp_status sp_errors(sp_ctx* ctx, int64_t* out5);
  * reservoir injection, (2) the histogram scan and bookkeeping, (3) the
  * scatter.  Synchronises after every step (for measurement only). */
 sp_status sp_step_profiled(sp_ctx* ctx, int n_steps, double* ms, int n_slots);
+/* Collision-kernel schedule: `cap` particles of shared-memory staging per
+ * warp (a warp takes consecutive cells whose particles fit; cells above it
+ * go to a one-warp-per-cell launch) and `warps` warps per block (1..8).
+ * The schedule changes no result.  SP_ERR_ARG if it does not fit. */
+sp_status sp_set_schedule(sp_ctx* ctx, int cap, int warps);
+/* Autotuner: for each candidate schedule (cap in 128..1024, warps in 2, 4,
+ * 8 that fit) advance steps_per_trial ordinary steps while timing the
+ * collision kernel with CUDA events, then keep the fastest schedule.  The
+ * trial steps are part of the run (results do not depend on the schedule);
+ * call it once the flow is developed.  *cap_out / *warps_out (may be NULL)
+ * receive the choice. */
+sp_status sp_autotune(sp_ctx* ctx, int steps_per_trial, int* cap_out, int* warps_out);
 /* Wait for the context's stream. */
 sp_status sp_sync(sp_ctx* ctx);
 /* Number of kernel launches one sp_step() issues (for launch accounting). */

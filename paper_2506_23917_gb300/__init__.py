@@ -49,7 +49,7 @@ class SpConfig(C.Structure):
 
 SYMBOLS = ["sp_init", "sp_set_particles", "sp_step", "sp_moments", "sp_get_particles",
            "sp_set_record", "sp_get_step_record", "sp_get_cell_start", "sp_get_sigc_max",
-           "sp_get_dt", "sp_errors", "sp_sync", "sp_step_profiled", "sp_launches_per_step", "sp_free",
+           "sp_get_dt", "sp_errors", "sp_sync", "sp_step_profiled", "sp_set_schedule", "sp_autotune", "sp_launches_per_step", "sp_free",
            "sp_status_str", "sp_sort_cells_static"]
 
 _lib = None
@@ -76,6 +76,8 @@ def lib():
         L.sp_errors.argtypes = [P, P]
         L.sp_sync.argtypes = [P]
         L.sp_step_profiled.argtypes = [P, C.c_int, P, C.c_int]
+        L.sp_set_schedule.argtypes = [P, C.c_int, C.c_int]
+        L.sp_autotune.argtypes = [P, C.c_int, P, P]
         L.sp_launches_per_step.argtypes = [P]
         L.sp_free.argtypes = [P]
         L.sp_sort_cells_static.argtypes = [P, C.c_int64, C.c_int64, P, P, P]
@@ -256,10 +258,27 @@ class Sim:
         _chk("sp_get_dt", lib().sp_get_dt(self.h, inst, _ptr(dt), _ptr(step)))
         return float(dt[0])
 
+    def step_index(self):
+        """Global step counter (steps advanced since sp_init)."""
+        dt = np.zeros(1)
+        step = np.zeros(1, dtype=np.int64)
+        _chk("sp_get_dt", lib().sp_get_dt(self.h, 0, _ptr(dt), _ptr(step)))
+        return int(step[0])
+
     def errors(self):
         out = np.zeros(5, dtype=np.int64)
         _chk("sp_errors", lib().sp_errors(self.h, _ptr(out)))
         return dict(zip(ERRORS, (int(x) for x in out)))
+
+    def set_schedule(self, cap, warps):
+        _chk("sp_set_schedule", lib().sp_set_schedule(self.h, cap, warps))
+
+    def autotune(self, steps_per_trial=3):
+        """Time the candidate collision schedules on real steps; keep the fastest."""
+        cap = np.zeros(1, dtype=np.int32)
+        w = np.zeros(1, dtype=np.int32)
+        _chk("sp_autotune", lib().sp_autotune(self.h, steps_per_trial, _ptr(cap), _ptr(w)))
+        return int(cap[0]), int(w[0])
 
     def launches_per_step(self):
         return int(lib().sp_launches_per_step(self.h))

@@ -44,7 +44,11 @@ struct sp_ctx {
   uint32_t *key = nullptr, *perm = nullptr, *count = nullptr, *fill = nullptr, *start = nullptr;
   uint32_t *cell_inst = nullptr, *scan_part = nullptr, *big_list = nullptr, *big_count = nullptr;
   uint32_t* ticket = nullptr;
+  uint2* batches = nullptr;
+  uint32_t* nbatch = nullptr;
   int collide_grid = 1;
+  int nsm = 1;
+  int sched_cap = kCapSmall, sched_warps = kWarpsDefault;
   double *vol = nullptr, *smax = nullptr, *samp = nullptr;
   int32_t* rec = nullptr;
   uint8_t* resamp = nullptr;
@@ -137,6 +141,11 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
     P->g64.body_c[d] = P->body_c[d];
   }
   P->g64.body_r = P->body_r;
+  for (int d = 0; d < 3; ++d) {
+    const double span = fabs(P->hi[d]) + fabs(P->lo[d]) + (P->hi[d] - P->lo[d]);
+    P->g64.eps[d] = 1e-12 * span;
+    P->g32.eps[d] = (float)(1e-5 * span);
+  }
   for (int f = 0; f < 6; ++f) P->g64.face_RT[f] = c.R * c.face_T[f];
   P->g64.body_RT = c.R * c.body_Tw;
   P->g64.sigc_coef = P->sigc_coef;
@@ -241,10 +250,13 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.big_list = c->big_list;
   a.big_count = c->big_count;
   a.ticket = c->ticket;
+  a.batches = c->batches;
+  a.nbatch = c->nbatch;
   a.err = c->err;
   a.NC = c->NC;
   a.cap = c->cap;
   a.big_cap = c->prec == SP_FP64 ? kBigCap64 : kBigCap32;
+  a.cap_small = c->sched_cap;
   return a;
 }
 
@@ -270,17 +282,34 @@ InjectArgs make_inject_args(sp_ctx* c, int par) {
   return a;
 }
 
-// Persistent launch: enough blocks to fill every SM, never more than the
-// number of 32-cell chunks needs.
+// Persistent launch: enough blocks to fill every SM, never more than one
+// warp per possible batch.
 int small_grid(const sp_ctx* c) {
-  const int64_t chunks = (c->NC + 31) / 32;
-  const int64_t need = (chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t need = (c->NC + c->sched_warps - 1) / c->sched_warps;
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, c->collide_grid));
 }
 
 void launch_collide_p(sp_ctx* c, const StepArgs& a, bool big, int grid) {
-  if (c->prec == SP_FP64) launch_collide_f64(c->dim, a, big, grid, c->stream);
-  else launch_collide_f32(c->dim, a, big, grid, c->stream);
+  const int warps = big ? 1 : c->sched_warps;
+  if (c->prec == SP_FP64) launch_collide_f64(c->dim, a, big, grid, warps, c->stream);
+  else launch_collide_f32(c->dim, a, big, grid, warps, c->stream);
+}
+
+// Collision-kernel schedule: staging capacity per warp and warps per block.
+// Returns false if it does not fit the shared memory or the block limits.
+bool apply_schedule(sp_ctx* c, int cap, int warps) {
+  if (cap < 32 || cap > (c->prec == SP_FP64 ? kBigCap64 : kBigCap32) || warps < 1 ||
+      warps > kMaxWarpsPerBlock)
+    return false;
+  const size_t smem = c->prec == SP_FP64 ? collide_smem_f64(warps, cap) : collide_smem_f32(warps, cap);
+  if (smem > (size_t)kMaxDynSmem) return false;
+  const int per_sm = c->prec == SP_FP64 ? collide_blocks_per_sm_f64(c->dim, warps, cap)
+                                        : collide_blocks_per_sm_f32(c->dim, warps, cap);
+  if (per_sm < 1) return false;
+  c->sched_cap = cap;
+  c->sched_warps = warps;
+  c->collide_grid = c->nsm * per_sm;
+  return true;
 }
 
 // Enqueue one step reading buffer `par` and writing buffer 1 - par.  With
@@ -290,6 +319,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   int n = 0;
   const StepArgs a = make_step_args(c, par);
   if (ev) cudaEventRecord(ev[0], c->stream);
+  launch_plan(c->start, c->NC, c->sched_cap, c->batches, c->nbatch, c->big_list, c->big_count, c->stream); ++n;
   launch_collide_p(c, a, false, small_grid(c)); ++n;
   launch_collide_p(c, a, true, 2 * 152); ++n;
   if (ev) cudaEventRecord(ev[1], c->stream);
@@ -306,7 +336,8 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream); n += 3;
   launch_cell_finalize(c->count, c->fill, c->NC, c->stream); ++n;
   launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
-                       c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->stream); ++n;
+                       c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->nbatch,
+                       c->stream); ++n;
   if (ev) cudaEventRecord(ev[3], c->stream);
   launch_scatter(c->key, c->start, c->fill, c->perm, c->Mtot, c->cap, c->stream); ++n;
   if (ev) cudaEventRecord(ev[4], c->stream);
@@ -513,6 +544,8 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->big_list, 4 * NC));
     CK(dalloc(&c->big_count, 4));
     CK(dalloc(&c->ticket, 4));
+    CK(dalloc(&c->batches, sizeof(uint2) * NC));
+    CK(dalloc(&c->nbatch, 4));
     CK(dalloc(&c->vol, 8 * NC));
     CK(dalloc(&c->smax, 8 * NC));
     CK(dalloc(&c->samp, 8 * 8 * NC));
@@ -552,10 +585,11 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(cudaMemsetAsync(c->step_d, 0, 4, s));
     CK(cudaMemsetAsync(c->big_count, 0, 4, s));
     CK(cudaMemsetAsync(c->ticket, 0, 4, s));
-    int dev = 0, nsm = 1;
+    CK(cudaMemsetAsync(c->nbatch, 0, 4, s));
+    int dev = 0;
     CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    c->collide_grid = nsm * (precision == SP_FP64 ? collide_blocks_per_sm_f64(dim) : collide_blocks_per_sm_f32(dim));
+    CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (!apply_schedule(c, kCapSmall, kWarpsDefault) && !apply_schedule(c, 256, 2)) return SP_ERR_CUDA;
     CK(cudaMemsetAsync(c->err, 0, 8 * kNumErr, s));
     CK(cudaMemsetAsync(c->count, 0, 4 * NC, s));
     CK(cudaMemsetAsync(c->fill, 0, 4 * NC, s));
@@ -648,6 +682,52 @@ sp_status sp_step_profiled(sp_ctx* c, int n_steps, double* ms, int n_slots) {
   for (int k = 0; k < n_slots && k < 4; ++k) ms[k] = acc[k];
   CK(cudaGetLastError());
   return SP_OK;
+}
+
+sp_status sp_set_schedule(sp_ctx* c, int cap, int warps) {
+  if (!c) return SP_ERR_ARG;
+  if (!apply_schedule(c, cap, warps)) return SP_ERR_ARG;
+  destroy_graphs(c);
+  return SP_OK;
+}
+
+sp_status sp_autotune(sp_ctx* c, int steps_per_trial, int* cap_out, int* warps_out) {
+  if (!c || steps_per_trial < 1) return SP_ERR_ARG;
+  sp_status s = ensure_ready(c);
+  if (s != SP_OK) return s;
+  static const int caps[] = {128, 256, 384, 512, 768, 1024};
+  static const int warps[] = {2, 4, 8};
+  const int cap0 = c->sched_cap, w0 = c->sched_warps;
+  int best_cap = cap0, best_w = w0;
+  float best = 3.4e38f;
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
+  for (int ci : caps)
+    for (int wi : warps) {
+      if (!apply_schedule(c, ci, wi)) continue;
+      float tot = 0;
+      for (int it = 0; it < steps_per_trial; ++it) {
+        enqueue_step(c, c->cur, ev);
+        CK(cudaEventSynchronize(ev[4]));
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+        tot += t;
+        c->cur ^= 1;
+        c->step_host += 1;
+      }
+      if (tot < best) {
+        best = tot;
+        best_cap = ci;
+        best_w = wi;
+      }
+    }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  if (!apply_schedule(c, best_cap, best_w)) apply_schedule(c, cap0, w0);
+  destroy_graphs(c);
+  if (cap_out) *cap_out = c->sched_cap;
+  if (warps_out) *warps_out = c->sched_warps;
+  CK(cudaGetLastError());
+  return check_errors(c);
 }
 
 sp_status sp_sync(sp_ctx* c) {
@@ -825,7 +905,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

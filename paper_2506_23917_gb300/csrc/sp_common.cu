@@ -119,7 +119,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                                 unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                                 uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                                 const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                                uint32_t* big_count, uint32_t* ticket) {
+                                uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch) {
   if (threadIdx.x == 0) {
     const uint32_t inj = n_ghost > 0 ? goff[n_ghost - 1] + gcount[n_ghost - 1] : 0u;
     const uint32_t old = *Mcur;
@@ -128,6 +128,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
     *step = *step + 1u;
     *big_count = 0u;
     *ticket = 0u;
+    *nbatch = 0u;
   }
   for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
     const unsigned long long inf = 0x7FF0000000000000ull;
@@ -139,7 +140,61 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
     dt_min[i] = inf;
   }
 }
+// Work plan of a step: consecutive cells are grouped into batches whose
+// particles fit a warp's staging area (at most 32 cells each); cells above
+// it go to the big-cell list.  One warp per 32-cell chunk; batches of a
+// chunk are appended to a global list (their order does not matter: batches
+// are independent).
+__global__ void k_plan(const uint32_t* start, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+                       uint32_t* big_list, uint32_t* big_count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nchunks = (NC + 31) / 32;
+  for (int64_t chunk = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
+       chunk += nw) {
+    const int64_t c0 = chunk * 32;
+    const int nc = (int)((NC - c0) < 32 ? (NC - c0) : 32);
+    int cum = lane < nc ? (int)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
+      if (lane >= o) cum += y;
+    }
+    int kk = 0, nb = 0;
+    uint2 mine = make_uint2(0, 0);
+    while (kk < nc) {
+      const int before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
+      const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap);
+      const int G = __popc(fit);
+      if (G == 0) {
+        if (lane == 0) {
+          const uint32_t i = atomicAdd(big_count, 1u);
+          big_list[i] = (uint32_t)(c0 + kk);
+        }
+        kk += 1;
+        continue;
+      }
+      if (lane == nb) mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
+      ++nb;
+      kk += G;
+    }
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(nbatch, (uint32_t)nb);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (lane < nb) batches[base + lane] = mine;
+  }
+}
+
 }  // namespace
+
+void launch_plan(const uint32_t* start, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+                 uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
+  const int64_t chunks = (NC + 31) / 32;
+  int64_t g = (chunks + 7) / 8;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  k_plan<<<(unsigned)g, 256, 0, s>>>(start, NC, cap, batches, nbatch, big_list, big_count);
+}
 
 int64_t scan_partial_size(int64_t n) { return (n + kTile - 1) / kTile + 1; }
 
@@ -171,9 +226,9 @@ void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                           uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                           const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                          uint32_t* big_count, uint32_t* ticket, cudaStream_t s) {
+                          uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch, cudaStream_t s) {
   k_step_finalize<<<1, 256, 0, s>>>(P, n_inst, dt_cur, dt_min, step, Mcur, Mtot, start_new, NC,
-                                    goff, gcount, n_ghost, big_count, ticket);
+                                    goff, gcount, n_ghost, big_count, ticket, nbatch);
 }
 
 }  // namespace sp

@@ -110,6 +110,37 @@ __device__ __forceinline__ void sincos2pi(float u, float* s, float* c) { sincosp
 __device__ __forceinline__ double cos2pi(double u) { return cos(2.0 * kPi * u); }
 __device__ __forceinline__ float cos2pi(float u) { return cospif(2.0f * u); }
 
+// The five uniforms of NTC candidate kk: pair (u1, u2), acceptance u3,
+// scattering cos(chi) from u4 and azimuth from u5.  FP64 mode: three Philox
+// blocks (shared layout with the oracle).  FP32 mode: one block; u4 and u5
+// take 16 bits each of the fourth word ((2k+1) 2^-17), ample for angles.
+template <class T>
+struct NtcDraw {
+  T u1, u2, u3, u4, u5;
+};
+__device__ __forceinline__ NtcDraw<double> ntc_draw(double, uint32_t step, uint32_t kl, uint32_t kk,
+                                                    uint32_t key0, uint32_t key1) {
+  Uni<double> r(step, kl, kk, kPurpNtc << 24, key0, key1);
+  NtcDraw<double> d;
+  d.u1 = r.get(0);
+  d.u2 = r.get(1);
+  d.u3 = r.get(2);
+  d.u4 = r.get(3);
+  d.u5 = r.get(4);
+  return d;
+}
+__device__ __forceinline__ NtcDraw<float> ntc_draw(float, uint32_t step, uint32_t kl, uint32_t kk,
+                                                   uint32_t key0, uint32_t key1) {
+  const uint4 w = philox10(step, kl, kk, kPurpNtc << 24, key0, key1);
+  NtcDraw<float> d;
+  d.u1 = u01f(w.x);
+  d.u2 = u01f(w.y);
+  d.u3 = u01f(w.z);
+  d.u4 = (float)(2u * (w.w >> 16) + 1u) * 7.62939453125e-6f;
+  d.u5 = (float)(2u * (w.w & 0xFFFFu) + 1u) * 7.62939453125e-6f;
+  return d;
+}
+
 template <class T>
 __device__ __forceinline__ T tinf();
 template <>
@@ -177,14 +208,24 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
     }
     T tf = tinf<T>();
     int fa = -1, fs = 0;
+    // straight end point inside the box by a margin far above rounding: no
+    // face can be reached, the exit times need not be formed
+    bool inside = true;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      if (v[d] > (T)0) {
-        const T t = (G.hi[d] - x[d]) / v[d];
-        if (t < tf) { tf = t; fa = d; fs = 1; }
-      } else if (v[d] < (T)0) {
-        const T t = (G.lo[d] - x[d]) / v[d];
-        if (t < tf) { tf = t; fa = d; fs = 0; }
+      const T xe = x[d] + v[d] * trem;
+      inside = inside && xe > G.lo[d] + G.eps[d] && xe < G.hi[d] - G.eps[d];
+    }
+    if (!inside) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        if (v[d] > (T)0) {
+          const T t = (G.hi[d] - x[d]) / v[d];
+          if (t < tf) { tf = t; fa = d; fs = 1; }
+        } else if (v[d] < (T)0) {
+          const T t = (G.lo[d] - x[d]) / v[d];
+          if (t < tf) { tf = t; fa = d; fs = 0; }
+        }
       }
     }
     T tb = tinf<T>();
@@ -301,12 +342,16 @@ struct __align__(16) CellTab {
   int kl[32];    // instance-local cell index (Philox counter)
   int nres[32];
   int nar[32];
-  int pad[3];
+  int nacc[32];
+  int coff[33];  // candidate offsets of the flattened NTC loop
+  int pad[2];
   T U[3][32];
   T q[3][32];
   T RT[32], s2RT[32], Amax[32], Pres[32], omp[32], dt[32];
   T Up[3][32];
   T f[32];
+  T acc[7][32];  // per-cell sums of the current reduction
+  T smax[32];    // (sigma_T c_r)_max while candidates run
 };
 
 // Staging per particle: velocities (3 T), source index, clash tag, cell.
@@ -317,6 +362,42 @@ __host__ __device__ constexpr size_t stage_bytes_per_particle() {
 template <class T>
 __host__ __device__ constexpr size_t warp_stage_bytes(int cap) {
   return (sizeof(CellTab<T>) + (size_t)cap * stage_bytes_per_particle<T>() + 15) / 16 * 16;
+}
+
+// Per-cell sums over all M slots of a batch in one pass: slots are grouped
+// by cell (sseg is nondecreasing), so a lane-ordered segmented scan of each
+// 32-slot chunk leaves the chunk's partial sum of a cell in the last lane
+// holding that cell, which adds it to acc[k][cell].  The order of additions
+// is fixed (by slot), so the sums are reproducible.  acc must be zero for
+// the batch's cells on entry.
+template <class T, int K, class F>
+__device__ __forceinline__ void seg_sums(int M, const uint8_t* sseg, T (*acc)[32], F f) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < M; base += 32) {
+    const int s = base + lane;
+    const bool valid = s < M;
+    const int c = valid ? (int)sseg[s] : 255;
+    T v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = 0;
+    if (valid) f(s, v);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int co = __shfl_up_sync(kFull, c, o);
+      const bool same = lane >= o && co == c;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const T y = __shfl_up_sync(kFull, v[k], o);
+        if (same) v[k] += y;
+      }
+    }
+    const int cn = __shfl_down_sync(kFull, c, 1);
+    if (valid && (lane == 31 || cn != c)) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k][c] += v[k];
+    }
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -353,6 +434,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   if (lane == 0) ct->off[G] = M;
   __syncwarp();
   // ---- 1. source indices, cell of each slot, stable order within cells
+#pragma unroll 4
   for (int s = lane; s < M; s += 32) sidx[s] = a.perm[p0 + s];
   for (int i = 0; i < G; ++i) {
     const int o0 = ct->off[i], o1 = ct->off[i + 1];
@@ -367,14 +449,33 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (t + 1 < ct->off[c + 1] && sidx[t] > sidx[t + 1]) mine_uns |= 1u << c;
   }
   const unsigned uns = __reduce_or_sync(kFull, mine_uns);
-  if (uns) {
-    const int nmax = __reduce_max_sync(kFull, ((uns >> lane) & 1u) ? (unsigned)Ni : 0u);
+  // small cells: each slot's rank among its cell's (distinct) source
+  // indices, written through stag as scratch; big cells: a sorting network
+  const unsigned uns_big = __ballot_sync(kFull, ((uns >> lane) & 1u) && Ni > 64);
+  const unsigned uns_small = uns & ~uns_big;
+  if (uns_small) {
+    for (int s = lane; s < M; s += 32) {
+      const int c = sseg[s];
+      if (!((uns_small >> c) & 1u)) continue;
+      const int lo = ct->off[c], hi = ct->off[c + 1];
+      const uint32_t v = sidx[s];
+      int r = 0;
+      for (int j = lo; j < hi; ++j) r += sidx[j] < v;
+      stag[lo + r] = (int)v;
+    }
+    __syncwarp();
+    for (int s = lane; s < M; s += 32)
+      if ((uns_small >> sseg[s]) & 1u) sidx[s] = (uint32_t)stag[s];
+    __syncwarp();
+  }
+  if (uns_big) {
+    const int nmax = __reduce_max_sync(kFull, ((uns_big >> lane) & 1u) ? (unsigned)Ni : 0u);
     const int n2 = next_pow2(nmax);
     // sorting network with all comparators pointing up: sorts a segment of
     // any length in place (slots past its end act as +infinity)
     for (int k = 2; k <= n2; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
-        for (unsigned rem = uns; rem; rem &= rem - 1) {
+        for (unsigned rem = uns_big; rem; rem &= rem - 1) {
           const int c = __ffs(rem) - 1;
           const int lo = ct->off[c], n = ct->off[c + 1] - lo;
           if (k > 2 * n) continue;  // every comparator of this stage is out of range
@@ -398,6 +499,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     const T* Av0 = (const T*)a.Avel[0];
     const T* Av1 = (const T*)a.Avel[1];
     const T* Av2 = (const T*)a.Avel[2];
+#pragma unroll 4
     for (int s = lane; s < M; s += 32) {
       const uint32_t o = sidx[s];
       svx[s] = Av0[o];
@@ -407,42 +509,46 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     }
   }
   __syncwarp();
-  // ---- 3. moment sums per cell (warp-cooperative), kept by lane i
+  // ---- 3. moment sums per cell (segmented, one pass each), kept by lane i
+  if (own)
+    for (int k = 0; k < 7; ++k) ct->acc[k][lane] = 0;
+  __syncwarp();
+  seg_sums<T, 3>(M, sseg, ct->acc, [&](int s, T* v) {
+    v[0] = svx[s];
+    v[1] = svy[s];
+    v[2] = svz[s];
+  });
+  if (own && Ni > 0) {  // the shift of the central sums: the cell mean
+    ct->U[0][lane] = ct->acc[0][lane] / (T)Ni;
+    ct->U[1][lane] = ct->acc[1][lane] / (T)Ni;
+    ct->U[2][lane] = ct->acc[2][lane] / (T)Ni;
+  }
+  __syncwarp();
+  seg_sums<T, 4>(M, sseg, ct->acc + 3, [&](int s, T* v) {
+    const int c = sseg[s];
+    const T C0 = svx[s] - ct->U[0][c], C1 = svy[s] - ct->U[1][c], C2 = svz[s] - ct->U[2][c];
+    const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+    v[0] = c2;
+    v[1] = c2 * C0;
+    v[2] = c2 * C1;
+    v[3] = c2 * C2;
+  });
   T m0 = 0, m1 = 0, m2 = 0, mS2 = 0, mS3x = 0, mS3y = 0, mS3z = 0;
-  for (int i = 0; i < G; ++i) {
-    const int o0 = ct->off[i], n = ct->off[i + 1] - o0;
-    if (n == 0) continue;
-    T s0 = 0, s1 = 0, s2 = 0;
-    for (int s = o0 + lane; s < o0 + n; s += 32) {
-      s0 += svx[s];
-      s1 += svy[s];
-      s2 += svz[s];
-    }
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    T S2 = 0, S3x = 0, S3y = 0, S3z = 0;
-    if (n >= 2) {
-      const T U0 = s0 / (T)n, U1 = s1 / (T)n, U2 = s2 / (T)n;
-      for (int s = o0 + lane; s < o0 + n; s += 32) {
-        const T C0 = svx[s] - U0, C1 = svy[s] - U1, C2 = svz[s] - U2;
-        const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
-        S2 += c2;
-        S3x += c2 * C0;
-        S3y += c2 * C1;
-        S3z += c2 * C2;
-      }
-      S2 = warp_sum(S2);
-      S3x = warp_sum(S3x);
-      S3y = warp_sum(S3y);
-      S3z = warp_sum(S3z);
-    }
-    if (lane == i) {
-      m0 = s0; m1 = s1; m2 = s2;
-      mS2 = S2; mS3x = S3x; mS3y = S3y; mS3z = S3z;
+  if (own) {
+    m0 = ct->acc[0][lane];
+    m1 = ct->acc[1][lane];
+    m2 = ct->acc[2][lane];
+    if (Ni >= 2) {
+      mS2 = ct->acc[3][lane];
+      mS3x = ct->acc[4][lane];
+      mS3y = ct->acc[5][lane];
+      mS3z = ct->acc[6][lane];
     }
   }
-  // ---- 4. per-cell FP64 arithmetic, lane i <-> cell i
+  // ---- 4. per-cell arithmetic, lane i <-> cell i.  FP64 mode: all in FP64
+  // (the oracle's expressions).  FP32 mode: the cell scalars in FP32, with
+  // FP64 kept for the exp(-dt/tau) split weight (below), the rescale factor
+  // and the time-average accumulators.
   const InstParams& Pi = a.P[inst];
   CellMoments m;
   m.T = 0;
@@ -453,173 +559,215 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   m.dtc = m.tau;
   int64_t ncol = 0;
   T smaxT = 0;
-  double ratio = 1.0;
+  T ratioT = 1;
+  T sbgkT = 0, tauT = 0;
+  bool shk = false;
   bool sample = false;
   if (own) {
     sample = (int64_t)step >= (int64_t)Pi.n_steady;
-    const double V = a.vol[kc];
+    const T V = (T)a.vol[kc];
+    T Ut[3] = {0, 0, 0}, Tt = 0, qt[3] = {0, 0, 0}, nt = 0;
+    T taut = tinf<T>(), dtct = tinf<T>();
     if (Ni > 0) {
-      m.U[0] = (double)m0 / (double)Ni;
-      m.U[1] = (double)m1 / (double)Ni;
-      m.U[2] = (double)m2 / (double)Ni;
-      m.n = (double)Ni * Pi.Fn / V;
+      Ut[0] = m0 / (T)Ni;
+      Ut[1] = m1 / (T)Ni;
+      Ut[2] = m2 / (T)Ni;
+      nt = (T)Ni * (T)Pi.Fn / V;
     }
     if (Ni >= 2) {
-      m.T = (double)mS2 / (3.0 * Pi.R * (double)(Ni - 1));
+      Tt = mS2 / ((T)3.0 * (T)Pi.R * (T)(Ni - 1));
       if (Ni >= 3) {
-        const double den = (double)(Ni - 1) * (double)(Ni - 2);
-        m.q[0] = 0.5 * (double)Ni * (double)mS3x / den;
-        m.q[1] = 0.5 * (double)Ni * (double)mS3y / den;
-        m.q[2] = 0.5 * (double)Ni * (double)mS3z / den;
+        const T den = (T)(Ni - 1) * (T)(Ni - 2);
+        qt[0] = (T)0.5 * (T)Ni * mS3x / den;
+        qt[1] = (T)0.5 * (T)Ni * mS3y / den;
+        qt[2] = (T)0.5 * (T)Ni * mS3z / den;
       }
-      const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
-      if (m.T > 0) {
-        const double p = m.n * Pi.m * Pi.R * m.T;
-        const double mu = Pi.mu_ref * pow(m.T / Pi.T_ref, Pi.omega);
-        m.tau = mu / p;
-        m.dtc = Pi.Lmin / (umag + sqrt(Pi.gamma * Pi.R * m.T));
-      } else if (umag > 0) {
-        m.dtc = Pi.Lmin / umag;
+      const T umag = tsqrt(Ut[0] * Ut[0] + Ut[1] * Ut[1] + Ut[2] * Ut[2]);
+      if (Tt > (T)0) {
+        const T p = nt * (T)Pi.m * (T)Pi.R * Tt;
+        const T mu = (T)Pi.mu_ref * tpow(Tt / (T)Pi.T_ref, (T)Pi.omega);
+        taut = mu / p;
+        dtct = (T)Pi.Lmin / (umag + tsqrt((T)Pi.gamma * (T)Pi.R * Tt));
+      } else if (umag > (T)0) {
+        dtct = (T)Pi.Lmin / umag;
       }
-      if (m.dtc < __longlong_as_double(0x7FF0000000000000ll))
-        atomicMin(&a.dt_min[inst], (unsigned long long)__double_as_longlong(m.dtc));
+      if (dtct < tinf<T>())
+        atomicMin(&a.dt_min[inst], (unsigned long long)__double_as_longlong((double)dtct));
     }
-    ratio = dsmc_ratio(Pi, Ni, m);
-    const double dtG = a.dt_cur[inst];
-    ct->dt[lane] = (T)dtG;
+    m.U[0] = Ut[0]; m.U[1] = Ut[1]; m.U[2] = Ut[2];
+    m.T = Tt;
+    m.q[0] = qt[0]; m.q[1] = qt[1]; m.q[2] = qt[2];
+    m.n = nt;
+    m.tau = taut;
+    m.dtc = dtct;
+    // DSMC ratio of the split (Eqs. tDSMC, tShakhov)
+    if (Pi.mode == 1) ratioT = 1;
+    else if (Pi.mode == 2) ratioT = 0;
+    else if (Ni < 2 || !(Tt > (T)0) || dtct <= taut) ratioT = 1;
+    else ratioT = taut / dtct;
+    const T dtG = (T)a.dt_cur[inst];
+    ct->dt[lane] = dtG;
     ct->Pres[lane] = 0;
-    if (Ni >= 2 && m.T > 0) {
-      double dsmc, sbgk;
+    if (Ni >= 2 && Tt > (T)0) {
+      T dsmc, sbgk;
       if (Pi.mode == 1) { dsmc = dtG; sbgk = 0; }
       else if (Pi.mode == 2) { dsmc = 0; sbgk = dtG; }
-      else if (m.dtc <= m.tau) { dsmc = dtG; sbgk = 0; }
+      else if (dtct <= taut) { dsmc = dtG; sbgk = 0; }
       else {
-        const double r = m.tau / m.dtc;
+        const T r = taut / dtct;
         dsmc = r * dtG;
-        sbgk = (1.0 - r) * dtG;
+        sbgk = ((T)1.0 - r) * dtG;
       }
-      if (dsmc > 0) {
-        const double smax0 = a.smax[kc];
-        smaxT = (T)smax0;
-        const double ncr = 0.5 * (double)Ni * (double)(Ni - 1) * Pi.Fn * smax0 * dsmc / V;
+      if (dsmc > (T)0) {
+        smaxT = (T)a.smax[kc];
+        const T ncr = (T)0.5 * (T)Ni * (T)(Ni - 1) * (T)Pi.Fn * smaxT * dsmc / V;
         Uni<T> rr(step, (uint32_t)ct->kl[lane], kSentinel, kPurpNtc << 24, Pi.key0, Pi.key1);
-        ncol = (int64_t)floor(ncr + (double)rr.get(0));
+        ncol = (int64_t)tfloor(ncr + rr.get(0));
         if (ncol > kNcolCap) {
           ncol = kNcolCap;
           atomicAdd(&a.err[kErrNcol], 1ull);
         }
       }
-      if (sbgk > 0 && Ni >= 3) {
-        const double RTd = Pi.R * m.T;
-        const double qn = sqrt(m.q[0] * m.q[0] + m.q[1] * m.q[1] + m.q[2] * m.q[2]);
-        ct->Pres[lane] = (T)(1.0 - exp(-sbgk / m.tau));
-        ct->RT[lane] = (T)RTd;
-        ct->s2RT[lane] = (T)sqrt(2.0 * RTd);
-        ct->Amax[lane] = (T)(1.0 + 20.0 * (1.0 - Pi.Pr) * qn / (RTd * sqrt(RTd)));
-        ct->omp[lane] = (T)(1.0 - Pi.Pr);
+      if (sbgk > (T)0 && Ni >= 3) {
+        shk = true;
+        sbgkT = sbgk;
+        tauT = taut;
+        const T RTt = (T)Pi.R * Tt;
+        const T qn = tsqrt(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2]);
+        ct->RT[lane] = RTt;
+        ct->s2RT[lane] = tsqrt((T)2.0 * RTt);
+        ct->Amax[lane] = (T)1.0 + (T)20.0 * ((T)1.0 - (T)Pi.Pr) * qn / (RTt * tsqrt(RTt));
+        ct->omp[lane] = (T)1.0 - (T)Pi.Pr;
       }
     }
-    ct->U[0][lane] = (T)m.U[0];
-    ct->U[1][lane] = (T)m.U[1];
-    ct->U[2][lane] = (T)m.U[2];
-    ct->q[0][lane] = (T)m.q[0];
-    ct->q[1][lane] = (T)m.q[1];
-    ct->q[2][lane] = (T)m.q[2];
+    ct->U[0][lane] = Ut[0];
+    ct->U[1][lane] = Ut[1];
+    ct->U[2][lane] = Ut[2];
+    ct->q[0][lane] = qt[0];
+    ct->q[1][lane] = qt[1];
+    ct->q[2][lane] = qt[2];
+  }
+  // resampling probability 1 - exp(-dt_SBGK/tau) in FP64, only when a cell
+  // of the batch has a Shakhov part
+  if (__any_sync(kFull, shk) && shk)
+    ct->Pres[lane] = (T)(1.0 - exp(-(double)sbgkT / (double)tauT));
+  const double ratio = (double)ratioT;
+  __syncwarp();
+  // ---- 5. DSMC sub-step: the candidates of all cells of the batch,
+  // flattened cell by cell, 32 at a time, one per lane
+  {
+    int c_incl = (int)ncol;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, c_incl, o);
+      if (lane >= o) c_incl += y;
+    }
+    if (own) {
+      ct->coff[lane + 1] = c_incl;
+      ct->smax[lane] = smaxT;
+      ct->nacc[lane] = 0;
+    }
+    if (lane == 0) ct->coff[0] = 0;
   }
   __syncwarp();
-  // ---- 5. DSMC sub-step, cell by cell (candidates in order, conflict-free runs)
-  int nacc_i = 0;
-  const unsigned dcells = __ballot_sync(kFull, ncol > 0);
-  for (unsigned rem = dcells; rem; rem &= rem - 1) {
-    const int i = __ffs(rem) - 1;
-    const int64_t nc = __shfl_sync(kFull, (long long)ncol, i);
-    const int o0 = ct->off[i], N = ct->off[i + 1] - o0;
-    const InstParams& P = a.P[ct->inst[i]];
-    const uint32_t kl = (uint32_t)ct->kl[i];
-    T smax = __shfl_sync(kFull, smaxT, i);
-    const T coef = geo<T>(P).sigc_coef, ex = geo<T>(P).sigc_exp;
-    int myacc = 0;
-    for (int64_t base = 0; base < nc; base += 32) {
-      const int64_t kk = base + lane;
-      int ci = 0, cj = 0;
-      T u3 = 0, u4 = 0, u5 = 0;
-      if (kk < nc) {
-        Uni<T> r(step, kl, (uint32_t)kk, kPurpNtc << 24, P.key0, P.key1);
-        const T u1 = r.get(0), u2 = r.get(1);
-        u3 = r.get(2);
-        u4 = r.get(3);
-        u5 = r.get(4);
-        ci = (int)(u1 * (T)N);
-        if (ci > N - 1) ci = N - 1;
-        cj = (int)(u2 * (T)(N - 1));
-        if (cj > N - 2) cj = N - 2;
-        if (cj >= ci) cj += 1;
-        ci += o0;
-        cj += o0;
+  const int ctot = ct->coff[G];
+  for (int base = 0; base < ctot; base += 32) {
+    const int g = base + lane;
+    const bool valid = g < ctot;
+    int c = 255, ci = 0, cj = 0;
+    T u3 = 0, u4 = 0, u5 = 0;
+    if (valid) {
+      int lo = 0, hi = G - 1;  // largest cell index with coff <= g
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ct->coff[mid] <= g) lo = mid; else hi = mid - 1;
       }
-      const int nb = (int)((nc - base) < 32 ? (nc - base) : 32);
-      unsigned pending = nb == 32 ? kFull : ((1u << nb) - 1u);
-      // Runs of candidates on disjoint pairs: each sees the velocities left
-      // by all earlier candidates and (sigma c)_max is an inclusive prefix
-      // maximum, so the outcome equals the one-by-one NTC loop.
-      while (pending) {
-        const bool mine = (pending >> lane) & 1u;
-        if (mine) {
-          atomicMin(&stag[ci], lane);
-          atomicMin(&stag[cj], lane);
-        }
-        __syncwarp();
-        const bool clash = mine && (stag[ci] != lane || stag[cj] != lane);
-        const unsigned cmask = __ballot_sync(kFull, clash);
-        const int F = cmask ? __ffs(cmask) - 1 : 32;
-        const unsigned run = pending & (F == 32 ? kFull : ((1u << F) - 1u));
-        __syncwarp();
-        if (mine) {
-          stag[ci] = 0x7FFFFFFF;
-          stag[cj] = 0x7FFFFFFF;
-        }
-        const bool act = (run >> lane) & 1u;
-        T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;
-        if (act) {
-          ax = svx[ci]; ay = svy[ci]; az = svz[ci];
-          bx = svx[cj]; by = svy[cj]; bz = svz[cj];
-          const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
-          cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
-          sc = coef * tpow(cr, ex);
-        }
-        T pm = sc;
+      c = lo;
+      const int N = ct->off[c + 1] - ct->off[c];
+      const InstParams& P = a.P[ct->inst[c]];
+      const NtcDraw<T> dr = ntc_draw((T)0, step, (uint32_t)ct->kl[c], (uint32_t)(g - ct->coff[c]), P.key0, P.key1);
+      u3 = dr.u3;
+      u4 = dr.u4;
+      u5 = dr.u5;
+      ci = (int)(dr.u1 * (T)N);
+      if (ci > N - 1) ci = N - 1;
+      cj = (int)(dr.u2 * (T)(N - 1));
+      if (cj > N - 2) cj = N - 2;
+      if (cj >= ci) cj += 1;
+      ci += ct->off[c];
+      cj += ct->off[c];
+    }
+    const int cnext = __shfl_down_sync(kFull, c, 1);
+    const bool seg_last = valid && (lane == 31 || cnext != c);
+    const T coef = valid ? geo<T>(a.P[ct->inst[c]]).sigc_coef : (T)0;
+    const T ex = valid ? geo<T>(a.P[ct->inst[c]]).sigc_exp : (T)0;
+    unsigned pending = __ballot_sync(kFull, valid);
+    // A candidate runs once no earlier pending candidate of its cell shares
+    // a particle with it; runs of one cell are disjoint pairs, each sees the
+    // velocities left by all earlier candidates, and (sigma c)_max is the
+    // cell's inclusive prefix maximum: the outcome of the one-by-one loop.
+    while (pending) {
+      const bool mine = (pending >> lane) & 1u;
+      if (mine) {
+        atomicMin(&stag[ci], lane);
+        atomicMin(&stag[cj], lane);
+      }
+      __syncwarp();
+      bool blocked = mine && (stag[ci] != lane || stag[cj] != lane);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const T y = __shfl_up_sync(kFull, pm, o);
-          if (lane >= o && y > pm) pm = y;
-        }
-        const T smL = pm > smax ? pm : smax;
-        if (act && u3 < sc / smL) {
-          ++myacc;
-          const T cchi = (T)2.0 * u4 - (T)1.0;
-          const T schi = tsqrt((T)1.0 - cchi * cchi);
-          T sn, cs;
-          sincos2pi(u5, &sn, &cs);
-          const T w0 = cchi, w1 = schi * cs, w2 = schi * sn;
-          const T q0 = ax + bx, q1 = ay + by, q2 = az + bz;
-          svx[ci] = (T)0.5 * (q0 - cr * w0);
-          svy[ci] = (T)0.5 * (q1 - cr * w1);
-          svz[ci] = (T)0.5 * (q2 - cr * w2);
-          svx[cj] = (T)0.5 * (q0 + cr * w0);
-          svy[cj] = (T)0.5 * (q1 + cr * w1);
-          svz[cj] = (T)0.5 * (q2 + cr * w2);
-        }
-        const T top = __shfl_sync(kFull, pm, 31);
-        if (top > smax) smax = top;
-        pending &= ~run;
-        __syncwarp();
+      for (int o = 1; o < 32; o <<= 1) {
+        const bool y = __shfl_up_sync(kFull, blocked, o);
+        const int co = __shfl_up_sync(kFull, c, o);
+        if (lane >= o && co == c && y) blocked = true;
       }
+      const bool act = mine && !blocked;
+      __syncwarp();
+      if (mine) {
+        stag[ci] = 0x7FFFFFFF;
+        stag[cj] = 0x7FFFFFFF;
+      }
+      T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;
+      if (act) {
+        ax = svx[ci]; ay = svy[ci]; az = svz[ci];
+        bx = svx[cj]; by = svy[cj]; bz = svz[cj];
+        const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
+        cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
+        sc = coef * tpow(cr, ex);
+      }
+      T pm = sc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(kFull, pm, o);
+        const int co = __shfl_up_sync(kFull, c, o);
+        if (lane >= o && co == c && y > pm) pm = y;
+      }
+      const T smc = valid ? ct->smax[c] : (T)0;
+      const T smL = pm > smc ? pm : smc;
+      if (act && u3 < sc / smL) {
+        atomicAdd(&ct->nacc[c], 1);
+        const T cchi = (T)2.0 * u4 - (T)1.0;
+        const T schi = tsqrt((T)1.0 - cchi * cchi);
+        T sn, cs;
+        sincos2pi(u5, &sn, &cs);
+        const T w0 = cchi, w1 = schi * cs, w2 = schi * sn;
+        const T q0 = ax + bx, q1 = ay + by, q2 = az + bz;
+        svx[ci] = (T)0.5 * (q0 - cr * w0);
+        svy[ci] = (T)0.5 * (q1 - cr * w1);
+        svz[ci] = (T)0.5 * (q2 - cr * w2);
+        svx[cj] = (T)0.5 * (q0 + cr * w0);
+        svy[cj] = (T)0.5 * (q1 + cr * w1);
+        svz[cj] = (T)0.5 * (q2 + cr * w2);
+      }
+      __syncwarp();
+      if (seg_last && pm > smc) ct->smax[c] = pm;
+      pending &= ~__ballot_sync(kFull, act);
+      __syncwarp();
     }
-    const int acc = warp_sum(myacc);
-    if (lane == i) {
-      nacc_i = acc;
-      a.smax[kc] = (double)smax;
-    }
+  }
+  int nacc_i = 0;
+  if (own && ncol > 0) {
+    nacc_i = ct->nacc[lane];
+    a.smax[kc] = (double)ct->smax[lane];
   }
   // ---- 6. Shakhov sub-step, all particles of the batch in parallel
   for (int s = lane; s < M; s += 32) {
@@ -665,37 +813,29 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   const int nres_i = own ? ct->nres[lane] : 0;
   const unsigned rcells = __ballot_sync(kFull, nres_i > 0);
   if (rcells) {
-    T rp0 = 0, rp1 = 0, rp2 = 0, rS2 = 0;
-    for (unsigned rem = rcells; rem; rem &= rem - 1) {
-      const int i = __ffs(rem) - 1;
-      const int o0 = ct->off[i], n = ct->off[i + 1] - o0;
-      T p0s = 0, p1s = 0, p2s = 0;
-      for (int s = o0 + lane; s < o0 + n; s += 32) {
-        p0s += svx[s];
-        p1s += svy[s];
-        p2s += svz[s];
-      }
-      p0s = warp_sum(p0s);
-      p1s = warp_sum(p1s);
-      p2s = warp_sum(p2s);
-      const T Up0 = p0s / (T)n, Up1 = p1s / (T)n, Up2 = p2s / (T)n;
-      T S2 = 0;
-      for (int s = o0 + lane; s < o0 + n; s += 32) {
-        const T C0 = svx[s] - Up0, C1 = svy[s] - Up1, C2 = svz[s] - Up2;
-        S2 += C0 * C0 + C1 * C1 + C2 * C2;
-      }
-      S2 = warp_sum(S2);
-      if (lane == i) {
-        rp0 = Up0; rp1 = Up1; rp2 = Up2;
-        rS2 = S2;
-      }
+    if (own)
+      for (int k = 0; k < 4; ++k) ct->acc[k][lane] = 0;
+    __syncwarp();
+    seg_sums<T, 3>(M, sseg, ct->acc, [&](int s, T* v) {
+      v[0] = svx[s];
+      v[1] = svy[s];
+      v[2] = svz[s];
+    });
+    if (nres_i > 0) {
+      ct->Up[0][lane] = ct->acc[0][lane] / (T)Ni;
+      ct->Up[1][lane] = ct->acc[1][lane] / (T)Ni;
+      ct->Up[2][lane] = ct->acc[2][lane] / (T)Ni;
     }
+    __syncwarp();
+    seg_sums<T, 1>(M, sseg, ct->acc + 3, [&](int s, T* v) {
+      const int c = sseg[s];
+      const T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
+      v[0] = C0 * C0 + C1 * C1 + C2 * C2;
+    });
+    const T rS2 = own ? ct->acc[3][lane] : (T)0;
     if (nres_i > 0) {
       const double Tp = (double)rS2 / (3.0 * Pi.R * (double)(Ni - 1));
       ct->f[lane] = Tp > 0 ? (T)sqrt(m.T / Tp) : (T)-1;
-      ct->Up[0][lane] = rp0;
-      ct->Up[1][lane] = rp1;
-      ct->Up[2][lane] = rp2;
     }
     __syncwarp();
     for (int s = lane; s < M; s += 32) {
@@ -710,22 +850,24 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     __syncwarp();
   }
   // ---- 8. time-averaged sums (Step 5)
-  const unsigned scells = __ballot_sync(kFull, sample && Ni > 0);
+  const bool anys = __any_sync(kFull, sample && Ni > 0);
   T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
-  for (unsigned rem = scells; rem; rem &= rem - 1) {
-    const int i = __ffs(rem) - 1;
-    const int o0 = ct->off[i], o1 = ct->off[i + 1];
-    T v0 = 0, v1 = 0, v2 = 0, w0 = 0, w1 = 0, w2 = 0;
-    for (int s = o0 + lane; s < o1; s += 32) {
+  if (anys) {
+    if (own)
+      for (int k = 0; k < 6; ++k) ct->acc[k][lane] = 0;
+    __syncwarp();
+    seg_sums<T, 6>(M, sseg, ct->acc, [&](int s, T* v) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
-      v0 += x0; v1 += x1; v2 += x2;
-      w0 += x0 * x0; w1 += x1 * x1; w2 += x2 * x2;
-    }
-    v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
-    w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
-    if (lane == i) {
-      a0 = v0; a1 = v1; a2 = v2;
-      b0 = w0; b1 = w1; b2 = w2;
+      v[0] = x0;
+      v[1] = x1;
+      v[2] = x2;
+      v[3] = x0 * x0;
+      v[4] = x1 * x1;
+      v[5] = x2 * x2;
+    });
+    if (own) {
+      a0 = ct->acc[0][lane]; a1 = ct->acc[1][lane]; a2 = ct->acc[2][lane];
+      b0 = ct->acc[3][lane]; b1 = ct->acc[4][lane]; b2 = ct->acc[5][lane];
     }
   }
   if (own) {
@@ -749,31 +891,46 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       a.rec[3 * NC + kc] = ct->nar[lane];
     }
   }
-  // ---- 9. free flight of the next interval (Step 2), key and histogram
+  // ---- 9. free flight of the next interval (Step 2), key and histogram;
+  // positions of four rounds are loaded before any is used
   T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
   T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
-  for (int sb = 0; sb < M; sb += 32) {
-    const int s = sb + lane;
-    uint32_t key = kSentinel;
-    if (s < M) {
-      const int c = sseg[s];
-      const InstParams& P = a.P[ct->inst[c]];
-      const uint32_t o = sidx[s];
-      T x[3] = {0, 0, 0};
+  for (int sb0 = 0; sb0 < M; sb0 += 128) {
+    T xr[4][DIM];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) x[d] = ((const T*)a.Apos[d])[o];
-      T v[3] = {svx[s], svy[s], svz[s]};
-      const bool gone = move_particle<T, DIM>(P, x, v, ct->dt[c], step, kPurpWall, (uint32_t)ct->kl[c],
-                                              (uint32_t)(s - ct->off[c]), 0u, a.err);
-      if (!gone) key = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
+    for (int u = 0; u < 4; ++u) {
+      const int s = sb0 + 32 * u + lane;
+      if (s < M) {
+        const uint32_t o = sidx[s];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) Bx[d][p0 + s] = x[d];
-      Bv[0][p0 + s] = v[0];
-      Bv[1][p0 + s] = v[1];
-      Bv[2][p0 + s] = v[2];
-      a.key[p0 + s] = key;
+        for (int d = 0; d < DIM; ++d) xr[u][d] = ((const T*)a.Apos[d])[o];
+      }
     }
-    warp_count(key, a.count);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int sb = sb0 + 32 * u;
+      if (sb >= M) break;
+      const int s = sb + lane;
+      uint32_t key = kSentinel;
+      if (s < M) {
+        const int c = sseg[s];
+        const InstParams& P = a.P[ct->inst[c]];
+        T x[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) x[d] = xr[u][d];
+        T v[3] = {svx[s], svy[s], svz[s]};
+        const bool gone = move_particle<T, DIM>(P, x, v, ct->dt[c], step, kPurpWall, (uint32_t)ct->kl[c],
+                                                (uint32_t)(s - ct->off[c]), 0u, a.err);
+        if (!gone) key = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) Bx[d][p0 + s] = x[d];
+        Bv[0][p0 + s] = v[0];
+        Bv[1][p0 + s] = v[1];
+        Bv[2][p0 + s] = v[2];
+        a.key[p0 + s] = key;
+      }
+      warp_count(key, a.count);
+    }
   }
   __syncwarp();
 }
@@ -788,10 +945,10 @@ __device__ inline void drop_cell(const StepArgs& a, int64_t k) {
 }
 
 template <class T, int DIM>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_collide(StepArgs a, int big) {
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_collide(StepArgs a, int big) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cap = big ? a.big_cap : kCapSmall;
+  const int cap = big ? a.big_cap : a.cap_small;
   if (big && warp != 0) return;
   unsigned char* base = smem + (size_t)(big ? 0 : warp) * warp_stage_bytes<T>(cap);
   CellTab<T>* ct = (CellTab<T>*)base;
@@ -802,37 +959,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_collide(StepArgs a, int
   int* stag = (int*)(sidx + cap);
   uint8_t* sseg = (uint8_t*)(stag + cap);
   if (!big) {
-    const int64_t nchunks = (a.NC + 31) / 32;
+    const uint32_t nb = *a.nbatch;
     for (;;) {
-      uint32_t chunk = 0;
-      if (lane == 0) chunk = atomicAdd(a.ticket, 1u);
-      chunk = __shfl_sync(kFull, chunk, 0);
-      if ((int64_t)chunk >= nchunks) break;
-      const int64_t c0 = (int64_t)chunk * 32;
-      const int nc = (int)((a.NC - c0) < 32 ? (a.NC - c0) : 32);
-      int cum = lane < nc ? (int)(a.start[c0 + lane + 1] - a.start[c0 + lane]) : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, cum, o);
-        if (lane >= o) cum += y;
-      }
-      int kk = 0;
-      while (kk < nc) {
-        const int before = kk > 0 ? __shfl_sync(kFull, cum, kk - 1) : 0;
-        const unsigned fit = __ballot_sync(kFull, lane >= kk && lane < nc && cum - before <= cap);
-        const int G = __popc(fit);
-        if (G == 0) {
-          // a single cell above the warp's staging area
-          if (lane == 0) {
-            const uint32_t i = atomicAdd(a.big_count, 1u);
-            a.big_list[i] = (uint32_t)(c0 + kk);
-          }
-          kk += 1;
-          continue;
-        }
-        process_batch<T, DIM>(a, c0 + kk, G, ct, sidx, stag, sseg, svx, svy, svz);
-        kk += G;
-      }
+      uint32_t t = 0;
+      if (lane == 0) t = atomicAdd(a.ticket, 1u);
+      t = __shfl_sync(kFull, t, 0);
+      if (t >= nb) break;
+      const uint2 b = a.batches[t];
+      process_batch<T, DIM>(a, (int64_t)b.x, (int)b.y, ct, sidx, stag, sseg, svx, svy, svz);
     }
   } else {
     const uint32_t nbig = *a.big_count;

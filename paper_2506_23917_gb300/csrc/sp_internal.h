@@ -9,8 +9,10 @@ namespace sp {
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // key of a removed particle
 constexpr int kMaxBounce = 16;               // wall events per particle per step
 constexpr int64_t kNcolCap = int64_t(1) << 24;
-constexpr int kWarpsPerBlock = 4;            // collide kernel, small cells
-constexpr int kCapSmall = 512;               // per-warp staging capacity (particles)
+constexpr int kMaxWarpsPerBlock = 8;         // collide kernel block size limit
+constexpr int kCapSmall = 512;               // default per-warp staging capacity (particles)
+constexpr int kWarpsDefault = 4;             // default warps per block
+constexpr int kMaxDynSmem = 232448;          // 227 KB per block (opt-in maximum)
 
 // Philox stream purposes (high byte of counter word 3).
 constexpr uint32_t kPurpNtc = 1, kPurpShk = 2, kPurpWall = 3, kPurpInj = 4, kPurpInjWall = 5;
@@ -23,6 +25,7 @@ enum { kErrCapacity = 0, kErrCellCap = 1, kErrBounce = 2, kErrAr = 3, kErrNcol =
 template <class T>
 struct Geo {
   T lo[3], hi[3], inv_d[3];
+  T eps[3];      // inside-box margin of the free-flight fast path
   T body_c[3], body_r;
   T face_RT[6];  // R * T_face
   T body_RT;     // R * T_wall of the body
@@ -84,11 +87,14 @@ struct StepArgs {
   const uint32_t* step; // global step index
   uint32_t* big_list;   // cells above kCapSmall
   uint32_t* big_count;
-  uint32_t* ticket;     // work-stealing counter over 32-cell chunks
+  uint32_t* ticket;     // work-stealing counter over the batch list
+  const uint2* batches; // (first cell, cell count) of each batch
+  const uint32_t* nbatch;
   unsigned long long* err;  // [kNumErr]
   int64_t NC;
   int64_t cap;
   int big_cap;          // staging capacity of the big-cell launch
+  int cap_small;        // staging capacity per warp of the main launch
 };
 
 struct InjectArgs {
@@ -110,7 +116,8 @@ struct InjectArgs {
 
 // Launch wrappers, one set per precision (sp_kern_f64.cu, sp_kern_f32.cu).
 #define SP_DECLARE_LAUNCHERS(tag)                                                                  \
-  void launch_collide_##tag(int dim, const StepArgs& a, bool big, int grid, cudaStream_t s);      \
+  void launch_collide_##tag(int dim, const StepArgs& a, bool big, int grid, int warps,           \
+                            cudaStream_t s);                                                     \
   void launch_inject_##tag(int dim, const InjectArgs& a, int pass, cudaStream_t s);               \
   void launch_moments_##tag(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s); \
   void launch_keys_##tag(int dim, const void* const pos[3], int64_t M, const uint32_t* part_inst, \
@@ -121,7 +128,8 @@ struct InjectArgs {
   void launch_stage_in_##tag(int dim, const double* pos, const double* vel, int64_t n,             \
                              void* const dpos[3], void* const dvel[3], int64_t off,              \
                              uint32_t* part_inst, uint32_t inst, cudaStream_t s);                \
-  int collide_blocks_per_sm_##tag(int dim);                                                       \
+  int collide_blocks_per_sm_##tag(int dim, int warps, int cap);                                 \
+  size_t collide_smem_##tag(int warps, int cap);                                                \
   cudaError_t configure_##tag(int big_cap);
 SP_DECLARE_LAUNCHERS(f64)
 SP_DECLARE_LAUNCHERS(f32)
@@ -129,13 +137,15 @@ SP_DECLARE_LAUNCHERS(f32)
 // Precision-independent kernels (sp_common.cu).
 void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s);
 void launch_cell_finalize(uint32_t* count, uint32_t* fill, int64_t NC, cudaStream_t s);
+void launch_plan(const uint32_t* start, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+                 uint32_t* big_list, uint32_t* big_count, cudaStream_t s);
 void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* fill, uint32_t* perm,
                     const uint32_t* Mtot, int64_t cap, cudaStream_t s);
 void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                           uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                           const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                          uint32_t* big_count, uint32_t* ticket, cudaStream_t s);
+                          uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch, cudaStream_t s);
 int64_t scan_partial_size(int64_t n);
 
 }  // namespace sp

@@ -7,10 +7,10 @@ namespace {
 using T = float;
 
 template <int DIM>
-void collide_dim(const StepArgs& a, bool big, int grid, cudaStream_t s) {
+void collide_dim(const StepArgs& a, bool big, int grid, int warps, cudaStream_t s) {
   if (!big) {
-    const size_t smem = (size_t)kWarpsPerBlock * warp_stage_bytes<T>(kCapSmall);
-    k_collide<T, DIM><<<grid, 32 * kWarpsPerBlock, smem, s>>>(a, 0);
+    const size_t smem = (size_t)warps * warp_stage_bytes<T>(a.cap_small);
+    k_collide<T, DIM><<<grid, 32 * warps, smem, s>>>(a, 0);
   } else {
     const size_t smem = warp_stage_bytes<T>(a.big_cap);
     k_collide<T, DIM><<<grid, 32, smem, s>>>(a, 1);
@@ -32,19 +32,21 @@ void keys_dim(const void* const pos[3], int64_t M, const uint32_t* part_inst, co
 }
 
 template <int DIM>
-cudaError_t configure_dim(int big_cap) {
-  const size_t small = (size_t)kWarpsPerBlock * warp_stage_bytes<T>(kCapSmall);
-  const size_t big = warp_stage_bytes<T>(big_cap);
-  const size_t mx = small > big ? small : big;
-  return cudaFuncSetAttribute(k_collide<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+cudaError_t configure_dim(int) {
+  cudaError_t e = cudaFuncSetAttribute(k_collide<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e == cudaSuccess)  // staging lives in shared memory: prefer the largest carveout
+    e = cudaFuncSetAttribute(k_collide<T, DIM>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 }  // namespace
 
-void launch_collide_f32(int dim, const StepArgs& a, bool big, int grid, cudaStream_t s) {
-  if (dim == 1) collide_dim<1>(a, big, grid, s);
-  else if (dim == 2) collide_dim<2>(a, big, grid, s);
-  else collide_dim<3>(a, big, grid, s);
+void launch_collide_f32(int dim, const StepArgs& a, bool big, int grid, int warps, cudaStream_t s) {
+  if (dim == 1) collide_dim<1>(a, big, grid, warps, s);
+  else if (dim == 2) collide_dim<2>(a, big, grid, warps, s);
+  else collide_dim<3>(a, big, grid, warps, s);
 }
+
+size_t collide_smem_f32(int warps, int cap) { return (size_t)warps * warp_stage_bytes<T>(cap); }
 
 void launch_inject_f32(int dim, const InjectArgs& a, int pass, cudaStream_t s) {
   if (a.n_ghost == 0) return;
@@ -88,13 +90,13 @@ void launch_stage_in_f32(int dim, const double* pos, const double* vel, int64_t 
                                             (T*)dvel[0], (T*)dvel[1], (T*)dvel[2], off, part_inst, inst);
 }
 
-int collide_blocks_per_sm_f32(int dim) {
+int collide_blocks_per_sm_f32(int dim, int warps, int cap) {
   int n = 0;
-  const size_t smem = (size_t)kWarpsPerBlock * warp_stage_bytes<T>(kCapSmall);
-  if (dim == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 1>, 32 * kWarpsPerBlock, smem);
-  else if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 2>, 32 * kWarpsPerBlock, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 3>, 32 * kWarpsPerBlock, smem);
-  return n > 0 ? n : 1;
+  const size_t smem = (size_t)warps * warp_stage_bytes<T>(cap);
+  if (dim == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 1>, 32 * warps, smem);
+  else if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 2>, 32 * warps, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 3>, 32 * warps, smem);
+  return n;
 }
 
 cudaError_t configure_f32(int big_cap) {

@@ -193,3 +193,28 @@ def test_capacity_overflow_is_reported(sp):
     with pytest.raises(sp.SpError) as e:
         small.set_particles(0, pos, vel)
     assert e.value.code == -3
+
+
+def test_schedule_and_autotune_do_not_change_results(sp):
+    """Batch composition (staging capacity, warps per block) and the
+    autotuner's choice must not change any result."""
+    cfg, regions = W.box2d(nx=24, ny=12, ppc=40.0)
+    pos, vel = W.fill_regions(cfg, regions, 7)
+    runs = []
+    for sched in ((512, 4), (128, 2), (1024, 2), None):
+        s = sp.Sim(cfg, sp.FP64, capacity=4 * vel.shape[1])
+        s.set_particles(0, pos, vel)
+        if sched is None:
+            s.step(2)
+            cap, w = s.autotune(steps_per_trial=1)
+            assert cap >= 128 and w in (2, 4, 8)
+        else:
+            s.set_schedule(*sched)
+        s.step(30 - s.step_index())
+        s.sync()
+        runs.append((s.particles(0), s.sigc_max(0)))
+        s.close()
+    for r in runs[1:]:
+        for x, y in zip(r[0], runs[0][0]):
+            np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(r[1], runs[0][1])
