@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--profile-steps", type=int, default=40)
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--reproducible", action="store_true",
+                   help="FP32: restore the source order inside cells in the timed run")
     p.add_argument("--batch-steps", type=int, default=200)
     return p.parse_args()
 
@@ -355,6 +357,8 @@ def main():
     stream = torch.cuda.current_stream()
     prec = sp.FP32 if args.precision == "fp32" else sp.FP64
     sim = sp.Sim(cfg, prec, capacity=cap)
+    if prec == sp.FP32 and not args.reproducible:
+        sim.set_reproducible(False)  # FP32 mode is judged statistically
     sim.set_particles(0, pos, vel)
     sim.step(args.develop)
     sim.sync()
@@ -384,6 +388,27 @@ def main():
     t_max, upd_sum = reduce_timing(ms, upd, dist, "cuda")
     value = upd_sum / (t_max * 1e-3)
     ms_per_step = t_max / args.steps
+
+    # --- the same workload with the within-cell order restored every step
+    # (bit-reproducible runs; FP64 mode always runs this way)
+    repro = None
+    if prec == sp.FP32 and not args.reproducible:
+        sim.set_reproducible(True)
+        sim.step(5)
+        sim.sync()
+        m0r = sim.count(0)
+        kr = max(50, args.steps // 4)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(kr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sim.sync()
+        tr = e0.elapsed_time(e1)
+        repro = {"value": world * kr * 0.5 * (m0r + sim.count(0)) / (tr * 1e-3), "unit": UNIT,
+                 "ms_per_step": tr / kr, "steps": kr,
+                 "note": "source order restored inside every cell (bit-reproducible)"}
+        sim.set_reproducible(False)
 
     # --- roofline of the dominant kernel (collision + free flight), measured
     # with CUDA events around each kernel group on the library's stream
@@ -421,6 +446,10 @@ def main():
                        "graph": "one CUDA graph per step", "parallelism": f"replicas{world}",
                        "schedule": {"cap": sched[0], "warps_per_block": sched[1]} if sched else "default"},
             "clocks": clk, "gpu_launches": launches * args.steps, "roofline": roofline}
+    line["config"]["within_cell_order"] = ("source order (bit-reproducible)" if (prec == sp.FP64 or args.reproducible)
+                                           else "scatter order (statistically identical, not bit-reproducible)")
+    if repro:
+        line["fp32_reproducible_order"] = repro
 
     # --- plain FP64 form of the same workload
     if not args.no_fp64 and prec == sp.FP32:

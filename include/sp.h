@@ -166,6 +166,14 @@ sp_status sp_errors(sp_ctx* ctx, int64_t* out5);
  * reservoir injection, (2) the histogram scan and bookkeeping, (3) the
  * scatter.  Synchronises after every step (for measurement only). */
 sp_status sp_step_profiled(sp_ctx* ctx, int n_steps, double* ms, int n_slots);
+/* Within-cell order of the particles.  on = 1 (default): every step restores
+ * the source order inside each cell (a stable counting sort overall), so a
+ * run is bit-reproducible and FP64 mode matches the CPU oracle particle for
+ * particle.  on = 0 (FP32 mode only; SP_ERR_ARG in FP64 mode): cells keep
+ * the order in which the scatter's atomics placed them; every draw is still
+ * an independent uniform per slot and pair selection is still uniform, so
+ * results are statistically the same but differ bit-wise from run to run. */
+sp_status sp_set_reproducible(sp_ctx* ctx, int on);
 /* Collision-kernel schedule: `cap` particles of shared-memory staging per
  * warp (a warp takes consecutive cells whose particles fit; cells above it
  * go to a one-warp-per-cell launch) and `warps` warps per block (1..8).

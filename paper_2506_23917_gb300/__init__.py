@@ -49,7 +49,7 @@ class SpConfig(C.Structure):
 
 SYMBOLS = ["sp_init", "sp_set_particles", "sp_step", "sp_moments", "sp_get_particles",
            "sp_set_record", "sp_get_step_record", "sp_get_cell_start", "sp_get_sigc_max",
-           "sp_get_dt", "sp_errors", "sp_sync", "sp_step_profiled", "sp_set_schedule", "sp_autotune", "sp_launches_per_step", "sp_free",
+           "sp_get_dt", "sp_errors", "sp_sync", "sp_step_profiled", "sp_set_schedule", "sp_set_reproducible", "sp_autotune", "sp_launches_per_step", "sp_free",
            "sp_status_str", "sp_sort_cells_static"]
 
 _lib = None
@@ -77,6 +77,7 @@ def lib():
         L.sp_sync.argtypes = [P]
         L.sp_step_profiled.argtypes = [P, C.c_int, P, C.c_int]
         L.sp_set_schedule.argtypes = [P, C.c_int, C.c_int]
+        L.sp_set_reproducible.argtypes = [P, C.c_int]
         L.sp_autotune.argtypes = [P, C.c_int, P, P]
         L.sp_launches_per_step.argtypes = [P]
         L.sp_free.argtypes = [P]
@@ -269,6 +270,9 @@ class Sim:
         out = np.zeros(5, dtype=np.int64)
         _chk("sp_errors", lib().sp_errors(self.h, _ptr(out)))
         return dict(zip(ERRORS, (int(x) for x in out)))
+
+    def set_reproducible(self, on=True):
+        _chk("sp_set_reproducible", lib().sp_set_reproducible(self.h, 1 if on else 0))
 
     def set_schedule(self, cap, warps):
         _chk("sp_set_schedule", lib().sp_set_schedule(self.h, cap, warps))

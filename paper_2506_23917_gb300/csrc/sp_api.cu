@@ -49,6 +49,7 @@ struct sp_ctx {
   int collide_grid = 1;
   int nsm = 1;
   int sched_cap = kCapSmall, sched_warps = kWarpsDefault;
+  int stable = 1;
   double *vol = nullptr, *smax = nullptr, *samp = nullptr;
   int32_t* rec = nullptr;
   uint8_t* resamp = nullptr;
@@ -257,6 +258,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.cap = c->cap;
   a.big_cap = c->prec == SP_FP64 ? kBigCap64 : kBigCap32;
   a.cap_small = c->sched_cap;
+  a.stable = c->stable;
   return a;
 }
 
@@ -681,6 +683,16 @@ sp_status sp_step_profiled(sp_ctx* c, int n_steps, double* ms, int n_slots) {
   for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
   for (int k = 0; k < n_slots && k < 4; ++k) ms[k] = acc[k];
   CK(cudaGetLastError());
+  return SP_OK;
+}
+
+sp_status sp_set_reproducible(sp_ctx* c, int on) {
+  if (!c) return SP_ERR_ARG;
+  if (c->prec == SP_FP64 && !on) return SP_ERR_ARG;  // FP64 mode always keeps the source order
+  if ((on != 0) != (c->stable != 0)) {
+    c->stable = on != 0;
+    destroy_graphs(c);
+  }
   return SP_OK;
 }
 

@@ -284,22 +284,30 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
       for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
       continue;
     }
+    // (static indices only: x and v stay in registers)
 #pragma unroll
-    for (int d = 0; d < DIM; ++d)
+    for (int d = 0; d < DIM; ++d) {
       if (d != fa) x[d] += v[d] * tf;
-    x[fa] = fs ? G.hi[fa] : G.lo[fa];
+      else x[d] = fs ? G.hi[d] : G.lo[d];
+    }
     trem -= tf;
     const int f = 2 * fa + fs;
     const int bc = P.face_bc[f];
     if (bc == 0) {
-      v[fa] = -v[fa];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+        if (d == fa) v[d] = -v[d];
     } else if (bc == 1) {
       Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
       T cn, t1, t2;
       diffuse_sample<T>(G.face_RT[f], r, &cn, &t1, &t2);
-      v[fa] = fs ? -cn : cn;
-      v[(fa + 1) % 3] = t1;
-      v[(fa + 2) % 3] = t2;
+      const int f1 = fa == 2 ? 0 : fa + 1, f2 = fa == 0 ? 2 : fa - 1;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (d == fa) v[d] = fs ? -cn : cn;
+        else if (d == f1) v[d] = t1;
+        else if (d == f2) v[d] = t2;
+      }
     } else {
       return true;
     }
@@ -367,15 +375,16 @@ __host__ __device__ constexpr size_t warp_stage_bytes(int cap) {
 // Per-cell sums over all M slots of a batch in one pass: slots are grouped
 // by cell (sseg is nondecreasing), so a lane-ordered segmented scan of each
 // 32-slot chunk leaves the chunk's partial sum of a cell in the last lane
-// holding that cell, which adds it to acc[k][cell].  The order of additions
-// is fixed (by slot), so the sums are reproducible.  acc must be zero for
-// the batch's cells on entry.
+// holding that cell, which adds it to acc[k][cell].  Chunks are aligned to
+// multiples of 32 of the global slot index (p0 is the batch's first slot),
+// so the order of additions of a cell depends only on its own slots, not on
+// how cells were grouped into batches.  acc must be zero on entry.
 template <class T, int K, class F>
-__device__ __forceinline__ void seg_sums(int M, const uint8_t* sseg, T (*acc)[32], F f) {
+__device__ __forceinline__ void seg_sums(int M, uint32_t p0, const uint8_t* sseg, T (*acc)[32], F f) {
   const int lane = threadIdx.x & 31;
-  for (int base = 0; base < M; base += 32) {
+  for (int base = -(int)(p0 & 31u); base < M; base += 32) {
     const int s = base + lane;
-    const bool valid = s < M;
+    const bool valid = s >= 0 && s < M;
     const int c = valid ? (int)sseg[s] : 255;
     T v[K];
 #pragma unroll
@@ -442,12 +451,14 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   }
   __syncwarp();
   // cells whose source indices arrived out of order (the scatter's atomics
-  // keep each scattering warp's run ascending, so most cells are in order)
+  // keep only each scattering warp's run ascending); skipped when the run
+  // does not ask for the reproducible (source) order
   unsigned mine_uns = 0;
-  for (int t = lane; t < M; t += 32) {
-    const int c = sseg[t];
-    if (t + 1 < ct->off[c + 1] && sidx[t] > sidx[t + 1]) mine_uns |= 1u << c;
-  }
+  if (a.stable)
+    for (int t = lane; t < M; t += 32) {
+      const int c = sseg[t];
+      if (t + 1 < ct->off[c + 1] && sidx[t] > sidx[t + 1]) mine_uns |= 1u << c;
+    }
   const unsigned uns = __reduce_or_sync(kFull, mine_uns);
   // small cells: each slot's rank among its cell's (distinct) source
   // indices, written through stag as scratch; big cells: a sorting network
@@ -513,7 +524,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   if (own)
     for (int k = 0; k < 7; ++k) ct->acc[k][lane] = 0;
   __syncwarp();
-  seg_sums<T, 3>(M, sseg, ct->acc, [&](int s, T* v) {
+  seg_sums<T, 3>(M, p0, sseg, ct->acc, [&](int s, T* v) {
     v[0] = svx[s];
     v[1] = svy[s];
     v[2] = svz[s];
@@ -524,7 +535,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     ct->U[2][lane] = ct->acc[2][lane] / (T)Ni;
   }
   __syncwarp();
-  seg_sums<T, 4>(M, sseg, ct->acc + 3, [&](int s, T* v) {
+  seg_sums<T, 4>(M, p0, sseg, ct->acc + 3, [&](int s, T* v) {
     const int c = sseg[s];
     const T C0 = svx[s] - ct->U[0][c], C1 = svy[s] - ct->U[1][c], C2 = svz[s] - ct->U[2][c];
     const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
@@ -816,7 +827,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (own)
       for (int k = 0; k < 4; ++k) ct->acc[k][lane] = 0;
     __syncwarp();
-    seg_sums<T, 3>(M, sseg, ct->acc, [&](int s, T* v) {
+    seg_sums<T, 3>(M, p0, sseg, ct->acc, [&](int s, T* v) {
       v[0] = svx[s];
       v[1] = svy[s];
       v[2] = svz[s];
@@ -827,7 +838,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       ct->Up[2][lane] = ct->acc[2][lane] / (T)Ni;
     }
     __syncwarp();
-    seg_sums<T, 1>(M, sseg, ct->acc + 3, [&](int s, T* v) {
+    seg_sums<T, 1>(M, p0, sseg, ct->acc + 3, [&](int s, T* v) {
       const int c = sseg[s];
       const T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
       v[0] = C0 * C0 + C1 * C1 + C2 * C2;
@@ -856,7 +867,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (own)
       for (int k = 0; k < 6; ++k) ct->acc[k][lane] = 0;
     __syncwarp();
-    seg_sums<T, 6>(M, sseg, ct->acc, [&](int s, T* v) {
+    seg_sums<T, 6>(M, p0, sseg, ct->acc, [&](int s, T* v) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
       v[0] = x0;
       v[1] = x1;
@@ -945,7 +956,7 @@ __device__ inline void drop_cell(const StepArgs& a, int64_t k) {
 }
 
 template <class T, int DIM>
-__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_collide(StepArgs a, int big) {
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs a, int big) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cap = big ? a.big_cap : a.cap_small;
@@ -985,7 +996,10 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) k_collide(StepArgs a, 
 // ---------------------------------------------------------------------------
 template <class T, int DIM>
 __global__ void k_inject(InjectArgs a, int pass) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per reservoir cell; lanes take its particles m = lane, lane+32,
+  // ...; survivors keep the (cell, m) order through ballot prefix counts
+  const int lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (g >= a.n_ghost) return;
   const GhostCell G = a.ghosts[g];
   const InstParams& P = a.P[G.inst];
@@ -1003,46 +1017,62 @@ __global__ void k_inject(InjectArgs a, int pass) {
   T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
   T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
   const T s2RT = (T)G.s2RT;
-  for (int64_t m = 0; m < ng; ++m) {
-    Uni<T> r(step, G.gc, (uint32_t)m, (kPurpInj << 24) | sb, P.key0, P.key1);
-    T x[3] = {0, 0, 0}, v[3];
+  T blo[3], bhi[3], u0[3];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) x[d] = (T)G.blo[d] + r.get(d) * ((T)G.bhi[d] - (T)G.blo[d]);
-    const T R1 = r.get(3), R2 = r.get(4), R3 = r.get(5), R4 = r.get(6);
-    const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
-    T sn3, cs3;
-    sincos2pi(R3, &sn3, &cs3);
-    v[0] = (T)G.u[0] + s2RT * cos2pi(R1) * r2;
-    v[1] = (T)G.u[1] + s2RT * cs3 * r4;
-    v[2] = (T)G.u[2] + s2RT * sn3 * r4;
-    const T vn = v[ax];
-    if (side == 0 ? !(vn > (T)0) : !(vn < (T)0)) continue;
-    const T te = (face - x[ax]) / vn;
-    if (!(te < dt)) continue;
-    bool ok = true;
+  for (int d = 0; d < 3; ++d) {
+    blo[d] = (T)G.blo[d];
+    bhi[d] = (T)G.bhi[d];
+    u0[d] = (T)G.u[d];
+  }
+  for (int64_t m0 = 0; m0 < ng; m0 += 32) {
+    const int64_t m = m0 + lane;
+    bool ok = m < ng;
+    T x[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+    if (ok) {
+      Uni<T> r(step, G.gc, (uint32_t)m, (kPurpInj << 24) | sb, P.key0, P.key1);
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      if (d == ax) continue;
-      T y = x[d] + v[d] * te;
-      if (y < GE.lo[d]) {
-        if (P.face_bc[2 * d] != 0) { ok = false; break; }
-        y = (T)2.0 * GE.lo[d] - y;
-        v[d] = -v[d];
-      } else if (y > GE.hi[d]) {
-        if (P.face_bc[2 * d + 1] != 0) { ok = false; break; }
-        y = (T)2.0 * GE.hi[d] - y;
-        v[d] = -v[d];
+      for (int d = 0; d < DIM; ++d) x[d] = blo[d] + r.get(d) * (bhi[d] - blo[d]);
+      const T R1 = r.get(3), R2 = r.get(4), R3 = r.get(5), R4 = r.get(6);
+      const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
+      T sn3, cs3;
+      sincos2pi(R3, &sn3, &cs3);
+      v[0] = u0[0] + s2RT * cos2pi(R1) * r2;
+      v[1] = u0[1] + s2RT * cs3 * r4;
+      v[2] = u0[2] + s2RT * sn3 * r4;
+      const T vn = v[ax];
+      ok = side == 0 ? (vn > (T)0) : (vn < (T)0);
+      T te = 0;
+      if (ok) {
+        te = (face - x[ax]) / vn;
+        ok = te < dt;
       }
-      if (y < GE.lo[d] || y > GE.hi[d]) { ok = false; break; }
-      x[d] = y;
+      if (ok) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          if (d == ax || !ok) continue;
+          T y = x[d] + v[d] * te;
+          if (y < GE.lo[d]) {
+            if (P.face_bc[2 * d] != 0) { ok = false; continue; }
+            y = (T)2.0 * GE.lo[d] - y;
+            v[d] = -v[d];
+          } else if (y > GE.hi[d]) {
+            if (P.face_bc[2 * d + 1] != 0) { ok = false; continue; }
+            y = (T)2.0 * GE.hi[d] - y;
+            v[d] = -v[d];
+          }
+          if (y < GE.lo[d] || y > GE.hi[d]) { ok = false; continue; }
+          x[d] = y;
+        }
+      }
+      if (ok) {
+        x[ax] = face;
+        ok = !move_particle<T, DIM>(P, x, v, dt - te, step, kPurpInjWall, G.gc, (uint32_t)m,
+                                    (uint32_t)G.face << 16, a.err);
+      }
     }
-    if (!ok) continue;
-    x[ax] = face;
-    if (move_particle<T, DIM>(P, x, v, dt - te, step, kPurpInjWall, G.gc, (uint32_t)m,
-                              (uint32_t)G.face << 16, a.err))
-      continue;
-    if (pass == 1) {
-      const int64_t idx = base + nsurv;
+    const unsigned sv = __ballot_sync(kFull, ok);
+    if (pass == 1 && ok) {
+      const int64_t idx = base + nsurv + __popc(sv & ((1u << lane) - 1u));
       if (idx >= a.cap) {
         atomicAdd(&a.err[kErrCapacity], 1ull);
       } else {
@@ -1056,9 +1086,9 @@ __global__ void k_inject(InjectArgs a, int pass) {
         atomicAdd(&a.count[key], 1u);
       }
     }
-    ++nsurv;
+    nsurv += __popc(sv);
   }
-  if (pass == 0) a.gcount[g] = nsurv;
+  if (pass == 0 && lane == 0) a.gcount[g] = nsurv;
 }
 
 // ---------------------------------------------------------------------------

@@ -95,6 +95,7 @@ struct StepArgs {
   int64_t cap;
   int big_cap;          // staging capacity of the big-cell launch
   int cap_small;        // staging capacity per warp of the main launch
+  int stable;           // restore source order within cells (reproducible runs)
 };
 
 struct InjectArgs {

@@ -19,7 +19,7 @@ void collide_dim(const StepArgs& a, bool big, int grid, int warps, cudaStream_t 
 
 template <int DIM>
 void inject_dim(const InjectArgs& a, int pass, cudaStream_t s) {
-  const int64_t g = (a.n_ghost + 127) / 128;
+  const int64_t g = (a.n_ghost + 3) / 4;  // one warp per reservoir cell
   k_inject<T, DIM><<<(unsigned)g, 128, 0, s>>>(a, pass);
 }
 
