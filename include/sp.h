@@ -91,6 +91,8 @@ typedef struct sp_config {
   uint64_t seed;          /* Philox key of this instance                     */
   int32_t mode;           /* sp_mode: hybrid, or one sub-step forced         */
   int32_t ar_max;         /* cap on Shakhov acceptance-rejection attempts    */
+  int32_t n_surf;         /* surface elements of the body for wall tallies
+                             (0: none); see sp_get_surface()                 */
 } sp_config;
 
 typedef struct sp_ctx sp_ctx;
@@ -156,6 +158,37 @@ sp_status sp_get_cell_start(sp_ctx* ctx, int inst, uint32_t* start);
 sp_status sp_get_sigc_max(sp_ctx* ctx, int inst, double* out);
 /* Delta t of the next step of instance inst, and the global step index. */
 sp_status sp_get_dt(sp_ctx* ctx, int inst, double* dt, int64_t* step);
+/* Surface tallies of instance inst's body, summed over the sampled steps
+ * (step index >= n_steady): out host [7][n_surf] = (hits, momentum given to
+ * the wall x, y, z, energy given to the wall, momentum given along the
+ * inward normal, momentum given along e_theta), each hit weighted by F_N m;
+ * *time = sampled physical time.  Element b of a circle covers the polar
+ * angle theta = atan2(n_y, n_x) in [-pi + 2 pi b/n_surf,
+ * -pi + 2 pi (b+1)/n_surf); of a sphere, theta = acos(n_x) in
+ * [pi b/n_surf, pi (b+1)/n_surf).  e_theta is the unit direction of
+ * increasing theta at the hit point (zero on a sphere's axis).  Divided by
+ * element area and time these are the wall stress and heat flux behind the
+ * paper's surface pressure, shear, heat flux and force coefficients
+ * (Sec. IV.B-E); sp_surface_coefficients() forms them. */
+sp_status sp_get_surface(sp_ctx* ctx, int inst, double* out, double* time);
+/* Surface and body coefficients from wall tallies (host arithmetic only; no
+ * context or GPU needed).  cfg: the instance's configuration (its body,
+ * n_surf and domain box); tallies: host [7][n_surf] as returned by
+ * sp_get_surface; time: the sampled time; rho_inf, u_inf, p_inf: free-stream
+ * density, speed (along +x) and pressure, with q_inf = rho_inf u_inf^2 / 2.
+ * elem (host [4][n_surf], caller-owned): A_b = area of element b inside the
+ * domain box (2-D: arc length times the z extent), found by sub-sampling
+ * the element; Cp = (p_b - p_inf)/q_inf with p_b the normal momentum flux
+ * into the wall; Cf = tau_b/q_inf with tau_b the momentum flux along
+ * e_theta; Ch = (energy flux into the wall)/(q_inf u_inf).  Elements with
+ * no area inside the box get zeros.  body (host [4]): Cd = F_x/(q_inf A_ref),
+ * CL = F_y/(q_inf A_ref), Ch over the whole in-domain surface, and
+ * A_ref = half the integral of |n_x| over the in-domain surface (the frontal
+ * area of that part of a convex body).  SP_ERR_ARG for a missing body,
+ * n_surf < 1, time <= 0 or q_inf <= 0. */
+sp_status sp_surface_coefficients(const sp_config* cfg, const double* tallies, double time,
+                                  double rho_inf, double u_inf, double p_inf, double* elem,
+                                  double* body);
 /* Device error counters: [0] capacity overflow, [1] cell above staging
  * capacity, [2] bounce cap, [3] AR cap, [4] NTC candidate cap.
  * Clears nothing. */

@@ -33,7 +33,7 @@ class OrConfig(C.Structure):
         ("body", C.c_int32), ("body_c", C.c_double * 3), ("body_r", C.c_double),
         ("body_Tw", C.c_double), ("cell_volume", C.POINTER(C.c_double)),
         ("sigc_T0", C.c_double), ("n_steady", C.c_int32), ("seed", C.c_uint64),
-        ("mode", C.c_int32), ("ar_max", C.c_int32),
+        ("mode", C.c_int32), ("ar_max", C.c_int32), ("n_surf", C.c_int32),
     ]
 
 
@@ -62,6 +62,7 @@ def lib():
         L.or_step_index.argtypes = [P]
         L.or_step_index.restype = C.c_int64
         L.or_get_totals.argtypes = [P, P]
+        L.or_get_surface.argtypes = [P, P, P]
         L.or_free.argtypes = [P]
         L.or_philox4x32_10.argtypes = [P, P, P]
         L.or_u01_from_words.argtypes = [C.c_uint32, C.c_uint32]
@@ -108,6 +109,7 @@ def make_config(cfg: dict):
     s.seed = cfg["seed"]
     s.mode = cfg["mode"]
     s.ar_max = cfg["ar_max"]
+    s.n_surf = int(cfg.get("n_surf", 0))
     return s, keep
 
 
@@ -222,6 +224,16 @@ class Oracle:
         ns = np.zeros(1, dtype=np.int64)
         lib().or_get_sample(self.h, _ptr(out), _ptr(ns))
         return out, int(ns[0])
+
+    def surface(self):
+        """(tallies [7][n_surf] = hits, momentum to the wall x/y/z, energy to
+        the wall, momentum along the inward normal, momentum along e_theta;
+        sampled time)."""
+        ns = int(self.cfg.get("n_surf", 0))
+        out = np.zeros((7, max(ns, 1)))
+        t = np.zeros(1)
+        lib().or_get_surface(self.h, _ptr(out), _ptr(t))
+        return out[:, :ns], float(t[0])
 
     def totals(self):
         out = np.zeros(4, dtype=np.int64)

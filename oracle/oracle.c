@@ -42,6 +42,9 @@
  *   - Open (inflow) faces: a reservoir of ghost cells outside the face is
  *     refilled each step at the face state and its particles that cross the
  *     face within the step are kept (the paper's ghost cells of Sec. IV.A).
+ *     Where two inflow faces meet, each face's reservoir also covers the
+ *     corner block beyond the other; a particle is kept only by the face it
+ *     crosses first, so no phase-space region is injected twice.
  */
 #define _GNU_SOURCE
 #include "oracle.h"
@@ -89,6 +92,10 @@ struct or_ctx {
   int64_t rec_n;
   uint32_t *perm;    /* [M] */
   int64_t totals[4];
+  /* surface tallies (Step 5 sampling of wall fluxes) */
+  double *surf; /* [7][n_surf] */
+  double surf_time;
+  int sampling_now;
 };
 
 /* ---------------------------------------------------------------------
@@ -404,7 +411,46 @@ static int move_particle(or_ctx* c, double* x, double* v, double trem, uint32_t 
       }
       double cn, t1, t2;
       diffuse_sample(c, g->body_Tw, purpose, a, b, sub, &cn, &t1, &t2);
+      double vin[3] = {v[0], v[1], v[2]};
       for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
+      if (c->sampling_now && g->n_surf > 0) {
+        /* momentum and energy the wall receives from this hit */
+        int ns = g->n_surf;
+        double th, frac;
+        if (g->body == OR_BODY_CIRCLE) {
+          th = atan2(nv[1], nv[0]);
+          frac = (th + M_PI) / (2.0 * M_PI);
+        } else {
+          double cx = nv[0] < -1.0 ? -1.0 : (nv[0] > 1.0 ? 1.0 : nv[0]);
+          th = acos(cx);
+          frac = th / M_PI;
+        }
+        int bin = (int)floor(frac * (double)ns);
+        if (bin < 0) bin = 0;
+        if (bin > ns - 1) bin = ns - 1;
+        double w = g->Fn * g->m;
+        double ein = vin[0] * vin[0] + vin[1] * vin[1] + vin[2] * vin[2];
+        double eout = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        double dp[3], et[3] = {0, 0, 0};
+        for (int d = 0; d < 3; ++d) dp[d] = w * (vin[d] - v[d]);
+        /* direction of increasing polar angle at the hit point */
+        if (g->body == OR_BODY_CIRCLE) {
+          et[0] = -nv[1];
+          et[1] = nv[0];
+        } else {
+          double sn = sqrt(nv[1] * nv[1] + nv[2] * nv[2]);
+          if (sn > 0) {
+            et[0] = -sn;
+            et[1] = nv[0] * nv[1] / sn;
+            et[2] = nv[0] * nv[2] / sn;
+          }
+        }
+        c->surf[0 * ns + bin] += 1.0;
+        for (int d = 0; d < 3; ++d) c->surf[(1 + d) * ns + bin] += dp[d];
+        c->surf[4 * ns + bin] += 0.5 * w * (ein - eout);
+        c->surf[5 * ns + bin] -= dp[0] * nv[0] + dp[1] * nv[1] + dp[2] * nv[2];
+        c->surf[6 * ns + bin] += dp[0] * et[0] + dp[1] * et[1] + dp[2] * et[2];
+      }
       continue;
     }
     for (int d = 0; d < g->dim; ++d)
@@ -463,6 +509,8 @@ int or_init(const or_config* cfg, or_ctx** out) {
   c->samp = (double*)calloc(8 * c->ncells, sizeof(double));
   c->rec = (int64_t*)calloc(4 * c->ncells, sizeof(int64_t));
   if (g->ar_max < 1) g->ar_max = 1;
+  if (g->n_surf < 0) g->n_surf = 0;
+  c->surf = (double*)calloc(7 * (g->n_surf > 0 ? g->n_surf : 1), sizeof(double));
   *out = c;
   return OR_OK;
 }
@@ -470,7 +518,7 @@ int or_init(const or_config* cfg, or_ctx** out) {
 void or_free(or_ctx* c) {
   if (!c) return;
   free(c->vol); free(c->p); free(c->start); free(c->smax); free(c->samp);
-  free(c->rec); free(c->resamp); free(c->perm);
+  free(c->rec); free(c->resamp); free(c->perm); free(c->surf);
   free(c);
 }
 
@@ -551,11 +599,19 @@ static void inject(or_ctx* c, part** buf, uint32_t** keys, int64_t* n, int64_t* 
   for (int f = 0; f < 6; ++f) {
     int ax = f / 2, side = f % 2;
     if (ax >= g->dim || g->face_bc[f] != OR_BC_INFLOW) continue;
-    int ta[2], nt = 0;
+    /* tangential extent of the reservoir: the face's cells, plus the corner
+     * blocks beyond every neighbouring face that is itself an inflow face */
+    int ta[2], nt = 0, elo[2] = {0, 0}, ntc[2] = {1, 1};
     for (int d = 0; d < g->dim; ++d)
       if (d != ax) ta[nt++] = d;
     int64_t ntan = 1;
-    for (int i = 0; i < nt; ++i) ntan *= g->n[ta[i]];
+    for (int i = 0; i < nt; ++i) {
+      int d = ta[i];
+      elo[i] = g->face_bc[2 * d] == OR_BC_INFLOW ? g->ghost_layers : 0;
+      int ehi = g->face_bc[2 * d + 1] == OR_BC_INFLOW ? g->ghost_layers : 0;
+      ntc[i] = g->n[d] + elo[i] + ehi;
+      ntan *= ntc[i];
+    }
     int64_t nghost = ntan * g->ghost_layers;
     double RT = g->R * g->face_T[f];
     double s2RT = sqrt(2.0 * RT);
@@ -567,8 +623,8 @@ static void inject(or_ctx* c, part** buf, uint32_t** keys, int64_t* n, int64_t* 
       int64_t tt = t;
       for (int i = 0; i < nt; ++i) {
         int d = ta[i];
-        int64_t id = tt % g->n[d];
-        tt /= g->n[d];
+        int64_t id = tt % ntc[i] - elo[i];
+        tt /= ntc[i];
         blo[d] = g->lo[d] + (double)id * c->dl[d];
         bhi[d] = g->lo[d] + (double)(id + 1) * c->dl[d];
       }
@@ -664,7 +720,11 @@ int or_step(or_ctx* c, int nsteps) {
         S[7 * nc + k] += ratio_of(g, &mm);
       }
     }
-    if (sample) c->nsamp += 1;
+    if (sample) {
+      c->nsamp += 1;
+      c->surf_time += dtG;
+    }
+    c->sampling_now = sample;
     /* Step 2 of the next interval: move, remove, inject. */
     int64_t cap = Mn + 1024, n = 0;
     part* buf = (part*)malloc(sizeof(part) * cap);
@@ -765,6 +825,13 @@ int or_get_sample(const or_ctx* c, double* out, int64_t* nsamp) {
   if (nsamp) *nsamp = c->nsamp;
   return OR_OK;
 }
+int or_get_surface(const or_ctx* c, double* out, double* time) {
+  int ns = c->cfg.n_surf;
+  if (out && ns > 0) memcpy(out, c->surf, sizeof(double) * 7 * ns);
+  if (time) *time = c->surf_time;
+  return OR_OK;
+}
+
 int or_get_totals(const or_ctx* c, int64_t* out4) {
   memcpy(out4, c->totals, sizeof c->totals);
   return OR_OK;

@@ -52,6 +52,7 @@ typedef struct or_config {
   uint64_t seed;
   int32_t mode;           /* OR_MODE_*                                            */
   int32_t ar_max;         /* Shakhov acceptance-rejection attempt cap             */
+  int32_t n_surf;         /* surface elements of the body (0: no surface tallies) */
 } or_config;
 
 typedef struct or_ctx or_ctx;
@@ -81,6 +82,14 @@ int or_get_sigc_max(const or_ctx* c, double* out);
 int or_get_sample(const or_ctx* c, double* out /* [8][ncells] */, int64_t* nsamp);
 double or_dt(const or_ctx* c);
 int64_t or_step_index(const or_ctx* c);
+/* Surface tallies of the body over the sampled steps: out [7][n_surf] =
+ * (hits, momentum given to the wall x, y, z, energy given to the wall,
+ * momentum given along the inward normal, momentum given along e_theta),
+ * time = sampled time.  Element b of a circle spans polar angle
+ * theta = atan2(n_y, n_x) in [-pi + 2 pi b/n, -pi + 2 pi (b+1)/n); of a
+ * sphere, theta = acos(n_x) in [pi b/n, pi (b+1)/n).  e_theta is the unit
+ * direction of increasing theta at the hit point (zero on a sphere's axis). */
+int or_get_surface(const or_ctx* c, double* out, double* time);
 /* counters over the whole run: removed, injected, move_capped, ar_capped */
 int or_get_totals(const or_ctx* c, int64_t* out4);
 void or_free(or_ctx* c);

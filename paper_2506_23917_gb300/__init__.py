@@ -43,14 +43,14 @@ class SpConfig(C.Structure):
         ("body", C.c_int32), ("body_c", C.c_double * 3), ("body_r", C.c_double),
         ("body_Tw", C.c_double), ("cell_volume", C.POINTER(C.c_double)),
         ("sigc_T0", C.c_double), ("n_steady", C.c_int32), ("seed", C.c_uint64),
-        ("mode", C.c_int32), ("ar_max", C.c_int32),
+        ("mode", C.c_int32), ("ar_max", C.c_int32), ("n_surf", C.c_int32),
     ]
 
 
 SYMBOLS = ["sp_init", "sp_set_particles", "sp_step", "sp_moments", "sp_get_particles",
            "sp_set_record", "sp_get_step_record", "sp_get_cell_start", "sp_get_sigc_max",
-           "sp_get_dt", "sp_errors", "sp_sync", "sp_step_profiled", "sp_set_schedule", "sp_set_reproducible", "sp_autotune", "sp_launches_per_step", "sp_free",
-           "sp_status_str", "sp_sort_cells_static"]
+           "sp_get_dt", "sp_get_surface", "sp_errors", "sp_sync", "sp_step_profiled", "sp_set_schedule", "sp_set_reproducible", "sp_autotune", "sp_launches_per_step", "sp_free",
+           "sp_status_str", "sp_sort_cells_static", "sp_surface_coefficients"]
 
 _lib = None
 
@@ -74,6 +74,7 @@ def lib():
         L.sp_get_sigc_max.argtypes = [P, C.c_int, P]
         L.sp_get_dt.argtypes = [P, C.c_int, P, P]
         L.sp_errors.argtypes = [P, P]
+        L.sp_get_surface.argtypes = [P, C.c_int, P, P]
         L.sp_sync.argtypes = [P]
         L.sp_step_profiled.argtypes = [P, C.c_int, P, C.c_int]
         L.sp_set_schedule.argtypes = [P, C.c_int, C.c_int]
@@ -82,6 +83,8 @@ def lib():
         L.sp_launches_per_step.argtypes = [P]
         L.sp_free.argtypes = [P]
         L.sp_sort_cells_static.argtypes = [P, C.c_int64, C.c_int64, P, P, P]
+        L.sp_surface_coefficients.argtypes = [C.POINTER(SpConfig), P, C.c_double, C.c_double,
+                                              C.c_double, C.c_double, P, P]
         L.sp_status_str.argtypes = [C.c_int]
         L.sp_status_str.restype = C.c_char_p
         _lib = L
@@ -126,7 +129,27 @@ def make_config(cfg: dict):
     s.seed = cfg["seed"]
     s.mode = cfg["mode"]
     s.ar_max = cfg["ar_max"]
+    s.n_surf = int(cfg.get("n_surf", 0))
     return s, keep
+
+
+SURF_FIELDS = 7
+
+
+def surface_coefficients(cfg: dict, tallies, time, rho_inf, u_inf, p_inf):
+    """sp_surface_coefficients: per element (A, Cp, Cf, Ch) as [4][n_surf]
+    and body dict(Cd, CL, Ch, A_ref)."""
+    s, keep = make_config(cfg)
+    ns = int(cfg.get("n_surf", 0))
+    tal = np.ascontiguousarray(tallies, dtype=np.float64)
+    if tal.shape != (SURF_FIELDS, ns):
+        raise ValueError(f"tallies must be [{SURF_FIELDS}][{ns}]")
+    elem = np.zeros((4, max(ns, 1)))
+    body = np.zeros(4)
+    _chk("sp_surface_coefficients",
+         lib().sp_surface_coefficients(C.byref(s), _ptr(tal), float(time), float(rho_inf), float(u_inf),
+                                       float(p_inf), _ptr(elem), _ptr(body)))
+    return elem[:, :ns], dict(Cd=body[0], CL=body[1], Ch=body[2], A_ref=body[3])
 
 
 def current_stream():
@@ -265,6 +288,16 @@ class Sim:
         step = np.zeros(1, dtype=np.int64)
         _chk("sp_get_dt", lib().sp_get_dt(self.h, 0, _ptr(dt), _ptr(step)))
         return int(step[0])
+
+    def surface(self, inst=0):
+        """(tallies [7][n_surf]: hits, momentum to the wall x/y/z, energy to
+        the wall, momentum along the inward normal, momentum along e_theta;
+        sampled time)."""
+        ns = int(self.cfgs[inst].get("n_surf", 0))
+        out = np.zeros((SURF_FIELDS, max(ns, 1)))
+        t = np.zeros(1)
+        _chk("sp_get_surface", lib().sp_get_surface(self.h, inst, _ptr(out), _ptr(t)))
+        return out[:, :ns], float(t[0])
 
     def errors(self):
         out = np.zeros(5, dtype=np.int64)

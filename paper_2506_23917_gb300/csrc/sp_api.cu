@@ -50,6 +50,9 @@ struct sp_ctx {
   int nsm = 1;
   int sched_cap = kCapSmall, sched_warps = kWarpsDefault;
   int stable = 1;
+  double* surf = nullptr;       // [elements][kSurfFields] wall tallies
+  double* surf_time = nullptr;  // [n_inst] sampled time
+  int64_t n_surf_tot = 0;
   double *vol = nullptr, *smax = nullptr, *samp = nullptr;
   int32_t* rec = nullptr;
   uint8_t* resamp = nullptr;
@@ -135,6 +138,8 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
   P->ar_max = c.ar_max < 1 ? 1 : c.ar_max;
   P->cell_off = cell_off;
   P->ncells = (int64_t)P->n[0] * P->n[1] * P->n[2];
+  P->n_surf = (c.body != SP_BODY_NONE && c.n_surf > 0) ? c.n_surf : 0;
+  P->FnM = c.Fn * c.m;
   for (int d = 0; d < 3; ++d) {
     P->g64.lo[d] = P->lo[d];
     P->g64.hi[d] = P->hi[d];
@@ -182,11 +187,19 @@ void build_ghosts(const sp_config& c, const InstParams& P, int inst, std::vector
   for (int f = 0; f < 6; ++f) {
     const int ax = f / 2, side = f % 2;
     if (ax >= c.dim || c.face_bc[f] != SP_BC_INFLOW) continue;
-    int ta[2], nt = 0;
+    // tangential cells: the face's own, plus the corner blocks beyond each
+    // neighbouring inflow face (a particle is kept by the face it crosses)
+    int ta[2], nt = 0, elo[2] = {0, 0}, ntc[2] = {1, 1};
     for (int d = 0; d < c.dim; ++d)
       if (d != ax) ta[nt++] = d;
     int64_t ntan = 1;
-    for (int i = 0; i < nt; ++i) ntan *= P.n[ta[i]];
+    for (int i = 0; i < nt; ++i) {
+      const int d = ta[i];
+      elo[i] = c.face_bc[2 * d] == SP_BC_INFLOW ? c.ghost_layers : 0;
+      const int ehi = c.face_bc[2 * d + 1] == SP_BC_INFLOW ? c.ghost_layers : 0;
+      ntc[i] = P.n[d] + elo[i] + ehi;
+      ntan *= ntc[i];
+    }
     const int64_t ng = ntan * c.ghost_layers;
     const double RT = c.R * c.face_T[f];
     const double s2RT = sqrt(2.0 * RT);
@@ -204,8 +217,8 @@ void build_ghosts(const sp_config& c, const InstParams& P, int inst, std::vector
       int64_t tt = t;
       for (int i = 0; i < nt; ++i) {
         const int d = ta[i];
-        const int64_t id = tt % P.n[d];
-        tt /= P.n[d];
+        const int64_t id = tt % ntc[i] - elo[i];
+        tt /= ntc[i];
         G.blo[d] = c.lo[d] + (double)id * P.dl[d];
         G.bhi[d] = c.lo[d] + (double)(id + 1) * P.dl[d];
       }
@@ -259,6 +272,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.big_cap = c->prec == SP_FP64 ? kBigCap64 : kBigCap32;
   a.cap_small = c->sched_cap;
   a.stable = c->stable;
+  a.surf = c->n_surf_tot > 0 ? c->surf : nullptr;
   return a;
 }
 
@@ -281,6 +295,7 @@ InjectArgs make_inject_args(sp_ctx* c, int par) {
   a.Mcur = c->Mcur;
   a.err = c->err;
   a.cap = c->cap;
+  a.surf = c->n_surf_tot > 0 ? c->surf : nullptr;
   return a;
 }
 
@@ -339,7 +354,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   launch_cell_finalize(c->count, c->fill, c->NC, c->stream); ++n;
   launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
                        c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->nbatch,
-                       c->stream); ++n;
+                       c->surf_time, c->stream); ++n;
   if (ev) cudaEventRecord(ev[3], c->stream);
   launch_scatter(c->key, c->start, c->fill, c->perm, c->Mtot, c->cap, c->stream); ++n;
   if (ev) cudaEventRecord(ev[4], c->stream);
@@ -510,11 +525,14 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
   c->cap = capacity;
   c->cfg.assign(cfgs, cfgs + n_instances);
   c->hP.resize(n_instances);
-  int64_t off = 0;
+  int64_t off = 0, soff = 0;
   for (int i = 0; i < n_instances; ++i) {
     fill_params(cfgs[i], &c->hP[i], off);
     off += c->hP[i].ncells;
+    c->hP[i].surf_off = soff;
+    soff += c->hP[i].n_surf;
   }
+  c->n_surf_tot = soff;
   c->NC = off;
   if (c->NC >= (int64_t)0xFFFFFFF0) { delete c; return SP_ERR_ARG; }
   c->dstage.assign(n_instances, nullptr);
@@ -554,6 +572,8 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->dP, sizeof(InstParams) * n_instances));
     CK(dalloc(&c->dt_cur, 8 * n_instances));
     CK(dalloc(&c->dt_min, 8 * n_instances));
+    CK(dalloc(&c->surf, 8 * kSurfFields * std::max<int64_t>(c->n_surf_tot, 1)));
+    CK(dalloc(&c->surf_time, 8 * n_instances));
     CK(dalloc(&c->step_d, 4));
     CK(dalloc(&c->Mcur, 4));
     CK(dalloc(&c->Mtot, 4));
@@ -584,6 +604,8 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(cudaMemcpyAsync(c->vol, vol.data(), 8 * NC, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->smax, sm.data(), 8 * NC, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(c->samp, 0, 8 * 8 * NC, s));
+    CK(cudaMemsetAsync(c->surf, 0, 8 * kSurfFields * std::max<int64_t>(c->n_surf_tot, 1), s));
+    CK(cudaMemsetAsync(c->surf_time, 0, 8 * n_instances, s));
     CK(cudaMemsetAsync(c->step_d, 0, 4, s));
     CK(cudaMemsetAsync(c->big_count, 0, 4, s));
     CK(cudaMemsetAsync(c->ticket, 0, 4, s));
@@ -898,6 +920,94 @@ sp_status sp_get_dt(sp_ctx* c, int inst, double* dt, int64_t* step) {
   return SP_OK;
 }
 
+sp_status sp_get_surface(sp_ctx* c, int inst, double* out, double* time) {
+  if (!c || inst < 0 || inst >= c->n_inst) return SP_ERR_ARG;
+  const InstParams& P = c->hP[inst];
+  if (out && P.n_surf > 0) {
+    std::vector<double> h(kSurfFields * (size_t)P.n_surf);
+    CK(cudaMemcpyAsync(h.data(), c->surf + kSurfFields * P.surf_off, 8 * h.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < P.n_surf; ++b)
+      for (int f = 0; f < kSurfFields; ++f) out[(size_t)f * P.n_surf + b] = h[kSurfFields * (size_t)b + f];
+  }
+  if (time) {
+    CK(cudaMemcpyAsync(time, c->surf_time + inst, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return SP_OK;
+}
+
+sp_status sp_surface_coefficients(const sp_config* cfg, const double* tal, double time, double rho_inf,
+                                  double u_inf, double p_inf, double* elem, double* body) {
+  if (!cfg || !tal || !elem || !body) return SP_ERR_ARG;
+  const int ns = cfg->n_surf;
+  const double qinf = 0.5 * rho_inf * u_inf * u_inf;
+  const bool circle = cfg->body == SP_BODY_CIRCLE, sphere = cfg->body == SP_BODY_SPHERE;
+  if ((!circle && !sphere) || ns < 1 || !(time > 0) || !(qinf > 0) || !(cfg->body_r > 0))
+    return SP_ERR_ARG;
+  const double r = cfg->body_r, kPi = 3.14159265358979323846;
+  const double depth = circle ? cfg->hi[2] - cfg->lo[2] : 1.0;
+  auto inside = [&](const double* x) {
+    for (int d = 0; d < cfg->dim; ++d)
+      if (x[d] < cfg->lo[d] || x[d] > cfg->hi[d]) return false;
+    return true;
+  };
+  double Aref2 = 0, F[2] = {0, 0}, E = 0, Atot = 0;
+  for (int b = 0; b < ns; ++b) {
+    // area of the element inside the box, and its |n_x|-weighted area, by
+    // midpoint sub-sampling of the element
+    double A = 0, Ax = 0;
+    if (circle) {
+      const int K = 2048;
+      const double th0 = -kPi + 2.0 * kPi * b / ns, dth = 2.0 * kPi / ns / K;
+      for (int k = 0; k < K; ++k) {
+        const double th = th0 + (k + 0.5) * dth;
+        const double x[3] = {cfg->body_c[0] + r * cos(th), cfg->body_c[1] + r * sin(th), 0.0};
+        if (!inside(x)) continue;
+        A += r * dth * depth;
+        Ax += fabs(cos(th)) * r * dth * depth;
+      }
+    } else {
+      const int KT = 64, KP = 512;
+      const double th0 = kPi * b / ns, dth = kPi / ns / KT, dph = 2.0 * kPi / KP;
+      for (int i = 0; i < KT; ++i) {
+        const double th = th0 + (i + 0.5) * dth;
+        for (int j = 0; j < KP; ++j) {
+          const double ph = (j + 0.5) * dph;
+          const double x[3] = {cfg->body_c[0] + r * cos(th), cfg->body_c[1] + r * sin(th) * cos(ph),
+                               cfg->body_c[2] + r * sin(th) * sin(ph)};
+          if (!inside(x)) continue;
+          const double dA = r * r * sin(th) * dth * dph;
+          A += dA;
+          Ax += fabs(cos(th)) * dA;
+        }
+      }
+    }
+    elem[0 * (size_t)ns + b] = A;
+    if (A > 0) {
+      const double at = A * time;
+      elem[1 * (size_t)ns + b] = (tal[5 * (size_t)ns + b] / at - p_inf) / qinf;
+      elem[2 * (size_t)ns + b] = tal[6 * (size_t)ns + b] / at / qinf;
+      elem[3 * (size_t)ns + b] = tal[4 * (size_t)ns + b] / at / (qinf * u_inf);
+    } else {
+      elem[1 * (size_t)ns + b] = elem[2 * (size_t)ns + b] = elem[3 * (size_t)ns + b] = 0.0;
+    }
+    Aref2 += Ax;
+    Atot += A;
+    F[0] += tal[1 * (size_t)ns + b];
+    F[1] += tal[2 * (size_t)ns + b];
+    E += tal[4 * (size_t)ns + b];
+  }
+  const double Aref = 0.5 * Aref2;
+  if (!(Aref > 0)) return SP_ERR_ARG;
+  body[0] = F[0] / time / (qinf * Aref);
+  body[1] = F[1] / time / (qinf * Aref);
+  body[2] = E / time / (qinf * u_inf * Atot);
+  body[3] = Aref;
+  return SP_OK;
+}
+
 sp_status sp_errors(sp_ctx* c, int64_t* out5) {
   if (!c || !out5) return SP_ERR_ARG;
   unsigned long long h[kNumErr];
@@ -917,7 +1027,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

@@ -119,7 +119,10 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                                 unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                                 uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                                 const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                                uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch) {
+                                uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch,
+                                double* surf_time) {
+  const uint32_t st = *step;  // index of the step that just ran (read by all first)
+  __syncthreads();
   if (threadIdx.x == 0) {
     const uint32_t inj = n_ghost > 0 ? goff[n_ghost - 1] + gcount[n_ghost - 1] : 0u;
     const uint32_t old = *Mcur;
@@ -132,6 +135,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
   }
   for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
     const unsigned long long inf = 0x7FF0000000000000ull;
+    if ((int64_t)st >= (int64_t)P[i].n_steady) surf_time[i] += dt_cur[i];
     if (P[i].dt_fixed > 0) {
       dt_cur[i] = P[i].dt_fixed;
     } else if (dt_min[i] != inf) {
@@ -226,9 +230,10 @@ void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                           uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                           const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                          uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch, cudaStream_t s) {
+                          uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch,
+                          double* surf_time, cudaStream_t s) {
   k_step_finalize<<<1, 256, 0, s>>>(P, n_inst, dt_cur, dt_min, step, Mcur, Mtot, start_new, NC,
-                                    goff, gcount, n_ghost, big_count, ticket, nbatch);
+                                    goff, gcount, n_ghost, big_count, ticket, nbatch, surf_time);
 }
 
 }  // namespace sp

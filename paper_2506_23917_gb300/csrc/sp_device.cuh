@@ -197,9 +197,9 @@ __device__ __forceinline__ void diffuse_sample(T RTw, Uni<T>& r, T* cn, T* t1, T
 // Moves one particle for time trem.  Returns true when it left the domain.
 // Draw stream of bounce b: (step, sa, sb, purpose<<24 | subbase + 2b).
 template <class T, int DIM>
-__device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t step,
-                              uint32_t purpose, uint32_t sa, uint32_t sb, uint32_t subbase,
-                              unsigned long long* err) {
+__device__ bool move_particle(const InstParams& P, double* surf_all, T* x, T* v, T trem,
+                              uint32_t step, uint32_t purpose, uint32_t sa, uint32_t sb,
+                              uint32_t subbase, unsigned long long* err) {
   const Geo<T>& G = geo<T>(P);
   for (int bounce = 0;; ++bounce) {
     if (bounce >= kMaxBounce) {
@@ -280,8 +280,48 @@ __device__ bool move_particle(const InstParams& P, T* x, T* v, T trem, uint32_t 
       Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
       T cn, t1, t2;
       diffuse_sample<T>(G.body_RT, r, &cn, &t1, &t2);
+      const T vin0 = v[0], vin1 = v[1], vin2 = v[2];
 #pragma unroll
       for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
+      if (surf_all != nullptr && P.n_surf > 0 && (int64_t)step >= (int64_t)P.n_steady) {
+        // momentum and energy the wall receives from this hit (FP64 tallies)
+        double frac;
+        if (P.body == 1) {
+          frac = ((double)atan2(nv[1], nv[0]) + kPi) / (2.0 * kPi);
+        } else {
+          const double cx = (double)nv[0] < -1.0 ? -1.0 : ((double)nv[0] > 1.0 ? 1.0 : (double)nv[0]);
+          frac = acos(cx) / kPi;
+        }
+        int bin = (int)floor(frac * (double)P.n_surf);
+        if (bin < 0) bin = 0;
+        if (bin > P.n_surf - 1) bin = P.n_surf - 1;
+        double* t = surf_all + kSurfFields * (P.surf_off + bin);
+        const double ein = (double)vin0 * vin0 + (double)vin1 * vin1 + (double)vin2 * vin2;
+        const double eout = (double)v[0] * v[0] + (double)v[1] * v[1] + (double)v[2] * v[2];
+        const double dp0 = P.FnM * ((double)vin0 - (double)v[0]);
+        const double dp1 = P.FnM * ((double)vin1 - (double)v[1]);
+        const double dp2 = P.FnM * ((double)vin2 - (double)v[2]);
+        // direction of increasing polar angle at the hit point
+        double et0 = 0, et1 = 0, et2 = 0;
+        if (P.body == 1) {
+          et0 = -(double)nv[1];
+          et1 = (double)nv[0];
+        } else {
+          const double sn = sqrt((double)nv[1] * nv[1] + (double)nv[2] * nv[2]);
+          if (sn > 0) {
+            et0 = -sn;
+            et1 = (double)nv[0] * nv[1] / sn;
+            et2 = (double)nv[0] * nv[2] / sn;
+          }
+        }
+        atomicAdd(t + 0, 1.0);
+        atomicAdd(t + 1, dp0);
+        atomicAdd(t + 2, dp1);
+        atomicAdd(t + 3, dp2);
+        atomicAdd(t + 4, 0.5 * P.FnM * (ein - eout));
+        atomicAdd(t + 5, -(dp0 * nv[0] + dp1 * nv[1] + dp2 * nv[2]));
+        atomicAdd(t + 6, dp0 * et0 + dp1 * et1 + dp2 * et2);
+      }
       continue;
     }
     // (static indices only: x and v stay in registers)
@@ -930,8 +970,8 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
 #pragma unroll
         for (int d = 0; d < DIM; ++d) x[d] = xr[u][d];
         T v[3] = {svx[s], svy[s], svz[s]};
-        const bool gone = move_particle<T, DIM>(P, x, v, ct->dt[c], step, kPurpWall, (uint32_t)ct->kl[c],
-                                                (uint32_t)(s - ct->off[c]), 0u, a.err);
+        const bool gone = move_particle<T, DIM>(P, a.surf, x, v, ct->dt[c], step, kPurpWall,
+                                                (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), 0u, a.err);
         if (!gone) key = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) Bx[d][p0 + s] = x[d];
@@ -1066,7 +1106,7 @@ __global__ void k_inject(InjectArgs a, int pass) {
       }
       if (ok) {
         x[ax] = face;
-        ok = !move_particle<T, DIM>(P, x, v, dt - te, step, kPurpInjWall, G.gc, (uint32_t)m,
+        ok = !move_particle<T, DIM>(P, a.surf, x, v, dt - te, step, kPurpInjWall, G.gc, (uint32_t)m,
                                     (uint32_t)G.face << 16, a.err);
       }
     }

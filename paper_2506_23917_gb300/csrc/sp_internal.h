@@ -8,6 +8,7 @@ namespace sp {
 
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // key of a removed particle
 constexpr int kMaxBounce = 16;               // wall events per particle per step
+constexpr int kSurfFields = 7;  // wall tallies per surface element
 constexpr int64_t kNcolCap = int64_t(1) << 24;
 constexpr int kMaxWarpsPerBlock = 8;         // collide kernel block size limit
 constexpr int kCapSmall = 512;               // default per-warp staging capacity (particles)
@@ -49,6 +50,9 @@ struct InstParams {
   int ar_max;
   int64_t cell_off;  // first global cell of the instance
   int64_t ncells;
+  int n_surf;        // surface elements of the body (0: no tallies)
+  int64_t surf_off;  // first element in the context's tally array
+  double FnM;        // F_N m: weight of one hit in the tallies
   Geo<double> g64;
   Geo<float> g32;
 };
@@ -96,6 +100,7 @@ struct StepArgs {
   int big_cap;          // staging capacity of the big-cell launch
   int cap_small;        // staging capacity per warp of the main launch
   int stable;           // restore source order within cells (reproducible runs)
+  double* surf;         // [elements][kSurfFields] wall tallies
 };
 
 struct InjectArgs {
@@ -113,6 +118,7 @@ struct InjectArgs {
   const uint32_t* Mcur; // particles of the current state (base of appends)
   unsigned long long* err;
   int64_t cap;
+  double* surf;
 };
 
 // Launch wrappers, one set per precision (sp_kern_f64.cu, sp_kern_f32.cu).
@@ -146,7 +152,8 @@ void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
                           uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                           const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
-                          uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch, cudaStream_t s);
+                          uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch,
+                          double* surf_time, cudaStream_t s);
 int64_t scan_partial_size(int64_t n);
 
 }  // namespace sp

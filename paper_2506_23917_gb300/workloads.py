@@ -73,6 +73,7 @@ def base_config(dim, n, lo, hi):
         face_u=[[0.0, 0.0, 0.0] for _ in range(6)], ghost_layers=1,
         body=BODY_NONE, body_c=[0.0, 0.0, 0.0], body_r=0.0, body_Tw=1.0,
         cell_volume=None, sigc_T0=1.0, n_steady=0, seed=1, mode=MODE_HYBRID, ar_max=64,
+        n_surf=0,
     )
 
 
@@ -322,7 +323,7 @@ def cylinder(scale=1.0, ppc=40.0, Kn=0.01, Ma=5.0, seed=1, n_steady=1000, T_inf=
     cfg.update(m=m, R=R_gas, omega=omega, T_ref=T_ref, d_ref=d_ref,
                mu_ref=vhs_mu_ref(m, d_ref, T_ref, omega), Fn=n_inf * V0 / ppc, cfl=0.5,
                sigc_T0=T_inf, seed=seed, n_steady=n_steady, ghost_layers=ghost_layers,
-               body=BODY_CIRCLE, body_c=[0.0, 0.0, 0.0], body_r=Rb, body_Tw=T_inf)
+               body=BODY_CIRCLE, body_c=[0.0, 0.0, 0.0], body_r=Rb, body_Tw=T_inf, n_surf=360)
     fb = [BC_INFLOW, BC_OUTFLOW, BC_SPECULAR, BC_INFLOW, BC_SPECULAR, BC_SPECULAR]
     cfg["face_bc"] = fb
     cfg["face_T"] = [T_inf] * 6
@@ -350,7 +351,7 @@ def sphere(scale=1.0, ppc=30.0, Kn=0.005, Ma=10.0, seed=1, n_steady=750, T_inf=6
     cfg.update(m=m, R=R_gas, omega=omega, T_ref=T_ref, d_ref=d_ref,
                mu_ref=vhs_mu_ref(m, d_ref, T_ref, omega), Fn=n_inf * V0 / ppc, cfl=0.5,
                sigc_T0=T_inf, seed=seed, n_steady=n_steady, body=BODY_SPHERE,
-               body_c=[0.0, 0.0, 0.0], body_r=Rb, body_Tw=Tw_ratio * T_inf)
+               body_c=[0.0, 0.0, 0.0], body_r=Rb, body_Tw=Tw_ratio * T_inf, n_surf=90)
     fb = [BC_INFLOW, BC_OUTFLOW, BC_SPECULAR, BC_INFLOW, BC_INFLOW, BC_INFLOW]
     cfg["face_bc"] = fb
     cfg["face_T"] = [T_inf] * 6

@@ -68,6 +68,20 @@ def compare_record(o, s, inst=0, what=""):
     return c_o
 
 
+def compare_surface(o, s, inst=0, what=""):
+    """Body wall tallies: hit counts exact, momentum and energy given to the
+    wall within the tolerance (the device adds them with atomics, in any
+    order), and the sampled time."""
+    to, t_o = o.surface()
+    ts, t_s = s.surface(inst)
+    assert to.shape == ts.shape and to.shape[1] > 0
+    np.testing.assert_array_equal(ts[0], to[0], err_msg=what + " surface hits")
+    for k in range(1, 5):
+        _close(ts[k], to[k], what=f"{what} surface tally {k}")
+    _close([t_s], [t_o], what=what + " surface time")
+    return to
+
+
 def run_pair(sp, cfg, pos, vel, steps, capacity=None):
     o = oracle.Oracle(cfg)
     o.set_particles(pos, vel)
@@ -112,17 +126,23 @@ def test_big_cell_hybrid_matches_oracle(sp):
 
 def test_channel_with_body_inflow_outflow_matches_oracle(sp):
     cfg, regions = W.box2d(nx=24, ny=12, ppc=30.0)
+    cfg.update(n_surf=24, n_steady=4)
     pos, vel = W.fill_regions(cfg, regions, 3)
     o, s, tot = run_pair(sp, cfg, pos, vel, steps=12)
     t = o.totals()
     assert t["injected"] > 0 and t["removed"] > 0
+    tal = compare_surface(o, s, what="channel")
+    assert tal[0].sum() > 100
 
 
 def test_sphere_box_matches_oracle(sp):
     cfg, regions = W.box3d(n=(12, 8, 8), ppc=12.0)
+    cfg.update(n_surf=12, n_steady=1)
     pos, vel = W.fill_regions(cfg, regions, 5)
     o, s, tot = run_pair(sp, cfg, pos, vel, steps=6)
     assert o.totals()["injected"] > 0
+    tal = compare_surface(o, s, what="sphere")
+    assert tal[0].sum() > 50
 
 
 @pytest.mark.parametrize("mode", [W.MODE_DSMC, W.MODE_SHAKHOV])
