@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--develop", type=int, default=600)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--scale", type=float, default=1.0)
-    p.add_argument("--config", default="cylinder", choices=["cylinder", "sphere", "sod"])
+    p.add_argument("--config", default="cylinder", choices=["cylinder", "sphere", "sod", "jet"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--profile-steps", type=int, default=40)
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--schedule", default=None,
+                   help="CAP,WARPS: fixed collision-kernel schedule instead of the autotuner")
     p.add_argument("--reproducible", action="store_true",
                    help="FP32: restore the source order inside cells in the timed run")
     p.add_argument("--batch-steps", type=int, default=200)
@@ -62,6 +64,9 @@ def workload_name(scale, config="cylinder"):
         return f"sphere3d_{n[0]}x{n[1]}x{n[2]}_ppc30_Ma10_Kn0.005_Tw4_argon_vhs"
     if config == "sod":
         return "sod1d_200cells_ppc500_62.5_lam1e-3_hardsphere"
+    if config == "jet":
+        nc = max(8, int(round(512 * scale)))
+        return f"jet2d_{nc}x{nc}_orifice_ppc500_plenum4x_Ma1_Kn0.02_n2like_vhs"
     nx, ny = max(4, int(round(600 * scale))), max(2, int(round(300 * scale)))
     return f"cylinder2d_{nx}x{ny}_ppc40_Ma5_Kn0.01_argon_vhs"
 
@@ -69,6 +74,8 @@ def workload_name(scale, config="cylinder"):
 def make_workload(W, config, scale, seed):
     if config == "sphere":
         cfg, regions = W.sphere(scale=scale, seed=seed, n_steady=0)
+    elif config == "jet":
+        cfg, regions = W.jet(scale=scale, seed=seed, n_steady=0)
     elif config == "sod":
         cfg, regions = W.sod(ncell=200, ppc_left=500.0, lam_left=1e-3, seed=seed, n_steady=0)
     else:
@@ -362,7 +369,11 @@ def main():
     sim.set_particles(0, pos, vel)
     sim.step(args.develop)
     sim.sync()
-    sched = sim.autotune(steps_per_trial=3) if not args.no_tune else None
+    if args.schedule:
+        sched = tuple(int(x) for x in args.schedule.split(","))
+        sim.set_schedule(*sched)
+    else:
+        sched = sim.autotune(steps_per_trial=3) if not args.no_tune else None
     sim.step(args.warmup)
     sim.sync()
     M0 = sim.count(0)
@@ -421,7 +432,8 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = bytes_collide / (collide_ms * 1e-3) / 1e9
     src_hash = kernel_source_hash()
-    tpp = collide_traffic(src_hash)
+    # the committed ncu figure covers the FP32 cylinder only
+    tpp = collide_traffic(src_hash) if (args.config == "cylinder" and prec == sp.FP32) else None
     step_ms = sum(prof) / args.profile_steps
     step_bytes = (2 * S + 8) * Mp
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

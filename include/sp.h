@@ -93,6 +93,13 @@ typedef struct sp_config {
   int32_t ar_max;         /* cap on Shakhov acceptance-rejection attempts    */
   int32_t n_surf;         /* surface elements of the body for wall tallies
                              (0: none); see sp_get_surface()                 */
+  /* Open window of each outflow / inflow face (an orifice): on the face's
+   * tangential axes (the other axes below dim, in increasing order) the face
+   * is open where win_lo <= x <= win_hi; an axis with win_lo >= win_hi is
+   * unrestricted (all zeros: the whole face is open).  The rest of the face
+   * is a diffuse wall at face_T, and the reservoir of a windowed inflow face
+   * spans the window plus ghost_layers cells on each side. */
+  double win_lo[6][2], win_hi[6][2];
 } sp_config;
 
 typedef struct sp_ctx sp_ctx;

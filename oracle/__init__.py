@@ -34,6 +34,7 @@ class OrConfig(C.Structure):
         ("body_Tw", C.c_double), ("cell_volume", C.POINTER(C.c_double)),
         ("sigc_T0", C.c_double), ("n_steady", C.c_int32), ("seed", C.c_uint64),
         ("mode", C.c_int32), ("ar_max", C.c_int32), ("n_surf", C.c_int32),
+        ("win_lo", (C.c_double * 2) * 6), ("win_hi", (C.c_double * 2) * 6),
     ]
 
 
@@ -110,6 +111,10 @@ def make_config(cfg: dict):
     s.mode = cfg["mode"]
     s.ar_max = cfg["ar_max"]
     s.n_surf = int(cfg.get("n_surf", 0))
+    for f in range(6):
+        for i in range(2):
+            s.win_lo[f][i] = cfg.get("win_lo", [[0.0, 0.0]] * 6)[f][i]
+            s.win_hi[f][i] = cfg.get("win_hi", [[0.0, 0.0]] * 6)[f][i]
     return s, keep
 
 

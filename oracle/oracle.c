@@ -45,6 +45,9 @@
  *     Where two inflow faces meet, each face's reservoir also covers the
  *     corner block beyond the other; a particle is kept only by the face it
  *     crosses first, so no phase-space region is injected twice.
+ *   - A face may be open only on a window (an orifice); the rest of it is a
+ *     diffuse wall at the face temperature, and the reservoir of a windowed
+ *     inflow face spans the window plus ghost_layers cells on each side.
  */
 #define _GNU_SOURCE
 #include "oracle.h"
@@ -348,6 +351,18 @@ static void diffuse_sample(const or_ctx* c, double Tw, uint32_t purpose, uint32_
   *t2 = s * sin(2.0 * M_PI * R3) * r4;
 }
 
+/* Whether the crossing point x of face f lies in the face's open window. */
+static int face_open(const or_config* g, int f, const double* x) {
+  int ax = f / 2, i = 0;
+  for (int d = 0; d < g->dim; ++d) {
+    if (d == ax) continue;
+    if (g->win_lo[f][i] < g->win_hi[f][i] && (x[d] < g->win_lo[f][i] || x[d] > g->win_hi[f][i]))
+      return 0;
+    ++i;
+  }
+  return 1;
+}
+
 static int move_particle(or_ctx* c, double* x, double* v, double trem, uint32_t purpose, uint32_t a,
                          uint32_t b, uint32_t subbase) {
   const or_config* g = &c->cfg;
@@ -459,6 +474,7 @@ static int move_particle(or_ctx* c, double* x, double* v, double trem, uint32_t 
     trem -= tf;
     int f = 2 * fa + fs;
     int bc = g->face_bc[f];
+    if ((bc == OR_BC_OUTFLOW || bc == OR_BC_INFLOW) && !face_open(g, f, x)) bc = OR_BC_DIFFUSE;
     if (bc == OR_BC_SPECULAR) {
       v[fa] = -v[fa];
     } else if (bc == OR_BC_DIFFUSE) {
@@ -607,9 +623,18 @@ static void inject(or_ctx* c, part** buf, uint32_t** keys, int64_t* n, int64_t* 
     int64_t ntan = 1;
     for (int i = 0; i < nt; ++i) {
       int d = ta[i];
-      elo[i] = g->face_bc[2 * d] == OR_BC_INFLOW ? g->ghost_layers : 0;
-      int ehi = g->face_bc[2 * d + 1] == OR_BC_INFLOW ? g->ghost_layers : 0;
-      ntc[i] = g->n[d] + elo[i] + ehi;
+      int64_t i0 = g->face_bc[2 * d] == OR_BC_INFLOW ? -(int64_t)g->ghost_layers : 0;
+      int64_t i1 = g->n[d] + (g->face_bc[2 * d + 1] == OR_BC_INFLOW ? g->ghost_layers : 0);
+      /* a windowed face: only the cells within ghost_layers of its window */
+      if (g->win_lo[f][i] < g->win_hi[f][i]) {
+        int64_t w0 = (int64_t)floor((g->win_lo[f][i] - g->lo[d]) / c->dl[d]) - g->ghost_layers;
+        int64_t w1 = (int64_t)ceil((g->win_hi[f][i] - g->lo[d]) / c->dl[d]) + g->ghost_layers;
+        if (w0 > i0) i0 = w0;
+        if (w1 < i1) i1 = w1;
+        if (i1 < i0) i1 = i0;
+      }
+      elo[i] = (int)-i0;
+      ntc[i] = (int)(i1 - i0);
       ntan *= ntc[i];
     }
     int64_t nghost = ntan * g->ghost_layers;
@@ -674,6 +699,7 @@ static void inject(or_ctx* c, part** buf, uint32_t** keys, int64_t* n, int64_t* 
         }
         if (!ok) continue;
         q.x[ax] = face;
+        if (!face_open(g, f, q.x)) continue; /* blocked by the face's wall part */
         if (move_particle(c, q.x, q.v, dt - te, PURP_INJWALL, (uint32_t)gc, (uint32_t)m,
                           (uint32_t)f << 16))
           continue;

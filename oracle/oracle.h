@@ -53,6 +53,11 @@ typedef struct or_config {
   int32_t mode;           /* OR_MODE_*                                            */
   int32_t ar_max;         /* Shakhov acceptance-rejection attempt cap             */
   int32_t n_surf;         /* surface elements of the body (0: no surface tallies) */
+  /* Open part of each outflow / inflow face: on the face's tangential axes
+   * (the other axes below dim, in increasing order) the face is open where
+   * win_lo <= x <= win_hi; an axis with win_lo >= win_hi is not restricted.
+   * Elsewhere the face is a diffuse wall at face_T (an orifice with lips). */
+  double win_lo[6][2], win_hi[6][2];
 } or_config;
 
 typedef struct or_ctx or_ctx;

@@ -167,6 +167,15 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
   P->g32.body_RT = (float)P->g64.body_RT;
   P->g32.sigc_coef = (float)P->sigc_coef;
   P->g32.sigc_exp = (float)P->sigc_exp;
+  P->face_win = 0;
+  for (int f = 0; f < 6; ++f)
+    for (int i = 0; i < 2; ++i) {
+      P->g64.win_lo[f][i] = c.win_lo[f][i];
+      P->g64.win_hi[f][i] = c.win_hi[f][i];
+      P->g32.win_lo[f][i] = (float)c.win_lo[f][i];
+      P->g32.win_hi[f][i] = (float)c.win_hi[f][i];
+      if (i < c.dim - 1 && c.win_lo[f][i] < c.win_hi[f][i]) P->face_win |= 1 << f;
+    }
 }
 
 bool valid(const sp_config& c, int dim) {
@@ -195,9 +204,17 @@ void build_ghosts(const sp_config& c, const InstParams& P, int inst, std::vector
     int64_t ntan = 1;
     for (int i = 0; i < nt; ++i) {
       const int d = ta[i];
-      elo[i] = c.face_bc[2 * d] == SP_BC_INFLOW ? c.ghost_layers : 0;
-      const int ehi = c.face_bc[2 * d + 1] == SP_BC_INFLOW ? c.ghost_layers : 0;
-      ntc[i] = P.n[d] + elo[i] + ehi;
+      int64_t i0 = c.face_bc[2 * d] == SP_BC_INFLOW ? -(int64_t)c.ghost_layers : 0;
+      int64_t i1 = P.n[d] + (c.face_bc[2 * d + 1] == SP_BC_INFLOW ? c.ghost_layers : 0);
+      if (c.win_lo[f][i] < c.win_hi[f][i]) {  // windowed face: near the window only
+        const int64_t w0 = (int64_t)floor((c.win_lo[f][i] - c.lo[d]) / P.dl[d]) - c.ghost_layers;
+        const int64_t w1 = (int64_t)ceil((c.win_hi[f][i] - c.lo[d]) / P.dl[d]) + c.ghost_layers;
+        i0 = std::max(i0, w0);
+        i1 = std::min(i1, w1);
+        if (i1 < i0) i1 = i0;
+      }
+      elo[i] = (int)-i0;
+      ntc[i] = (int)(i1 - i0);
       ntan *= ntc[i];
     }
     const int64_t ng = ntan * c.ghost_layers;

@@ -180,6 +180,21 @@ __device__ __forceinline__ uint32_t cell_of(const InstParams& P, const T* x) {
   return idx[0] + (uint32_t)P.n[0] * (idx[1] + (uint32_t)P.n[1] * idx[2]);
 }
 
+// Whether the crossing point x of face f lies in the face's open window.
+template <class T, int DIM>
+__device__ __forceinline__ bool face_open(const Geo<T>& G, int f, const T* x) {
+  const int ax = f >> 1;
+  int i = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    if (d == ax) continue;
+    const T w0 = G.win_lo[f][i], w1 = G.win_hi[f][i];
+    if (w0 < w1 && (x[d] < w0 || x[d] > w1)) return false;
+    ++i;
+  }
+  return true;
+}
+
 // Diffuse re-emission at a wall with R T_w = RTw: normal speed
 // c_n = sqrt(-2 R T_w ln R1), tangential Box-Muller pair (R3, R4).
 template <class T>
@@ -332,7 +347,8 @@ __device__ bool move_particle(const InstParams& P, double* surf_all, T* x, T* v,
     }
     trem -= tf;
     const int f = 2 * fa + fs;
-    const int bc = P.face_bc[f];
+    int bc = P.face_bc[f];
+    if (bc >= 2 && ((P.face_win >> f) & 1) && !face_open<T, DIM>(G, f, x)) bc = 1;  // orifice lips
     if (bc == 0) {
 #pragma unroll
       for (int d = 0; d < DIM; ++d)
@@ -1106,6 +1122,9 @@ __global__ void k_inject(InjectArgs a, int pass) {
       }
       if (ok) {
         x[ax] = face;
+        if ((P.face_win >> G.face) & 1) ok = face_open<T, DIM>(GE, G.face, x);
+      }
+      if (ok) {
         ok = !move_particle<T, DIM>(P, a.surf, x, v, dt - te, step, kPurpInjWall, G.gc, (uint32_t)m,
                                     (uint32_t)G.face << 16, a.err);
       }

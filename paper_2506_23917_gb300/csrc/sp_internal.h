@@ -31,6 +31,7 @@ struct Geo {
   T face_RT[6];  // R * T_face
   T body_RT;     // R * T_wall of the body
   T sigc_coef, sigc_exp;
+  T win_lo[6][2], win_hi[6][2];  // open windows of outflow / inflow faces
 };
 
 // Per-instance constants, precomputed on the host.
@@ -41,6 +42,7 @@ struct InstParams {
   double m, R, gamma, Pr, omega, T_ref, mu_ref, Fn, cfl, dt_fixed;
   double sigc_coef, sigc_exp;  // sigma_T c_r = coef * c_r^exp
   int face_bc[6];
+  int face_win;      // bit f: face f is open only on its window
   double face_T[6];
   int body;
   double body_c[3], body_r, body_Tw;

@@ -73,7 +73,7 @@ def base_config(dim, n, lo, hi):
         face_u=[[0.0, 0.0, 0.0] for _ in range(6)], ghost_layers=1,
         body=BODY_NONE, body_c=[0.0, 0.0, 0.0], body_r=0.0, body_Tw=1.0,
         cell_volume=None, sigc_T0=1.0, n_steady=0, seed=1, mode=MODE_HYBRID, ar_max=64,
-        n_surf=0,
+        n_surf=0, win_lo=[[0.0, 0.0] for _ in range(6)], win_hi=[[0.0, 0.0] for _ in range(6)],
     )
 
 
@@ -331,6 +331,47 @@ def cylinder(scale=1.0, ppc=40.0, Kn=0.01, Ma=5.0, seed=1, n_steady=1000, T_inf=
     cfg["face_u"] = [[U, 0.0, 0.0] for _ in range(6)]
     cfg["cell_volume"] = circle_cut_volumes(cfg)
     regions = [dict(lo=[-3.0 * Rb, 0.0], hi=[3.0 * Rb, 3.0 * Rb], n=n_inf, T=T_inf, u=[U, 0, 0])]
+    return cfg, regions
+
+
+# A nitrogen-like monatomic VHS model: N2's mass, reference diameter and
+# viscosity exponent (Bird's tables) with a monatomic gamma of 5/3.
+NITROGEN_LIKE = dict(m=4.65e-26, d_ref=4.17e-10, T_ref=273.0, omega=0.74)
+
+
+def jet(scale=1.0, ppc=500.0, Kn=0.02, Ma=1.0, plenum=4.0, seed=1, n_steady=500, T0=300.0,
+        ghost_layers=3):
+    """2-D sonic jet expanding into vacuum (Sec. IV.C shape).
+
+    Orifice width w = 1 mm is the reference length; Kn = lambda_0 / w at the
+    orifice state n_0.  Domain [0, 8w] x [-4w, 4w] on a 512 x 512 grid at
+    scale 1 (cell w/64).  The left face is an inflow only on the orifice
+    |y| <= w/2 (Ma = 1 at n_0, T_0); the rest of it is a diffuse wall at T_0
+    (the lips).  The other faces are outflow to vacuum.  A plenum block
+    [0, w] x [-w, w] starts at plenum * n_0 and rest, and drains into the
+    vacuum, so per-cell occupancy spans 0 to ~plenum * ppc.
+    """
+    gas = NITROGEN_LIKE
+    m, d_ref, T_ref, omega = gas["m"], gas["d_ref"], gas["T_ref"], gas["omega"]
+    R_gas = KB / m
+    w = 1e-3
+    nc = max(8, int(round(512 * scale)))
+    cfg = base_config(2, [nc, nc], [0.0, -4.0 * w], [8.0 * w, 4.0 * w])
+    n0 = n_for_kn(Kn, w, d_ref, T_ref, T0, omega)
+    U = Ma * math.sqrt(5.0 / 3.0 * R_gas * T0)
+    dl = cell_size(cfg)
+    V0 = dl[0] * dl[1] * dl[2]
+    cfg.update(m=m, R=R_gas, omega=omega, T_ref=T_ref, d_ref=d_ref,
+               mu_ref=vhs_mu_ref(m, d_ref, T_ref, omega), Fn=n0 * V0 / ppc, cfl=0.5,
+               sigc_T0=T0, seed=seed, n_steady=n_steady, ghost_layers=ghost_layers)
+    fb = [BC_INFLOW, BC_OUTFLOW, BC_OUTFLOW, BC_OUTFLOW, BC_SPECULAR, BC_SPECULAR]
+    cfg["face_bc"] = fb
+    cfg["face_T"] = [T0] * 6
+    cfg["face_n"] = [n0, 0.0, 0.0, 0.0, 0.0, 0.0]
+    cfg["face_u"] = [[U, 0.0, 0.0] for _ in range(6)]
+    cfg["win_lo"][0] = [-0.5 * w, 0.0]
+    cfg["win_hi"][0] = [0.5 * w, 0.0]
+    regions = [dict(lo=[0.0, -w], hi=[w, w], n=plenum * n0, T=T0, u=[0.0, 0.0, 0.0])]
     return cfg, regions
 
 

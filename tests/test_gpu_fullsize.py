@@ -90,3 +90,32 @@ def test_full_size_fp32_graph_run_properties(sp, cyl):
         assert abs(np.mean(m[1][up]) / n_inf - 1) < 0.01
         assert abs(np.mean(m[2][up]) / U - 1) < 0.01
         assert abs(np.mean(m[5][up]) / 273.0 - 1) < 0.02
+
+
+def test_full_size_jet_uneven_occupancy(sp):
+    """Sonic jet, 512 x 512 grid: a plenum block at 2000 particles per cell
+    drains through the orifice region into vacuum, so occupancy spans 0 to
+    ~2000 per cell (cells above the per-warp staging capacity take the
+    big-cell launch).  FP32 (graph) and FP64 agree on the particle count and
+    on the density of the draining block."""
+    cfg, regions = W.jet(scale=1.0, n_steady=0)
+    pos, vel = W.fill_regions(cfg, regions, 3)
+    M0 = vel.shape[1]
+    assert M0 > 15_000_000
+    res = {}
+    for prec in (sp.FP32, sp.FP64):
+        s = sp.Sim(cfg, prec, capacity=int(1.2 * M0) + 500000)
+        s.set_particles(0, pos, vel)
+        occ = np.diff(s.cell_start(0).astype(np.int64))
+        assert occ.max() > 1500 and occ.min() == 0
+        s.step(100)
+        s.sync()
+        e = s.errors()
+        assert e["capacity"] == 0 and e["cell_cap"] == 0, e
+        res[prec] = (s.count(0), s.moments(0, 0))
+        s.close()
+    (n32, m32), (n64, m64) = res[sp.FP32], res[sp.FP64]
+    assert abs(n32 / n64 - 1) < 2e-3
+    dense = m64[1] > 0.5 * np.max(m64[1])
+    assert dense.sum() > 100
+    assert abs(np.sum(m32[1][dense]) / np.sum(m64[1][dense]) - 1) < 5e-3

@@ -145,6 +145,18 @@ def test_sphere_box_matches_oracle(sp):
     assert tal[0].sum() > 50
 
 
+def test_jet_orifice_matches_oracle(sp):
+    """Sonic jet: inflow only through an orifice window of the left face
+    (diffuse lips elsewhere), vacuum outflow, and a dense plenum block whose
+    cells exceed the per-warp staging capacity (big-cell launch)."""
+    cfg, regions = W.jet(scale=1.0 / 16, ppc=200.0, n_steady=2)
+    pos, vel = W.fill_regions(cfg, regions, 7)
+    o, s, tot = run_pair(sp, cfg, pos, vel, steps=6)
+    t = o.totals()
+    assert t["injected"] > 0 and t["removed"] > 0
+    assert np.diff(o.cell_start().astype(np.int64)).max() > 512
+
+
 @pytest.mark.parametrize("mode", [W.MODE_DSMC, W.MODE_SHAKHOV])
 def test_forced_modes_match_oracle(sp, mode):
     cfg, regions = W.sod(ncell=60, ppc_left=60.0, lam_left=1e-3, mode=mode)

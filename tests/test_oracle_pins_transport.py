@@ -10,6 +10,9 @@
   away from it;
 * the reservoir (ghost-cell) inflow injects, per unit area and time, the
   one-way flux of a drifting Maxwellian (Bird's textbook closed form);
+* a face open only on a window (an orifice) removes particles that cross it
+  inside the window and reflects the others diffusely, and a windowed
+  inflow face injects the one-way flux through the window's area only;
 * the sort is a stable counting sort by cell;
 * the analytic cut-cell volumes add up to the domain minus the body.
 """
@@ -146,6 +149,64 @@ def test_inflow_reservoir_flux_matches_drifting_maxwellian(Un_over_a):
     flux = n * (math.sqrt(T / (2 * math.pi)) * math.exp(-s * s) + 0.5 * Un * (1 + math.erf(s)))
     expect = flux * 1.0 * cfg["dt_fixed"] * steps / cfg["Fn"]
     assert abs(got - expect) < 4 * math.sqrt(expect) + 2
+
+
+def test_windowed_outflow_face_removes_inside_reflects_outside():
+    nc = 20
+    cfg = W.base_config(2, [nc, nc], [0.0, 0.0], [1.0, 1.0])
+    cfg.update(d_ref=1e-12, Fn=1.0, dt_fixed=0.1)
+    cfg["face_bc"] = [W.BC_OUTFLOW, W.BC_SPECULAR, W.BC_SPECULAR, W.BC_SPECULAR, 0, 0]
+    cfg["face_T"][0] = 1e-3  # slow re-emission: no second wall within the step
+    cfg["win_lo"][0] = [0.4, 0.0]
+    cfg["win_hi"][0] = [0.6, 0.0]
+    y = (np.arange(nc) + 0.5) / nc
+    pos = np.stack([np.full(nc, 0.02), y])
+    vel = np.zeros((3, nc))
+    vel[0] = -1.0
+    o = oracle.Oracle(cfg)
+    o.set_particles(pos, vel)
+    o.step(1)
+    inside = (y >= 0.4) & (y <= 0.6)
+    assert o.totals()["removed"] == int(inside.sum())
+    assert o.M == nc - int(inside.sum())
+    p, v, _ = o.particles()
+    # survivors were re-emitted from the wall part of the face (hit at
+    # t = 0.02, then 0.08 of free flight): moving away from it, hit point
+    # outside the window
+    assert np.all(v[0] > 0)
+    assert np.allclose(p[0], v[0] * 0.08, rtol=1e-9, atol=1e-12)
+    y_hit = p[1] - v[1] * 0.08
+    assert np.all((y_hit < 0.4) | (y_hit > 0.6))
+    assert np.allclose(np.sort(y_hit), np.sort(y[~inside]), atol=1e-12)
+
+
+@pytest.mark.parametrize("Un_over_a", [0.0, 1.0])
+def test_windowed_inflow_injects_through_window_only(Un_over_a):
+    nc, T, n = 40, 1.0, 1.0
+    cfg = W.base_config(2, [nc, nc], [0.0, 0.0], [1.0, 1.0])
+    cfg.update(d_ref=1e-12, Fn=1e-5, dt_fixed=0.002, ghost_layers=3)
+    cfg["face_bc"] = [W.BC_INFLOW, W.BC_OUTFLOW, W.BC_OUTFLOW, W.BC_OUTFLOW, 0, 0]
+    cfg["face_T"][0] = T
+    cfg["face_n"][0] = n
+    s2 = math.sqrt(2 * T)
+    Un = Un_over_a * s2
+    cfg["face_u"][0] = [Un, 0.0, 0.0]
+    cfg["win_lo"][0] = [0.25, 0.0]
+    cfg["win_hi"][0] = [0.5, 0.0]
+    o = oracle.Oracle(cfg)
+    o.set_particles(np.array([[0.9], [0.9]]), np.zeros((3, 1)))
+    steps = 30
+    o.step(steps)
+    got = o.totals()["injected"]
+    s = Un / s2
+    flux = n * (math.sqrt(T / (2 * math.pi)) * math.exp(-s * s) + 0.5 * Un * (1 + math.erf(s)))
+    expect = flux * 0.25 * cfg["dt_fixed"] * steps / cfg["Fn"]
+    assert abs(got - expect) < 4 * math.sqrt(expect) + 2
+    # every injected particle entered through the window
+    p, v, _ = o.particles()
+    fresh = p[0] < 0.9 - 1e-9
+    y0 = p[1][fresh] - v[1][fresh] * (p[0][fresh] / v[0][fresh])
+    assert np.all((y0 >= 0.25 - 1e-9) & (y0 <= 0.5 + 1e-9))
 
 
 def test_sort_is_stable_counting_sort():
