@@ -836,44 +836,92 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     nacc_i = ct->nacc[lane];
     a.smax[kc] = (double)ct->smax[lane];
   }
-  // ---- 6. Shakhov sub-step, all particles of the batch in parallel
-  for (int s = lane; s < M; s += 32) {
-    const int c = sseg[s];
-    const T Pres = ct->Pres[c];
-    if (!(Pres > (T)0)) continue;
-    const InstParams& P = a.P[ct->inst[c]];
-    const int slot = s - ct->off[c];
-    Uni<T> r(step, (uint32_t)ct->kl[c], (uint32_t)slot, kPurpShk << 24, P.key0, P.key1);
-    const T u0 = r.get(0);
-    if (!(u0 < Pres)) continue;
-    atomicAdd(&ct->nres[c], 1);
-    if (a.resamp) a.resamp[p0 + s] = 1;
-    const T RT = ct->RT[c], s2RT = ct->s2RT[c], Amax = ct->Amax[c], omp = ct->omp[c];
-    const T q0 = ct->q[0][c], q1 = ct->q[1][c], q2 = ct->q[2][c];
-    T C0 = 0, C1 = 0, C2 = 0;
-    int t = 0;
-    for (; t < P.ar_max; ++t) {
-      const T R1 = r.get(1 + 5 * t), R2 = r.get(2 + 5 * t), R3 = r.get(3 + 5 * t);
-      const T R4 = r.get(4 + 5 * t), R5 = r.get(5 + 5 * t);
-      const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
-      T sn3, cs3;
-      sincos2pi(R3, &sn3, &cs3);
-      C0 = s2RT * cos2pi(R1) * r2;
-      C1 = s2RT * cs3 * r4;
-      C2 = s2RT * sn3 * r4;
-      const T qC = q0 * C0 + q1 * C1 + q2 * C2;
-      const T CC = C0 * C0 + C1 * C1 + C2 * C2;
-      const T A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
-      if (R5 * Amax < A) break;
+  // ---- 6. Shakhov sub-step.  First the Bernoulli draw of every slot, with
+  // the resampled slots compacted into a list (stag is free after the DSMC
+  // loop); then the acceptance-rejection loops as a lane pool: a lane that
+  // finishes a particle takes the next one from the list, so the warp's
+  // iterations follow the total number of attempts instead of the slowest
+  // lane of every 32 slots.  Every draw is keyed by (cell, slot, attempt),
+  // so the order of the work changes no result.
+  if (__any_sync(kFull, shk)) {
+    int nlist = 0;
+    for (int sb = 0; sb < M; sb += 32) {
+      const int s = sb + lane;
+      bool res = false;
+      if (s < M) {
+        const int c = sseg[s];
+        const T Pres = ct->Pres[c];
+        if (Pres > (T)0) {
+          const InstParams& P = a.P[ct->inst[c]];
+          Uni<T> r(step, (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), kPurpShk << 24, P.key0, P.key1);
+          res = r.get(0) < Pres;
+        }
+      }
+      const unsigned bal = __ballot_sync(kFull, res);
+      if (res) {
+        stag[nlist + __popc(bal & ((1u << lane) - 1u))] = s;
+        atomicAdd(&ct->nres[sseg[s]], 1);
+        if (a.resamp) a.resamp[p0 + s] = 1;
+      }
+      nlist += __popc(bal);
     }
-    if (t == P.ar_max) {
-      t = P.ar_max - 1;
-      atomicAdd(&a.err[kErrAr], 1ull);
+    __syncwarp();
+    if (nlist > 0) {
+      int s = lane < nlist ? stag[lane] : -1;
+      int next = 32, t = 0, c = 0, armax = 1;
+      T RT = 0, s2RT = 0, Amax = 0, omp = 0, q0 = 0, q1 = 0, q2 = 0;
+      Uni<T> r(0u, 0u, 0u, 0u, 0u, 0u);
+      auto take = [&](int slot) {
+        s = slot;
+        t = 0;
+        if (s < 0) return;
+        c = sseg[s];
+        const InstParams& P = a.P[ct->inst[c]];
+        r = Uni<T>(step, (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), kPurpShk << 24, P.key0, P.key1);
+        armax = P.ar_max;
+        RT = ct->RT[c];
+        s2RT = ct->s2RT[c];
+        Amax = ct->Amax[c];
+        omp = ct->omp[c];
+        q0 = ct->q[0][c];
+        q1 = ct->q[1][c];
+        q2 = ct->q[2][c];
+      };
+      take(s);
+      while (__any_sync(kFull, s >= 0)) {
+        bool done = false;
+        if (s >= 0) {
+          const T R1 = r.get(1 + 5 * t), R2 = r.get(2 + 5 * t), R3 = r.get(3 + 5 * t);
+          const T R4 = r.get(4 + 5 * t), R5 = r.get(5 + 5 * t);
+          const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
+          T sn3, cs3;
+          sincos2pi(R3, &sn3, &cs3);
+          const T C0 = s2RT * cos2pi(R1) * r2;
+          const T C1 = s2RT * cs3 * r4;
+          const T C2 = s2RT * sn3 * r4;
+          const T qC = q0 * C0 + q1 * C1 + q2 * C2;
+          const T CC = C0 * C0 + C1 * C1 + C2 * C2;
+          const T A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
+          const bool acc = R5 * Amax < A;
+          if (acc || t == armax - 1) {
+            if (!acc) atomicAdd(&a.err[kErrAr], 1ull);
+            atomicAdd(&ct->nar[c], t + 1);
+            svx[s] = ct->U[0][c] + C0;
+            svy[s] = ct->U[1][c] + C1;
+            svz[s] = ct->U[2][c] + C2;
+            done = true;
+          } else {
+            ++t;
+          }
+        }
+        const unsigned fin = __ballot_sync(kFull, done);
+        if (done) {
+          const int idx = next + __popc(fin & ((1u << lane) - 1u));
+          take(idx < nlist ? stag[idx] : -1);
+        }
+        next += __popc(fin);
+      }
     }
-    atomicAdd(&ct->nar[c], t + 1);
-    svx[s] = ct->U[0][c] + C0;
-    svy[s] = ct->U[1][c] + C1;
-    svz[s] = ct->U[2][c] + C2;
   }
   __syncwarp();
   // ---- 7. conservation rescale c' = U + (c_p - U_p) sqrt(T/T_p)
@@ -1025,23 +1073,34 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
   uint32_t* sidx = (uint32_t*)(svz + cap);
   int* stag = (int*)(sidx + cap);
   uint8_t* sseg = (uint8_t*)(stag + cap);
-  if (!big) {
-    const uint32_t nb = *a.nbatch;
-    for (;;) {
+  // One call site of process_batch for both launches, so that every cell
+  // runs through the same inlined code (identical rounding whichever launch
+  // or batch takes it).  Main launch: batches from the plan's list by
+  // work stealing.  Big-cell launch: a block per cell of the big list.
+  const uint32_t nb = big ? *a.big_count : *a.nbatch;
+  uint32_t it = big ? blockIdx.x : 0u;
+  for (;;) {
+    int64_t k0;
+    int G;
+    if (!big) {
       uint32_t t = 0;
       if (lane == 0) t = atomicAdd(a.ticket, 1u);
       t = __shfl_sync(kFull, t, 0);
       if (t >= nb) break;
       const uint2 b = a.batches[t];
-      process_batch<T, DIM>(a, (int64_t)b.x, (int)b.y, ct, sidx, stag, sseg, svx, svy, svz);
+      k0 = (int64_t)b.x;
+      G = (int)b.y;
+    } else {
+      if (it >= nb) break;
+      k0 = (int64_t)a.big_list[it];
+      it += gridDim.x;
+      G = 1;
+      if ((int)(a.start[k0 + 1] - a.start[k0]) > cap) {
+        drop_cell(a, k0);
+        continue;
+      }
     }
-  } else {
-    const uint32_t nbig = *a.big_count;
-    for (uint32_t i = blockIdx.x; i < nbig; i += gridDim.x) {
-      const int64_t k = (int64_t)a.big_list[i];
-      if ((int)(a.start[k + 1] - a.start[k]) > cap) drop_cell(a, k);
-      else process_batch<T, DIM>(a, k, 1, ct, sidx, stag, sseg, svx, svy, svz);
-    }
+    process_batch<T, DIM>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
   }
 }
 
