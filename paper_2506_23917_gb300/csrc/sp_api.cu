@@ -45,7 +45,9 @@ struct sp_ctx {
   uint32_t *cell_inst = nullptr, *scan_part = nullptr, *big_list = nullptr, *big_count = nullptr;
   uint32_t* ticket = nullptr;
   uint2* batches = nullptr;
-  uint32_t* nbatch = nullptr;
+  uint32_t* nbatch = nullptr;         // [2] heavy / other batches of the plan
+  uint8_t* hot = nullptr;             // [NC] slow-batch flags of the last step
+  unsigned long long* cyc = nullptr;  // [3] batch-cycle sum, count, threshold
   int collide_grid = 1;
   int nsm = 1;
   int sched_cap = kCapSmall, sched_warps = kWarpsDefault;
@@ -283,6 +285,8 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.ticket = c->ticket;
   a.batches = c->batches;
   a.nbatch = c->nbatch;
+  a.hot = c->hot;
+  a.cyc = c->cyc;
   a.err = c->err;
   a.NC = c->NC;
   a.cap = c->cap;
@@ -353,7 +357,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   int n = 0;
   const StepArgs a = make_step_args(c, par);
   if (ev) cudaEventRecord(ev[0], c->stream);
-  launch_plan(c->start, c->NC, c->sched_cap, c->batches, c->nbatch, c->big_list, c->big_count, c->stream); ++n;
+  launch_plan(c->start, c->hot, c->NC, c->sched_cap, c->batches, c->nbatch, c->big_list, c->big_count, c->stream); ++n;
   launch_collide_p(c, a, false, small_grid(c)); ++n;
   launch_collide_p(c, a, true, 2 * 152); ++n;
   if (ev) cudaEventRecord(ev[1], c->stream);
@@ -371,7 +375,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   launch_cell_finalize(c->count, c->fill, c->NC, c->stream); ++n;
   launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
                        c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->nbatch,
-                       c->surf_time, c->stream); ++n;
+                       c->surf_time, c->cyc, c->stream); ++n;
   if (ev) cudaEventRecord(ev[3], c->stream);
   launch_scatter(c->key, c->start, c->fill, c->perm, c->Mtot, c->cap, c->stream); ++n;
   if (ev) cudaEventRecord(ev[4], c->stream);
@@ -582,7 +586,9 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->big_count, 4));
     CK(dalloc(&c->ticket, 4));
     CK(dalloc(&c->batches, sizeof(uint2) * NC));
-    CK(dalloc(&c->nbatch, 4));
+    CK(dalloc(&c->nbatch, 8));
+    CK(dalloc(&c->hot, std::max<int64_t>(NC, 1)));
+    CK(dalloc(&c->cyc, 24));
     CK(dalloc(&c->vol, 8 * NC));
     CK(dalloc(&c->smax, 8 * NC));
     CK(dalloc(&c->samp, 8 * 8 * NC));
@@ -626,7 +632,10 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(cudaMemsetAsync(c->step_d, 0, 4, s));
     CK(cudaMemsetAsync(c->big_count, 0, 4, s));
     CK(cudaMemsetAsync(c->ticket, 0, 4, s));
-    CK(cudaMemsetAsync(c->nbatch, 0, 4, s));
+    CK(cudaMemsetAsync(c->nbatch, 0, 8, s));
+    CK(cudaMemsetAsync(c->hot, 0, std::max<int64_t>(c->NC, 1), s));
+    CK(cudaMemsetAsync(c->cyc, 0, 16, s));
+    CK(cudaMemsetAsync(c->cyc + 2, 0xFF, 8, s));
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -756,13 +765,15 @@ sp_status sp_autotune(sp_ctx* c, int steps_per_trial, int* cap_out, int* warps_o
   for (int ci : caps)
     for (int wi : warps) {
       if (!apply_schedule(c, ci, wi)) continue;
+      // one untimed step first: the batch partition changes with the
+      // schedule, and the heavy-batch flags of the old one are stale
       float tot = 0;
-      for (int it = 0; it < steps_per_trial; ++it) {
+      for (int it = 0; it <= steps_per_trial; ++it) {
         enqueue_step(c, c->cur, ev);
         CK(cudaEventSynchronize(ev[4]));
         float t = 0;
         CK(cudaEventElapsedTime(&t, ev[0], ev[1]));
-        tot += t;
+        if (it > 0) tot += t;
         c->cur ^= 1;
         c->step_host += 1;
       }
@@ -1044,7 +1055,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

@@ -120,7 +120,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                                 uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                                 const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
                                 uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch,
-                                double* surf_time) {
+                                double* surf_time, unsigned long long* cyc) {
   const uint32_t st = *step;  // index of the step that just ran (read by all first)
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -131,7 +131,12 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
     *step = *step + 1u;
     *big_count = 0u;
     *ticket = 0u;
-    *nbatch = 0u;
+    nbatch[0] = 0u;
+    nbatch[1] = 0u;
+    // batches slower than 2.5x this step's mean are planned first next step
+    cyc[2] = cyc[1] > 0 ? (cyc[0] / cyc[1]) * 5ull / 2ull : ~0ull;
+    cyc[0] = 0ull;
+    cyc[1] = 0ull;
   }
   for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
     const unsigned long long inf = 0x7FF0000000000000ull;
@@ -146,11 +151,14 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 }
 // Work plan of a step: consecutive cells are grouped into batches whose
 // particles fit a warp's staging area (at most 32 cells each); cells above
-// it go to the big-cell list.  One warp per 32-cell chunk; batches of a
-// chunk are appended to a global list (their order does not matter: batches
-// are independent).
-__global__ void k_plan(const uint32_t* start, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
-                       uint32_t* big_list, uint32_t* big_count) {
+// it go to the big-cell list.  One warp per 32-cell chunk.  Batches holding
+// a cell flagged hot (its batch was slow in the previous step: dense cells
+// with many collisions and resamplings) are listed from the front of the
+// array, the others from the back; the collision kernel hands out the front
+// ones first, so slow batches do not start last and leave SMs idle at the
+// end of the launch.  Batches are independent: their order changes no result.
+__global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches,
+                       uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nchunks = (NC + 31) / 32;
@@ -164,8 +172,10 @@ __global__ void k_plan(const uint32_t* start, int64_t NC, int cap, uint2* batche
       const int y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
       if (lane >= o) cum += y;
     }
+    const unsigned hmask = __ballot_sync(0xFFFFFFFFu, lane < nc && hot[c0 + lane] != 0);
     int kk = 0, nb = 0;
     uint2 mine = make_uint2(0, 0);
+    bool mine_hot = false;
     while (kk < nc) {
       const int before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
       const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap);
@@ -178,26 +188,39 @@ __global__ void k_plan(const uint32_t* start, int64_t NC, int cap, uint2* batche
         kk += 1;
         continue;
       }
-      if (lane == nb) mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
+      if (lane == nb) {
+        mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
+        const unsigned gm = G >= 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
+        mine_hot = ((hmask >> kk) & gm) != 0u;
+      }
       ++nb;
       kk += G;
     }
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(nbatch, (uint32_t)nb);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (lane < nb) batches[base + lane] = mine;
+    const bool have = lane < nb;
+    const unsigned hb = __ballot_sync(0xFFFFFFFFu, have && mine_hot);
+    const unsigned nbm = __ballot_sync(0xFFFFFFFFu, have && !mine_hot);
+    uint32_t bh = 0, bn = 0;
+    if (lane == 0) {
+      if (hb) bh = atomicAdd(&nbatch[0], (uint32_t)__popc(hb));
+      if (nbm) bn = atomicAdd(&nbatch[1], (uint32_t)__popc(nbm));
+    }
+    bh = __shfl_sync(0xFFFFFFFFu, bh, 0);
+    bn = __shfl_sync(0xFFFFFFFFu, bn, 0);
+    const unsigned below = (1u << lane) - 1u;
+    if (have && mine_hot) batches[bh + __popc(hb & below)] = mine;
+    if (have && !mine_hot) batches[NC - 1 - (int64_t)(bn + __popc(nbm & below))] = mine;
   }
 }
 
 }  // namespace
 
-void launch_plan(const uint32_t* start, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
                  uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
   const int64_t chunks = (NC + 31) / 32;
   int64_t g = (chunks + 7) / 8;
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
-  k_plan<<<(unsigned)g, 256, 0, s>>>(start, NC, cap, batches, nbatch, big_list, big_count);
+  k_plan<<<(unsigned)g, 256, 0, s>>>(start, hot, NC, cap, batches, nbatch, big_list, big_count);
 }
 
 int64_t scan_partial_size(int64_t n) { return (n + kTile - 1) / kTile + 1; }
@@ -231,9 +254,9 @@ void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                           const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
                           uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch,
-                          double* surf_time, cudaStream_t s) {
+                          double* surf_time, unsigned long long* cyc, cudaStream_t s) {
   k_step_finalize<<<1, 256, 0, s>>>(P, n_inst, dt_cur, dt_min, step, Mcur, Mtot, start_new, NC,
-                                    goff, gcount, n_ghost, big_count, ticket, nbatch, surf_time);
+                                    goff, gcount, n_ghost, big_count, ticket, nbatch, surf_time, cyc);
 }
 
 }  // namespace sp

@@ -1076,8 +1076,10 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
   // One call site of process_batch for both launches, so that every cell
   // runs through the same inlined code (identical rounding whichever launch
   // or batch takes it).  Main launch: batches from the plan's list by
-  // work stealing.  Big-cell launch: a block per cell of the big list.
-  const uint32_t nb = big ? *a.big_count : *a.nbatch;
+  // work stealing, heavy ones (from the front) first, then the others (from
+  // the back).  Big-cell launch: a block per cell of the big list.
+  const uint32_t nh = big ? 0u : a.nbatch[0];
+  const uint32_t nb = big ? *a.big_count : nh + a.nbatch[1];
   uint32_t it = big ? blockIdx.x : 0u;
   for (;;) {
     int64_t k0;
@@ -1087,7 +1089,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
       if (lane == 0) t = atomicAdd(a.ticket, 1u);
       t = __shfl_sync(kFull, t, 0);
       if (t >= nb) break;
-      const uint2 b = a.batches[t];
+      const uint2 b = t < nh ? a.batches[t] : a.batches[a.NC - 1 - (int64_t)(t - nh)];
       k0 = (int64_t)b.x;
       G = (int)b.y;
     } else {
@@ -1100,7 +1102,18 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
         continue;
       }
     }
+    const long long t0 = clock64();
     process_batch<T, DIM>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
+    if (!big) {
+      // the batch's cost steers the next step's order (no effect on results)
+      const unsigned long long cyc = (unsigned long long)(clock64() - t0);
+      if (lane == 0) {
+        atomicAdd(&a.cyc[0], cyc);
+        atomicAdd(&a.cyc[1], 1ull);
+      }
+      const uint8_t h = cyc > a.cyc[2] ? 1 : 0;
+      if (lane < G) a.hot[k0 + lane] = h;
+    }
   }
 }
 

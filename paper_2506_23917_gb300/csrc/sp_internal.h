@@ -95,7 +95,9 @@ struct StepArgs {
   uint32_t* big_count;
   uint32_t* ticket;     // work-stealing counter over the batch list
   const uint2* batches; // (first cell, cell count) of each batch
-  const uint32_t* nbatch;
+  const uint32_t* nbatch;  // [0] heavy batches (listed from the front), [1] others (from the back)
+  uint8_t* hot;         // [NC] the cell's batch was slower than the threshold last step
+  unsigned long long* cyc;  // [3] batch cycles this step (sum, count), threshold
   unsigned long long* err;  // [kNumErr]
   int64_t NC;
   int64_t cap;
@@ -146,7 +148,7 @@ SP_DECLARE_LAUNCHERS(f32)
 // Precision-independent kernels (sp_common.cu).
 void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s);
 void launch_cell_finalize(uint32_t* count, uint32_t* fill, int64_t NC, cudaStream_t s);
-void launch_plan(const uint32_t* start, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
                  uint32_t* big_list, uint32_t* big_count, cudaStream_t s);
 void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* fill, uint32_t* perm,
                     const uint32_t* Mtot, int64_t cap, cudaStream_t s);
@@ -155,7 +157,7 @@ void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           uint32_t* Mtot, const uint32_t* start_new, int64_t NC,
                           const uint32_t* goff, const uint32_t* gcount, int64_t n_ghost,
                           uint32_t* big_count, uint32_t* ticket, uint32_t* nbatch,
-                          double* surf_time, cudaStream_t s);
+                          double* surf_time, unsigned long long* cyc, cudaStream_t s);
 int64_t scan_partial_size(int64_t n);
 
 }  // namespace sp
