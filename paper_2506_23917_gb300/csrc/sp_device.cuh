@@ -419,9 +419,16 @@ struct __align__(16) CellTab {
 };
 
 // Staging per particle: velocities (3 T), source index, clash tag, cell.
+// In FP32 mode the source indices live in the x-velocity array until the
+// gather overwrites them slot by slot (the free flight re-reads them from
+// perm), which saves 4 bytes per particle and raises the resident warps.
+template <class T>
+__host__ __device__ constexpr bool idx_in_velocity() {
+  return sizeof(T) == 4;
+}
 template <class T>
 __host__ __device__ constexpr size_t stage_bytes_per_particle() {
-  return 3 * sizeof(T) + 4 + 4 + 1;
+  return 3 * sizeof(T) + (idx_in_velocity<T>() ? 0 : 4) + 4 + 1;
 }
 template <class T>
 __host__ __device__ constexpr size_t warp_stage_bytes(int cap) {
@@ -517,7 +524,8 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     }
   const unsigned uns = __reduce_or_sync(kFull, mine_uns);
   // small cells: each slot's rank among its cell's (distinct) source
-  // indices, written through stag as scratch; big cells: a sorting network
+  // indices, written through the (not yet gathered) y-velocity array as
+  // scratch; big cells: a sorting network
   const unsigned uns_big = __ballot_sync(kFull, ((uns >> lane) & 1u) && Ni > 64);
   const unsigned uns_small = uns & ~uns_big;
   if (uns_small) {
@@ -528,11 +536,11 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       const uint32_t v = sidx[s];
       int r = 0;
       for (int j = lo; j < hi; ++j) r += sidx[j] < v;
-      stag[lo + r] = (int)v;
+      ((uint32_t*)svy)[lo + r] = v;
     }
     __syncwarp();
     for (int s = lane; s < M; s += 32)
-      if ((uns_small >> sseg[s]) & 1u) sidx[s] = (uint32_t)stag[s];
+      if ((uns_small >> sseg[s]) & 1u) sidx[s] = ((const uint32_t*)svy)[s];
     __syncwarp();
   }
   if (uns_big) {
@@ -561,7 +569,14 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       }
     }
   }
-  // ---- 2. gather velocities
+  // the free flight re-reads the source indices from perm when they share
+  // the x-velocity array: store the restored order there
+  if (idx_in_velocity<T>() && uns) {
+    for (int s = lane; s < M; s += 32)
+      if ((uns >> sseg[s]) & 1u) a.perm[p0 + s] = sidx[s];
+  }
+  // ---- 2. gather velocities (with the indices in the x-velocity array,
+  // each lane reads slot s's index before it writes slot s's velocity)
   {
     const T* Av0 = (const T*)a.Avel[0];
     const T* Av1 = (const T*)a.Avel[1];
@@ -1016,7 +1031,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     for (int u = 0; u < 4; ++u) {
       const int s = sb0 + 32 * u + lane;
       if (s < M) {
-        const uint32_t o = sidx[s];
+        const uint32_t o = idx_in_velocity<T>() ? a.perm[p0 + s] : sidx[s];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) xr[u][d] = ((const T*)a.Apos[d])[o];
       }
@@ -1070,8 +1085,13 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
   T* svx = (T*)(base + sizeof(CellTab<T>));
   T* svy = svx + cap;
   T* svz = svy + cap;
-  uint32_t* sidx = (uint32_t*)(svz + cap);
-  int* stag = (int*)(sidx + cap);
+  unsigned char* tail = (unsigned char*)(svz + cap);
+  uint32_t* sidx = (uint32_t*)svx;
+  if (!idx_in_velocity<T>()) {
+    sidx = (uint32_t*)tail;
+    tail += 4 * (size_t)cap;
+  }
+  int* stag = (int*)tail;
   uint8_t* sseg = (uint8_t*)(stag + cap);
   // One call site of process_batch for both launches, so that every cell
   // runs through the same inlined code (identical rounding whichever launch

@@ -78,7 +78,7 @@ struct StepArgs {
   void* Bpos[3];
   void* Bvel[3];
   uint32_t* key;        // [cap]   key of each B slot
-  const uint32_t* perm; // [cap]   slot -> source index in A
+  uint32_t* perm;       // [cap]   slot -> source index in A (FP32: sorted in place per cell)
   const uint32_t* start;// [NC+1]  cell offsets of the current state
   uint32_t* count;      // [NC]    next-state histogram (atomics)
   const uint32_t* cell_inst;  // [NC]
