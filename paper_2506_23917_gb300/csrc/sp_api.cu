@@ -294,6 +294,8 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.cap_small = c->sched_cap;
   a.stable = c->stable;
   a.surf = c->n_surf_tot > 0 ? c->surf : nullptr;
+  a.one = c->n_inst == 1 ? 1 : 0;
+  a.P0 = c->hP[0];
   return a;
 }
 
@@ -341,8 +343,9 @@ bool apply_schedule(sp_ctx* c, int cap, int warps) {
     return false;
   const size_t smem = c->prec == SP_FP64 ? collide_smem_f64(warps, cap) : collide_smem_f32(warps, cap);
   if (smem > (size_t)kMaxDynSmem) return false;
-  const int per_sm = c->prec == SP_FP64 ? collide_blocks_per_sm_f64(c->dim, warps, cap)
-                                        : collide_blocks_per_sm_f32(c->dim, warps, cap);
+  const bool one = c->n_inst == 1;
+  const int per_sm = c->prec == SP_FP64 ? collide_blocks_per_sm_f64(c->dim, warps, cap, one)
+                                        : collide_blocks_per_sm_f32(c->dim, warps, cap, one);
   if (per_sm < 1) return false;
   c->sched_cap = cap;
   c->sched_warps = warps;

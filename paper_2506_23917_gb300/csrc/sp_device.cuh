@@ -212,7 +212,7 @@ __device__ __forceinline__ void diffuse_sample(T RTw, Uni<T>& r, T* cn, T* t1, T
 // Moves one particle for time trem.  Returns true when it left the domain.
 // Draw stream of bounce b: (step, sa, sb, purpose<<24 | subbase + 2b).
 template <class T, int DIM>
-__device__ bool move_particle(const InstParams& P, double* surf_all, T* x, T* v, T trem,
+__device__ __forceinline__ bool move_particle(const InstParams& P, double* surf_all, T* x, T* v, T trem,
                               uint32_t step, uint32_t purpose, uint32_t sa, uint32_t sb,
                               uint32_t subbase, unsigned long long* err) {
   const Geo<T>& G = geo<T>(P);
@@ -472,6 +472,16 @@ __device__ __forceinline__ void seg_sums(int M, uint32_t p0, const uint8_t* sseg
   }
 }
 
+// Parameters of instance i.  With a single instance (ONE) they come from
+// the copy in the kernel's parameter space, so that the geometry and gas
+// constants reach the arithmetic as constant-bank operands rather than as
+// per-particle loads.
+template <bool ONE>
+__device__ __forceinline__ const InstParams& inst_params(const StepArgs& a, uint32_t i) {
+  if constexpr (ONE) return a.P0;
+  else return a.P[i];
+}
+
 // ---------------------------------------------------------------------------
 // One batch of G consecutive cells [k0, k0+G) whose particles fit the warp's
 // staging area: gather in stable order -> Step 3 moments -> Step 4 split,
@@ -479,7 +489,7 @@ __device__ __forceinline__ void seg_sums(int M, uint32_t p0, const uint8_t* sseg
 // histogram.  Particle work is spread over the lanes across the whole
 // batch; per-cell FP64 arithmetic runs lane-per-cell (lane i <-> cell i).
 // ---------------------------------------------------------------------------
-template <class T, int DIM>
+template <class T, int DIM, bool ONE>
 __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* ct, uint32_t* sidx,
                               int* stag, uint8_t* sseg, T* svx, T* svy, T* svz) {
   const int lane = threadIdx.x & 31;
@@ -499,7 +509,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     inst = a.cell_inst[kc];
     ct->off[lane] = offi;
     ct->inst[lane] = (int)inst;
-    ct->kl[lane] = (int)(kc - a.P[inst].cell_off);
+    ct->kl[lane] = (int)(kc - inst_params<ONE>(a, inst).cell_off);
     ct->nres[lane] = 0;
     ct->nar[lane] = 0;
   }
@@ -631,7 +641,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   // (the oracle's expressions).  FP32 mode: the cell scalars in FP32, with
   // FP64 kept for the exp(-dt/tau) split weight (below), the rescale factor
   // and the time-average accumulators.
-  const InstParams& Pi = a.P[inst];
+  const InstParams& Pi = inst_params<ONE>(a, inst);
   CellMoments m;
   m.T = 0;
   m.q[0] = m.q[1] = m.q[2] = 0;
@@ -766,7 +776,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       }
       c = lo;
       const int N = ct->off[c + 1] - ct->off[c];
-      const InstParams& P = a.P[ct->inst[c]];
+      const InstParams& P = inst_params<ONE>(a, ct->inst[c]);
       const NtcDraw<T> dr = ntc_draw((T)0, step, (uint32_t)ct->kl[c], (uint32_t)(g - ct->coff[c]), P.key0, P.key1);
       u3 = dr.u3;
       u4 = dr.u4;
@@ -781,8 +791,8 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     }
     const int cnext = __shfl_down_sync(kFull, c, 1);
     const bool seg_last = valid && (lane == 31 || cnext != c);
-    const T coef = valid ? geo<T>(a.P[ct->inst[c]]).sigc_coef : (T)0;
-    const T ex = valid ? geo<T>(a.P[ct->inst[c]]).sigc_exp : (T)0;
+    const T coef = valid ? geo<T>(inst_params<ONE>(a, ct->inst[c])).sigc_coef : (T)0;
+    const T ex = valid ? geo<T>(inst_params<ONE>(a, ct->inst[c])).sigc_exp : (T)0;
     unsigned pending = __ballot_sync(kFull, valid);
     // A candidate runs once no earlier pending candidate of its cell shares
     // a particle with it; runs of one cell are disjoint pairs, each sees the
@@ -867,7 +877,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         const int c = sseg[s];
         const T Pres = ct->Pres[c];
         if (Pres > (T)0) {
-          const InstParams& P = a.P[ct->inst[c]];
+          const InstParams& P = inst_params<ONE>(a, ct->inst[c]);
           Uni<T> r(step, (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), kPurpShk << 24, P.key0, P.key1);
           res = r.get(0) < Pres;
         }
@@ -891,7 +901,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         t = 0;
         if (s < 0) return;
         c = sseg[s];
-        const InstParams& P = a.P[ct->inst[c]];
+        const InstParams& P = inst_params<ONE>(a, ct->inst[c]);
         r = Uni<T>(step, (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), kPurpShk << 24, P.key0, P.key1);
         armax = P.ar_max;
         RT = ct->RT[c];
@@ -1044,7 +1054,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       uint32_t key = kSentinel;
       if (s < M) {
         const int c = sseg[s];
-        const InstParams& P = a.P[ct->inst[c]];
+        const InstParams& P = inst_params<ONE>(a, ct->inst[c]);
         T x[3] = {0, 0, 0};
 #pragma unroll
         for (int d = 0; d < DIM; ++d) x[d] = xr[u][d];
@@ -1074,7 +1084,7 @@ __device__ inline void drop_cell(const StepArgs& a, int64_t k) {
   for (uint32_t s = s0 + lane; s < s1; s += 32) a.key[s] = kSentinel;
 }
 
-template <class T, int DIM>
+template <class T, int DIM, bool ONE>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs a, int big) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1123,7 +1133,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
       }
     }
     const long long t0 = clock64();
-    process_batch<T, DIM>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
+    process_batch<T, DIM, ONE>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
     if (!big) {
       // the batch's cost steers the next step's order (no effect on results)
       const unsigned long long cyc = (unsigned long long)(clock64() - t0);

@@ -105,6 +105,8 @@ struct StepArgs {
   int cap_small;        // staging capacity per warp of the main launch
   int stable;           // restore source order within cells (reproducible runs)
   double* surf;         // [elements][kSurfFields] wall tallies
+  int one;              // a single instance: P0 is its parameter set
+  InstParams P0;        // instance 0, by value (kernel parameter space)
 };
 
 struct InjectArgs {
@@ -139,7 +141,7 @@ struct InjectArgs {
   void launch_stage_in_##tag(int dim, const double* pos, const double* vel, int64_t n,             \
                              void* const dpos[3], void* const dvel[3], int64_t off,              \
                              uint32_t* part_inst, uint32_t inst, cudaStream_t s);                \
-  int collide_blocks_per_sm_##tag(int dim, int warps, int cap);                                 \
+  int collide_blocks_per_sm_##tag(int dim, int warps, int cap, bool one);                                 \
   size_t collide_smem_##tag(int warps, int cap);                                                \
   cudaError_t configure_##tag(int big_cap);
 SP_DECLARE_LAUNCHERS(f64)

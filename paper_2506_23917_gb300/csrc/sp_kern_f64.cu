@@ -6,15 +6,21 @@ namespace sp {
 namespace {
 using T = double;
 
-template <int DIM>
-void collide_dim(const StepArgs& a, bool big, int grid, int warps, cudaStream_t s) {
+template <int DIM, bool ONE>
+void collide_dim1(const StepArgs& a, bool big, int grid, int warps, cudaStream_t s) {
   if (!big) {
     const size_t smem = (size_t)warps * warp_stage_bytes<T>(a.cap_small);
-    k_collide<T, DIM><<<grid, 32 * warps, smem, s>>>(a, 0);
+    k_collide<T, DIM, ONE><<<grid, 32 * warps, smem, s>>>(a, 0);
   } else {
     const size_t smem = warp_stage_bytes<T>(a.big_cap);
-    k_collide<T, DIM><<<grid, 32, smem, s>>>(a, 1);
+    k_collide<T, DIM, ONE><<<grid, 32, smem, s>>>(a, 1);
   }
+}
+
+template <int DIM>
+void collide_dim(const StepArgs& a, bool big, int grid, int warps, cudaStream_t s) {
+  if (a.one) collide_dim1<DIM, true>(a, big, grid, warps, s);
+  else collide_dim1<DIM, false>(a, big, grid, warps, s);
 }
 
 template <int DIM>
@@ -31,12 +37,28 @@ void keys_dim(const void* const pos[3], int64_t M, const uint32_t* part_inst, co
                                              part_inst, P, key, count);
 }
 
+template <int DIM, bool ONE>
+cudaError_t configure_dim1() {
+  cudaError_t e = cudaFuncSetAttribute(k_collide<T, DIM, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kMaxDynSmem);
+  if (e == cudaSuccess)  // staging lives in shared memory: prefer the largest carveout
+    e = cudaFuncSetAttribute(k_collide<T, DIM, ONE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
 template <int DIM>
 cudaError_t configure_dim(int) {
-  cudaError_t e = cudaFuncSetAttribute(k_collide<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-  if (e == cudaSuccess)  // staging lives in shared memory: prefer the largest carveout
-    e = cudaFuncSetAttribute(k_collide<T, DIM>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaError_t e = configure_dim1<DIM, true>();
+  if (e == cudaSuccess) e = configure_dim1<DIM, false>();
   return e;
+}
+
+template <int DIM>
+int blocks_per_sm(int warps, size_t smem, bool one) {
+  int n = 0;
+  if (one) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, DIM, true>, 32 * warps, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, DIM, false>, 32 * warps, smem);
+  return n;
 }
 }  // namespace
 
@@ -90,13 +112,11 @@ void launch_stage_in_f64(int dim, const double* pos, const double* vel, int64_t 
                                             (T*)dvel[0], (T*)dvel[1], (T*)dvel[2], off, part_inst, inst);
 }
 
-int collide_blocks_per_sm_f64(int dim, int warps, int cap) {
-  int n = 0;
+int collide_blocks_per_sm_f64(int dim, int warps, int cap, bool one) {
   const size_t smem = (size_t)warps * warp_stage_bytes<T>(cap);
-  if (dim == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 1>, 32 * warps, smem);
-  else if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 2>, 32 * warps, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<T, 3>, 32 * warps, smem);
-  return n;
+  if (dim == 1) return blocks_per_sm<1>(warps, smem, one);
+  if (dim == 2) return blocks_per_sm<2>(warps, smem, one);
+  return blocks_per_sm<3>(warps, smem, one);
 }
 
 cudaError_t configure_f64(int big_cap) {
