@@ -445,28 +445,42 @@ __host__ __device__ constexpr size_t warp_stage_bytes(int cap) {
 template <class T, int K, class F>
 __device__ __forceinline__ void seg_sums(int M, uint32_t p0, const uint8_t* sseg, T (*acc)[32], F f) {
   const int lane = threadIdx.x & 31;
-  for (int base = -(int)(p0 & 31u); base < M; base += 32) {
-    const int s = base + lane;
-    const bool valid = s >= 0 && s < M;
-    const int c = valid ? (int)sseg[s] : 255;
-    T v[K];
+  // two chunks per round: their scans are independent chains that overlap;
+  // the partials are added chunk by chunk in slot order, as one at a time
+  for (int base = -(int)(p0 & 31u); base < M; base += 64) {
+    const int sA = base + lane, sB = base + 32 + lane;
+    const bool vaA = sA >= 0 && sA < M, vaB = sB < M;
+    const int cA = vaA ? (int)sseg[sA] : 255, cB = vaB ? (int)sseg[sB] : 255;
+    T a[K], b[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = 0;
-    if (valid) f(s, v);
+    for (int k = 0; k < K; ++k) {
+      a[k] = 0;
+      b[k] = 0;
+    }
+    if (vaA) f(sA, a);
+    if (vaB) f(sB, b);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int co = __shfl_up_sync(kFull, c, o);
-      const bool same = lane >= o && co == c;
+      const int coA = __shfl_up_sync(kFull, cA, o);
+      const int coB = __shfl_up_sync(kFull, cB, o);
+      const bool sameA = lane >= o && coA == cA, sameB = lane >= o && coB == cB;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const T y = __shfl_up_sync(kFull, v[k], o);
-        if (same) v[k] += y;
+        const T yA = __shfl_up_sync(kFull, a[k], o);
+        const T yB = __shfl_up_sync(kFull, b[k], o);
+        if (sameA) a[k] += yA;
+        if (sameB) b[k] += yB;
       }
     }
-    const int cn = __shfl_down_sync(kFull, c, 1);
-    if (valid && (lane == 31 || cn != c)) {
+    const int cnA = __shfl_down_sync(kFull, cA, 1), cnB = __shfl_down_sync(kFull, cB, 1);
+    if (vaA && (lane == 31 || cnA != cA)) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k][c] += v[k];
+      for (int k = 0; k < K; ++k) acc[k][cA] += a[k];
+    }
+    __syncwarp();
+    if (vaB && (lane == 31 || cnB != cB)) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k][cB] += b[k];
     }
     __syncwarp();
   }
@@ -1032,11 +1046,13 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     }
   }
   // ---- 9. free flight of the next interval (Step 2), key and histogram;
-  // positions of four rounds are loaded before any is used
+  // positions of four rounds are loaded before any is used, then the rounds
+  // run through one copy of the free-flight code (the loaded positions
+  // rotate through registers)
   T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
   T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
   for (int sb0 = 0; sb0 < M; sb0 += 128) {
-    T xr[4][DIM];
+    T xr[4][DIM] = {};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int s = sb0 + 32 * u + lane;
@@ -1046,18 +1062,23 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         for (int d = 0; d < DIM; ++d) xr[u][d] = ((const T*)a.Apos[d])[o];
       }
     }
-#pragma unroll
+#pragma unroll 1
     for (int u = 0; u < 4; ++u) {
       const int sb = sb0 + 32 * u;
       if (sb >= M) break;
       const int s = sb + lane;
       uint32_t key = kSentinel;
+      T x[3] = {0, 0, 0};
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        x[d] = xr[0][d];
+        xr[0][d] = xr[1][d];
+        xr[1][d] = xr[2][d];
+        xr[2][d] = xr[3][d];
+      }
       if (s < M) {
         const int c = sseg[s];
         const InstParams& P = inst_params<ONE>(a, ct->inst[c]);
-        T x[3] = {0, 0, 0};
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) x[d] = xr[u][d];
         T v[3] = {svx[s], svy[s], svz[s]};
         const bool gone = move_particle<T, DIM>(P, a.surf, x, v, ct->dt[c], step, kPurpWall,
                                                 (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), 0u, a.err);
