@@ -87,6 +87,31 @@ struct Uni<float> {
   }
 };
 
+// N consecutive uniforms q0 .. q0+N-1 of a stream (the same values as
+// Uni<T>::get), for draws whose index is only known at run time: the
+// blocks they span are produced by a loop around one inlined Philox body
+// instead of one inlined body per draw.
+__device__ __forceinline__ float uni_word(const uint4& w, int r, float) {
+  return u01f(r == 0 ? w.x : r == 1 ? w.y : r == 2 ? w.z : w.w);
+}
+__device__ __forceinline__ double uni_word(const uint4& w, int r, double) {
+  return r ? u01d(w.z, w.w) : u01d(w.x, w.y);
+}
+template <class T, int N>
+__device__ __forceinline__ void uni_run(const Uni<T>& u, int q0, T (&out)[N]) {
+  constexpr int per = sizeof(T) == 8 ? 2 : 4;
+  const int b0 = q0 / per, b1 = (q0 + N - 1) / per;
+#pragma unroll 1
+  for (int b = b0; b <= b1; ++b) {
+    const uint4 w = philox10(u.c0, u.c1, u.c2, u.c3 + (uint32_t)b, u.k0, u.k1);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const int q = q0 + j;
+      if (q / per == b) out[j] = uni_word(w, q % per, (T)0);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Precision helpers
 // ---------------------------------------------------------------------------
@@ -269,14 +294,18 @@ __device__ __forceinline__ bool move_particle(const InstParams& P, double* surf_
       return false;
     }
     const uint32_t c3 = (purpose << 24) | (subbase + 2u * (uint32_t)bounce);
-    if (tb <= tf) {
+    // the wall reached first: the body (diffuse at T_w) or a face; diffuse
+    // re-emission of either runs through one copy of the sampling code,
+    // in the frame (inward normal nv, tangents e1, e2) of the surface hit
+    T nv[3] = {0, 0, 0}, e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
+    T RTw;
+    const bool body_hit = tb <= tf;
+    if (body_hit) {
 #pragma unroll
       for (int d = 0; d < DIM; ++d) x[d] += v[d] * tb;
       trem -= tb;
-      T nv[3] = {0, 0, 0};
       const int D = P.body == 1 ? 2 : 3;
       for (int d = 0; d < D; ++d) nv[d] = (x[d] - G.body_c[d]) / G.body_r;
-      T e1[3], e2[3];
       if (P.body == 1) {
         e1[0] = -nv[1]; e1[1] = nv[0]; e1[2] = 0;
         e2[0] = 0; e2[1] = 0; e2[2] = 1;
@@ -292,80 +321,79 @@ __device__ __forceinline__ bool move_particle(const InstParams& P, double* surf_
         e2[1] = nv[2] * e1[0] - nv[0] * e1[2];
         e2[2] = nv[0] * e1[1] - nv[1] * e1[0];
       }
-      Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
-      T cn, t1, t2;
-      diffuse_sample<T>(G.body_RT, r, &cn, &t1, &t2);
-      const T vin0 = v[0], vin1 = v[1], vin2 = v[2];
+      RTw = G.body_RT;
+    } else {
+      // (static indices only: x and v stay in registers)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
-      if (surf_all != nullptr && P.n_surf > 0 && (int64_t)step >= (int64_t)P.n_steady) {
-        // momentum and energy the wall receives from this hit (FP64 tallies)
-        double frac;
-        if (P.body == 1) {
-          frac = ((double)atan2(nv[1], nv[0]) + kPi) / (2.0 * kPi);
-        } else {
-          const double cx = (double)nv[0] < -1.0 ? -1.0 : ((double)nv[0] > 1.0 ? 1.0 : (double)nv[0]);
-          frac = acos(cx) / kPi;
-        }
-        int bin = (int)floor(frac * (double)P.n_surf);
-        if (bin < 0) bin = 0;
-        if (bin > P.n_surf - 1) bin = P.n_surf - 1;
-        double* t = surf_all + kSurfFields * (P.surf_off + bin);
-        const double ein = (double)vin0 * vin0 + (double)vin1 * vin1 + (double)vin2 * vin2;
-        const double eout = (double)v[0] * v[0] + (double)v[1] * v[1] + (double)v[2] * v[2];
-        const double dp0 = P.FnM * ((double)vin0 - (double)v[0]);
-        const double dp1 = P.FnM * ((double)vin1 - (double)v[1]);
-        const double dp2 = P.FnM * ((double)vin2 - (double)v[2]);
-        // direction of increasing polar angle at the hit point
-        double et0 = 0, et1 = 0, et2 = 0;
-        if (P.body == 1) {
-          et0 = -(double)nv[1];
-          et1 = (double)nv[0];
-        } else {
-          const double sn = sqrt((double)nv[1] * nv[1] + (double)nv[2] * nv[2]);
-          if (sn > 0) {
-            et0 = -sn;
-            et1 = (double)nv[0] * nv[1] / sn;
-            et2 = (double)nv[0] * nv[2] / sn;
-          }
-        }
-        atomicAdd(t + 0, 1.0);
-        atomicAdd(t + 1, dp0);
-        atomicAdd(t + 2, dp1);
-        atomicAdd(t + 3, dp2);
-        atomicAdd(t + 4, 0.5 * P.FnM * (ein - eout));
-        atomicAdd(t + 5, -(dp0 * nv[0] + dp1 * nv[1] + dp2 * nv[2]));
-        atomicAdd(t + 6, dp0 * et0 + dp1 * et1 + dp2 * et2);
+      for (int d = 0; d < DIM; ++d) {
+        if (d != fa) x[d] += v[d] * tf;
+        else x[d] = fs ? G.hi[d] : G.lo[d];
       }
-      continue;
-    }
-    // (static indices only: x and v stay in registers)
+      trem -= tf;
+      const int f = 2 * fa + fs;
+      int bc = P.face_bc[f];
+      if (bc >= 2 && ((P.face_win >> f) & 1) && !face_open<T, DIM>(G, f, x)) bc = 1;  // orifice lips
+      if (bc == 0) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      if (d != fa) x[d] += v[d] * tf;
-      else x[d] = fs ? G.hi[d] : G.lo[d];
-    }
-    trem -= tf;
-    const int f = 2 * fa + fs;
-    int bc = P.face_bc[f];
-    if (bc >= 2 && ((P.face_win >> f) & 1) && !face_open<T, DIM>(G, f, x)) bc = 1;  // orifice lips
-    if (bc == 0) {
-#pragma unroll
-      for (int d = 0; d < DIM; ++d)
-        if (d == fa) v[d] = -v[d];
-    } else if (bc == 1) {
-      Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
-      T cn, t1, t2;
-      diffuse_sample<T>(G.face_RT[f], r, &cn, &t1, &t2);
+        for (int d = 0; d < DIM; ++d)
+          if (d == fa) v[d] = -v[d];
+        continue;
+      }
+      if (bc != 1) return true;
+      // diffuse face: normal into the domain, tangents along the next axes
       const int f1 = fa == 2 ? 0 : fa + 1, f2 = fa == 0 ? 2 : fa - 1;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        if (d == fa) v[d] = fs ? -cn : cn;
-        else if (d == f1) v[d] = t1;
-        else if (d == f2) v[d] = t2;
+        nv[d] = d == fa ? (fs ? (T)-1 : (T)1) : (T)0;
+        e1[d] = d == f1 ? (T)1 : (T)0;
+        e2[d] = d == f2 ? (T)1 : (T)0;
       }
-    } else {
-      return true;
+      RTw = G.face_RT[f];
+    }
+    Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
+    T cn, t1, t2;
+    diffuse_sample<T>(RTw, r, &cn, &t1, &t2);
+    const T vin0 = v[0], vin1 = v[1], vin2 = v[2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
+    if (body_hit && surf_all != nullptr && P.n_surf > 0 && (int64_t)step >= (int64_t)P.n_steady) {
+      // momentum and energy the wall receives from this hit (FP64 tallies)
+      double frac;
+      if (P.body == 1) {
+        frac = ((double)atan2(nv[1], nv[0]) + kPi) / (2.0 * kPi);
+      } else {
+        const double cx = (double)nv[0] < -1.0 ? -1.0 : ((double)nv[0] > 1.0 ? 1.0 : (double)nv[0]);
+        frac = acos(cx) / kPi;
+      }
+      int bin = (int)floor(frac * (double)P.n_surf);
+      if (bin < 0) bin = 0;
+      if (bin > P.n_surf - 1) bin = P.n_surf - 1;
+      double* t = surf_all + kSurfFields * (P.surf_off + bin);
+      const double ein = (double)vin0 * vin0 + (double)vin1 * vin1 + (double)vin2 * vin2;
+      const double eout = (double)v[0] * v[0] + (double)v[1] * v[1] + (double)v[2] * v[2];
+      const double dp0 = P.FnM * ((double)vin0 - (double)v[0]);
+      const double dp1 = P.FnM * ((double)vin1 - (double)v[1]);
+      const double dp2 = P.FnM * ((double)vin2 - (double)v[2]);
+      // direction of increasing polar angle at the hit point
+      double et0 = 0, et1 = 0, et2 = 0;
+      if (P.body == 1) {
+        et0 = -(double)nv[1];
+        et1 = (double)nv[0];
+      } else {
+        const double sn = sqrt((double)nv[1] * nv[1] + (double)nv[2] * nv[2]);
+        if (sn > 0) {
+          et0 = -sn;
+          et1 = (double)nv[0] * nv[1] / sn;
+          et2 = (double)nv[0] * nv[2] / sn;
+        }
+      }
+      atomicAdd(t + 0, 1.0);
+      atomicAdd(t + 1, dp0);
+      atomicAdd(t + 2, dp1);
+      atomicAdd(t + 3, dp2);
+      atomicAdd(t + 4, 0.5 * P.FnM * (ein - eout));
+      atomicAdd(t + 5, -(dp0 * nv[0] + dp1 * nv[1] + dp2 * nv[2]));
+      atomicAdd(t + 6, dp0 * et0 + dp1 * et1 + dp2 * et2);
     }
   }
 }
@@ -445,42 +473,28 @@ __host__ __device__ constexpr size_t warp_stage_bytes(int cap) {
 template <class T, int K, class F>
 __device__ __forceinline__ void seg_sums(int M, uint32_t p0, const uint8_t* sseg, T (*acc)[32], F f) {
   const int lane = threadIdx.x & 31;
-  // two chunks per round: their scans are independent chains that overlap;
-  // the partials are added chunk by chunk in slot order, as one at a time
-  for (int base = -(int)(p0 & 31u); base < M; base += 64) {
-    const int sA = base + lane, sB = base + 32 + lane;
-    const bool vaA = sA >= 0 && sA < M, vaB = sB < M;
-    const int cA = vaA ? (int)sseg[sA] : 255, cB = vaB ? (int)sseg[sB] : 255;
-    T a[K], b[K];
+  for (int base = -(int)(p0 & 31u); base < M; base += 32) {
+    const int s = base + lane;
+    const bool valid = s >= 0 && s < M;
+    const int c = valid ? (int)sseg[s] : 255;
+    T v[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      a[k] = 0;
-      b[k] = 0;
-    }
-    if (vaA) f(sA, a);
-    if (vaB) f(sB, b);
+    for (int k = 0; k < K; ++k) v[k] = 0;
+    if (valid) f(s, v);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int coA = __shfl_up_sync(kFull, cA, o);
-      const int coB = __shfl_up_sync(kFull, cB, o);
-      const bool sameA = lane >= o && coA == cA, sameB = lane >= o && coB == cB;
+      const int co = __shfl_up_sync(kFull, c, o);
+      const bool same = lane >= o && co == c;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const T yA = __shfl_up_sync(kFull, a[k], o);
-        const T yB = __shfl_up_sync(kFull, b[k], o);
-        if (sameA) a[k] += yA;
-        if (sameB) b[k] += yB;
+        const T y = __shfl_up_sync(kFull, v[k], o);
+        if (same) v[k] += y;
       }
     }
-    const int cnA = __shfl_down_sync(kFull, cA, 1), cnB = __shfl_down_sync(kFull, cB, 1);
-    if (vaA && (lane == 31 || cnA != cA)) {
+    const int cn = __shfl_down_sync(kFull, c, 1);
+    if (valid && (lane == 31 || cn != c)) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k][cA] += a[k];
-    }
-    __syncwarp();
-    if (vaB && (lane == 31 || cnB != cB)) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) acc[k][cB] += b[k];
+      for (int k = 0; k < K; ++k) acc[k][c] += v[k];
     }
     __syncwarp();
   }
@@ -930,8 +944,9 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       while (__any_sync(kFull, s >= 0)) {
         bool done = false;
         if (s >= 0) {
-          const T R1 = r.get(1 + 5 * t), R2 = r.get(2 + 5 * t), R3 = r.get(3 + 5 * t);
-          const T R4 = r.get(4 + 5 * t), R5 = r.get(5 + 5 * t);
+          T Rt[5];
+          uni_run<T, 5>(r, 1 + 5 * t, Rt);
+          const T R1 = Rt[0], R2 = Rt[1], R3 = Rt[2], R4 = Rt[3], R5 = Rt[4];
           const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
           T sn3, cs3;
           sincos2pi(R3, &sn3, &cs3);
