@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--profile-steps", type=int, default=40)
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-modes", action="store_true",
+                   help="skip the pure-DSMC / pure-Shakhov legs of the same workload")
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--schedule", default=None,
                    help="CAP,WARPS: fixed collision-kernel schedule instead of the autotuner")
@@ -486,6 +488,37 @@ def main():
         line["fp64_plain"] = {"value": v64 * world, "unit": UNIT, "ms_per_step": t64 / k64, "steps": k64,
                               "collide_ms": p64[0] / 10, "fp32_over_fp64": value / (v64 * world)}
         sim64.close()
+
+    # --- the same workload with one collision sub-step forced everywhere
+    # (pure DSMC and pure stochastic-particle Shakhov), the method's two
+    # limits, in the headline's precision and schedule
+    if not args.no_modes and rank == 0:
+        modes = {}
+        for name, mode in (("dsmc", W.MODE_DSMC), ("shakhov", W.MODE_SHAKHOV)):
+            cfg_m = dict(cfg, mode=mode)
+            sm = sp.Sim(cfg_m, prec, capacity=cap)
+            if prec == sp.FP32 and not args.reproducible:
+                sm.set_reproducible(False)
+            sm.set_particles(0, pos, vel)
+            if sched:
+                sm.set_schedule(*sched)
+            sm.step(args.develop)
+            sm.step(args.warmup)
+            sm.sync()
+            km = max(100, args.steps // 10)
+            m0 = sm.count(0)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sm.step(km)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sm.sync()
+            tm = e0.elapsed_time(e1)
+            modes[name] = {"value": km * 0.5 * (m0 + sm.count(0)) / (tm * 1e-3), "unit": UNIT,
+                           "ms_per_step": tm / km, "steps": km}
+            sm.close()
+        modes["note"] = "same workload, mode forced in every cell (hybrid = the headline)"
+        line["pure_modes"] = modes
 
     # --- end to end through the C ABI with host buffers: per step, upload
     # the state from pinned host memory, advance one step, read the moments

@@ -100,6 +100,11 @@ typedef struct sp_config {
    * is a diffuse wall at face_T, and the reservoir of a windowed inflow face
    * spans the window plus ghost_layers cells on each side. */
   double win_lo[6][2], win_hi[6][2];
+  /* Fractional part of the NTC candidate count (Sec. II.A leaves it open):
+   * 0 = stochastic rounding with one uniform per cell and step (default);
+   * 1 = Bird's carried remainder, kept per cell from 0 and added to the
+   * next step's count (deterministic; no draw). */
+  int32_t ntc_carry;
 } sp_config;
 
 typedef struct sp_ctx sp_ctx;

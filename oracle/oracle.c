@@ -31,7 +31,8 @@
  *   - Diffuse normal speed c_n = sqrt(-2 R T_w ln R1) (the printed "cos" is a
  *     typo), tangential components Box-Muller at T_w.
  *   - A_max = A at |C| = 5 sqrt(RT), C parallel to q_s.
- *   - N_col fractional part: stochastic rounding with one uniform.
+ *   - N_col fractional part: stochastic rounding with one uniform; with
+ *     ntc_carry, Bird's carried remainder per cell (starting at 0).
  *   - VHS cross-section (Bird): sigma_T c_r = pi d_ref^2 (4 R T_ref)^(w-1/2)
  *     / Gamma(5/2 - w) * c_r^(2-2w).
  *   - Rescale targets U, T of Step 3; skipped when nothing was resampled.
@@ -85,6 +86,7 @@ struct or_ctx {
   int64_t M, cap;
   uint32_t *start; /* [ncells+1] */
   double *smax;
+  double *rem; /* carried NTC remainder per cell (ntc_carry) */
   double *samp; /* [8][ncells] */
   int64_t nsamp;
   double dt;
@@ -228,7 +230,7 @@ static double ratio_of(const or_config* g, const mom* mm) {
  * ps[0..N) are the cell's particles in slot order; k is the cell's index.
  * ------------------------------------------------------------------- */
 static void collide_cell(or_ctx* c, int64_t k, double V, part* ps, int64_t N, const mom* mm,
-                         double dtG, double* smax, int64_t rec[4], uint8_t* res) {
+                         double dtG, double* smax, double* rem, int64_t rec[4], uint8_t* res) {
   const or_config* g = &c->cfg;
   rec[0] = rec[1] = rec[2] = rec[3] = 0;
   if (N < 2 || !(mm->T > 0)) return;
@@ -239,8 +241,16 @@ static void collide_cell(or_ctx* c, int64_t k, double V, part* ps, int64_t N, co
   /* DSMC, NTC scheme (Sec. II.A). */
   if (dsmc > 0) {
     double ncr = 0.5 * (double)N * (double)(N - 1) * g->Fn * (*smax) * dsmc / V;
-    double ur = uq(c, kc, SENTINEL, PURP_NTC, 0, 0);
-    int64_t ncol = (int64_t)floor(ncr + ur);
+    int64_t ncol;
+    if (g->ntc_carry) {
+      /* Bird's carried remainder */
+      double x = ncr + *rem;
+      ncol = (int64_t)floor(x);
+      *rem = x - (double)ncol;
+    } else {
+      double ur = uq(c, kc, SENTINEL, PURP_NTC, 0, 0);
+      ncol = (int64_t)floor(ncr + ur);
+    }
     if (ncol > NCOL_CAP) ncol = NCOL_CAP;
     for (int64_t kk = 0; kk < ncol; ++kk) {
       double u1 = uq(c, kc, (uint32_t)kk, PURP_NTC, 0, 0);
@@ -518,6 +528,7 @@ int or_init(const or_config* cfg, or_ctx** out) {
   c->key[1] = (uint32_t)(g->seed >> 32);
   c->start = (uint32_t*)calloc(c->ncells + 1, sizeof(uint32_t));
   c->smax = (double*)malloc(sizeof(double) * c->ncells);
+  c->rem = (double*)calloc((size_t)(c->ncells > 0 ? c->ncells : 1), sizeof(double));
   /* (sigma_T c_r)_max seeded at 2 sigma_T(cbar_r) cbar_r, cbar_r = 4 sqrt(R T0 / pi). */
   double crb = 4.0 * sqrt(g->R * g->sigc_T0 / M_PI);
   double s0 = 2.0 * sigc_fast(c, crb);
@@ -533,7 +544,7 @@ int or_init(const or_config* cfg, or_ctx** out) {
 
 void or_free(or_ctx* c) {
   if (!c) return;
-  free(c->vol); free(c->p); free(c->start); free(c->smax); free(c->samp);
+  free(c->vol); free(c->p); free(c->start); free(c->smax); free(c->rem); free(c->samp);
   free(c->rec); free(c->resamp); free(c->perm); free(c->surf);
   free(c);
 }
@@ -727,7 +738,7 @@ int or_step(or_ctx* c, int nsteps) {
       moments_of(c, k, c->p + s0, N, &mm);
       if (N >= 2 && mm.dtc < mn) mn = mm.dtc;
       int64_t rec[4];
-      collide_cell(c, k, c->vol[k], c->p + s0, N, &mm, dtG, &c->smax[k], rec, c->resamp + s0);
+      collide_cell(c, k, c->vol[k], c->p + s0, N, &mm, dtG, &c->smax[k], &c->rem[k], rec, c->resamp + s0);
       for (int i = 0; i < 4; ++i) c->rec[i * c->ncells + k] = rec[i];
       if (sample) {
         double* S = c->samp;
@@ -880,7 +891,8 @@ int or_collide_cell(const or_config* cfg, int64_t step, uint32_t cell, double vo
   mom mm;
   /* the homogeneous cell uses its own volume and index for the draw stream */
   moments_of(c, 0, ps, N, &mm);
-  collide_cell(c, (int64_t)cell, volume, ps, N, &mm, dt_G, sigc_max, rec, resampled);
+  double rem = 0.0;
+  collide_cell(c, (int64_t)cell, volume, ps, N, &mm, dt_G, sigc_max, &rem, rec, resampled);
   for (int64_t i = 0; i < N; ++i)
     for (int d = 0; d < 3; ++d) vel[d * N + i] = ps[i].v[d];
   free(ps);

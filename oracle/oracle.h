@@ -58,6 +58,11 @@ typedef struct or_config {
    * win_lo <= x <= win_hi; an axis with win_lo >= win_hi is not restricted.
    * Elsewhere the face is a diffuse wall at face_T (an orifice with lips). */
   double win_lo[6][2], win_hi[6][2];
+  /* Fractional part of the NTC candidate count: 0 = stochastic rounding
+   * with one uniform per cell and step; 1 = Bird's carried remainder (the
+   * fraction is kept per cell, starting at 0, and added to the next step's
+   * count). */
+  int32_t ntc_carry;
 } or_config;
 
 typedef struct or_ctx or_ctx;

@@ -56,6 +56,7 @@ struct sp_ctx {
   double* surf_time = nullptr;  // [n_inst] sampled time
   int64_t n_surf_tot = 0;
   double *vol = nullptr, *smax = nullptr, *samp = nullptr;
+  double* rem = nullptr;  // [NC] carried NTC remainders
   int32_t* rec = nullptr;
   uint8_t* resamp = nullptr;
   double* dt_cur = nullptr;
@@ -138,6 +139,7 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
   P->key1 = (uint32_t)(c.seed >> 32);
   P->mode = c.mode;
   P->ar_max = c.ar_max < 1 ? 1 : c.ar_max;
+  P->ntc_carry = c.ntc_carry ? 1 : 0;
   P->cell_off = cell_off;
   P->ncells = (int64_t)P->n[0] * P->n[1] * P->n[2];
   P->n_surf = (c.body != SP_BODY_NONE && c.n_surf > 0) ? c.n_surf : 0;
@@ -273,6 +275,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.cell_inst = c->cell_inst;
   a.vol = c->vol;
   a.smax = c->smax;
+  a.rem = c->rem;
   a.samp = c->samp;
   a.rec = c->record ? c->rec : nullptr;
   a.resamp = c->record ? c->resamp : nullptr;
@@ -594,6 +597,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->cyc, 24));
     CK(dalloc(&c->vol, 8 * NC));
     CK(dalloc(&c->smax, 8 * NC));
+    CK(dalloc(&c->rem, 8 * std::max<int64_t>(NC, 1)));
     CK(dalloc(&c->samp, 8 * 8 * NC));
     CK(dalloc(&c->dP, sizeof(InstParams) * n_instances));
     CK(dalloc(&c->dt_cur, 8 * n_instances));
@@ -629,6 +633,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(cudaMemcpyAsync(c->cell_inst, ci.data(), 4 * NC, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->vol, vol.data(), 8 * NC, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->smax, sm.data(), 8 * NC, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->rem, 0, 8 * std::max<int64_t>(NC, 1), s));
     CK(cudaMemsetAsync(c->samp, 0, 8 * 8 * NC, s));
     CK(cudaMemsetAsync(c->surf, 0, 8 * kSurfFields * std::max<int64_t>(c->n_surf_tot, 1), s));
     CK(cudaMemsetAsync(c->surf_time, 0, 8 * n_instances, s));
@@ -1059,7 +1064,7 @@ sp_status sp_free(sp_ctx* c) {
     }
   for (double* p : c->dstage) cudaFree(p);
   void* ptrs[] = {c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
-                  c->big_count, c->vol, c->smax, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
+                  c->big_count, c->vol, c->smax, c->rem, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);
   delete c;

@@ -741,8 +741,14 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       if (dsmc > (T)0) {
         smaxT = (T)a.smax[kc];
         const T ncr = (T)0.5 * (T)Ni * (T)(Ni - 1) * (T)Pi.Fn * smaxT * dsmc / V;
-        Uni<T> rr(step, (uint32_t)ct->kl[lane], kSentinel, kPurpNtc << 24, Pi.key0, Pi.key1);
-        ncol = (int64_t)tfloor(ncr + rr.get(0));
+        if (Pi.ntc_carry) {  // Bird's carried remainder (FP64 state per cell)
+          const double x = (double)ncr + a.rem[kc];
+          ncol = (int64_t)floor(x);
+          a.rem[kc] = x - (double)ncol;
+        } else {
+          Uni<T> rr(step, (uint32_t)ct->kl[lane], kSentinel, kPurpNtc << 24, Pi.key0, Pi.key1);
+          ncol = (int64_t)tfloor(ncr + rr.get(0));
+        }
         if (ncol > kNcolCap) {
           ncol = kNcolCap;
           atomicAdd(&a.err[kErrNcol], 1ull);

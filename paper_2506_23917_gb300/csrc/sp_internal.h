@@ -50,6 +50,7 @@ struct InstParams {
   uint32_t key0, key1;
   int mode;
   int ar_max;
+  int ntc_carry;     // carried NTC remainder instead of stochastic rounding
   int64_t cell_off;  // first global cell of the instance
   int64_t ncells;
   int n_surf;        // surface elements of the body (0: no tallies)
@@ -84,6 +85,7 @@ struct StepArgs {
   const uint32_t* cell_inst;  // [NC]
   const double* vol;    // [NC]
   double* smax;         // [NC]
+  double* rem;          // [NC] carried NTC remainder
   double* samp;         // [8][NC]
   int32_t* rec;         // [4][NC] or null
   uint8_t* resamp;      // [cap] or null

@@ -157,6 +157,16 @@ def test_jet_orifice_matches_oracle(sp):
     assert np.diff(o.cell_start().astype(np.int64)).max() > 512
 
 
+def test_carried_remainder_ntc_matches_oracle(sp):
+    """Bird's carried NTC remainder (per-cell state across steps) in place
+    of stochastic rounding: candidate counts bit-exact every step."""
+    cfg, regions = W.sod(ncell=60, ppc_left=60.0, lam_left=1e-3)
+    cfg["ntc_carry"] = 1
+    pos, vel = W.fill_regions(cfg, regions, 4)
+    o, s, tot = run_pair(sp, cfg, pos, vel, steps=10)
+    assert tot[0] > 0
+
+
 @pytest.mark.parametrize("mode", [W.MODE_DSMC, W.MODE_SHAKHOV])
 def test_forced_modes_match_oracle(sp, mode):
     cfg, regions = W.sod(ncell=60, ppc_left=60.0, lam_left=1e-3, mode=mode)

@@ -274,3 +274,40 @@ def test_moment_estimators_are_unbiased():
     assert abs(T.mean() - 1.0) < 4 * T.std() / math.sqrt(nc)
     assert abs(qx.mean() - 1.0) < 4 * qx.std() / math.sqrt(nc)
     assert abs(m[FIELD["qy"]].mean()) < 4 * m[FIELD["qy"]].std() / math.sqrt(nc)
+
+
+def _closed_cell_candidates(carry, steps, seed=1):
+    """A closed homogeneous cell in pure DSMC with a fixed step and a
+    (sigma c)_max seed far above any pair's sigma c, so that the NTC count
+    N(N-1) F_N (sigma c)_max dt / (2 V) is the same every step."""
+    N = 200
+    cfg = W.homogeneous(N=N, Kn=0.3, mode=W.MODE_DSMC, dt=0.01, seed=seed)
+    cfg["sigc_T0"] = 50.0
+    cfg["ntc_carry"] = carry
+    pos, vel = W.homogeneous_particles(cfg, N, Tx=1.0, Tyz=1.0, seed=seed)
+    o = oracle.Oracle(cfg)
+    o.set_particles(pos, vel)
+    smax0 = o.sigc_max()[0]
+    ncr = 0.5 * N * (N - 1) * cfg["Fn"] * smax0 * cfg["dt_fixed"] / 1.0
+    counts = []
+    for _ in range(steps):
+        o.step(1)
+        counts.append(int(o.record()[0][0][0]))
+    assert o.sigc_max()[0] == smax0  # never raised: the count per step is constant
+    return np.array(counts), ncr
+
+
+def test_carried_remainder_ntc_count_telescopes():
+    """Bird's carried remainder: after K steps the candidates add up to
+    floor(K * N_col_real) exactly, and every step takes floor or ceil of
+    N_col_real; stochastic rounding only matches it on average."""
+    K = 300
+    c, ncr = _closed_cell_candidates(1, K)
+    assert ncr % 1.0 > 0.05 and ncr % 1.0 < 0.95
+    assert c.sum() == math.floor(K * ncr)
+    assert set(np.unique(c)) <= {math.floor(ncr), math.ceil(ncr)}
+    for k in range(1, K + 1):
+        assert abs(c[:k].sum() - k * ncr) < 1.0
+    r, _ = _closed_cell_candidates(0, K)
+    assert abs(r.sum() - K * ncr) < 5 * math.sqrt(K * 0.25) + 1
+    assert r.sum() != c.sum() or not np.array_equal(r, c)
