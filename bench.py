@@ -375,7 +375,7 @@ def main():
         sched = tuple(int(x) for x in args.schedule.split(","))
         sim.set_schedule(*sched)
     else:
-        sched = sim.autotune(steps_per_trial=3) if not args.no_tune else None
+        sched = sim.autotune(steps_per_trial=20) if not args.no_tune else None
     sim.step(args.warmup)
     sim.sync()
     M0 = sim.count(0)

@@ -226,8 +226,8 @@ sp_status sp_set_reproducible(sp_ctx* ctx, int on);
 sp_status sp_set_schedule(sp_ctx* ctx, int cap, int warps);
 /* Autotuner: for each candidate schedule (cap in 128..1024, warps in 2, 4,
  * 8 that fit) advance one untimed step and then steps_per_trial ordinary
- * steps while timing the collision kernel with CUDA events, then keep the
- * fastest schedule.  The
+ * steps while timing the collision kernel with CUDA events; time the three
+ * fastest once more the same way and keep the one with the least total.  The
  * trial steps are part of the run (results do not depend on the schedule);
  * call it once the flow is developed.  *cap_out / *warps_out (may be NULL)
  * receive the choice. */

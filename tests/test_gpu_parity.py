@@ -252,7 +252,7 @@ def test_schedule_and_autotune_do_not_change_results(sp):
             assert cap >= 128 and w in (2, 4, 8)
         else:
             s.set_schedule(*sched)
-        s.step(45 - s.step_index())
+        s.step(60 - s.step_index())
         s.sync()
         runs.append((s.particles(0), s.sigc_max(0)))
         s.close()
