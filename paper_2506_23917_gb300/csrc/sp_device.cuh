@@ -112,6 +112,15 @@ __device__ __forceinline__ void uni_run(const Uni<T>& u, int q0, T (&out)[N]) {
   }
 }
 
+// Asynchronous global -> shared copy of one 4- or 8-byte element (no
+// register staging), and the wait for all of this thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gsrc), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Precision helpers
 // ---------------------------------------------------------------------------
@@ -619,14 +628,16 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     const T* Av0 = (const T*)a.Avel[0];
     const T* Av1 = (const T*)a.Avel[1];
     const T* Av2 = (const T*)a.Avel[2];
+    // every lane issues all of its copies before waiting once
 #pragma unroll 4
     for (int s = lane; s < M; s += 32) {
       const uint32_t o = sidx[s];
-      svx[s] = Av0[o];
-      svy[s] = Av1[o];
-      svz[s] = Av2[o];
+      cp_async<sizeof(T)>(&svx[s], &Av0[o]);
+      cp_async<sizeof(T)>(&svy[s], &Av1[o]);
+      cp_async<sizeof(T)>(&svz[s], &Av2[o]);
       stag[s] = 0x7FFFFFFF;
     }
+    cp_async_wait_all();
   }
   __syncwarp();
   // ---- 3. moment sums per cell (segmented, one pass each), kept by lane i
