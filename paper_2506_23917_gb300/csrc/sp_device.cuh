@@ -553,12 +553,14 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   if (lane == 0) ct->off[G] = M;
   __syncwarp();
   // ---- 1. source indices, cell of each slot, stable order within cells
+  // (the index copies run while the cell of each slot is written)
 #pragma unroll 4
-  for (int s = lane; s < M; s += 32) sidx[s] = a.perm[p0 + s];
+  for (int s = lane; s < M; s += 32) cp_async<4>(&sidx[s], &a.perm[p0 + s]);
   for (int i = 0; i < G; ++i) {
     const int o0 = ct->off[i], o1 = ct->off[i + 1];
     for (int s = o0 + lane; s < o1; s += 32) sseg[s] = (uint8_t)i;
   }
+  cp_async_wait_all();
   __syncwarp();
   // cells whose source indices arrived out of order (the scatter's atomics
   // keep only each scattering warp's run ascending); skipped when the run
