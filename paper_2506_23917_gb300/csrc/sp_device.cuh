@@ -1037,25 +1037,25 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     }
     __syncwarp();
   }
-  // ---- 8. time-averaged sums (Step 5)
+  // ---- 8. time-averaged sums (Step 5).  Both collision sub-steps conserve
+  // each cell's momentum (the DSMC pair rule and the rescale to U), so the
+  // momentum sums are those of Step 3 up to rounding; only the per-component
+  // squares need a pass over the post-collision velocities.
   const bool anys = __any_sync(kFull, sample && Ni > 0);
-  T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
+  const T a0 = m0, a1 = m1, a2 = m2;
+  T b0 = 0, b1 = 0, b2 = 0;
   if (anys) {
     if (own)
-      for (int k = 0; k < 6; ++k) ct->acc[k][lane] = 0;
+      for (int k = 0; k < 3; ++k) ct->acc[k][lane] = 0;
     __syncwarp();
-    seg_sums<T, 6>(M, p0, sseg, ct->acc, [&](int s, T* v) {
+    seg_sums<T, 3>(M, p0, sseg, ct->acc, [&](int s, T* v) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
-      v[0] = x0;
-      v[1] = x1;
-      v[2] = x2;
-      v[3] = x0 * x0;
-      v[4] = x1 * x1;
-      v[5] = x2 * x2;
+      v[0] = x0 * x0;
+      v[1] = x1 * x1;
+      v[2] = x2 * x2;
     });
     if (own) {
-      a0 = ct->acc[0][lane]; a1 = ct->acc[1][lane]; a2 = ct->acc[2][lane];
-      b0 = ct->acc[3][lane]; b1 = ct->acc[4][lane]; b2 = ct->acc[5][lane];
+      b0 = ct->acc[0][lane]; b1 = ct->acc[1][lane]; b2 = ct->acc[2][lane];
     }
   }
   if (own) {
