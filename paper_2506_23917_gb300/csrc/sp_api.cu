@@ -1,7 +1,7 @@
 // sp_api.cu -- host driver and C ABI of libsp (see include/sp.h).
 //
 // Per step the driver enqueues, on the context's stream:
-//   1. k_collide (warp per cell, cells up to kCapSmall particles) and its
+//   1. k_plan + k_collide (batches of cells per warp) and its
 //      big-cell launch (one warp per cell with a large staging area):
 //      gather through perm in stable order -> Step 3 moments -> Step 4
 //      DSMC / Shakhov / rescale -> Step 5 sums -> Step 2 free flight of the
@@ -9,7 +9,8 @@
 //   2. reservoir injection at inflow faces (count, scan, write);
 //   3. exclusive scan of the histogram -> cell offsets of the new state;
 //   4. bookkeeping (particle count, Delta t of the next step, step index);
-//   5. scatter of source indices into the new cell order.
+//   5. scatter of source indices into the new cell order (the histogram is
+//      the cursor and ends at zero, ready for the next step).
 // The sequence is captured once per buffer parity as a CUDA graph and
 // replayed by sp_step().
 #include <algorithm>
@@ -41,7 +42,7 @@ struct sp_ctx {
   // device buffers
   void* pos[2][3] = {{nullptr}};
   void* vel[2][3] = {{nullptr}};
-  uint32_t *key = nullptr, *perm = nullptr, *count = nullptr, *fill = nullptr, *start = nullptr;
+  uint32_t *key = nullptr, *perm = nullptr, *count = nullptr, *start = nullptr;
   uint32_t *cell_inst = nullptr, *scan_part = nullptr, *big_list = nullptr, *big_count = nullptr;
   uint32_t* ticket = nullptr;
   uint2* batches = nullptr;
@@ -378,12 +379,11 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   }
   if (ev) cudaEventRecord(ev[2], c->stream);
   launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream); n += 3;
-  launch_cell_finalize(c->count, c->fill, c->NC, c->stream); ++n;
   launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
                        c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->nbatch,
                        c->surf_time, c->cyc, c->stream); ++n;
   if (ev) cudaEventRecord(ev[3], c->stream);
-  launch_scatter(c->key, c->start, c->fill, c->perm, c->Mtot, c->cap, c->stream); ++n;
+  launch_scatter(c->key, c->start, c->count, c->perm, c->Mtot, c->cap, c->stream); ++n;
   if (ev) cudaEventRecord(ev[4], c->stream);
   return n;
 }
@@ -451,17 +451,14 @@ sp_status upload(sp_ctx* c) {
     off += n;
   }
   CK(cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * c->NC, c->stream));
-  CK(cudaMemsetAsync(c->fill, 0, sizeof(uint32_t) * c->NC, c->stream));
   const void* P3[3] = {c->pos[c->cur][0], c->pos[c->cur][1], c->pos[c->cur][2]};
   if (c->prec == SP_FP64) launch_keys_f64(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
   else launch_keys_f32(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
   launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream);
-  launch_cell_finalize(c->count, c->fill, c->NC, c->stream);
   c->hM = (uint32_t)M;
   CK(cudaMemcpyAsync(c->Mtot, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->Mcur, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
-  launch_scatter(c->key, c->start, c->fill, c->perm, c->Mtot, c->cap, c->stream);
-  CK(cudaMemsetAsync(c->fill, 0, sizeof(uint32_t) * c->NC, c->stream));
+  launch_scatter(c->key, c->start, c->count, c->perm, c->Mtot, c->cap, c->stream);
   // Delta t from the moments of this state
   for (int i = 0; i < c->n_inst; ++i) c->hinf[i] = 0x7FF0000000000000ull;
   CK(cudaMemcpyAsync(c->dt_min, c->hinf.data(), 8 * c->n_inst, cudaMemcpyHostToDevice, c->stream));
@@ -584,7 +581,6 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->part_inst, 4 * cap));
     CK(dalloc(&c->perm, 4 * cap));
     CK(dalloc(&c->count, 4 * NC));
-    CK(dalloc(&c->fill, 4 * NC));
     CK(dalloc(&c->start, 4 * (NC + 1)));
     CK(dalloc(&c->cell_inst, 4 * NC));
     CK(dalloc(&c->scan_part, 4 * scan_partial_size(NC)));
@@ -650,7 +646,6 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     if (!apply_schedule(c, kCapSmall, kWarpsDefault) && !apply_schedule(c, 256, 2)) return SP_ERR_CUDA;
     CK(cudaMemsetAsync(c->err, 0, 8 * kNumErr, s));
     CK(cudaMemsetAsync(c->count, 0, 4 * NC, s));
-    CK(cudaMemsetAsync(c->fill, 0, 4 * NC, s));
     CK(cudaStreamSynchronize(s));
     return SP_OK;
   }();
@@ -1084,7 +1079,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->fill, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->rem, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

@@ -89,17 +89,12 @@ __global__ void k_scan_down(const uint32_t* in, uint32_t* out, int64_t n, const 
   if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = partial[nb];
 }
 
-__global__ void k_zero2(uint32_t* a, uint32_t* b, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    a[i] = 0;
-    b[i] = 0;
-  }
-}
-
-// perm[start[key] + rank] = source index; the rank within a cell comes from
-// warp-aggregated atomics, so the order inside a cell is arbitrary here and
-// restored to source order by the collision kernel (a stable sort overall).
-__global__ void k_scatter(const uint32_t* key, const uint32_t* start, uint32_t* fill, uint32_t* perm,
+// perm[start[key] + rank] = source index.  The histogram itself is the
+// cursor: warp-aggregated atomic decrements hand out each cell's positions
+// from its end, and leave the histogram at zero for the next step's counts.
+// The order inside a cell is arbitrary here and restored to source order by
+// the collision kernel when the run is reproducible.
+__global__ void k_scatter(const uint32_t* key, const uint32_t* start, uint32_t* count, uint32_t* perm,
                           const uint32_t* Mtot, int64_t cap) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t M = (int64_t)*Mtot;
@@ -109,7 +104,7 @@ __global__ void k_scatter(const uint32_t* key, const uint32_t* start, uint32_t* 
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
   uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&fill[k], (uint32_t)__popc(peers));
+  if (lane == leader) base = atomicSub(&count[k], (uint32_t)__popc(peers)) - (uint32_t)__popc(peers);
   base = __shfl_sync(peers, base, leader);
   const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
   perm[start[k] + base + rank] = (uint32_t)i;
@@ -236,17 +231,10 @@ void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial
   k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partial, nb);
 }
 
-void launch_cell_finalize(uint32_t* count, uint32_t* fill, int64_t NC, cudaStream_t s) {
-  int64_t g = (NC + 255) / 256;
-  if (g > 4096) g = 4096;
-  if (g < 1) g = 1;
-  k_zero2<<<(unsigned)g, 256, 0, s>>>(count, fill, NC);
-}
-
-void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* fill, uint32_t* perm,
+void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* count, uint32_t* perm,
                     const uint32_t* Mtot, int64_t cap, cudaStream_t s) {
   const int64_t g = (cap + 255) / 256;
-  k_scatter<<<(unsigned)(g > 0 ? g : 1), 256, 0, s>>>(key, start, fill, perm, Mtot, cap);
+  k_scatter<<<(unsigned)(g > 0 ? g : 1), 256, 0, s>>>(key, start, count, perm, Mtot, cap);
 }
 
 void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,

@@ -151,10 +151,9 @@ SP_DECLARE_LAUNCHERS(f32)
 
 // Precision-independent kernels (sp_common.cu).
 void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s);
-void launch_cell_finalize(uint32_t* count, uint32_t* fill, int64_t NC, cudaStream_t s);
 void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
                  uint32_t* big_list, uint32_t* big_count, cudaStream_t s);
-void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* fill, uint32_t* perm,
+void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* count, uint32_t* perm,
                     const uint32_t* Mtot, int64_t cap, cudaStream_t s);
 void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
                           unsigned long long* dt_min, uint32_t* step, uint32_t* Mcur,
