@@ -525,21 +525,24 @@ def main():
     if not args.no_e2e:
         po, vo, _ = sim.particles(0)
         n_e2e = po.shape[1]
-        hp = torch.from_numpy(np.ascontiguousarray(po)).pin_memory()
-        hv = torch.from_numpy(np.ascontiguousarray(vo)).pin_memory()
+        # the context's own precision on the host side (FP32 state: FP32 input)
+        hdt = np.float32 if prec == sp.FP32 else np.float64
+        hp = torch.from_numpy(np.ascontiguousarray(po, dtype=hdt)).pin_memory()
+        hv = torch.from_numpy(np.ascontiguousarray(vo, dtype=hdt)).pin_memory()
+        upload = sim.set_particles_ptr_f32 if prec == sp.FP32 else sim.set_particles_ptr
         out = torch.empty((len(sp.FIELDS), sim.ncells[0]), dtype=torch.float64).pin_memory()
         K2 = 20
         for it in range(K2 + 2):
             if it == 2:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-            sim.set_particles_ptr(0, hp.data_ptr(), hv.data_ptr(), n_e2e)
+            upload(0, hp.data_ptr(), hv.data_ptr(), n_e2e)
             sim.step(1)
             sim.moments_into(0, 0, out.data_ptr())
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         line["e2e"] = {"value": world * K2 * n_e2e / te, "unit": UNIT,
-                       "h2d_bytes_per_step": 8 * (cfg["dim"] + 3) * n_e2e,
+                       "h2d_bytes_per_step": hp.element_size() * (cfg["dim"] + 3) * n_e2e,
                        "d2h_bytes_per_step": 8 * len(sp.FIELDS) * sim.ncells[0],
                        "note": "per step: pinned host state -> device, one step, moments -> pinned host"}
 

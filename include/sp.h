@@ -138,6 +138,10 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
  * and the step counter are kept.  Errors: SP_ERR_CAPACITY if n exceeds the
  * capacity. */
 sp_status sp_set_particles(sp_ctx* ctx, int inst, const double* pos, const double* vel, int64_t n);
+/* sp_set_particles with host FP32 arrays (same layout and behaviour): half
+ * the host-to-device bytes for FP32 contexts, whose state is FP32 anyway.
+ * In an FP64 context the values are widened exactly. */
+sp_status sp_set_particles_f32(sp_ctx* ctx, int inst, const float* pos, const float* vel, int64_t n);
 
 /* Advance all instances by n_steps global steps (asynchronous). */
 sp_status sp_step(sp_ctx* ctx, int n_steps);

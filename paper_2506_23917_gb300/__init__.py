@@ -51,7 +51,8 @@ class SpConfig(C.Structure):
 SYMBOLS = ["sp_init", "sp_set_particles", "sp_step", "sp_moments", "sp_get_particles",
            "sp_set_record", "sp_get_step_record", "sp_get_cell_start", "sp_get_sigc_max",
            "sp_get_dt", "sp_get_surface", "sp_errors", "sp_sync", "sp_step_profiled", "sp_set_schedule", "sp_set_reproducible", "sp_autotune", "sp_launches_per_step", "sp_free",
-           "sp_status_str", "sp_sort_cells_static", "sp_surface_coefficients"]
+           "sp_status_str", "sp_sort_cells_static", "sp_surface_coefficients",
+           "sp_set_particles_f32"]
 
 _lib = None
 
@@ -66,6 +67,7 @@ def lib():
         P = C.c_void_p
         L.sp_init.argtypes = [C.POINTER(SpConfig), C.c_int, C.c_int, C.c_int64, P, C.POINTER(P)]
         L.sp_set_particles.argtypes = [P, C.c_int, P, P, C.c_int64]
+        L.sp_set_particles_f32.argtypes = [P, C.c_int, P, P, C.c_int64]
         L.sp_step.argtypes = [P, C.c_int]
         L.sp_moments.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
         L.sp_get_particles.argtypes = [P, C.c_int, P, P, P, P]
@@ -221,6 +223,18 @@ class Sim:
     def set_particles_ptr(self, inst, pos_ptr, vel_ptr, n):
         """Like set_particles with raw host pointers (e.g. pinned torch tensors)."""
         _chk("sp_set_particles", lib().sp_set_particles(self.h, inst, C.c_void_p(pos_ptr), C.c_void_p(vel_ptr), n))
+
+    def set_particles_f32(self, inst, pos, vel):
+        """Like set_particles with FP32 host arrays (half the transfer)."""
+        pos = np.ascontiguousarray(pos, dtype=np.float32)
+        vel = np.ascontiguousarray(vel, dtype=np.float32)
+        n = vel.shape[1]
+        _chk("sp_set_particles_f32", lib().sp_set_particles_f32(self.h, inst, _ptr(pos), _ptr(vel), n))
+
+    def set_particles_ptr_f32(self, inst, pos_ptr, vel_ptr, n):
+        """set_particles_f32 with raw host pointers (e.g. pinned torch tensors)."""
+        _chk("sp_set_particles_f32",
+             lib().sp_set_particles_f32(self.h, inst, C.c_void_p(pos_ptr), C.c_void_p(vel_ptr), n))
 
     def step(self, n=1):
         _chk("sp_step", lib().sp_step(self.h, n))

@@ -58,6 +58,8 @@ struct sp_ctx {
   int64_t n_surf_tot = 0;
   double *vol = nullptr, *smax = nullptr, *samp = nullptr;
   double* rem = nullptr;  // [NC] carried NTC remainders
+  double* mom = nullptr;  // [SP_NFIELDS][largest instance] output of sp_moments kind 0
+  int64_t mom_cells = 0;
   int32_t* rec = nullptr;
   uint8_t* resamp = nullptr;
   double* dt_cur = nullptr;
@@ -76,6 +78,7 @@ struct sp_ctx {
   int launches = 0;
   std::vector<double*> dstage;    // per instance: FP64 [dim][n] then [3][n], device
   std::vector<int64_t> stage_n, stage_cap;
+  std::vector<int> stage_f32;     // per instance: the staged data is FP32
   uint32_t* part_inst = nullptr;  // [cap] instance of each uploaded particle
   std::vector<uint32_t> prev_start;  // [NC+1] of the state before the last step (record mode)
   std::vector<unsigned long long> hinf, hmin;  // host mirrors used by upload()
@@ -441,12 +444,21 @@ sp_status upload(sp_ctx* c) {
     const int64_t n = c->stage_n[i];
     if (n > 0) {
       const double* sp = c->dstage[i];
-      if (c->prec == SP_FP64)
+      const float* sf = (const float*)c->dstage[i];
+      if (c->stage_f32[i]) {
+        if (c->prec == SP_FP64)
+          launch_stage_in32_f64(dim, sf, sf + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
+                                (uint32_t)i, c->stream);
+        else
+          launch_stage_in32_f32(dim, sf, sf + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
+                                (uint32_t)i, c->stream);
+      } else if (c->prec == SP_FP64) {
         launch_stage_in_f64(dim, sp, sp + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
                             (uint32_t)i, c->stream);
-      else
+      } else {
         launch_stage_in_f32(dim, sp, sp + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
                             (uint32_t)i, c->stream);
+      }
     }
     off += n;
   }
@@ -562,6 +574,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
   c->dstage.assign(n_instances, nullptr);
   c->stage_n.assign(n_instances, 0);
   c->stage_cap.assign(n_instances, 0);
+  c->stage_f32.assign(n_instances, 0);
   c->hinf.assign(n_instances, 0x7FF0000000000000ull);
   c->hmin.assign(n_instances, 0);
   c->hdt.assign(n_instances, 0.0);
@@ -673,6 +686,29 @@ sp_status sp_set_particles(sp_ctx* c, int inst, const double* pos, const double*
     CK(cudaMemcpyAsync(c->dstage[inst] + c->dim * n, vel, 8 * 3 * n, cudaMemcpyHostToDevice, c->stream));
   }
   c->stage_n[inst] = n;
+  c->stage_f32[inst] = 0;
+  c->dirty = true;
+  return SP_OK;
+}
+
+sp_status sp_set_particles_f32(sp_ctx* c, int inst, const float* pos, const float* vel, int64_t n) {
+  if (!c || inst < 0 || inst >= c->n_inst || n < 0 || (n > 0 && (!pos || !vel))) return SP_ERR_ARG;
+  if (n > c->cap) return SP_ERR_CAPACITY;
+  const int64_t need = (int64_t)(c->dim + 3) * n;  // floats; the staging area counts doubles
+  if ((need + 1) / 2 > c->stage_cap[inst]) {
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->dstage[inst]) CK(cudaFree(c->dstage[inst]));
+    c->dstage[inst] = nullptr;
+    CK(dalloc(&c->dstage[inst], 4 * need + 8));
+    c->stage_cap[inst] = (need + 1) / 2;
+  }
+  if (n > 0) {
+    float* f = (float*)c->dstage[inst];
+    CK(cudaMemcpyAsync(f, pos, 4 * c->dim * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(f + c->dim * n, vel, 4 * 3 * n, cudaMemcpyHostToDevice, c->stream));
+  }
+  c->stage_n[inst] = n;
+  c->stage_f32[inst] = 1;
   c->dirty = true;
   return SP_OK;
 }
@@ -837,14 +873,20 @@ sp_status sp_moments(sp_ctx* c, int inst, int kind, double* out, int n_fields) {
   const int64_t nc = P.ncells;
   const int nf = std::min(n_fields, (int)SP_NFIELDS);
   if (kind == 0) {
-    double* d = nullptr;
-    CK(dalloc(&d, 8 * SP_NFIELDS * nc));
+    if (nc > c->mom_cells) {  // one device buffer, grown on demand
+      CK(cudaStreamSynchronize(c->stream));
+      if (c->mom) CK(cudaFree(c->mom));
+      c->mom = nullptr;
+      c->mom_cells = 0;
+      CK(dalloc(&c->mom, 8 * SP_NFIELDS * nc));
+      c->mom_cells = nc;
+    }
+    double* d = c->mom;
     StepArgs a = make_step_args(c, c->cur);
     if (c->prec == SP_FP64) launch_moments_f64(a, P.cell_off, P.cell_off + nc, d, c->stream);
     else launch_moments_f32(a, P.cell_off, P.cell_off + nc, d, c->stream);
     CK(cudaMemcpyAsync(out, d, 8 * nf * nc, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    CK(cudaFree(d));
   } else {
     std::vector<double> S(8 * nc), vol(nc);
     for (int f = 0; f < 8; ++f)
@@ -1079,7 +1121,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->mom, c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->rem, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

@@ -1400,8 +1400,8 @@ __global__ void k_keys(const T* x0, const T* x1, const T* x2, int64_t M, const u
 }
 
 // Host-provided FP64 particles of one instance -> state buffers at offset off.
-template <class T>
-__global__ void k_stage_in(const double* pos, const double* vel, int dim, int64_t n, T* p0, T* p1, T* p2,
+template <class T, class S>
+__global__ void k_stage_in(const S* pos, const S* vel, int dim, int64_t n, T* p0, T* p1, T* p2,
                            T* v0, T* v1, T* v2, int64_t off, uint32_t* part_inst, uint32_t inst) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;

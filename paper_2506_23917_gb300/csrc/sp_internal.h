@@ -140,6 +140,9 @@ struct InjectArgs {
   void launch_gather_##tag(int dim, const void* const Apos[3], const void* const Avel[3],        \
                            const uint32_t* perm, int64_t s0, int64_t n, double* out_pos,          \
                            double* out_vel, cudaStream_t s);                                      \
+  void launch_stage_in32_##tag(int dim, const float* pos, const float* vel, int64_t n,              \
+                               void* const dpos[3], void* const dvel[3], int64_t off,            \
+                               uint32_t* part_inst, uint32_t inst, cudaStream_t s);              \
   void launch_stage_in_##tag(int dim, const double* pos, const double* vel, int64_t n,             \
                              void* const dpos[3], void* const dvel[3], int64_t off,              \
                              uint32_t* part_inst, uint32_t inst, cudaStream_t s);                \

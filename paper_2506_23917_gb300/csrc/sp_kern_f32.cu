@@ -112,6 +112,15 @@ void launch_stage_in_f32(int dim, const double* pos, const double* vel, int64_t 
                                             (T*)dvel[0], (T*)dvel[1], (T*)dvel[2], off, part_inst, inst);
 }
 
+void launch_stage_in32_f32(int dim, const float* pos, const float* vel, int64_t n, void* const dpos[3],
+                          void* const dvel[3], int64_t off, uint32_t* part_inst, uint32_t inst,
+                          cudaStream_t s) {
+  if (n == 0) return;
+  const int64_t g = (n + 255) / 256;
+  k_stage_in<T><<<(unsigned)g, 256, 0, s>>>(pos, vel, dim, n, (T*)dpos[0], (T*)dpos[1], (T*)dpos[2],
+                                            (T*)dvel[0], (T*)dvel[1], (T*)dvel[2], off, part_inst, inst);
+}
+
 int collide_blocks_per_sm_f32(int dim, int warps, int cap, bool one) {
   const size_t smem = (size_t)warps * warp_stage_bytes<T>(cap);
   if (dim == 1) return blocks_per_sm<1>(warps, smem, one);

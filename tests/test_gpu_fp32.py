@@ -142,3 +142,33 @@ def test_fp32_closed_box_conserves_energy(sp):
         _, v, _ = s.particles(0)
         assert abs((v ** 2).sum() / e0 - 1.0) < 5e-5
     assert s.count(0) == N
+
+
+@pytest.mark.parametrize("prec_name", ["FP32", "FP64"])
+def test_fp32_host_input_gives_the_same_state(prec_name):
+    """sp_set_particles_f32 (FP32 host arrays) leaves the same state as
+    sp_set_particles given the same values as FP64 arrays, and the same
+    state after a few steps."""
+    import paper_2506_23917_gb300 as sp
+    from paper_2506_23917_gb300 import build
+
+    build.build()
+    prec = getattr(sp, prec_name)
+    cfg, regions = W.box2d(nx=24, ny=12, ppc=30.0)
+    pos, vel = W.fill_regions(cfg, regions, 3)
+    pos32, vel32 = pos.astype(np.float32), vel.astype(np.float32)
+    a = sp.Sim(cfg, prec, capacity=4 * vel.shape[1])
+    b = sp.Sim(cfg, prec, capacity=4 * vel.shape[1])
+    a.set_particles(0, pos32.astype(np.float64), vel32.astype(np.float64))
+    b.set_particles_f32(0, pos32, vel32)
+    for sim in (a, b):
+        sim.step(5)
+        sim.sync()
+    pa, va, ca = a.particles(0)
+    pb, vb, cb = b.particles(0)
+    np.testing.assert_array_equal(ca, cb)
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(va, vb)
+    assert a.dt(0) == b.dt(0)
+    a.close()
+    b.close()
