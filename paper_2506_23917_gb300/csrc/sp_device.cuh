@@ -1314,49 +1314,68 @@ __global__ void k_inject(InjectArgs a, int pass) {
 // sums).  With out == nullptr only dt_min is updated.
 template <class T>
 __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
+  // sums warp per cell, 32 cells in a row; then the FP64 scalars lane per
+  // cell (lane j <-> cell kb + j), so each FP64 instruction serves 32 cells
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nc = c1 - c0;
-  for (int64_t k = c0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c1; k += nw) {
-    const uint32_t s0 = a.start[k];
-    const int N = (int)(a.start[k + 1] - s0);
-    const InstParams& P = a.P[a.cell_inst[k]];
-    // two passes straight from global memory
-    const T* Av0 = (const T*)a.Avel[0];
-    const T* Av1 = (const T*)a.Avel[1];
-    const T* Av2 = (const T*)a.Avel[2];
-    double U[3] = {0, 0, 0};
-    {
-      T s0x = 0, s1x = 0, s2x = 0;
-      for (int s = lane; s < N; s += 32) {
-        const uint32_t o = a.perm[s0 + s];
-        s0x += Av0[o]; s1x += Av1[o]; s2x += Av2[o];
+  const T* Av0 = (const T*)a.Avel[0];
+  const T* Av1 = (const T*)a.Avel[1];
+  const T* Av2 = (const T*)a.Avel[2];
+  for (int64_t kb = c0 + 32 * ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); kb < c1;
+       kb += 32 * nw) {
+    int myN = 0;
+    double myU[3] = {0, 0, 0};
+    T myS2 = 0, myS3[3] = {0, 0, 0};
+    const int nj = (int)((c1 - kb) < 32 ? (c1 - kb) : 32);
+    for (int j = 0; j < nj; ++j) {
+      const int64_t k = kb + j;
+      const uint32_t s0 = a.start[k];
+      const int N = (int)(a.start[k + 1] - s0);
+      double U[3] = {0, 0, 0};
+      {
+        T s0x = 0, s1x = 0, s2x = 0;
+        for (int s = lane; s < N; s += 32) {
+          const uint32_t o = a.perm[s0 + s];
+          s0x += Av0[o]; s1x += Av1[o]; s2x += Av2[o];
+        }
+        s0x = warp_sum(s0x); s1x = warp_sum(s1x); s2x = warp_sum(s2x);
+        if (N > 0) { U[0] = (double)s0x / N; U[1] = (double)s1x / N; U[2] = (double)s2x / N; }
       }
-      s0x = warp_sum(s0x); s1x = warp_sum(s1x); s2x = warp_sum(s2x);
-      if (N > 0) { U[0] = (double)s0x / N; U[1] = (double)s1x / N; U[2] = (double)s2x / N; }
+      T S2 = 0, S3x = 0, S3y = 0, S3z = 0;
+      if (N >= 2) {
+        const T Ux = (T)U[0], Uy = (T)U[1], Uz = (T)U[2];
+        for (int s = lane; s < N; s += 32) {
+          const uint32_t o = a.perm[s0 + s];
+          const T C0 = Av0[o] - Ux, C1 = Av1[o] - Uy, C2 = Av2[o] - Uz;
+          const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+          S2 += c2; S3x += c2 * C0; S3y += c2 * C1; S3z += c2 * C2;
+        }
+        S2 = warp_sum(S2); S3x = warp_sum(S3x); S3y = warp_sum(S3y); S3z = warp_sum(S3z);
+      }
+      if (lane == j) {
+        myN = N;
+        myU[0] = U[0]; myU[1] = U[1]; myU[2] = U[2];
+        myS2 = S2; myS3[0] = S3x; myS3[1] = S3y; myS3[2] = S3z;
+      }
     }
+    if (lane >= nj) continue;
+    const int64_t k = kb + lane;
+    const int N = myN;
+    const InstParams& P = a.P[a.cell_inst[k]];
     CellMoments m;
-    m.U[0] = U[0]; m.U[1] = U[1]; m.U[2] = U[2];
+    m.U[0] = myU[0]; m.U[1] = myU[1]; m.U[2] = myU[2];
     m.n = N > 0 ? (double)N * P.Fn / a.vol[k] : 0.0;
     m.T = 0; m.q[0] = m.q[1] = m.q[2] = 0;
     m.tau = __longlong_as_double(0x7FF0000000000000ll);
     m.dtc = m.tau;
     if (N >= 2) {
-      const T Ux = (T)U[0], Uy = (T)U[1], Uz = (T)U[2];
-      T S2 = 0, S3x = 0, S3y = 0, S3z = 0;
-      for (int s = lane; s < N; s += 32) {
-        const uint32_t o = a.perm[s0 + s];
-        const T C0 = Av0[o] - Ux, C1 = Av1[o] - Uy, C2 = Av2[o] - Uz;
-        const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
-        S2 += c2; S3x += c2 * C0; S3y += c2 * C1; S3z += c2 * C2;
-      }
-      S2 = warp_sum(S2); S3x = warp_sum(S3x); S3y = warp_sum(S3y); S3z = warp_sum(S3z);
-      m.T = (double)S2 / (3.0 * P.R * (double)(N - 1));
+      m.T = (double)myS2 / (3.0 * P.R * (double)(N - 1));
       if (N >= 3) {
         const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
-        m.q[0] = f * (double)S3x; m.q[1] = f * (double)S3y; m.q[2] = f * (double)S3z;
+        m.q[0] = f * (double)myS3[0]; m.q[1] = f * (double)myS3[1]; m.q[2] = f * (double)myS3[2];
       }
-      const double umag = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+      const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
       if (m.T > 0) {
         const double p = m.n * P.m * P.R * m.T;
         m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
@@ -1365,24 +1384,22 @@ __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
         m.dtc = P.Lmin / umag;
       }
     }
-    if (lane == 0) {
-      if (out) {
-        const int64_t i = k - c0;
-        out[0 * nc + i] = (double)N;
-        out[1 * nc + i] = m.n;
-        out[2 * nc + i] = m.U[0];
-        out[3 * nc + i] = m.U[1];
-        out[4 * nc + i] = m.U[2];
-        out[5 * nc + i] = m.T;
-        out[6 * nc + i] = m.q[0];
-        out[7 * nc + i] = m.q[1];
-        out[8 * nc + i] = m.q[2];
-        out[9 * nc + i] = m.tau;
-        out[10 * nc + i] = m.dtc;
-        out[11 * nc + i] = dsmc_ratio(P, N, m);
-      } else if (N >= 2 && m.dtc < __longlong_as_double(0x7FF0000000000000ll)) {
-        atomicMin(&a.dt_min[a.cell_inst[k]], (unsigned long long)__double_as_longlong(m.dtc));
-      }
+    if (out) {
+      const int64_t i = k - c0;
+      out[0 * nc + i] = (double)N;
+      out[1 * nc + i] = m.n;
+      out[2 * nc + i] = m.U[0];
+      out[3 * nc + i] = m.U[1];
+      out[4 * nc + i] = m.U[2];
+      out[5 * nc + i] = m.T;
+      out[6 * nc + i] = m.q[0];
+      out[7 * nc + i] = m.q[1];
+      out[8 * nc + i] = m.q[2];
+      out[9 * nc + i] = m.tau;
+      out[10 * nc + i] = m.dtc;
+      out[11 * nc + i] = dsmc_ratio(P, N, m);
+    } else if (N >= 2 && m.dtc < __longlong_as_double(0x7FF0000000000000ll)) {
+      atomicMin(&a.dt_min[a.cell_inst[k]], (unsigned long long)__double_as_longlong(m.dtc));
     }
   }
 }

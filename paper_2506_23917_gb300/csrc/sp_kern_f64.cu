@@ -79,7 +79,7 @@ void launch_inject_f64(int dim, const InjectArgs& a, int pass, cudaStream_t s) {
 
 void launch_moments_f64(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s) {
   const int64_t nc = c1 - c0;
-  int64_t g = (nc + 7) / 8;
+  int64_t g = (nc + 255) / 256;  // a warp per 32 cells, 8 warps per block
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
   k_moments<T><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, out);
