@@ -1408,12 +1408,14 @@ template <class T, int DIM>
 __global__ void k_keys(const T* x0, const T* x1, const T* x2, int64_t M, const uint32_t* part_inst,
                        const InstParams* Ps, uint32_t* key, uint32_t* count) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const InstParams& P = Ps[part_inst[i]];
-  T x[3] = {x0[i], DIM > 1 ? x1[i] : (T)0, DIM > 2 ? x2[i] : (T)0};
-  const uint32_t k = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
-  key[i] = k;
-  atomicAdd(&count[k], 1u);
+  uint32_t k = kSentinel;
+  if (i < M) {
+    const InstParams& P = Ps[part_inst[i]];
+    T x[3] = {x0[i], DIM > 1 ? x1[i] : (T)0, DIM > 2 ? x2[i] : (T)0};
+    k = (uint32_t)P.cell_off + cell_of<T, DIM>(P, x);
+    key[i] = k;
+  }
+  warp_count(k, count);  // one atomic per cell per warp (input sorted by cell: few)
 }
 
 // Host-provided FP64 particles of one instance -> state buffers at offset off.
