@@ -519,6 +519,43 @@ __device__ __forceinline__ const InstParams& inst_params(const StepArgs& a, uint
   else return a.P[i];
 }
 
+// Per-cell sums with an order fixed by the cell alone (so results do not
+// depend on how cells are grouped into batches): a cell of at most
+// kLaneSumMax particles is summed by its own lane (lane i <-> cell i) in
+// slot order, with no shuffles; the cells above it by the warp's segmented
+// scan.  Writes acc[k][i] for every own cell i.
+constexpr int kLaneSumMax = 256;
+template <class T, int K, class F>
+__device__ __forceinline__ void cell_sums(int M, uint32_t p0, const uint8_t* sseg, T (*acc)[32], bool own,
+                                          int offi, int Ni, F f) {
+  const int lane = threadIdx.x & 31;
+  const bool small = own && Ni <= kLaneSumMax;
+  if (small) {
+    T a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = 0;
+    for (int s = offi; s < offi + Ni; ++s) {
+      T v[K];
+      f(s, v);
+#pragma unroll
+      for (int k = 0; k < K; ++k) a[k] += v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k][lane] = a[k];
+  } else if (own) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k][lane] = 0;
+  }
+  const unsigned bigs = __ballot_sync(kFull, own && !small);
+  __syncwarp();
+  if (bigs) {
+    seg_sums<T, K>(M, p0, sseg, acc, [&](int s, T* v) {
+      if ((bigs >> sseg[s]) & 1u) f(s, v);
+    });
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // One batch of G consecutive cells [k0, k0+G) whose particles fit the warp's
 // staging area: gather in stable order -> Step 3 moments -> Step 4 split,
@@ -646,7 +683,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   if (own)
     for (int k = 0; k < 7; ++k) ct->acc[k][lane] = 0;
   __syncwarp();
-  seg_sums<T, 3>(M, p0, sseg, ct->acc, [&](int s, T* v) {
+  cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, T* v) {
     v[0] = svx[s];
     v[1] = svy[s];
     v[2] = svz[s];
@@ -657,7 +694,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     ct->U[2][lane] = ct->acc[2][lane] / (T)Ni;
   }
   __syncwarp();
-  seg_sums<T, 4>(M, p0, sseg, ct->acc + 3, [&](int s, T* v) {
+  cell_sums<T, 4>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, T* v) {
     const int c = sseg[s];
     const T C0 = svx[s] - ct->U[0][c], C1 = svy[s] - ct->U[1][c], C2 = svz[s] - ct->U[2][c];
     const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
@@ -1004,7 +1041,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (own)
       for (int k = 0; k < 4; ++k) ct->acc[k][lane] = 0;
     __syncwarp();
-    seg_sums<T, 3>(M, p0, sseg, ct->acc, [&](int s, T* v) {
+    cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, T* v) {
       v[0] = svx[s];
       v[1] = svy[s];
       v[2] = svz[s];
@@ -1015,7 +1052,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       ct->Up[2][lane] = ct->acc[2][lane] / (T)Ni;
     }
     __syncwarp();
-    seg_sums<T, 1>(M, p0, sseg, ct->acc + 3, [&](int s, T* v) {
+    cell_sums<T, 1>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, T* v) {
       const int c = sseg[s];
       const T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
       v[0] = C0 * C0 + C1 * C1 + C2 * C2;
@@ -1048,7 +1085,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (own)
       for (int k = 0; k < 3; ++k) ct->acc[k][lane] = 0;
     __syncwarp();
-    seg_sums<T, 3>(M, p0, sseg, ct->acc, [&](int s, T* v) {
+    cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, T* v) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
       v[0] = x0 * x0;
       v[1] = x1 * x1;
