@@ -536,7 +536,7 @@ __device__ __forceinline__ void cell_sums(int M, uint32_t p0, const uint8_t* sse
     for (int k = 0; k < K; ++k) a[k] = 0;
     for (int s = offi; s < offi + Ni; ++s) {
       T v[K];
-      f(s, v);
+      f(s, lane, v);
 #pragma unroll
       for (int k = 0; k < K; ++k) a[k] += v[k];
     }
@@ -550,7 +550,8 @@ __device__ __forceinline__ void cell_sums(int M, uint32_t p0, const uint8_t* sse
   __syncwarp();
   if (bigs) {
     seg_sums<T, K>(M, p0, sseg, acc, [&](int s, T* v) {
-      if ((bigs >> sseg[s]) & 1u) f(s, v);
+      const int c = sseg[s];
+      if ((bigs >> c) & 1u) f(s, c, v);
     });
   }
   __syncwarp();
@@ -683,7 +684,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   if (own)
     for (int k = 0; k < 7; ++k) ct->acc[k][lane] = 0;
   __syncwarp();
-  cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, T* v) {
+  cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, int c, T* v) {
     v[0] = svx[s];
     v[1] = svy[s];
     v[2] = svz[s];
@@ -694,8 +695,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     ct->U[2][lane] = ct->acc[2][lane] / (T)Ni;
   }
   __syncwarp();
-  cell_sums<T, 4>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, T* v) {
-    const int c = sseg[s];
+  cell_sums<T, 4>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, int c, T* v) {
     const T C0 = svx[s] - ct->U[0][c], C1 = svy[s] - ct->U[1][c], C2 = svz[s] - ct->U[2][c];
     const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
     v[0] = c2;
@@ -1034,6 +1034,11 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     }
   }
   __syncwarp();
+  // FP32 staging: the free flight's source indices, copied from perm into
+  // the clash-tag array (free from here on) while the next phases run
+  if (idx_in_velocity<T>()) {
+    for (int s = lane; s < M; s += 32) cp_async<4>(&stag[s], &a.perm[p0 + s]);
+  }
   // ---- 7. conservation rescale c' = U + (c_p - U_p) sqrt(T/T_p)
   const int nres_i = own ? ct->nres[lane] : 0;
   const unsigned rcells = __ballot_sync(kFull, nres_i > 0);
@@ -1041,7 +1046,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (own)
       for (int k = 0; k < 4; ++k) ct->acc[k][lane] = 0;
     __syncwarp();
-    cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, T* v) {
+    cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, int c, T* v) {
       v[0] = svx[s];
       v[1] = svy[s];
       v[2] = svz[s];
@@ -1052,8 +1057,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       ct->Up[2][lane] = ct->acc[2][lane] / (T)Ni;
     }
     __syncwarp();
-    cell_sums<T, 1>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, T* v) {
-      const int c = sseg[s];
+    cell_sums<T, 1>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, int c, T* v) {
       const T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
       v[0] = C0 * C0 + C1 * C1 + C2 * C2;
     });
@@ -1085,7 +1089,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (own)
       for (int k = 0; k < 3; ++k) ct->acc[k][lane] = 0;
     __syncwarp();
-    cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, T* v) {
+    cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, int c, T* v) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
       v[0] = x0 * x0;
       v[1] = x1 * x1;
@@ -1122,13 +1126,15 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   // rotate through registers)
   T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
   T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
+  if (idx_in_velocity<T>()) cp_async_wait_all();
+  __syncwarp();
   for (int sb0 = 0; sb0 < M; sb0 += 128) {
     T xr[4][DIM] = {};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int s = sb0 + 32 * u + lane;
       if (s < M) {
-        const uint32_t o = idx_in_velocity<T>() ? a.perm[p0 + s] : sidx[s];
+        const uint32_t o = idx_in_velocity<T>() ? (uint32_t)stag[s] : sidx[s];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) xr[u][d] = ((const T*)a.Apos[d])[o];
       }
