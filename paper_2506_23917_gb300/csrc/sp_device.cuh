@@ -577,7 +577,10 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   const int64_t kc = k0 + (own ? lane : 0);
   int Ni = 0, offi = 0;
   uint32_t inst = 0;
+  double vol_k = 1.0, smax_k = 0.0;  // loaded early: used by the cell math
   if (own) {
+    vol_k = a.vol[kc];
+    smax_k = a.smax[kc];
     const uint32_t s0 = a.start[kc];
     Ni = (int)(a.start[kc + 1] - s0);
     offi = (int)(s0 - p0);
@@ -735,7 +738,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   bool sample = false;
   if (own) {
     sample = (int64_t)step >= (int64_t)Pi.n_steady;
-    const T V = (T)a.vol[kc];
+    const T V = (T)vol_k;
     T Ut[3] = {0, 0, 0}, Tt = 0, qt[3] = {0, 0, 0}, nt = 0;
     T taut = tinf<T>(), dtct = tinf<T>();
     if (Ni > 0) {
@@ -789,7 +792,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         sbgk = ((T)1.0 - r) * dtG;
       }
       if (dsmc > (T)0) {
-        smaxT = (T)a.smax[kc];
+        smaxT = (T)smax_k;
         const T ncr = (T)0.5 * (T)Ni * (T)(Ni - 1) * (T)Pi.Fn * smaxT * dsmc / V;
         if (Pi.ntc_carry) {  // Bird's carried remainder (FP64 state per cell)
           const double x = (double)ncr + a.rem[kc];
@@ -1085,6 +1088,11 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   const bool anys = __any_sync(kFull, sample && Ni > 0);
   const T a0 = m0, a1 = m1, a2 = m2;
   T b0 = 0, b1 = 0, b2 = 0;
+  double sv[8];  // the accumulators, requested before the sums
+  if (own && sample) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sv[k] = a.samp[k * NC + kc];
+  }
   if (anys) {
     if (own)
       for (int k = 0; k < 3; ++k) ct->acc[k][lane] = 0;
@@ -1102,16 +1110,16 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   if (own) {
     if (sample) {
       double* S = a.samp;
-      S[0 * NC + kc] += (double)Ni;
+      S[0 * NC + kc] = sv[0] + (double)Ni;
       if (Ni > 0) {
-        S[1 * NC + kc] += (double)a0;
-        S[2 * NC + kc] += (double)a1;
-        S[3 * NC + kc] += (double)a2;
-        S[4 * NC + kc] += (double)b0;
-        S[5 * NC + kc] += (double)b1;
-        S[6 * NC + kc] += (double)b2;
+        S[1 * NC + kc] = sv[1] + (double)a0;
+        S[2 * NC + kc] = sv[2] + (double)a1;
+        S[3 * NC + kc] = sv[3] + (double)a2;
+        S[4 * NC + kc] = sv[4] + (double)b0;
+        S[5 * NC + kc] = sv[5] + (double)b1;
+        S[6 * NC + kc] = sv[6] + (double)b2;
       }
-      S[7 * NC + kc] += ratio;
+      S[7 * NC + kc] = sv[7] + ratio;
     }
     if (a.rec) {
       a.rec[0 * NC + kc] = (int32_t)ncol;
