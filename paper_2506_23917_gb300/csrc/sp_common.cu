@@ -128,6 +128,8 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
     *ticket = 0u;
     nbatch[0] = 0u;
     nbatch[1] = 0u;
+    nbatch[2] = 0u;
+    nbatch[3] = 0u;
     // batches slower than 2.5x this step's mean are planned first next step
     cyc[2] = cyc[1] > 0 ? (cyc[0] / cyc[1]) * 5ull / 2ull : ~0ull;
     cyc[0] = 0ull;
@@ -148,10 +150,17 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 // particles fit a warp's staging area (at most 32 cells each); cells above
 // it go to the big-cell list.  One warp per 32-cell chunk.  Batches holding
 // a cell flagged hot (its batch was slow in the previous step: dense cells
-// with many collisions and resamplings) are listed from the front of the
-// array, the others from the back; the collision kernel hands out the front
-// ones first, so slow batches do not start last and leave SMs idle at the
-// end of the launch.  Batches are independent: their order changes no result.
+// with many collisions and resamplings) form the first class; the others
+// are classed by particle count: large (at least cap/2), medium (cap/4 up
+// to cap/2) and small.  The collision kernel hands out the classes in that
+// order, longest first, so that the batches still running when the list
+// runs out are short ones and the SMs finish the launch together.  A warp
+// takes only a few batches per launch, so without this the last large
+// batches alone would keep a few SMs busy for a third of the launch.
+// Layout of the [2 NC] array: heavy from the front and small from the back
+// of [0, NC), large from the front and medium from the back of [NC, 2 NC)
+// (each pair holds at most NC batches).  Batches are independent: their
+// order changes no result.
 __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches,
                        uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
   const int lane = threadIdx.x & 31;
@@ -170,7 +179,7 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
     const unsigned hmask = __ballot_sync(0xFFFFFFFFu, lane < nc && hot[c0 + lane] != 0);
     int kk = 0, nb = 0;
     uint2 mine = make_uint2(0, 0);
-    bool mine_hot = false;
+    int mine_cls = 0;
     while (kk < nc) {
       const int before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
       const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap);
@@ -183,27 +192,28 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
         kk += 1;
         continue;
       }
+      const int np = __shfl_sync(0xFFFFFFFFu, cum, kk + G - 1) - before;
       if (lane == nb) {
         mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
         const unsigned gm = G >= 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
-        mine_hot = ((hmask >> kk) & gm) != 0u;
+        mine_cls = ((hmask >> kk) & gm) != 0u ? 0 : (2 * np >= cap ? 1 : (4 * np >= cap ? 2 : 3));
       }
       ++nb;
       kk += G;
     }
     const bool have = lane < nb;
-    const unsigned hb = __ballot_sync(0xFFFFFFFFu, have && mine_hot);
-    const unsigned nbm = __ballot_sync(0xFFFFFFFFu, have && !mine_hot);
-    uint32_t bh = 0, bn = 0;
-    if (lane == 0) {
-      if (hb) bh = atomicAdd(&nbatch[0], (uint32_t)__popc(hb));
-      if (nbm) bn = atomicAdd(&nbatch[1], (uint32_t)__popc(nbm));
-    }
-    bh = __shfl_sync(0xFFFFFFFFu, bh, 0);
-    bn = __shfl_sync(0xFFFFFFFFu, bn, 0);
     const unsigned below = (1u << lane) - 1u;
-    if (have && mine_hot) batches[bh + __popc(hb & below)] = mine;
-    if (have && !mine_hot) batches[NC - 1 - (int64_t)(bn + __popc(nbm & below))] = mine;
+#pragma unroll
+    for (int cls = 0; cls < 4; ++cls) {
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, have && mine_cls == cls);
+      if (m == 0u) continue;
+      uint32_t b0 = 0;
+      if (lane == 0) b0 = atomicAdd(&nbatch[cls], (uint32_t)__popc(m));
+      b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+      const int64_t j = (int64_t)b0 + __popc(m & below);
+      const int64_t at = cls == 0 ? j : cls == 1 ? NC + j : cls == 2 ? 2 * NC - 1 - j : NC - 1 - j;
+      if (have && mine_cls == cls) batches[at] = mine;
+    }
   }
 }
 

@@ -1211,11 +1211,13 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
   uint8_t* sseg = (uint8_t*)(stag + cap);
   // One call site of process_batch for both launches, so that every cell
   // runs through the same inlined code (identical rounding whichever launch
-  // or batch takes it).  Main launch: batches from the plan's list by
-  // work stealing, heavy ones (from the front) first, then the others (from
-  // the back).  Big-cell launch: a block per cell of the big list.
+  // or batch takes it).  Main launch: batches from the plan's four class
+  // lists by work stealing, heavy, large, medium, then small.  Big-cell
+  // launch: a block per cell of the big list.
   const uint32_t nh = big ? 0u : a.nbatch[0];
-  const uint32_t nb = big ? *a.big_count : nh + a.nbatch[1];
+  const uint32_t nl = big ? 0u : nh + a.nbatch[1];
+  const uint32_t nm = big ? 0u : nl + a.nbatch[2];
+  const uint32_t nb = big ? *a.big_count : nm + a.nbatch[3];
   uint32_t it = big ? blockIdx.x : 0u;
   for (;;) {
     int64_t k0;
@@ -1225,7 +1227,11 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
       if (lane == 0) t = atomicAdd(a.ticket, 1u);
       t = __shfl_sync(kFull, t, 0);
       if (t >= nb) break;
-      const uint2 b = t < nh ? a.batches[t] : a.batches[a.NC - 1 - (int64_t)(t - nh)];
+      const int64_t at = t < nh ? (int64_t)t
+                       : t < nl ? a.NC + (int64_t)(t - nh)
+                       : t < nm ? 2 * a.NC - 1 - (int64_t)(t - nl)
+                                : a.NC - 1 - (int64_t)(t - nm);
+      const uint2 b = a.batches[at];
       k0 = (int64_t)b.x;
       G = (int)b.y;
     } else {

@@ -96,8 +96,8 @@ struct StepArgs {
   uint32_t* big_list;   // cells above kCapSmall
   uint32_t* big_count;
   uint32_t* ticket;     // work-stealing counter over the batch list
-  const uint2* batches; // (first cell, cell count) of each batch
-  const uint32_t* nbatch;  // [0] heavy batches (listed from the front), [1] others (from the back)
+  const uint2* batches; // [2 NC] (first cell, cell count) of each batch, four class lists
+  const uint32_t* nbatch;  // [4] batches per class: heavy, large, medium, small (taken in that order)
   uint8_t* hot;         // [NC] the cell's batch was slower than the threshold last step
   unsigned long long* cyc;  // [3] batch cycles this step (sum, count), threshold
   unsigned long long* err;  // [kNumErr]
