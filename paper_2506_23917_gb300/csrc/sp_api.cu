@@ -48,7 +48,7 @@ struct sp_ctx {
   uint2* batches = nullptr;
   uint32_t* nbatch = nullptr;         // [4] batches of the plan per class (heavy, large, medium, small)
   uint8_t* hot = nullptr;             // [NC] slow-batch flags of the last step
-  unsigned long long* cyc = nullptr;  // [3] batch-cycle sum, count, threshold
+  unsigned long long* cyc = nullptr;  // [3] batch-cycle sum, particle sum, hot threshold per particle
   int collide_grid = 1;
   int nsm = 1;
   int sched_cap = kCapSmall, sched_warps = kWarpsDefault;

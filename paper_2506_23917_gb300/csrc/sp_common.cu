@@ -130,8 +130,9 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
     nbatch[1] = 0u;
     nbatch[2] = 0u;
     nbatch[3] = 0u;
-    // batches slower than 2.5x this step's mean are planned first next step
-    cyc[2] = cyc[1] > 0 ? (cyc[0] / cyc[1]) * 5ull / 2ull : ~0ull;
+    // threshold of the hot flag: cycles per particle, 2.5 times
+    // this step's mean over all batches
+    cyc[2] = cyc[1] > 0 ? (cyc[0] * 5ull) / (2ull * cyc[1]) : ~0ull;
     cyc[0] = 0ull;
     cyc[1] = 0ull;
   }
@@ -148,9 +149,13 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 }
 // Work plan of a step: consecutive cells are grouped into batches whose
 // particles fit a warp's staging area (at most 32 cells each); cells above
-// it go to the big-cell list.  One warp per 32-cell chunk.  Batches holding
-// a cell flagged hot (its batch was slow in the previous step: dense cells
-// with many collisions and resamplings) form the first class; the others
+// it go to the big-cell list.  One warp per 32-cell chunk.  Cells flagged
+// hot (their batch cost more per particle than 2.5 times the step's
+// mean: cells where most particles are resampled with many rejections, or
+// with many collision candidates) weigh kHotWeight times their particles
+// when batches are packed, so their work is spread over that many more
+// warps instead of one slow batch setting the end of the launch.  Batches
+// holding a hot cell form the first class; the others
 // are classed by particle count: large (at least cap/2), medium (cap/4 up
 // to cap/2) and small.  The collision kernel hands out the classes in that
 // order, longest first, so that the batches still running when the list
@@ -170,29 +175,43 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
        chunk += nw) {
     const int64_t c0 = chunk * 32;
     const int nc = (int)((NC - c0) < 32 ? (NC - c0) : 32);
-    int cum = lane < nc ? (int)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
+    const bool is_hot = lane < nc && hot[c0 + lane] != 0;
+    const int64_t n_k = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
+    // particles (cum) and weight (wcum: hot cells count kHotWeight times)
+    int64_t cum = n_k, wcum = is_hot ? kHotWeight * n_k : n_k;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
-      if (lane >= o) cum += y;
+      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
+      const int64_t wy = __shfl_up_sync(0xFFFFFFFFu, wcum, o);
+      if (lane >= o) {
+        cum += y;
+        wcum += wy;
+      }
     }
-    const unsigned hmask = __ballot_sync(0xFFFFFFFFu, lane < nc && hot[c0 + lane] != 0);
+    const unsigned hmask = __ballot_sync(0xFFFFFFFFu, is_hot);
     int kk = 0, nb = 0;
     uint2 mine = make_uint2(0, 0);
     int mine_cls = 0;
     while (kk < nc) {
-      const int before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
-      const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap);
-      const int G = __popc(fit);
+      const int64_t before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
+      const int64_t wbefore = kk > 0 ? __shfl_sync(0xFFFFFFFFu, wcum, kk - 1) : 0;
+      const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && wcum - wbefore <= cap);
+      int G = __popc(fit);
       if (G == 0) {
-        if (lane == 0) {
-          const uint32_t i = atomicAdd(big_count, 1u);
-          big_list[i] = (uint32_t)(c0 + kk);
+        // the cell alone outweighs a batch: a batch of its own if its
+        // particles fit the staging area, else the big-cell list
+        if (__shfl_sync(0xFFFFFFFFu, cum, kk) - before <= cap) {
+          G = 1;
+        } else {
+          if (lane == 0) {
+            const uint32_t i = atomicAdd(big_count, 1u);
+            big_list[i] = (uint32_t)(c0 + kk);
+          }
+          kk += 1;
+          continue;
         }
-        kk += 1;
-        continue;
       }
-      const int np = __shfl_sync(0xFFFFFFFFu, cum, kk + G - 1) - before;
+      const int np = (int)(__shfl_sync(0xFFFFFFFFu, cum, kk + G - 1) - before);
       if (lane == nb) {
         mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
         const unsigned gm = G >= 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);

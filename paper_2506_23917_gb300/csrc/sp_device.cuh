@@ -120,6 +120,8 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gsrc), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Request a global line into L2 (no register result, nothing waits on it).
+__device__ __forceinline__ void prefetch_l2(const void* g) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(g)); }
 
 // ---------------------------------------------------------------------------
 // Precision helpers
@@ -671,13 +673,17 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     const T* Av0 = (const T*)a.Avel[0];
     const T* Av1 = (const T*)a.Avel[1];
     const T* Av2 = (const T*)a.Avel[2];
-    // every lane issues all of its copies before waiting once
+    // every lane issues all of its copies before waiting once; the
+    // positions, read only by the free flight at the end of the batch, are
+    // requested into L2 now so that those reads do not wait on HBM
 #pragma unroll 4
     for (int s = lane; s < M; s += 32) {
       const uint32_t o = sidx[s];
       cp_async<sizeof(T)>(&svx[s], &Av0[o]);
       cp_async<sizeof(T)>(&svy[s], &Av1[o]);
       cp_async<sizeof(T)>(&svz[s], &Av2[o]);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) prefetch_l2(&((const T*)a.Apos[d])[o]);
       stag[s] = 0x7FFFFFFF;
     }
     cp_async_wait_all();
@@ -1247,13 +1253,19 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
     const long long t0 = clock64();
     process_batch<T, DIM, ONE>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
     if (!big) {
-      // the batch's cost steers the next step's order (no effect on results)
+      // the batch's cost steers the next step's plan (no effect on results):
+      // hot if it cost more than the threshold per particle, counting at
+      // least cap/4 particles so that the fixed cost of a small batch does
+      // not flag it
       const unsigned long long cyc = (unsigned long long)(clock64() - t0);
+      const unsigned long long Mb = a.start[k0 + G] - a.start[k0];
       if (lane == 0) {
         atomicAdd(&a.cyc[0], cyc);
-        atomicAdd(&a.cyc[1], 1ull);
+        atomicAdd(&a.cyc[1], Mb);
       }
-      const uint8_t h = cyc > a.cyc[2] ? 1 : 0;
+      const unsigned long long thr = a.cyc[2];
+      const unsigned long long Mq = Mb > (unsigned long long)(cap / 4) ? Mb : (unsigned long long)(cap / 4);
+      const uint8_t h = (thr != ~0ull && cyc > thr * Mq) ? 1 : 0;
       if (lane < G) a.hot[k0 + lane] = h;
     }
   }

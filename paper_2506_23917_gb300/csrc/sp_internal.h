@@ -10,6 +10,7 @@ constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // key of a removed particle
 constexpr int kMaxBounce = 16;               // wall events per particle per step
 constexpr int kSurfFields = 7;  // wall tallies per surface element
 constexpr int64_t kNcolCap = int64_t(1) << 24;
+constexpr int kHotWeight = 4;                // plan weight of a hot cell's particles (see k_plan)
 constexpr int kMaxWarpsPerBlock = 8;         // collide kernel block size limit
 constexpr int kCapSmall = 512;               // default per-warp staging capacity (particles)
 constexpr int kWarpsDefault = 4;             // default warps per block
@@ -99,7 +100,7 @@ struct StepArgs {
   const uint2* batches; // [2 NC] (first cell, cell count) of each batch, four class lists
   const uint32_t* nbatch;  // [4] batches per class: heavy, large, medium, small (taken in that order)
   uint8_t* hot;         // [NC] the cell's batch was slower than the threshold last step
-  unsigned long long* cyc;  // [3] batch cycles this step (sum, count), threshold
+  unsigned long long* cyc;  // [3] batch cycles and particles this step (sums), hot threshold per particle
   unsigned long long* err;  // [kNumErr]
   int64_t NC;
   int64_t cap;
