@@ -886,11 +886,22 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     const bool seg_last = valid && (lane == 31 || cnext != c);
     const T coef = valid ? geo<T>(inst_params<ONE>(a, ct->inst[c])).sigc_coef : (T)0;
     const T ex = valid ? geo<T>(inst_params<ONE>(a, ct->inst[c])).sigc_exp : (T)0;
+    const T smc = valid ? ct->smax[c] : (T)0;  // the cell's (sigma c)_max before this round
     unsigned pending = __ballot_sync(kFull, valid);
-    // A candidate runs once no earlier pending candidate of its cell shares
-    // a particle with it; runs of one cell are disjoint pairs, each sees the
-    // velocities left by all earlier candidates, and (sigma c)_max is the
-    // cell's inclusive prefix maximum: the outcome of the one-by-one loop.
+    // The one-by-one loop over a cell's candidates, run several at a time.
+    // A candidate is evaluated (relative speed and sigma c from its pair's
+    // current velocities) once no earlier pending candidate of its cell
+    // shares a particle with it: its velocities are then final.  Its
+    // acceptance test needs (sigma c)_max as the inclusive prefix maximum
+    // over all earlier candidates of the cell.  It is decided when every
+    // earlier candidate of the cell has been evaluated (the exact test), or
+    // when it fails already against the prefix maximum of the evaluated
+    // ones (the full maximum can only be larger, so it fails too: rejected,
+    // nothing changes).  Accepted candidates of one pass share no particle,
+    // and every pass decides at least the first pending candidate of each
+    // cell, so the outcome is that of the one-by-one loop.
+    bool known = false;
+    T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;
     while (pending) {
       const bool mine = (pending >> lane) & 1u;
       if (mine) {
@@ -898,37 +909,38 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         atomicMin(&stag[cj], lane);
       }
       __syncwarp();
-      bool blocked = mine && (stag[ci] != lane || stag[cj] != lane);
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const bool y = __shfl_up_sync(kFull, blocked, o);
-        const int co = __shfl_up_sync(kFull, c, o);
-        if (lane >= o && co == c && y) blocked = true;
-      }
-      const bool act = mine && !blocked;
+      const bool ev = mine && stag[ci] == lane && stag[cj] == lane;
       __syncwarp();
       if (mine) {
         stag[ci] = 0x7FFFFFFF;
         stag[cj] = 0x7FFFFFFF;
       }
-      T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;
-      if (act) {
+      if (ev && !known) {
         ax = svx[ci]; ay = svy[ci]; az = svz[ci];
         bx = svx[cj]; by = svy[cj]; bz = svz[cj];
         const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
         cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
         sc = coef * tpow(cr, ex);
+        known = true;
       }
-      T pm = sc;
+      // inclusive prefix over the cell's lanes: maximum of the evaluated
+      // sigma c, and whether all of them are evaluated
+      T pm = known ? sc : (T)-1;
+      bool all = known;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const T y = __shfl_up_sync(kFull, pm, o);
         const int co = __shfl_up_sync(kFull, c, o);
-        if (lane >= o && co == c && y > pm) pm = y;
+        const bool ya = __shfl_up_sync(kFull, all, o);
+        if (lane >= o && co == c) {
+          if (y > pm) pm = y;
+          all = all && ya;
+        }
       }
-      const T smc = valid ? ct->smax[c] : (T)0;
       const T smL = pm > smc ? pm : smc;
-      if (act && u3 < sc / smL) {
+      const bool pass = ev && u3 < sc / smL;
+      const bool decided = ev && (all || !pass);
+      if (decided && pass) {
         atomicAdd(&ct->nacc[c], 1);
         const T cchi = (T)2.0 * u4 - (T)1.0;
         const T schi = tsqrt((T)1.0 - cchi * cchi);
@@ -943,11 +955,19 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         svy[cj] = (T)0.5 * (q1 + cr * w1);
         svz[cj] = (T)0.5 * (q2 + cr * w2);
       }
-      __syncwarp();
-      if (seg_last && pm > smc) ct->smax[c] = pm;
-      pending &= ~__ballot_sync(kFull, act);
+      pending &= ~__ballot_sync(kFull, decided);
       __syncwarp();
     }
+    // the round's candidates raise the cell's (sigma c)_max
+    T pm = sc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(kFull, pm, o);
+      const int co = __shfl_up_sync(kFull, c, o);
+      if (lane >= o && co == c && y > pm) pm = y;
+    }
+    if (seg_last && pm > smc) ct->smax[c] = pm;
+    __syncwarp();
   }
   int nacc_i = 0;
   if (own && ncol > 0) {
