@@ -1007,7 +1007,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (nlist > 0) {
       int s = lane < nlist ? stag[lane] : -1;
       int next = 32, t = 0, c = 0, armax = 1;
-      T RT = 0, s2RT = 0, Amax = 0, omp = 0, q0 = 0, q1 = 0, q2 = 0;
+      T RT = 0, s2RT = 0, Amax = 0, omp = 0, q0 = 0, q1 = 0, q2 = 0, kA = 0, iRT = 0;
       Uni<T> r(0u, 0u, 0u, 0u, 0u, 0u);
       auto take = [&](int slot) {
         s = slot;
@@ -1021,6 +1021,10 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         s2RT = ct->s2RT[c];
         Amax = ct->Amax[c];
         omp = ct->omp[c];
+        if constexpr (sizeof(T) == 4) {  // FP32: the attempts' divisions as products
+          kA = omp / ((T)5.0 * RT * RT);
+          iRT = (T)1.0 / RT;
+        }
         q0 = ct->q[0][c];
         q1 = ct->q[1][c];
         q2 = ct->q[2][c];
@@ -1029,9 +1033,21 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       while (__any_sync(kFull, s >= 0)) {
         bool done = false;
         if (s >= 0) {
-          T Rt[5];
-          uni_run<T, 5>(r, 1 + 5 * t, Rt);
-          const T R1 = Rt[0], R2 = Rt[1], R3 = Rt[2], R4 = Rt[3], R5 = Rt[4];
+          T R1, R2, R3, R4, R5;
+          if constexpr (sizeof(T) == 4) {
+            // FP32: one Philox block per attempt (block 1 + t; block 0 holds
+            // the Bernoulli draw); the two angles share a word, 16 bits each
+            const uint4 w = philox10(r.c0, r.c1, r.c2, r.c3 + 1u + (uint32_t)t, r.k0, r.k1);
+            R2 = u01f(w.x);
+            R4 = u01f(w.y);
+            R1 = (float)(2u * (w.z >> 16) + 1u) * 7.62939453125e-6f;
+            R3 = (float)(2u * (w.z & 0xFFFFu) + 1u) * 7.62939453125e-6f;
+            R5 = u01f(w.w);
+          } else {
+            T Rt[5];
+            uni_run<T, 5>(r, 1 + 5 * t, Rt);
+            R1 = Rt[0]; R2 = Rt[1]; R3 = Rt[2]; R4 = Rt[3]; R5 = Rt[4];
+          }
           const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
           T sn3, cs3;
           sincos2pi(R3, &sn3, &cs3);
@@ -1040,7 +1056,9 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
           const T C2 = s2RT * sn3 * r4;
           const T qC = q0 * C0 + q1 * C1 + q2 * C2;
           const T CC = C0 * C0 + C1 * C1 + C2 * C2;
-          const T A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
+          T A;
+          if constexpr (sizeof(T) == 4) A = (T)1.0 + kA * qC * (CC * iRT - (T)5.0);
+          else A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
           const bool acc = R5 * Amax < A;
           if (acc || t == armax - 1) {
             if (!acc) atomicAdd(&a.err[kErrAr], 1ull);
