@@ -742,6 +742,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   T sbgkT = 0, tauT = 0;
   bool shk = false;
   bool sample = false;
+  unsigned long long dtbits = ~0ull;  // the cell's Delta t_c (positive: bits order as values)
   if (own) {
     sample = (int64_t)step >= (int64_t)Pi.n_steady;
     const T V = (T)vol_k;
@@ -770,8 +771,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       } else if (umag > (T)0) {
         dtct = (T)Pi.Lmin / umag;
       }
-      if (dtct < tinf<T>())
-        atomicMin(&a.dt_min[inst], (unsigned long long)__double_as_longlong((double)dtct));
+      if (dtct < tinf<T>()) dtbits = (unsigned long long)__double_as_longlong((double)dtct);
     }
     m.U[0] = Ut[0]; m.U[1] = Ut[1]; m.U[2] = Ut[2];
     m.T = Tt;
@@ -831,6 +831,19 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     ct->q[0][lane] = qt[0];
     ct->q[1][lane] = qt[1];
     ct->q[2][lane] = qt[2];
+  }
+  // the instance's minimum Delta t_c: with one instance the warp's minimum
+  // goes in one atomic (32 atomics per batch on one address otherwise)
+  if constexpr (ONE) {
+    unsigned long long mn = dtbits;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(kFull, mn, o);
+      mn = y < mn ? y : mn;
+    }
+    if (lane == 0 && mn != ~0ull) atomicMin(&a.dt_min[0], mn);
+  } else {
+    if (dtbits != ~0ull) atomicMin(&a.dt_min[inst], dtbits);
   }
   // resampling probability 1 - exp(-dt_SBGK/tau) in FP64, only when a cell
   // of the batch has a Shakhov part
