@@ -367,7 +367,11 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   int n = 0;
   const StepArgs a = make_step_args(c, par);
   if (ev) cudaEventRecord(ev[0], c->stream);
-  launch_plan(c->start, c->hot, c->NC, c->sched_cap, c->batches, c->nbatch, c->big_list, c->big_count, c->stream); ++n;
+  // hot cells weigh kHotWeight in FP32 mode, where the kernel is
+  // latency-bound and the end of the launch matters; the FP64 pipe bounds
+  // FP64 mode, where fewer, larger batches are faster (weight 1)
+  launch_plan(c->start, c->hot, c->NC, c->sched_cap, c->prec == SP_FP32 ? kHotWeight : 1, c->batches, c->nbatch,
+              c->big_list, c->big_count, c->stream); ++n;
   launch_collide_p(c, a, false, small_grid(c)); ++n;
   launch_collide_p(c, a, true, 2 * 152); ++n;
   if (ev) cudaEventRecord(ev[1], c->stream);

@@ -152,7 +152,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 // it go to the big-cell list.  One warp per 32-cell chunk.  Cells flagged
 // hot (their batch cost more per particle than 2.5 times the step's
 // mean: cells where most particles are resampled with many rejections, or
-// with many collision candidates) weigh kHotWeight times their particles
+// with many collision candidates) weigh hot_weight times their particles
 // when batches are packed, so their work is spread over that many more
 // warps instead of one slow batch setting the end of the launch.  Batches
 // holding a hot cell form the first class; the others
@@ -166,8 +166,8 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 // of [0, NC), large from the front and medium from the back of [NC, 2 NC)
 // (each pair holds at most NC batches).  Batches are independent: their
 // order changes no result.
-__global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches,
-                       uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
+__global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, int hot_weight,
+                       uint2* batches, uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nchunks = (NC + 31) / 32;
@@ -178,7 +178,7 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
     const bool is_hot = lane < nc && hot[c0 + lane] != 0;
     const int64_t n_k = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
     // particles (cum) and weight (wcum: hot cells count kHotWeight times)
-    int64_t cum = n_k, wcum = is_hot ? kHotWeight * n_k : n_k;
+    int64_t cum = n_k, wcum = is_hot ? hot_weight * n_k : n_k;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int64_t y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
@@ -238,13 +238,13 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
 
 }  // namespace
 
-void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
-                 uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
+void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, int hot_weight, uint2* batches,
+                 uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
   const int64_t chunks = (NC + 31) / 32;
   int64_t g = (chunks + 7) / 8;
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
-  k_plan<<<(unsigned)g, 256, 0, s>>>(start, hot, NC, cap, batches, nbatch, big_list, big_count);
+  k_plan<<<(unsigned)g, 256, 0, s>>>(start, hot, NC, cap, hot_weight, batches, nbatch, big_list, big_count);
 }
 
 int64_t scan_partial_size(int64_t n) { return (n + kTile - 1) / kTile + 1; }

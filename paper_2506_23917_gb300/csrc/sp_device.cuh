@@ -515,6 +515,11 @@ __device__ __forceinline__ void seg_sums(int M, uint32_t p0, const uint8_t* sseg
 // the copy in the kernel's parameter space, so that the geometry and gas
 // constants reach the arithmetic as constant-bank operands rather than as
 // per-particle loads.
+// 32-slot rounds of the free flight whose positions are loaded together
+// (registers: rounds x DIM values of T)
+template <class T>
+constexpr int kFlightRounds = sizeof(T) == 4 ? 16 : 4;
+
 template <bool ONE>
 __device__ __forceinline__ const InstParams& inst_params(const StepArgs& a, uint32_t i) {
   if constexpr (ONE) return a.P0;
@@ -1186,17 +1191,18 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     }
   }
   // ---- 9. free flight of the next interval (Step 2), key and histogram;
-  // positions of sixteen rounds are loaded before any is used, then the rounds
+  // positions of kFlightRounds rounds are loaded before any is used, then the rounds
   // run through one copy of the free-flight code (the loaded positions
   // rotate through registers)
   T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
   T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
   if (idx_in_velocity<T>()) cp_async_wait_all();
   __syncwarp();
-  for (int sb0 = 0; sb0 < M; sb0 += 512) {
-    T xr[16][DIM] = {};
+  constexpr int R = kFlightRounds<T>;
+  for (int sb0 = 0; sb0 < M; sb0 += 32 * R) {
+    T xr[R][DIM] = {};
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
+    for (int u = 0; u < R; ++u) {
       const int s = sb0 + 32 * u + lane;
       if (s < M) {
         const uint32_t o = idx_in_velocity<T>() ? (uint32_t)stag[s] : sidx[s];
@@ -1205,7 +1211,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       }
     }
 #pragma unroll 1
-    for (int u = 0; u < 16; ++u) {
+    for (int u = 0; u < R; ++u) {
       const int sb = sb0 + 32 * u;
       if (sb >= M) break;
       const int s = sb + lane;
@@ -1215,7 +1221,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       for (int d = 0; d < DIM; ++d) {
         x[d] = xr[0][d];
 #pragma unroll
-        for (int k = 0; k < 15; ++k) xr[k][d] = xr[k + 1][d];
+        for (int k = 0; k < R - 1; ++k) xr[k][d] = xr[k + 1][d];
       }
       if (s < M) {
         const int c = sseg[s];
