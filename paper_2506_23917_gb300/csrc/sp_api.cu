@@ -75,6 +75,8 @@ struct sp_ctx {
   bool uploaded = false, dirty = false, record = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_ok = false;
+  cudaStream_t side = nullptr;       // capture-time branch of the step graph (injection)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int launches = 0;
   std::vector<double*> dstage;    // per instance: FP64 [dim][n] then [3][n], device
   std::vector<int64_t> stage_n, stage_cap;
@@ -363,10 +365,28 @@ bool apply_schedule(sp_ctx* c, int cap, int warps) {
 // Enqueue one step reading buffer `par` and writing buffer 1 - par.  With
 // ev != nullptr, events ev[0..4] bracket the four kernel groups (collide,
 // inject, scan + bookkeeping, scatter).
-int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
+int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = false) {
   int n = 0;
   const StepArgs a = make_step_args(c, par);
   if (ev) cudaEventRecord(ev[0], c->stream);
+  // The reservoir injection reads nothing the collision kernel writes (the
+  // previous step's particle count and Delta t; its particles go after the
+  // current ones, its histogram counts are atomics), so in the step graph
+  // it is a branch that runs beside the collision kernel, in the issue
+  // slots and SMs that kernel leaves free; the cell scan joins the two.
+  const bool fork = branch && !ev && c->n_ghost > 0;
+  if (fork) {
+    cudaEventRecord(c->fork_ev, c->stream);
+    cudaStreamWaitEvent(c->side, c->fork_ev, 0);
+    const InjectArgs ia = make_inject_args(c, par);
+    if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 0, c->side);
+    else launch_inject_f32(c->dim, ia, 0, c->side);
+    launch_scan(c->gcount, c->goff, c->n_ghost, c->gscan_part, c->side);
+    if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 1, c->side);
+    else launch_inject_f32(c->dim, ia, 1, c->side);
+    cudaEventRecord(c->join_ev, c->side);
+    n += 5;
+  }
   // hot cells weigh kHotWeight in FP32 mode, where the kernel is
   // latency-bound and the end of the launch matters; the FP64 pipe bounds
   // FP64 mode, where fewer, larger batches are faster (weight 1)
@@ -375,7 +395,9 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   launch_collide_p(c, a, false, small_grid(c)); ++n;
   launch_collide_p(c, a, true, 2 * 152); ++n;
   if (ev) cudaEventRecord(ev[1], c->stream);
-  if (c->n_ghost > 0) {
+  if (fork) {
+    cudaStreamWaitEvent(c->stream, c->join_ev, 0);
+  } else if (c->n_ghost > 0) {
     const InjectArgs ia = make_inject_args(c, par);
     if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 0, c->stream);
     else launch_inject_f32(c->dim, ia, 0, c->stream);
@@ -406,6 +428,11 @@ void destroy_graphs(sp_ctx* c) {
 
 sp_status build_graphs(sp_ctx* c) {
   destroy_graphs(c);
+  if (!c->side) {
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+  }
   for (int par = 0; par < 2; ++par) {
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -414,7 +441,7 @@ sp_status build_graphs(sp_ctx* c) {
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      c->launches = enqueue_step(c, par);
+      c->launches = enqueue_step(c, par, nullptr, true);
       e = cudaStreamEndCapture(cs, &g);
     }
     c->stream = saved;
@@ -1119,6 +1146,11 @@ sp_status sp_free(sp_ctx* c) {
   if (!c) return SP_ERR_ARG;
   cudaStreamSynchronize(c->stream);
   destroy_graphs(c);
+  if (c->side) {
+    cudaStreamDestroy(c->side);
+    cudaEventDestroy(c->fork_ev);
+    cudaEventDestroy(c->join_ev);
+  }
   for (int b = 0; b < 2; ++b)
     for (int d = 0; d < 3; ++d) {
       cudaFree(c->pos[b][d]);

@@ -103,11 +103,12 @@ __global__ void k_scatter(const uint32_t* key, const uint32_t* start, uint32_t* 
   if (k == kSentinel) return;
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
+  const uint32_t sk = __ldg(&start[k]);  // requested before the atomic: the two latencies overlap
   uint32_t base = 0;
   if (lane == leader) base = atomicSub(&count[k], (uint32_t)__popc(peers)) - (uint32_t)__popc(peers);
   base = __shfl_sync(peers, base, leader);
   const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-  perm[start[k] + base + rank] = (uint32_t)i;
+  perm[sk + base + rank] = (uint32_t)i;
 }
 
 __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
