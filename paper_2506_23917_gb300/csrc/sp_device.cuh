@@ -136,6 +136,16 @@ __device__ __forceinline__ double tfloor(double x) { return floor(x); }
 __device__ __forceinline__ float tfloor(float x) { return floorf(x); }
 __device__ __forceinline__ double tfabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tfabs(float x) { return fabsf(x); }
+// Division and power of the per-cell scalars: FP64 mode keeps the IEEE
+// operations (the oracle's rounding); FP32 mode, whose cell scalars only set
+// rates and split weights, uses the hardware approximations (division within
+// 2 ulp for divisors below 2^126, power through exp2/log2), which shorten the
+// dependent chain that one lane runs per cell.
+__device__ __forceinline__ double cdiv(double x, double y) { return x / y; }
+__device__ __forceinline__ float cdiv(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double cpow(double x, double e) { return pow(x, e); }
+__device__ __forceinline__ float cpow(float x, float e) { return __powf(x, e); }
+
 // cos / sin of 2 pi u
 __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) {
   const double th = 2.0 * kPi * u;
@@ -754,27 +764,27 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     T Ut[3] = {0, 0, 0}, Tt = 0, qt[3] = {0, 0, 0}, nt = 0;
     T taut = tinf<T>(), dtct = tinf<T>();
     if (Ni > 0) {
-      Ut[0] = m0 / (T)Ni;
-      Ut[1] = m1 / (T)Ni;
-      Ut[2] = m2 / (T)Ni;
-      nt = (T)Ni * (T)Pi.Fn / V;
+      Ut[0] = cdiv(m0, (T)Ni);
+      Ut[1] = cdiv(m1, (T)Ni);
+      Ut[2] = cdiv(m2, (T)Ni);
+      nt = cdiv((T)Ni * (T)Pi.Fn, V);
     }
     if (Ni >= 2) {
-      Tt = mS2 / ((T)3.0 * (T)Pi.R * (T)(Ni - 1));
+      Tt = cdiv(mS2, (T)3.0 * (T)Pi.R * (T)(Ni - 1));
       if (Ni >= 3) {
         const T den = (T)(Ni - 1) * (T)(Ni - 2);
-        qt[0] = (T)0.5 * (T)Ni * mS3x / den;
-        qt[1] = (T)0.5 * (T)Ni * mS3y / den;
-        qt[2] = (T)0.5 * (T)Ni * mS3z / den;
+        qt[0] = cdiv((T)0.5 * (T)Ni * mS3x, den);
+        qt[1] = cdiv((T)0.5 * (T)Ni * mS3y, den);
+        qt[2] = cdiv((T)0.5 * (T)Ni * mS3z, den);
       }
       const T umag = tsqrt(Ut[0] * Ut[0] + Ut[1] * Ut[1] + Ut[2] * Ut[2]);
       if (Tt > (T)0) {
         const T p = nt * (T)Pi.m * (T)Pi.R * Tt;
-        const T mu = (T)Pi.mu_ref * tpow(Tt / (T)Pi.T_ref, (T)Pi.omega);
-        taut = mu / p;
-        dtct = (T)Pi.Lmin / (umag + tsqrt((T)Pi.gamma * (T)Pi.R * Tt));
+        const T mu = (T)Pi.mu_ref * cpow(cdiv(Tt, (T)Pi.T_ref), (T)Pi.omega);
+        taut = cdiv(mu, p);
+        dtct = cdiv((T)Pi.Lmin, umag + tsqrt((T)Pi.gamma * (T)Pi.R * Tt));
       } else if (umag > (T)0) {
-        dtct = (T)Pi.Lmin / umag;
+        dtct = cdiv((T)Pi.Lmin, umag);
       }
       if (dtct < tinf<T>()) dtbits = (unsigned long long)__double_as_longlong((double)dtct);
     }
@@ -788,7 +798,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (Pi.mode == 1) ratioT = 1;
     else if (Pi.mode == 2) ratioT = 0;
     else if (Ni < 2 || !(Tt > (T)0) || dtct <= taut) ratioT = 1;
-    else ratioT = taut / dtct;
+    else ratioT = cdiv(taut, dtct);
     const T dtG = (T)a.dt_cur[inst];
     ct->dt[lane] = dtG;
     ct->Pres[lane] = 0;
@@ -798,13 +808,13 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       else if (Pi.mode == 2) { dsmc = 0; sbgk = dtG; }
       else if (dtct <= taut) { dsmc = dtG; sbgk = 0; }
       else {
-        const T r = taut / dtct;
+        const T r = cdiv(taut, dtct);
         dsmc = r * dtG;
         sbgk = ((T)1.0 - r) * dtG;
       }
       if (dsmc > (T)0) {
         smaxT = (T)smax_k;
-        const T ncr = (T)0.5 * (T)Ni * (T)(Ni - 1) * (T)Pi.Fn * smaxT * dsmc / V;
+        const T ncr = cdiv((T)0.5 * (T)Ni * (T)(Ni - 1) * (T)Pi.Fn * smaxT * dsmc, V);
         if (Pi.ntc_carry) {  // Bird's carried remainder (FP64 state per cell)
           const double x = (double)ncr + a.rem[kc];
           ncol = (int64_t)floor(x);
@@ -826,7 +836,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         const T qn = tsqrt(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2]);
         ct->RT[lane] = RTt;
         ct->s2RT[lane] = tsqrt((T)2.0 * RTt);
-        ct->Amax[lane] = (T)1.0 + (T)20.0 * ((T)1.0 - (T)Pi.Pr) * qn / (RTt * tsqrt(RTt));
+        ct->Amax[lane] = (T)1.0 + cdiv((T)20.0 * ((T)1.0 - (T)Pi.Pr) * qn, RTt * tsqrt(RTt));
         ct->omp[lane] = (T)1.0 - (T)Pi.Pr;
       }
     }
