@@ -136,11 +136,12 @@ __device__ __forceinline__ double tfloor(double x) { return floor(x); }
 __device__ __forceinline__ float tfloor(float x) { return floorf(x); }
 __device__ __forceinline__ double tfabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tfabs(float x) { return fabsf(x); }
-// Division and power of the per-cell scalars: FP64 mode keeps the IEEE
-// operations (the oracle's rounding); FP32 mode, whose cell scalars only set
-// rates and split weights, uses the hardware approximations (division within
-// 2 ulp for divisors below 2^126, power through exp2/log2), which shorten the
-// dependent chain that one lane runs per cell.
+// Division and power of the per-cell scalars and of the pairs' sigma c:
+// FP64 mode keeps the IEEE operations (the oracle's rounding); FP32 mode,
+// where these only set rates, split weights and acceptance probabilities,
+// uses the hardware approximations (division within 2 ulp for divisors
+// below 2^126, power through exp2/log2), which shorten the dependent chains
+// on the lanes.
 __device__ __forceinline__ double cdiv(double x, double y) { return x / y; }
 __device__ __forceinline__ float cdiv(float x, float y) { return __fdividef(x, y); }
 __device__ __forceinline__ double cpow(double x, double e) { return pow(x, e); }
@@ -714,9 +715,9 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     v[2] = svz[s];
   });
   if (own && Ni > 0) {  // the shift of the central sums: the cell mean
-    ct->U[0][lane] = ct->acc[0][lane] / (T)Ni;
-    ct->U[1][lane] = ct->acc[1][lane] / (T)Ni;
-    ct->U[2][lane] = ct->acc[2][lane] / (T)Ni;
+    ct->U[0][lane] = cdiv(ct->acc[0][lane], (T)Ni);
+    ct->U[1][lane] = cdiv(ct->acc[1][lane], (T)Ni);
+    ct->U[2][lane] = cdiv(ct->acc[2][lane], (T)Ni);
   }
   __syncwarp();
   cell_sums<T, 4>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, int c, T* v) {
@@ -948,7 +949,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         bx = svx[cj]; by = svy[cj]; bz = svz[cj];
         const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
         cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
-        sc = coef * tpow(cr, ex);
+        sc = coef * cpow(cr, ex);
         known = true;
       }
       // inclusive prefix over the cell's lanes: maximum of the evaluated
@@ -966,7 +967,11 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         }
       }
       const T smL = pm > smc ? pm : smc;
-      const bool pass = ev && u3 < sc / smL;
+      // P_c = sigma c / (sigma c)_max against u3; FP32 mode compares the
+      // product (also monotone in (sigma c)_max, as the early rejection needs)
+      bool pass;
+      if constexpr (sizeof(T) == 4) pass = ev && u3 * smL < sc;
+      else pass = ev && u3 < sc / smL;
       const bool decided = ev && (all || !pass);
       if (decided && pass) {
         atomicAdd(&ct->nacc[c], 1);
