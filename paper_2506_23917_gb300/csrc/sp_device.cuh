@@ -146,6 +146,19 @@ __device__ __forceinline__ double cdiv(double x, double y) { return x / y; }
 __device__ __forceinline__ float cdiv(float x, float y) { return __fdividef(x, y); }
 __device__ __forceinline__ double cpow(double x, double e) { return pow(x, e); }
 __device__ __forceinline__ float cpow(float x, float e) { return __powf(x, e); }
+// Square root and natural logarithm on the per-particle sampling paths
+// (pair speeds, Box-Muller radii): FP32 mode uses the hardware
+// approximations (sqrt.approx, lg2.approx scaled by ln 2).
+__device__ __forceinline__ double csqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float csqrt(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double clog(double x) { return log(x); }
+__device__ __forceinline__ float clog(float x) { return __logf(x); }
+__device__ __forceinline__ double tmax0(double x) { return x; }  // exact log: -log(R) >= 0 already
+__device__ __forceinline__ float tmax0(float x) { return fmaxf(x, 0.0f); }
 
 // cos / sin of 2 pi u
 __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) {
@@ -948,7 +961,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         ax = svx[ci]; ay = svy[ci]; az = svz[ci];
         bx = svx[cj]; by = svy[cj]; bz = svz[cj];
         const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
-        cr = tsqrt(g0 * g0 + g1 * g1 + g2 * g2);
+        cr = csqrt(g0 * g0 + g1 * g1 + g2 * g2);
         sc = coef * cpow(cr, ex);
         known = true;
       }
@@ -976,7 +989,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       if (decided && pass) {
         atomicAdd(&ct->nacc[c], 1);
         const T cchi = (T)2.0 * u4 - (T)1.0;
-        const T schi = tsqrt((T)1.0 - cchi * cchi);
+        const T schi = csqrt((T)1.0 - cchi * cchi);
         T sn, cs;
         sincos2pi(u5, &sn, &cs);
         const T w0 = cchi, w1 = schi * cs, w2 = schi * sn;
@@ -1081,7 +1094,8 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
             uni_run<T, 5>(r, 1 + 5 * t, Rt);
             R1 = Rt[0]; R2 = Rt[1]; R3 = Rt[2]; R4 = Rt[3]; R5 = Rt[4];
           }
-          const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
+          // (max: near R = 1 the approximate logarithm may round above 0)
+          const T r2 = csqrt(tmax0(-clog(R2))), r4 = csqrt(tmax0(-clog(R4)));
           T sn3, cs3;
           sincos2pi(R3, &sn3, &cs3);
           const T C0 = s2RT * cos2pi(R1) * r2;
