@@ -269,6 +269,45 @@ __device__ __forceinline__ void diffuse_sample(T RTw, Uni<T>& r, T* cn, T* t1, T
   *t2 = s * sn * r4;
 }
 
+// FP32 free flight: whether the straight flight over trem stays inside the
+// box by the rounding margin and misses the body (the first test of
+// move_particle, without its square root and division: for a pair
+// approaching the body, t < trem <=> -b - trem a < sqrt(disc)); if so x is
+// moved to the end point.  Branch-free, so that two particles' tests
+// interleave.
+template <class T, int DIM>
+__device__ __forceinline__ bool flight_fast(const InstParams& P, T* x, const T* v, T trem) {
+  const Geo<T>& G = geo<T>(P);
+  T xe[DIM];
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    xe[d] = x[d] + v[d] * trem;
+    ok = ok && xe[d] > G.lo[d] + G.eps[d] && xe[d] < G.hi[d] - G.eps[d];
+  }
+  if (P.body != 0) {
+    T bb = 0, aa = 0, cc = 0;
+#pragma unroll
+    for (int d = 0; d < (DIM < 3 ? DIM : 3); ++d) {
+      if (d == 2 && P.body == 1) break;
+      const T dx = x[d] - G.body_c[d];
+      bb += v[d] * dx;
+      aa += v[d] * v[d];
+      cc += dx * dx;
+    }
+    cc -= G.body_r * G.body_r;
+    const T disc = bb * bb - aa * cc;
+    const T q = -bb - trem * aa;
+    const bool hit = bb < (T)0 && aa > (T)0 && disc >= (T)0 && (q < (T)0 || q * q < disc);
+    ok = ok && !hit;
+  }
+  if (ok) {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) x[d] = xe[d];
+  }
+  return ok;
+}
+
 // Moves one particle for time trem.  Returns true when it left the domain.
 // Draw stream of bounce b: (step, sa, sb, purpose<<24 | subbase + 2b).
 template <class T, int DIM>
@@ -1239,6 +1278,64 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         for (int d = 0; d < DIM; ++d) xr[u][d] = ((const T*)a.Apos[d])[o];
       }
     }
+    if constexpr (sizeof(T) == 4) {
+      // FP32: rounds in pairs.  The straight-flight tests, end points and
+      // keys of both rounds are formed first, branch-free, so that their
+      // dependent chains interleave; then each round (B rotated into A's
+      // registers: one copy of the code) stores its particles, running the
+      // full free flight for those the test did not clear.
+#pragma unroll 1
+      for (int u = 0; u < R; u += 2) {
+        const int sb = sb0 + 32 * u;
+        if (sb >= M) break;
+        int sA = sb + lane, sB = sA + 32;
+        T xA[3] = {0, 0, 0}, xB[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          xA[d] = xr[0][d];
+          xB[d] = xr[1][d];
+#pragma unroll
+          for (int k = 0; k + 2 < R; ++k) xr[k][d] = xr[k + 2][d];
+        }
+        bool okA = sA < M, okB = sB < M;
+        int cA = okA ? sseg[sA] : 0, cB = okB ? sseg[sB] : 0;
+        T vA[3] = {okA ? svx[sA] : (T)0, okA ? svy[sA] : (T)0, okA ? svz[sA] : (T)0};
+        T vB[3] = {okB ? svx[sB] : (T)0, okB ? svy[sB] : (T)0, okB ? svz[sB] : (T)0};
+        T dtA = ct->dt[cA], dtB = ct->dt[cB];
+        const InstParams& PA = inst_params<ONE>(a, ct->inst[cA]);
+        const InstParams& PB = inst_params<ONE>(a, ct->inst[cB]);
+        bool fA = flight_fast<T, DIM>(PA, xA, vA, dtA);
+        bool fB = flight_fast<T, DIM>(PB, xB, vB, dtB);
+        uint32_t kA = (uint32_t)PA.cell_off + cell_of<T, DIM>(PA, xA);
+        uint32_t kB = (uint32_t)PB.cell_off + cell_of<T, DIM>(PB, xB);
+#pragma unroll 1
+        for (int j = 0; j < 2; ++j) {
+          uint32_t key = kSentinel;
+          if (okA) {
+            key = kA;
+            if (!fA) {
+              const InstParams& P = inst_params<ONE>(a, ct->inst[cA]);
+              const bool gone = move_particle<T, DIM>(P, a.surf, xA, vA, dtA, step, kPurpWall, (uint32_t)ct->kl[cA],
+                                                      (uint32_t)(sA - ct->off[cA]), 0u, a.err);
+              key = gone ? kSentinel : (uint32_t)P.cell_off + cell_of<T, DIM>(P, xA);
+            }
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) Bx[d][p0 + sA] = xA[d];
+            Bv[0][p0 + sA] = vA[0];
+            Bv[1][p0 + sA] = vA[1];
+            Bv[2][p0 + sA] = vA[2];
+            a.key[p0 + sA] = key;
+          }
+          warp_count(key, a.count);
+          sA = sB; okA = okB; cA = cB; dtA = dtB; fA = fB; kA = kB;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            xA[d] = xB[d];
+            vA[d] = vB[d];
+          }
+        }
+      }
+    } else {
 #pragma unroll 1
     for (int u = 0; u < R; ++u) {
       const int sb = sb0 + 32 * u;
@@ -1267,6 +1364,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         a.key[p0 + s] = key;
       }
       warp_count(key, a.count);
+    }
     }
   }
   __syncwarp();
