@@ -582,6 +582,11 @@ __device__ __forceinline__ void seg_sums(int M, uint32_t p0, const uint8_t* sseg
 // (registers: rounds x DIM values of T)
 template <class T>
 constexpr int kFlightRounds = sizeof(T) == 4 ? 16 : 4;
+// FP32 rounds whose straight-flight tests are formed together: pairs in
+// 2-D (+10 % on the cylinder; groups of 4: +4 %, of 8: -9 %); 1-D and 3-D
+// keep one round at a time (pairs cost the 3-D sphere 10 %)
+template <int DIM>
+constexpr int kFlightGroup = DIM == 2 ? 2 : 1;
 
 template <bool ONE>
 __device__ __forceinline__ const InstParams& inst_params(const StepArgs& a, uint32_t i) {
@@ -1278,60 +1283,72 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
         for (int d = 0; d < DIM; ++d) xr[u][d] = ((const T*)a.Apos[d])[o];
       }
     }
-    if constexpr (sizeof(T) == 4) {
-      // FP32: rounds in pairs.  The straight-flight tests, end points and
-      // keys of both rounds are formed first, branch-free, so that their
-      // dependent chains interleave; then each round (B rotated into A's
-      // registers: one copy of the code) stores its particles, running the
-      // full free flight for those the test did not clear.
+    if constexpr (sizeof(T) == 4 && kFlightGroup<DIM> > 1) {
+      // FP32: rounds in groups of W.  The straight-flight tests, end points
+      // and keys of the group are formed first, branch-free, so that their
+      // dependent chains interleave; then each round (the next rotated into
+      // the first registers: one copy of the code) stores its particles,
+      // running the full free flight for those the test did not clear.
+      constexpr int W = kFlightGroup<DIM>;
 #pragma unroll 1
-      for (int u = 0; u < R; u += 2) {
+      for (int u = 0; u < R; u += W) {
         const int sb = sb0 + 32 * u;
         if (sb >= M) break;
-        int sA = sb + lane, sB = sA + 32;
-        T xA[3] = {0, 0, 0}, xB[3] = {0, 0, 0};
+        int sg[W], cg[W];
+        bool okg[W], fg[W];
+        T xg[W][3], vg[W][3], dtg[W];
+        uint32_t kg[W];
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          xA[d] = xr[0][d];
-          xB[d] = xr[1][d];
+        for (int j = 0; j < W; ++j) {
+          sg[j] = sb + 32 * j + lane;
+          okg[j] = sg[j] < M;
 #pragma unroll
-          for (int k = 0; k + 2 < R; ++k) xr[k][d] = xr[k + 2][d];
+          for (int d = 0; d < 3; ++d) xg[j][d] = d < DIM ? xr[j][d] : (T)0;
+          cg[j] = okg[j] ? sseg[sg[j]] : 0;
+          vg[j][0] = okg[j] ? svx[sg[j]] : (T)0;
+          vg[j][1] = okg[j] ? svy[sg[j]] : (T)0;
+          vg[j][2] = okg[j] ? svz[sg[j]] : (T)0;
+          dtg[j] = ct->dt[cg[j]];
         }
-        bool okA = sA < M, okB = sB < M;
-        int cA = okA ? sseg[sA] : 0, cB = okB ? sseg[sB] : 0;
-        T vA[3] = {okA ? svx[sA] : (T)0, okA ? svy[sA] : (T)0, okA ? svz[sA] : (T)0};
-        T vB[3] = {okB ? svx[sB] : (T)0, okB ? svy[sB] : (T)0, okB ? svz[sB] : (T)0};
-        T dtA = ct->dt[cA], dtB = ct->dt[cB];
-        const InstParams& PA = inst_params<ONE>(a, ct->inst[cA]);
-        const InstParams& PB = inst_params<ONE>(a, ct->inst[cB]);
-        bool fA = flight_fast<T, DIM>(PA, xA, vA, dtA);
-        bool fB = flight_fast<T, DIM>(PB, xB, vB, dtB);
-        uint32_t kA = (uint32_t)PA.cell_off + cell_of<T, DIM>(PA, xA);
-        uint32_t kB = (uint32_t)PB.cell_off + cell_of<T, DIM>(PB, xB);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+          for (int k = 0; k + W < R; ++k) xr[k][d] = xr[k + W][d];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          const InstParams& Pj = inst_params<ONE>(a, ct->inst[cg[j]]);
+          fg[j] = flight_fast<T, DIM>(Pj, xg[j], vg[j], dtg[j]);
+          kg[j] = (uint32_t)Pj.cell_off + cell_of<T, DIM>(Pj, xg[j]);
+        }
 #pragma unroll 1
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < W; ++j) {
           uint32_t key = kSentinel;
-          if (okA) {
-            key = kA;
-            if (!fA) {
-              const InstParams& P = inst_params<ONE>(a, ct->inst[cA]);
-              const bool gone = move_particle<T, DIM>(P, a.surf, xA, vA, dtA, step, kPurpWall, (uint32_t)ct->kl[cA],
-                                                      (uint32_t)(sA - ct->off[cA]), 0u, a.err);
-              key = gone ? kSentinel : (uint32_t)P.cell_off + cell_of<T, DIM>(P, xA);
+          if (okg[0]) {
+            key = kg[0];
+            if (!fg[0]) {
+              const int c = cg[0];
+              const InstParams& P = inst_params<ONE>(a, ct->inst[c]);
+              const bool gone = move_particle<T, DIM>(P, a.surf, xg[0], vg[0], dtg[0], step, kPurpWall,
+                                                      (uint32_t)ct->kl[c], (uint32_t)(sg[0] - ct->off[c]), 0u, a.err);
+              key = gone ? kSentinel : (uint32_t)P.cell_off + cell_of<T, DIM>(P, xg[0]);
             }
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) Bx[d][p0 + sA] = xA[d];
-            Bv[0][p0 + sA] = vA[0];
-            Bv[1][p0 + sA] = vA[1];
-            Bv[2][p0 + sA] = vA[2];
-            a.key[p0 + sA] = key;
+            for (int d = 0; d < DIM; ++d) Bx[d][p0 + sg[0]] = xg[0][d];
+            Bv[0][p0 + sg[0]] = vg[0][0];
+            Bv[1][p0 + sg[0]] = vg[0][1];
+            Bv[2][p0 + sg[0]] = vg[0][2];
+            a.key[p0 + sg[0]] = key;
           }
           warp_count(key, a.count);
-          sA = sB; okA = okB; cA = cB; dtA = dtB; fA = fB; kA = kB;
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            xA[d] = xB[d];
-            vA[d] = vB[d];
+          for (int i = 0; i + 1 < W; ++i) {
+            sg[i] = sg[i + 1]; cg[i] = cg[i + 1]; okg[i] = okg[i + 1]; fg[i] = fg[i + 1];
+            dtg[i] = dtg[i + 1]; kg[i] = kg[i + 1];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              xg[i][d] = xg[i + 1][d];
+              vg[i][d] = vg[i + 1][d];
+            }
           }
         }
       }
