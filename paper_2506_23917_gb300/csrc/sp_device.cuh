@@ -672,7 +672,13 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   // (the index copies run while the cell of each slot is written)
 #pragma unroll 4
   for (int s = lane; s < M; s += 32) cp_async<4>(&sidx[s], &a.perm[p0 + s]);
-  for (int i = 0; i < G; ++i) {
+  // each lane writes its own cell's slots (one pass for all cells of the
+  // batch instead of one warp-wide pass per cell); cells above
+  // kLaneSumMax particles are written by the whole warp
+  if (own && Ni <= kLaneSumMax)
+    for (int s = offi; s < offi + Ni; ++s) sseg[s] = (uint8_t)lane;
+  for (unsigned big = __ballot_sync(kFull, own && Ni > kLaneSumMax); big; big &= big - 1) {
+    const int i = __ffs(big) - 1;
     const int o0 = ct->off[i], o1 = ct->off[i + 1];
     for (int s = o0 + lane; s < o1; s += 32) sseg[s] = (uint8_t)i;
   }
