@@ -768,39 +768,88 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     cp_async_wait_all();
   }
   __syncwarp();
-  // ---- 3. moment sums per cell (segmented, one pass each), kept by lane i
-  if (own)
-    for (int k = 0; k < 7; ++k) ct->acc[k][lane] = 0;
-  __syncwarp();
-  cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, int c, T* v) {
-    v[0] = svx[s];
-    v[1] = svy[s];
-    v[2] = svz[s];
-  });
-  if (own && Ni > 0) {  // the shift of the central sums: the cell mean
-    ct->U[0][lane] = cdiv(ct->acc[0][lane], (T)Ni);
-    ct->U[1][lane] = cdiv(ct->acc[1][lane], (T)Ni);
-    ct->U[2][lane] = cdiv(ct->acc[2][lane], (T)Ni);
-  }
-  __syncwarp();
-  cell_sums<T, 4>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, int c, T* v) {
-    const T C0 = svx[s] - ct->U[0][c], C1 = svy[s] - ct->U[1][c], C2 = svz[s] - ct->U[2][c];
-    const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
-    v[0] = c2;
-    v[1] = c2 * C0;
-    v[2] = c2 * C1;
-    v[3] = c2 * C2;
-  });
+  // ---- 3. moment sums per cell (segmented, one pass each), kept by lane i.
+  // FP32 mode, cells of at most kLaneSumMax particles: one pass, shifted by
+  // the velocity D = c - c_1 of the cell's first particle (close to the
+  // mean, so FP32 loses nothing to cancellation): sums of D, of D D^T and of
+  // |D|^2 D, from which the central sums follow exactly (below).  All other
+  // cells: two passes, the second shifted by the cell mean.
+  bool one_pass = false;
   T m0 = 0, m1 = 0, m2 = 0, mS2 = 0, mS3x = 0, mS3y = 0, mS3z = 0;
-  if (own) {
-    m0 = ct->acc[0][lane];
-    m1 = ct->acc[1][lane];
-    m2 = ct->acc[2][lane];
-    if (Ni >= 2) {
-      mS2 = ct->acc[3][lane];
-      mS3x = ct->acc[4][lane];
-      mS3y = ct->acc[5][lane];
-      mS3z = ct->acc[6][lane];
+  if constexpr (sizeof(T) == 4) {
+    one_pass = own && Ni > 0 && Ni <= kLaneSumMax;
+    if (one_pass) {
+      const T c0x = svx[offi], c0y = svy[offi], c0z = svz[offi];
+      T sx = 0, sy = 0, sz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0, tx = 0, ty = 0, tz = 0;
+      for (int q = offi; q < offi + Ni; ++q) {
+        const T dx = svx[q] - c0x, dy = svy[q] - c0y, dz = svz[q] - c0z;
+        sx += dx;
+        sy += dy;
+        sz += dz;
+        mxx += dx * dx;
+        myy += dy * dy;
+        mzz += dz * dz;
+        mxy += dx * dy;
+        mxz += dx * dz;
+        myz += dy * dz;
+        const T d2 = dx * dx + dy * dy + dz * dz;
+        tx += d2 * dx;
+        ty += d2 * dy;
+        tz += d2 * dz;
+      }
+      const T fN = (T)Ni, iN = cdiv((T)1, fN);
+      const T ex = sx * iN, ey = sy * iN, ez = sz * iN;  // U - c_1
+      m0 = fN * c0x + sx;
+      m1 = fN * c0y + sy;
+      m2 = fN * c0z + sz;
+      if (Ni >= 2) {
+        // C = D - e: sum |C|^2 = tr M - N |e|^2 and
+        // sum |C|^2 C = T3 - e tr M - 2 M e + 2 e (e.S) + |e|^2 S - N |e|^2 e
+        const T trM = mxx + myy + mzz, e2 = ex * ex + ey * ey + ez * ez, eS = ex * sx + ey * sy + ez * sz;
+        mS2 = trM - fN * e2;
+        const T Mex = mxx * ex + mxy * ey + mxz * ez;
+        const T Mey = mxy * ex + myy * ey + myz * ez;
+        const T Mez = mxz * ex + myz * ey + mzz * ez;
+        mS3x = tx - ex * trM - (T)2 * Mex + (T)2 * ex * eS + e2 * sx - fN * e2 * ex;
+        mS3y = ty - ey * trM - (T)2 * Mey + (T)2 * ey * eS + e2 * sy - fN * e2 * ey;
+        mS3z = tz - ez * trM - (T)2 * Mez + (T)2 * ez * eS + e2 * sz - fN * e2 * ez;
+      }
+    }
+  }
+  const bool two_pass = own && !one_pass;
+  if (__any_sync(kFull, two_pass)) {
+    if (two_pass)
+      for (int k = 0; k < 7; ++k) ct->acc[k][lane] = 0;
+    __syncwarp();
+    cell_sums<T, 3>(M, p0, sseg, ct->acc, two_pass, offi, Ni, [&](int s, int c, T* v) {
+      v[0] = svx[s];
+      v[1] = svy[s];
+      v[2] = svz[s];
+    });
+    if (two_pass && Ni > 0) {  // the shift of the central sums: the cell mean
+      ct->U[0][lane] = cdiv(ct->acc[0][lane], (T)Ni);
+      ct->U[1][lane] = cdiv(ct->acc[1][lane], (T)Ni);
+      ct->U[2][lane] = cdiv(ct->acc[2][lane], (T)Ni);
+    }
+    __syncwarp();
+    cell_sums<T, 4>(M, p0, sseg, ct->acc + 3, two_pass, offi, Ni, [&](int s, int c, T* v) {
+      const T C0 = svx[s] - ct->U[0][c], C1 = svy[s] - ct->U[1][c], C2 = svz[s] - ct->U[2][c];
+      const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+      v[0] = c2;
+      v[1] = c2 * C0;
+      v[2] = c2 * C1;
+      v[3] = c2 * C2;
+    });
+    if (two_pass) {
+      m0 = ct->acc[0][lane];
+      m1 = ct->acc[1][lane];
+      m2 = ct->acc[2][lane];
+      if (Ni >= 2) {
+        mS2 = ct->acc[3][lane];
+        mS3x = ct->acc[4][lane];
+        mS3y = ct->acc[5][lane];
+        mS3z = ct->acc[6][lane];
+      }
     }
   }
   // ---- 4. per-cell arithmetic, lane i <-> cell i.  FP64 mode: all in FP64
