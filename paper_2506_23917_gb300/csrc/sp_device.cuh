@@ -781,6 +781,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     if (one_pass) {
       const T c0x = svx[offi], c0y = svy[offi], c0z = svz[offi];
       T sx = 0, sy = 0, sz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0, tx = 0, ty = 0, tz = 0;
+#pragma unroll 2
       for (int q = offi; q < offi + Ni; ++q) {
         const T dx = svx[q] - c0x, dy = svy[q] - c0y, dz = svz[q] - c0z;
         sx += dx;
