@@ -94,21 +94,37 @@ __global__ void k_scan_down(const uint32_t* in, uint32_t* out, int64_t n, const 
 // from its end, and leave the histogram at zero for the next step's counts.
 // The order inside a cell is arbitrary here and restored to source order by
 // the collision kernel when the run is reproducible.
+constexpr int kScatterPer = 4;  // elements per thread, strided by the block size
 __global__ void k_scatter(const uint32_t* key, const uint32_t* start, uint32_t* count, uint32_t* perm,
                           const uint32_t* Mtot, int64_t cap) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // each thread's kScatterPer elements are requested together, so that their
+  // load -> match -> atomic -> store chains overlap
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kScatterPer + threadIdx.x;
   const int64_t M = (int64_t)*Mtot;
-  const uint32_t k = (i < M && i < cap) ? key[i] : kSentinel;
-  const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
-  if (k == kSentinel) return;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  const uint32_t sk = __ldg(&start[k]);  // requested before the atomic: the two latencies overlap
-  uint32_t base = 0;
-  if (lane == leader) base = atomicSub(&count[k], (uint32_t)__popc(peers)) - (uint32_t)__popc(peers);
-  base = __shfl_sync(peers, base, leader);
-  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-  perm[sk + base + rank] = (uint32_t)i;
+  uint32_t k[kScatterPer], base[kScatterPer], sk[kScatterPer];
+  unsigned peers[kScatterPer];
+#pragma unroll
+  for (int j = 0; j < kScatterPer; ++j) {
+    const int64_t i = i0 + (int64_t)j * blockDim.x;
+    k[j] = (i < M && i < cap) ? key[i] : kSentinel;
+  }
+#pragma unroll
+  for (int j = 0; j < kScatterPer; ++j) {
+    peers[j] = __match_any_sync(0xFFFFFFFFu, k[j]);
+    sk[j] = k[j] != kSentinel ? __ldg(&start[k[j]]) : 0u;
+    base[j] = 0;
+    if (k[j] != kSentinel && lane == __ffs(peers[j]) - 1)
+      base[j] = atomicSub(&count[k[j]], (uint32_t)__popc(peers[j])) - (uint32_t)__popc(peers[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < kScatterPer; ++j) {
+    const uint32_t b = __shfl_sync(0xFFFFFFFFu, base[j], __ffs(peers[j]) - 1);
+    if (k[j] != kSentinel) {
+      const uint32_t rank = __popc(peers[j] & ((1u << lane) - 1u));
+      perm[sk[j] + b + rank] = (uint32_t)(i0 + (int64_t)j * blockDim.x);
+    }
+  }
 }
 
 __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
@@ -263,7 +279,7 @@ void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial
 
 void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* count, uint32_t* perm,
                     const uint32_t* Mtot, int64_t cap, cudaStream_t s) {
-  const int64_t g = (cap + 255) / 256;
+  const int64_t g = (cap + 256 * kScatterPer - 1) / (256 * kScatterPer);
   k_scatter<<<(unsigned)(g > 0 ? g : 1), 256, 0, s>>>(key, start, count, perm, Mtot, cap);
 }
 
