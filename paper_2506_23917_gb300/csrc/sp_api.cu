@@ -385,7 +385,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 1, c->side);
     else launch_inject_f32(c->dim, ia, 1, c->side);
     cudaEventRecord(c->join_ev, c->side);
-    n += 5;
+    n += 4;
   }
   // hot cells weigh kHotWeight in FP32 mode, where the kernel is
   // latency-bound and the end of the launch matters; the FP64 pipe bounds
@@ -404,10 +404,10 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     launch_scan(c->gcount, c->goff, c->n_ghost, c->gscan_part, c->stream);
     if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 1, c->stream);
     else launch_inject_f32(c->dim, ia, 1, c->stream);
-    n += 5;
+    n += 4;
   }
   if (ev) cudaEventRecord(ev[2], c->stream);
-  launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream); n += 3;
+  launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream); n += 2;
   launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
                        c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->nbatch,
                        c->surf_time, c->cyc, c->stream); ++n;

@@ -51,20 +51,6 @@ __global__ void k_scan_reduce(const uint32_t* in, int64_t n, uint32_t* partial) 
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the block totals by one block (any count).
-__global__ void k_scan_top(uint32_t* partial, int64_t nb) {
-  uint32_t carry = 0;
-  for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
-    const int64_t j = b0 + threadIdx.x;
-    const uint32_t v = j < nb ? partial[j] : 0;
-    uint32_t tot;
-    const uint32_t e = block_excl_scan(v, &tot);
-    if (j < nb) partial[j] = carry + e;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) partial[nb] = carry;
-}
-
 // out[j] = sum of in[0..j), out[n] = total.  Each thread owns kScanItems
 // consecutive elements of the block's tile.
 __global__ void k_scan_down(const uint32_t* in, uint32_t* out, int64_t n, const uint32_t* partial,
@@ -78,15 +64,21 @@ __global__ void k_scan_down(const uint32_t* in, uint32_t* out, int64_t n, const 
     v[i] = j < n ? in[j] : 0;
     s += v[i];
   }
+  // the block's offset: the sum of the earlier blocks' totals (read here
+  // rather than scanned by a separate launch)
+  uint32_t pre = 0;
+  for (int64_t b = threadIdx.x; b < (int64_t)blockIdx.x; b += kScanThreads) pre += partial[b];
+  uint32_t off;
+  block_excl_scan(pre, &off);
   uint32_t tot;
-  uint32_t run = partial[blockIdx.x] + block_excl_scan(s, &tot);
+  uint32_t run = off + block_excl_scan(s, &tot);
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t j = base + i;
     if (j < n) out[j] = run;
     run += v[i];
   }
-  if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = partial[nb];
+  if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = off + tot;
 }
 
 // perm[start[key] + rank] = source index.  The histogram itself is the
@@ -273,7 +265,6 @@ void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial
     return;
   }
   k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
-  k_scan_top<<<1, kScanThreads, 0, s>>>(partial, nb);
   k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partial, nb);
 }
 
