@@ -597,8 +597,9 @@ __device__ __forceinline__ const InstParams& inst_params(const StepArgs& a, uint
 // Per-cell sums with an order fixed by the cell alone (so results do not
 // depend on how cells are grouped into batches): a cell of at most
 // kLaneSumMax particles is summed by its own lane (lane i <-> cell i) in
-// slot order, with no shuffles; the cells above it by the warp's segmented
-// scan.  Writes acc[k][i] for every own cell i.
+// slot order, with no shuffles; the cells above it by the warp (FP64: the
+// segmented scan; FP32: a share of slots per lane and a butterfly).  Writes
+// acc[k][i] for every own cell i.
 constexpr int kLaneSumMax = 256;
 template <class T, int K, class F>
 __device__ __forceinline__ void cell_sums(int M, uint32_t p0, const uint8_t* sseg, T (*acc)[32], bool own,
@@ -624,10 +625,39 @@ __device__ __forceinline__ void cell_sums(int M, uint32_t p0, const uint8_t* sse
   const unsigned bigs = __ballot_sync(kFull, own && !small);
   __syncwarp();
   if (bigs) {
-    seg_sums<T, K>(M, p0, sseg, acc, [&](int s, T* v) {
-      const int c = sseg[s];
-      if ((bigs >> c) & 1u) f(s, c, v);
-    });
+    if constexpr (sizeof(T) == 4) {
+      // FP32: each big cell by the whole warp, one contiguous share of its
+      // slots per lane, then a butterfly over the lanes (the order depends
+      // only on the cell's particle count)
+      for (unsigned b = bigs; b; b &= b - 1) {
+        const int c = __ffs(b) - 1;
+        const int o0 = __shfl_sync(kFull, offi, c), n = __shfl_sync(kFull, Ni, c);
+        const int per = (n + 31) / 32;
+        const int s0 = o0 + lane * per;
+        const int s1 = s0 + per < o0 + n ? s0 + per : o0 + n;
+        T a[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) a[k] = 0;
+        for (int s = s0; s < s1; ++s) {
+          T v[K];
+          f(s, c, v);
+#pragma unroll
+          for (int k = 0; k < K; ++k) a[k] += v[k];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int k = 0; k < K; ++k) a[k] += __shfl_xor_sync(kFull, a[k], o);
+        if (lane == c)
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc[k][c] += a[k];
+      }
+    } else {
+      seg_sums<T, K>(M, p0, sseg, acc, [&](int s, T* v) {
+        const int c = sseg[s];
+        if ((bigs >> c) & 1u) f(s, c, v);
+      });
+    }
   }
   __syncwarp();
 }
