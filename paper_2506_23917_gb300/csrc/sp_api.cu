@@ -46,7 +46,7 @@ struct sp_ctx {
   uint32_t *cell_inst = nullptr, *scan_part = nullptr, *big_list = nullptr, *big_count = nullptr;
   uint32_t* ticket = nullptr;
   uint2* batches = nullptr;
-  uint32_t* nbatch = nullptr;         // [4] batches of the plan per class (heavy, large, medium, small)
+  uint32_t* nbatch = nullptr;         // [kBatchClasses] batches of the plan per class
   uint8_t* hot = nullptr;             // [NC] slow-batch flags of the last step
   unsigned long long* cyc = nullptr;  // [3] batch-cycle sum, particle sum, hot threshold per particle
   int collide_grid = 1;
@@ -631,8 +631,8 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->big_list, 4 * NC));
     CK(dalloc(&c->big_count, 4));
     CK(dalloc(&c->ticket, 4));
-    CK(dalloc(&c->batches, sizeof(uint2) * 2 * NC));
-    CK(dalloc(&c->nbatch, 16));
+    CK(dalloc(&c->batches, sizeof(uint2) * kBatchClasses * NC));
+    CK(dalloc(&c->nbatch, 4 * kBatchClasses));
     CK(dalloc(&c->hot, std::max<int64_t>(NC, 1)));
     CK(dalloc(&c->cyc, 24));
     CK(dalloc(&c->vol, 8 * NC));
@@ -680,7 +680,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(cudaMemsetAsync(c->step_d, 0, 4, s));
     CK(cudaMemsetAsync(c->big_count, 0, 4, s));
     CK(cudaMemsetAsync(c->ticket, 0, 4, s));
-    CK(cudaMemsetAsync(c->nbatch, 0, 16, s));
+    CK(cudaMemsetAsync(c->nbatch, 0, 4 * kBatchClasses, s));
     CK(cudaMemsetAsync(c->hot, 0, std::max<int64_t>(c->NC, 1), s));
     CK(cudaMemsetAsync(c->cyc, 0, 16, s));
     CK(cudaMemsetAsync(c->cyc + 2, 0xFF, 8, s));

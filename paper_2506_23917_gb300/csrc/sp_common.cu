@@ -135,10 +135,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
     *step = *step + 1u;
     *big_count = 0u;
     *ticket = 0u;
-    nbatch[0] = 0u;
-    nbatch[1] = 0u;
-    nbatch[2] = 0u;
-    nbatch[3] = 0u;
+    for (int k = 0; k < kBatchClasses; ++k) nbatch[k] = 0u;
     // threshold of the hot flag: cycles per particle, 2.5 times
     // this step's mean over all batches
     cyc[2] = cyc[1] > 0 ? (cyc[0] * 5ull) / (2ull * cyc[1]) : ~0ull;
@@ -164,17 +161,14 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 // with many collision candidates) weigh hot_weight times their particles
 // when batches are packed, so their work is spread over that many more
 // warps instead of one slow batch setting the end of the launch.  Batches
-// holding a hot cell form the first class; the others
-// are classed by particle count: large (at least cap/2), medium (cap/4 up
-// to cap/2) and small.  The collision kernel hands out the classes in that
-// order, longest first, so that the batches still running when the list
-// runs out are short ones and the SMs finish the launch together.  A warp
-// takes only a few batches per launch, so without this the last large
-// batches alone would keep a few SMs busy for a third of the launch.
-// Layout of the [2 NC] array: heavy from the front and small from the back
-// of [0, NC), large from the front and medium from the back of [NC, 2 NC)
-// (each pair holds at most NC batches).  Batches are independent: their
-// order changes no result.
+// holding a hot cell form the first class; the others are classed by
+// particle count in eighths of cap, largest first.  The collision kernel
+// hands out the classes in that order, longest first, so that the batches
+// still running when the list runs out are short ones and the SMs finish
+// the launch together.  A warp takes only a few batches per launch, so
+// without this the last large batches alone would keep a few SMs busy for a
+// third of the launch.  Class k's list is batches[k NC ...].  Batches are
+// independent: their order changes no result.
 __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, int hot_weight,
                        uint2* batches, uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
   const int lane = threadIdx.x & 31;
@@ -224,7 +218,8 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
       if (lane == nb) {
         mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
         const unsigned gm = G >= 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
-        mine_cls = ((hmask >> kk) & gm) != 0u ? 0 : (2 * np >= cap ? 1 : (4 * np >= cap ? 2 : 3));
+        const int eighths = (int)((8 * (int64_t)np) / cap);  // 0 .. 8
+        mine_cls = ((hmask >> kk) & gm) != 0u ? 0 : kBatchClasses - 1 - (eighths < 7 ? eighths : 7);
       }
       ++nb;
       kk += G;
@@ -232,14 +227,14 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
     const bool have = lane < nb;
     const unsigned below = (1u << lane) - 1u;
 #pragma unroll
-    for (int cls = 0; cls < 4; ++cls) {
+    for (int cls = 0; cls < kBatchClasses; ++cls) {
       const unsigned m = __ballot_sync(0xFFFFFFFFu, have && mine_cls == cls);
       if (m == 0u) continue;
       uint32_t b0 = 0;
       if (lane == 0) b0 = atomicAdd(&nbatch[cls], (uint32_t)__popc(m));
       b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
       const int64_t j = (int64_t)b0 + __popc(m & below);
-      const int64_t at = cls == 0 ? j : cls == 1 ? NC + j : cls == 2 ? 2 * NC - 1 - j : NC - 1 - j;
+      const int64_t at = (int64_t)cls * NC + j;
       if (have && mine_cls == cls) batches[at] = mine;
     }
   }

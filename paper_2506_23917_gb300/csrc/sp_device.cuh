@@ -1565,10 +1565,15 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
   // or batch takes it).  Main launch: batches from the plan's four class
   // lists by work stealing, heavy, large, medium, then small.  Big-cell
   // launch: a block per cell of the big list.
-  const uint32_t nh = big ? 0u : a.nbatch[0];
-  const uint32_t nl = big ? 0u : nh + a.nbatch[1];
-  const uint32_t nm = big ? 0u : nl + a.nbatch[2];
-  const uint32_t nb = big ? *a.big_count : nm + a.nbatch[3];
+  // the end of each class in ticket order (main launch)
+  uint32_t cend[kBatchClasses];
+  uint32_t nb = 0;
+#pragma unroll
+  for (int k = 0; k < kBatchClasses; ++k) {
+    nb += big ? 0u : a.nbatch[k];
+    cend[k] = nb;
+  }
+  if (big) nb = *a.big_count;
   uint32_t it = big ? blockIdx.x : 0u;
   for (;;) {
     int64_t k0;
@@ -1578,11 +1583,15 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
       if (lane == 0) t = atomicAdd(a.ticket, 1u);
       t = __shfl_sync(kFull, t, 0);
       if (t >= nb) break;
-      const int64_t at = t < nh ? (int64_t)t
-                       : t < nl ? a.NC + (int64_t)(t - nh)
-                       : t < nm ? 2 * a.NC - 1 - (int64_t)(t - nl)
-                                : a.NC - 1 - (int64_t)(t - nm);
-      const uint2 b = a.batches[at];
+      int cls = 0;
+      uint32_t c0 = 0;
+#pragma unroll
+      for (int k = 0; k + 1 < kBatchClasses; ++k)
+        if (t >= cend[k]) {
+          cls = k + 1;
+          c0 = cend[k];
+        }
+      const uint2 b = a.batches[(int64_t)cls * a.NC + (int64_t)(t - c0)];
       k0 = (int64_t)b.x;
       G = (int)b.y;
     } else {

@@ -10,6 +10,7 @@ constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // key of a removed particle
 constexpr int kMaxBounce = 16;               // wall events per particle per step
 constexpr int kSurfFields = 7;  // wall tallies per surface element
 constexpr int64_t kNcolCap = int64_t(1) << 24;
+constexpr int kBatchClasses = 9;             // batch lists: hot, then 8 by particle count (largest first)
 constexpr int kHotWeight = 4;                // plan weight of a hot cell's particles, FP32 mode (see k_plan)
 constexpr int kMaxWarpsPerBlock = 8;         // collide kernel block size limit
 constexpr int kCapSmall = 512;               // default per-warp staging capacity (particles)
@@ -97,8 +98,8 @@ struct StepArgs {
   uint32_t* big_list;   // cells above kCapSmall
   uint32_t* big_count;
   uint32_t* ticket;     // work-stealing counter over the batch list
-  const uint2* batches; // [2 NC] (first cell, cell count) of each batch, four class lists
-  const uint32_t* nbatch;  // [4] batches per class: heavy, large, medium, small (taken in that order)
+  const uint2* batches; // [kBatchClasses][NC] (first cell, cell count) of each batch, per class
+  const uint32_t* nbatch;  // [kBatchClasses] batches per class (taken in class order)
   uint8_t* hot;         // [NC] the cell's batch was slower than the threshold last step
   unsigned long long* cyc;  // [3] batch cycles and particles this step (sums), hot threshold per particle
   unsigned long long* err;  // [kNumErr]
