@@ -75,8 +75,9 @@ struct sp_ctx {
   bool uploaded = false, dirty = false, record = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_ok = false;
-  cudaStream_t side = nullptr;       // capture-time branch of the step graph (injection)
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaStream_t side = nullptr;       // capture-time branches of the step graph (injection,
+  cudaStream_t side2 = nullptr;      // big-cell launch)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr, fork2_ev = nullptr, join2_ev = nullptr;
   int launches = 0;
   std::vector<double*> dstage;    // per instance: FP64 [dim][n] then [3][n], device
   std::vector<int64_t> stage_n, stage_cap;
@@ -338,10 +339,10 @@ int small_grid(const sp_ctx* c) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, c->collide_grid));
 }
 
-void launch_collide_p(sp_ctx* c, const StepArgs& a, bool big, int grid) {
+void launch_collide_p(sp_ctx* c, const StepArgs& a, bool big, int grid, cudaStream_t s) {
   const int warps = big ? 1 : c->sched_warps;
-  if (c->prec == SP_FP64) launch_collide_f64(c->dim, a, big, grid, warps, c->stream);
-  else launch_collide_f32(c->dim, a, big, grid, warps, c->stream);
+  if (c->prec == SP_FP64) launch_collide_f64(c->dim, a, big, grid, warps, s);
+  else launch_collide_f32(c->dim, a, big, grid, warps, s);
 }
 
 // Collision-kernel schedule: staging capacity per warp and warps per block.
@@ -392,8 +393,20 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
   // FP64 mode, where fewer, larger batches are faster (weight 1)
   launch_plan(c->start, c->hot, c->NC, c->sched_cap, c->prec == SP_FP32 ? kHotWeight : 1, c->batches, c->nbatch,
               c->big_list, c->big_count, c->stream); ++n;
-  launch_collide_p(c, a, false, small_grid(c)); ++n;
-  launch_collide_p(c, a, true, 2 * 152); ++n;
+  if (branch) {
+    // the big-cell launch (cells disjoint from the batches') is a branch
+    // beside the main launch: its blocks start as SMs free up at the end of
+    // the main launch instead of after all of it
+    cudaEventRecord(c->fork2_ev, c->stream);
+    cudaStreamWaitEvent(c->side2, c->fork2_ev, 0);
+    launch_collide_p(c, a, true, 2 * 152, c->side2); ++n;
+    cudaEventRecord(c->join2_ev, c->side2);
+    launch_collide_p(c, a, false, small_grid(c), c->stream); ++n;
+    cudaStreamWaitEvent(c->stream, c->join2_ev, 0);
+  } else {
+    launch_collide_p(c, a, false, small_grid(c), c->stream); ++n;
+    launch_collide_p(c, a, true, 2 * 152, c->stream); ++n;
+  }
   if (ev) cudaEventRecord(ev[1], c->stream);
   if (fork) {
     cudaStreamWaitEvent(c->stream, c->join_ev, 0);
@@ -432,6 +445,9 @@ sp_status build_graphs(sp_ctx* c) {
     CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->fork2_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->join2_ev, cudaEventDisableTiming));
   }
   for (int par = 0; par < 2; ++par) {
     cudaStream_t cs;
@@ -1150,6 +1166,9 @@ sp_status sp_free(sp_ctx* c) {
     cudaStreamDestroy(c->side);
     cudaEventDestroy(c->fork_ev);
     cudaEventDestroy(c->join_ev);
+    cudaStreamDestroy(c->side2);
+    cudaEventDestroy(c->fork2_ev);
+    cudaEventDestroy(c->join2_ev);
   }
   for (int b = 0; b < 2; ++b)
     for (int d = 0; d < 3; ++d) {
