@@ -388,11 +388,8 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     cudaEventRecord(c->join_ev, c->side);
     n += 4;
   }
-  // hot cells weigh kHotWeight in FP32 mode, where the kernel is
-  // latency-bound and the end of the launch matters; the FP64 pipe bounds
-  // FP64 mode, where fewer, larger batches are faster (weight 1)
-  launch_plan(c->start, c->hot, c->NC, c->sched_cap, c->prec == SP_FP32 ? kHotWeight : 1, c->batches, c->nbatch,
-              c->big_list, c->big_count, c->stream); ++n;
+  launch_plan(c->start, c->hot, c->NC, c->sched_cap, c->batches, c->nbatch, c->big_list, c->big_count,
+              c->stream); ++n;
   if (branch) {
     // the big-cell launch (cells disjoint from the batches') is a branch
     // beside the main launch: its blocks start as SMs free up at the end of

@@ -155,13 +155,11 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 }
 // Work plan of a step: consecutive cells are grouped into batches whose
 // particles fit a warp's staging area (at most 32 cells each); cells above
-// it go to the big-cell list.  One warp per 32-cell chunk.  Cells flagged
-// hot (their batch cost more per particle than 2.5 times the step's
-// mean: cells where most particles are resampled with many rejections, or
-// with many collision candidates) weigh hot_weight times their particles
-// when batches are packed, so their work is spread over that many more
-// warps instead of one slow batch setting the end of the launch.  Batches
-// holding a hot cell form the first class; the others are classed by
+// it go to the big-cell list.  One warp per 32-cell chunk.  Batches holding
+// a cell flagged hot (its batch cost more per particle than 2.5 times the
+// step's mean: cells where most particles are resampled with many
+// rejections, or with many collision candidates) form the first class, so
+// that they start first; the others are classed by
 // particle count in eighths of cap, largest first.  The collision kernel
 // hands out the classes in that order, longest first, so that the batches
 // still running when the list runs out are short ones and the SMs finish
@@ -169,8 +167,8 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 // without this the last large batches alone would keep a few SMs busy for a
 // third of the launch.  Class k's list is batches[k NC ...].  Batches are
 // independent: their order changes no result.
-__global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, int hot_weight,
-                       uint2* batches, uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
+__global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches,
+                       uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nchunks = (NC + 31) / 32;
@@ -179,17 +177,11 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
     const int64_t c0 = chunk * 32;
     const int nc = (int)((NC - c0) < 32 ? (NC - c0) : 32);
     const bool is_hot = lane < nc && hot[c0 + lane] != 0;
-    const int64_t n_k = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
-    // particles (cum) and weight (wcum: hot cells count kHotWeight times)
-    int64_t cum = n_k, wcum = is_hot ? hot_weight * n_k : n_k;
+    int64_t cum = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int64_t y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
-      const int64_t wy = __shfl_up_sync(0xFFFFFFFFu, wcum, o);
-      if (lane >= o) {
-        cum += y;
-        wcum += wy;
-      }
+      if (lane >= o) cum += y;
     }
     const unsigned hmask = __ballot_sync(0xFFFFFFFFu, is_hot);
     int kk = 0, nb = 0;
@@ -197,22 +189,15 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
     int mine_cls = 0;
     while (kk < nc) {
       const int64_t before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
-      const int64_t wbefore = kk > 0 ? __shfl_sync(0xFFFFFFFFu, wcum, kk - 1) : 0;
-      const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && wcum - wbefore <= cap);
-      int G = __popc(fit);
-      if (G == 0) {
-        // the cell alone outweighs a batch: a batch of its own if its
-        // particles fit the staging area, else the big-cell list
-        if (__shfl_sync(0xFFFFFFFFu, cum, kk) - before <= cap) {
-          G = 1;
-        } else {
-          if (lane == 0) {
-            const uint32_t i = atomicAdd(big_count, 1u);
-            big_list[i] = (uint32_t)(c0 + kk);
-          }
-          kk += 1;
-          continue;
+      const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap);
+      const int G = __popc(fit);
+      if (G == 0) {  // the cell alone exceeds the staging area: big-cell list
+        if (lane == 0) {
+          const uint32_t i = atomicAdd(big_count, 1u);
+          big_list[i] = (uint32_t)(c0 + kk);
         }
+        kk += 1;
+        continue;
       }
       const int np = (int)(__shfl_sync(0xFFFFFFFFu, cum, kk + G - 1) - before);
       if (lane == nb) {
@@ -242,13 +227,13 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
 
 }  // namespace
 
-void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, int hot_weight, uint2* batches,
-                 uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
+void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+                 uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
   const int64_t chunks = (NC + 31) / 32;
   int64_t g = (chunks + 7) / 8;
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
-  k_plan<<<(unsigned)g, 256, 0, s>>>(start, hot, NC, cap, hot_weight, batches, nbatch, big_list, big_count);
+  k_plan<<<(unsigned)g, 256, 0, s>>>(start, hot, NC, cap, batches, nbatch, big_list, big_count);
 }
 
 int64_t scan_partial_size(int64_t n) { return (n + kTile - 1) / kTile + 1; }

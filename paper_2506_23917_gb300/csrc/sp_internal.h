@@ -11,7 +11,6 @@ constexpr int kMaxBounce = 16;               // wall events per particle per ste
 constexpr int kSurfFields = 7;  // wall tallies per surface element
 constexpr int64_t kNcolCap = int64_t(1) << 24;
 constexpr int kBatchClasses = 9;             // batch lists: hot, then 8 by particle count (largest first)
-constexpr int kHotWeight = 4;                // plan weight of a hot cell's particles, FP32 mode (see k_plan)
 constexpr int kMaxWarpsPerBlock = 8;         // collide kernel block size limit
 constexpr int kCapSmall = 512;               // default per-warp staging capacity (particles)
 constexpr int kWarpsDefault = 4;             // default warps per block
@@ -156,8 +155,8 @@ SP_DECLARE_LAUNCHERS(f32)
 
 // Precision-independent kernels (sp_common.cu).
 void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s);
-void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, int hot_weight, uint2* batches,
-                 uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count, cudaStream_t s);
+void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+                 uint32_t* big_list, uint32_t* big_count, cudaStream_t s);
 void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* count, uint32_t* perm,
                     const uint32_t* Mtot, int64_t cap, cudaStream_t s);
 void launch_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
