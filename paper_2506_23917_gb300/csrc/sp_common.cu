@@ -169,59 +169,64 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 // independent: their order changes no result.
 __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches,
                        uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
+  // per block: the batches of each class (shared atomics), then one global
+  // atomic per class for the block's place in the class list
+  __shared__ uint32_t cnt[kBatchClasses], base[kBatchClasses];
   const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t nw = (int64_t)gridDim.x * wpb;
   const int64_t nchunks = (NC + 31) / 32;
-  for (int64_t chunk = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
-       chunk += nw) {
-    const int64_t c0 = chunk * 32;
-    const int nc = (int)((NC - c0) < 32 ? (NC - c0) : 32);
-    const bool is_hot = lane < nc && hot[c0 + lane] != 0;
-    int64_t cum = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
-      if (lane >= o) cum += y;
-    }
-    const unsigned hmask = __ballot_sync(0xFFFFFFFFu, is_hot);
-    int kk = 0, nb = 0;
+  const int64_t iters = (nchunks + nw - 1) / nw;  // the same for every warp of the block
+  for (int64_t it = 0; it < iters; ++it) {
+    const int64_t chunk = it * nw + (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
+    if (threadIdx.x < kBatchClasses) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int nb = 0;
     uint2 mine = make_uint2(0, 0);
     int mine_cls = 0;
-    while (kk < nc) {
-      const int64_t before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
-      const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap);
-      const int G = __popc(fit);
-      if (G == 0) {  // the cell alone exceeds the staging area: big-cell list
-        if (lane == 0) {
-          const uint32_t i = atomicAdd(big_count, 1u);
-          big_list[i] = (uint32_t)(c0 + kk);
-        }
-        kk += 1;
-        continue;
-      }
-      const int np = (int)(__shfl_sync(0xFFFFFFFFu, cum, kk + G - 1) - before);
-      if (lane == nb) {
-        mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
-        const unsigned gm = G >= 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
-        const int eighths = (int)((8 * (int64_t)np) / cap);  // 0 .. 8
-        mine_cls = ((hmask >> kk) & gm) != 0u ? 0 : kBatchClasses - 1 - (eighths < 7 ? eighths : 7);
-      }
-      ++nb;
-      kk += G;
-    }
-    const bool have = lane < nb;
-    const unsigned below = (1u << lane) - 1u;
+    uint32_t mine_at = 0;
+    if (chunk < nchunks) {
+      const int64_t c0 = chunk * 32;
+      const int nc = (int)((NC - c0) < 32 ? (NC - c0) : 32);
+      const bool is_hot = lane < nc && hot[c0 + lane] != 0;
+      int64_t cum = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
 #pragma unroll
-    for (int cls = 0; cls < kBatchClasses; ++cls) {
-      const unsigned m = __ballot_sync(0xFFFFFFFFu, have && mine_cls == cls);
-      if (m == 0u) continue;
-      uint32_t b0 = 0;
-      if (lane == 0) b0 = atomicAdd(&nbatch[cls], (uint32_t)__popc(m));
-      b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-      const int64_t j = (int64_t)b0 + __popc(m & below);
-      const int64_t at = (int64_t)cls * NC + j;
-      if (have && mine_cls == cls) batches[at] = mine;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
+        if (lane >= o) cum += y;
+      }
+      const unsigned hmask = __ballot_sync(0xFFFFFFFFu, is_hot);
+      int kk = 0;
+      while (kk < nc) {
+        const int64_t before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
+        const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap);
+        const int G = __popc(fit);
+        if (G == 0) {  // the cell alone exceeds the staging area: big-cell list
+          if (lane == 0) {
+            const uint32_t i = atomicAdd(big_count, 1u);
+            big_list[i] = (uint32_t)(c0 + kk);
+          }
+          kk += 1;
+          continue;
+        }
+        const int np = (int)(__shfl_sync(0xFFFFFFFFu, cum, kk + G - 1) - before);
+        if (lane == nb) {
+          mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
+          const unsigned gm = G >= 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
+          const int eighths = (int)((8 * (int64_t)np) / cap);  // 0 .. 8
+          mine_cls = ((hmask >> kk) & gm) != 0u ? 0 : kBatchClasses - 1 - (eighths < 7 ? eighths : 7);
+        }
+        ++nb;
+        kk += G;
+      }
+      if (lane < nb) mine_at = atomicAdd(&cnt[mine_cls], 1u);
     }
+    __syncthreads();
+    if (threadIdx.x < kBatchClasses)
+      base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&nbatch[threadIdx.x], cnt[threadIdx.x]) : 0u;
+    __syncthreads();
+    if (lane < nb) batches[(int64_t)mine_cls * NC + base[mine_cls] + mine_at] = mine;
+    __syncthreads();
   }
 }
 
