@@ -23,6 +23,11 @@
 #include "../../include/sp.h"
 #include "sp_internal.h"
 
+namespace sp {
+// Sort each cell's perm segment ascending (sp_noalloc.cu).
+void launch_order_cells(const uint32_t* start, int64_t ncells, uint32_t* perm, cudaStream_t s);
+}  // namespace sp
+
 using namespace sp;
 
 namespace {
@@ -515,6 +520,10 @@ sp_status upload(sp_ctx* c) {
   CK(cudaMemcpyAsync(c->Mtot, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->Mcur, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
   launch_scatter(c->key, c->start, c->count, c->perm, c->Mtot, c->cap, c->stream);
+  // the scatter's atomics leave each cell's order arbitrary: restore the
+  // source order, so that the moments below (and the first step's Delta t)
+  // sum each cell in the same order on every run
+  launch_order_cells(c->start, c->NC, c->perm, c->stream);
   // Delta t from the moments of this state
   for (int i = 0; i < c->n_inst; ++i) c->hinf[i] = 0x7FF0000000000000ull;
   CK(cudaMemcpyAsync(c->dt_min, c->hinf.data(), 8 * c->n_inst, cudaMemcpyHostToDevice, c->stream));
@@ -926,6 +935,10 @@ sp_status sp_moments(sp_ctx* c, int inst, int kind, double* out, int n_fields) {
       c->mom_cells = nc;
     }
     double* d = c->mom;
+    // reproducible runs: each cell summed in source order (the scatter's
+    // order inside a cell is arbitrary; the collision step restores the
+    // same order, so this changes no later result)
+    if (c->stable) launch_order_cells(c->start, c->NC, c->perm, c->stream);
     StepArgs a = make_step_args(c, c->cur);
     if (c->prec == SP_FP64) launch_moments_f64(a, P.cell_off, P.cell_off + nc, d, c->stream);
     else launch_moments_f32(a, P.cell_off, P.cell_off + nc, d, c->stream);

@@ -94,6 +94,15 @@ cudaError_t static_scratch(uint32_t** out) {
 }
 
 }  // namespace
+
+// Each cell's permutation entries put in ascending (source) order.
+void launch_order_cells(const uint32_t* start, int64_t ncells, uint32_t* perm, cudaStream_t s) {
+  if (ncells <= 0) return;
+  int64_t ob = (ncells + 7) / 8;
+  if (ob > 8192) ob = 8192;
+  k_static_order<<<(unsigned)ob, 256, 0, s>>>(start, ncells, perm);
+}
+
 }  // namespace sp
 
 extern "C" sp_status sp_sort_cells_static(const uint32_t* d_keys, int64_t n, int64_t ncells,
