@@ -237,6 +237,30 @@ def test_capacity_overflow_is_reported(sp):
     assert e.value.code == -3
 
 
+def test_moments_and_first_step_do_not_depend_on_scatter_order(sp):
+    """The scatter's atomics leave each cell in an arbitrary order.  The
+    upload puts the cells back in source order before the moments that set
+    the first Delta t, and sp_moments does so in FP64 mode: two contexts on
+    the same particles give bit-identical Delta t and instantaneous fields,
+    at upload and after steps with different batch plans."""
+    cfg, regions = W.box2d(nx=24, ny=12, ppc=40.0)
+    pos, vel = W.fill_regions(cfg, regions, 7)
+    out = []
+    for sched in ((512, 4), (128, 2), (1024, 2)):
+        s = sp.Sim(cfg, sp.FP64, capacity=4 * vel.shape[1])
+        s.set_particles(0, pos, vel)
+        s.set_schedule(*sched)
+        dt0, m0 = s.dt(0), s.moments(0, 0)
+        s.step(7)
+        s.sync()
+        out.append((dt0, m0, s.dt(0), s.moments(0, 0)))
+        s.close()
+    for r in out[1:]:
+        assert r[0] == out[0][0] and r[2] == out[0][2]
+        np.testing.assert_array_equal(r[1], out[0][1])
+        np.testing.assert_array_equal(r[3], out[0][3])
+
+
 def test_schedule_and_autotune_do_not_change_results(sp):
     """Batch composition (staging capacity, warps per block) and the
     autotuner's choice must not change any result."""
