@@ -520,10 +520,10 @@ sp_status upload(sp_ctx* c) {
   CK(cudaMemcpyAsync(c->Mtot, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->Mcur, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
   launch_scatter(c->key, c->start, c->count, c->perm, c->Mtot, c->cap, c->stream);
-  // the scatter's atomics leave each cell's order arbitrary: restore the
-  // source order, so that the moments below (and the first step's Delta t)
-  // sum each cell in the same order on every run
-  launch_order_cells(c->start, c->NC, c->perm, c->stream);
+  // the scatter's atomics leave each cell's order arbitrary: reproducible
+  // runs restore the source order, so that the moments below (and the first
+  // step's Delta t) sum each cell in the same order on every run
+  if (c->stable) launch_order_cells(c->start, c->NC, c->perm, c->stream);
   // Delta t from the moments of this state
   for (int i = 0; i < c->n_inst; ++i) c->hinf[i] = 0x7FF0000000000000ull;
   CK(cudaMemcpyAsync(c->dt_min, c->hinf.data(), 8 * c->n_inst, cudaMemcpyHostToDevice, c->stream));
