@@ -148,7 +148,11 @@ sp_status sp_step(sp_ctx* ctx, int n_steps);
 
 /* kind 0: moments of the current state (fields SP_F_*); kind 1: time-
  * averaged fields of Step 6 (N, n, ux, uy, uz, T and the mean DSMC ratio in
- * SP_F_ratio; the other fields are 0).  out: host [n_fields][ncells(inst)]. */
+ * SP_F_ratio; the other fields are 0).  out: host [n_fields][ncells(inst)].
+ * In reproducible runs (FP64, or sp_set_reproducible on) kind 0 sums each
+ * cell in source order, so the fields are bit-identical from run to run;
+ * it puts the cells' particles in that order on the device first, which is
+ * the order the next step would restore anyway (no later result changes). */
 sp_status sp_moments(sp_ctx* ctx, int inst, int kind, double* out, int n_fields);
 
 /* Current particles of instance inst in sorted order (host FP64, SoA).
