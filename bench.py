@@ -367,7 +367,7 @@ def main():
     prec = sp.FP32 if args.precision == "fp32" else sp.FP64
     sim = sp.Sim(cfg, prec, capacity=cap)
     if prec == sp.FP32 and not args.reproducible:
-        sim.set_reproducible(False)  # FP32 mode is judged statistically
+        sim.set_reproducible(False)  # FP32 mode is checked statistically
     sim.set_particles(0, pos, vel)
     sim.step(args.develop)
     sim.sync()

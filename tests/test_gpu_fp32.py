@@ -1,4 +1,4 @@
-"""FP32 particle mode on the GPU, judged statistically against the FP64 mode
+"""FP32 particle mode on the GPU, checked statistically against the FP64 mode
 (which matches the oracle particle for particle, see test_gpu_parity.py).
 
 Bar: time-averaged n, u_x and T within relative L2 1e-2 of the FP64 fields,
