@@ -88,6 +88,42 @@ def test_static_sort_matches_indexing_path_twice(sp):
         np.testing.assert_array_equal(vel[:, perm], ref_vel)
 
 
+def _stable_reference(keys, ncells):
+    """Cell offsets and the stable order of the kept keys (numpy's stable
+    argsort: equal keys keep their index order)."""
+    k = keys.astype(np.int64)
+    keep = k < ncells
+    counts = np.bincount(k[keep], minlength=ncells)
+    start = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint32)
+    idx = np.nonzero(keep)[0]
+    order = idx[np.argsort(k[keep], kind="stable")].astype(np.uint32)
+    return start, order
+
+
+def test_static_sort_edge_cases_match_stable_argsort(sp):
+    """Removed particles (0xFFFFFFFF), keys past the last cell, empty cells
+    and two heavily loaded cells: one of 6000 entries (sorted by a block in
+    shared memory) and one of 20000 (sorted by a block in global memory),
+    each mixed with a few thousand lightly loaded ones, twice in a row."""
+    import torch
+
+    rng = np.random.default_rng(5)
+    ncells = 3000
+    light = rng.integers(0, ncells, 30000)
+    heavy_a = np.full(6000, 17)
+    heavy_b = np.full(20000, 2999)
+    gone = np.full(500, 0xFFFFFFFF)
+    past = rng.integers(ncells, ncells + 50, 300)
+    keys = np.concatenate([light, heavy_a, heavy_b, gone, past]).astype(np.uint64)
+    for rep in range(2):
+        k = keys[rng.permutation(len(keys))].astype(np.uint32)
+        start, perm = _call(sp, torch, k, ncells)
+        ref_start, ref_order = _stable_reference(k, ncells)
+        np.testing.assert_array_equal(start, ref_start)
+        np.testing.assert_array_equal(perm[: start[-1]], ref_order)
+        assert np.diff(start.astype(np.int64)).max() == 20000 + np.sum(light == 2999)
+
+
 def test_static_sort_rejects_too_many_cells(sp):
     import torch
 
