@@ -63,6 +63,8 @@ def lib():
         L.or_step_index.argtypes = [P]
         L.or_step_index.restype = C.c_int64
         L.or_get_totals.argtypes = [P, P]
+        L.or_set_threads.argtypes = [P, C.c_int]
+        L.or_get_threads.argtypes = [P]
         L.or_get_surface.argtypes = [P, P, P]
         L.or_free.argtypes = [P]
         L.or_philox4x32_10.argtypes = [P, P, P]
@@ -240,6 +242,12 @@ class Oracle:
         t = np.zeros(1)
         lib().or_get_surface(self.h, _ptr(out), _ptr(t))
         return out[:, :ns], float(t[0])
+
+    def set_threads(self, n):
+        """Threads of the per-cell loop (identical results for any count);
+        returns the count in effect (1 without OpenMP)."""
+        lib().or_set_threads(self.h, int(n))
+        return int(lib().or_get_threads(self.h))
 
     def totals(self):
         out = np.zeros(4, dtype=np.int64)

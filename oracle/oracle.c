@@ -101,6 +101,7 @@ struct or_ctx {
   double *surf; /* [7][n_surf] */
   double surf_time;
   int sampling_now;
+  int nthreads; /* threads of the per-cell loop of a step (OpenMP; 1 = sequential) */
 };
 
 /* ---------------------------------------------------------------------
@@ -316,7 +317,12 @@ static void collide_cell(or_ctx* c, int64_t k, double V, part* ps, int64_t N, co
         double A = 1.0 + (1.0 - g->Pr) * qC / (5.0 * RT * RT) * (CC / RT - 5.0);
         rec[3] += 1;
         if (R5 * Amax < A) break;
-        if (t == g->ar_max - 1) c->totals[3] += 1;
+        if (t == g->ar_max - 1) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+          c->totals[3] += 1;
+        }
       }
       ps[s].v[0] = mm->U[0] + C0;
       ps[s].v[1] = mm->U[1] + C1;
@@ -506,6 +512,7 @@ int or_init(const or_config* cfg, or_ctx** out) {
   if (!cfg || !out || cfg->dim < 1 || cfg->dim > 3) return OR_ERR_ARG;
   or_ctx* c = (or_ctx*)calloc(1, sizeof *c);
   c->cfg = *cfg;
+  c->nthreads = 1;
   or_config* g = &c->cfg;
   for (int d = 0; d < 3; ++d) {
     if (d >= g->dim) { g->n[d] = 1; }
@@ -731,7 +738,13 @@ int or_step(or_ctx* c, int nsteps) {
     c->resamp = (uint8_t*)calloc(Mn ? Mn : 1, 1);
     c->rec_n = Mn;
     int sample = c->step >= g->n_steady;
-    /* Steps 3-5 per cell. */
+    /* Steps 3-5 per cell.  Cells are independent (every draw is keyed by
+     * the cell, each cell writes only its own slots and records), so with
+     * nthreads > 1 they are spread over threads with results identical to
+     * the sequential loop (the minimum is exact in any order). */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) reduction(min : mn) num_threads(c->nthreads > 0 ? c->nthreads : 1)
+#endif
     for (int64_t k = 0; k < c->ncells; ++k) {
       int64_t s0 = c->start[k], N = c->start[k + 1] - s0;
       mom mm;
@@ -868,6 +881,18 @@ int or_get_surface(const or_ctx* c, double* out, double* time) {
   if (time) *time = c->surf_time;
   return OR_OK;
 }
+
+int or_set_threads(or_ctx* c, int n) {
+  if (!c || n < 1) return OR_ERR_ARG;
+#ifdef _OPENMP
+  c->nthreads = n;
+#else
+  c->nthreads = 1;
+#endif
+  return OR_OK;
+}
+
+int or_get_threads(const or_ctx* c) { return c ? c->nthreads : 0; }
 
 int or_get_totals(const or_ctx* c, int64_t* out4) {
   memcpy(out4, c->totals, sizeof c->totals);

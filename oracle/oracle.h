@@ -102,6 +102,11 @@ int64_t or_step_index(const or_ctx* c);
 int or_get_surface(const or_ctx* c, double* out, double* time);
 /* counters over the whole run: removed, injected, move_capped, ar_capped */
 int or_get_totals(const or_ctx* c, int64_t* out4);
+/* Threads of the per-cell loop (Steps 3-5) of or_step: cells are
+ * independent, so any count gives results identical to 1 (the default).
+ * Without OpenMP the count stays 1. */
+int or_set_threads(or_ctx* c, int n);
+int or_get_threads(const or_ctx* c);
 void or_free(or_ctx* c);
 
 /* Building blocks exported for the pin tests. */

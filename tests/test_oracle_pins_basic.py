@@ -95,3 +95,31 @@ def test_hard_sphere_kernel_is_pi_d_squared_cr():
     cfg = _argon_cfg(0.5)
     for cr in (1.0, 250.0, 1234.5):
         assert abs(oracle.sigc(cfg, cr) / (math.pi * cfg["d_ref"] ** 2 * cr) - 1.0) < 1e-14
+
+
+def test_oracle_threads_give_identical_results():
+    """The all-core variant of the oracle (the per-cell loop over threads)
+    gives results identical to the sequential loop, bit for bit: every draw
+    is keyed by its cell and each cell writes only its own data."""
+    import oracle
+    from paper_2506_23917_gb300 import workloads as W
+
+    cfg, regions = W.box2d(nx=24, ny=12, ppc=30.0)
+    cfg.update(n_surf=12, n_steady=2)
+    pos, vel = W.fill_regions(cfg, regions, 3)
+    runs = []
+    for nt in (1, 4):
+        o = oracle.Oracle(cfg)
+        got = o.set_threads(nt)
+        o.set_particles(pos, vel)
+        o.step(6)
+        runs.append((got, o.particles(), o.record(), o.sigc_max(), o.moments(1), o.surface()[0], o.dt))
+    assert runs[1][0] in (1, 4)
+    a, b = runs
+    for x, y in zip(a[1], b[1]):
+        np.testing.assert_array_equal(x, y)
+    for x, y in zip(a[2], b[2]):
+        np.testing.assert_array_equal(x, y)
+    for i in (3, 4, 5):
+        np.testing.assert_array_equal(a[i], b[i])
+    assert a[6] == b[6]
