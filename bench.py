@@ -4,7 +4,8 @@
 Workload (default): 2-D hypersonic argon flow past a cylinder -- Ma 5,
 Kn = 0.01 on the radius, VHS omega = 0.81, diffuse wall at T_inf, 600 x 300
 cells with analytic circular cut cells, 40 particles per freestream cell
-(~6.6 M particles), FP32 particle state with FP64 per-cell moments.  The
+(~6.6 M particles), FP32 particle state with FP64 per-cell sums and
+per-cell arithmetic.  The
 flow is developed for --develop untimed steps from a uniform freestream,
 then --warmup steps, then exactly --steps timed steps (one CUDA graph per
 step).  value = particle-updates/s = (mean particle count) x steps / time,
@@ -43,7 +44,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--scale", type=float, default=1.0)
     p.add_argument("--config", default="cylinder", choices=["cylinder", "sphere", "sod", "jet"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp32c", "fp64"],
+                   help="fp32: FP32 state, FP64 per-cell sums and arithmetic; fp32c: the opt-in "
+                        "all-FP32 variant; fp64: FP64 everything")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -57,6 +60,7 @@ def parse():
     p.add_argument("--reproducible", action="store_true",
                    help="FP32: restore the source order inside cells in the timed run")
     p.add_argument("--batch-steps", type=int, default=200)
+    p.add_argument("--no-sod", action="store_true", help="skip the FP64 Sod shock-tube leg")
     return p.parse_args()
 
 
@@ -95,9 +99,10 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def collide_traffic(src_hash):
-    """Per-particle DRAM traffic of the collision kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
+def collide_profile(src_hash):
+    """Per-particle figures of the collision kernel from the committed ncu
+    summary (DRAM bytes, warp-instructions), if it was taken on the current
+    kernel source; else {}."""
     path = os.path.join(ROOT, "profiles", "collide_cylinder_traffic.txt")
     try:
         kv = {}
@@ -106,15 +111,15 @@ def collide_traffic(src_hash):
                 k, v = line.strip().split("=", 1)
                 kv[k.strip()] = v.strip()
         if kv.get("source_sha256") != src_hash:
-            return None
-        return float(kv["bytes_per_particle"])
+            return {}
+        return {k: float(v) for k, v in kv.items() if k in ("bytes_per_particle", "inst_per_particle")}
     except Exception:
-        return None
+        return {}
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sp_device.cuh", "sp_kern_f32.cu", "sp_internal.h"):
+    for f in ("sp_device.cuh", "sp_kern.cu", "sp_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2506_23917_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -185,11 +190,13 @@ def crop_config(cfg, x0, x1, y1):
     return c
 
 
-def time_oracle(cfg, pos, vel, budget_s, max_steps, min_steps=1):
-    """Step the oracle on (cfg, pos, vel) for up to budget_s seconds."""
+def time_oracle(cfg, pos, vel, budget_s, max_steps, min_steps=1, threads=1):
+    """Step the oracle on (cfg, pos, vel) for up to budget_s seconds, its
+    per-cell loop on `threads` threads (identical results for any count)."""
     import oracle
 
     o = oracle.Oracle(cfg)
+    o.set_threads(threads)
     o.set_particles(pos, vel)
     upd, t, n = 0, 0.0, 0
     while n < max_steps and (n < min_steps or t < budget_s):
@@ -202,14 +209,25 @@ def time_oracle(cfg, pos, vel, budget_s, max_steps, min_steps=1):
     return upd, t, n
 
 
-def cpu_sample(cfg, pos, vel, budget_s=15.0):
+def cpu_sample(cfg, pos, vel, budget_s=12.0):
+    """The oracle on a window of the developed state, single-threaded and on
+    every host core (the per-cell loop over threads)."""
+    import oracle
+
     x0, x1, y1 = -1.8, 0.4, 1.5
     c = crop_config(cfg, x0, x1, y1)
     m = (pos[0] >= c["lo"][0]) & (pos[0] < c["hi"][0]) & (pos[1] < c["hi"][1])
-    upd, t, n = time_oracle(c, pos[:, m], vel[:, m], budget_s, max_steps=10 ** 6, min_steps=2)
-    sample = (f"oracle (FP64, 1 thread) on a {c['n'][0]}x{c['n'][1]}-cell window "
-              f"[{x0},{x1}]x[0,{y1}] R of the developed state ({int(m.sum())} particles), {n} steps")
-    return upd / t, sample
+    cores = os.cpu_count() or 1
+    probe = oracle.Oracle(c)
+    cores = probe.set_threads(cores)
+    out = {}
+    for nt in sorted({1, cores}):
+        upd, t, n = time_oracle(c, pos[:, m], vel[:, m], budget_s, max_steps=10 ** 6, min_steps=2, threads=nt)
+        out[nt] = (upd / t, n)
+    sample = (f"oracle (FP64) on a {c['n'][0]}x{c['n'][1]}-cell window [{x0},{x1}]x[0,{y1}] R of the "
+              f"developed state ({int(m.sum())} particles), {out[cores][1]} steps on {cores} threads "
+              f"(per-cell loop over threads; the move, injection and sort stay sequential)")
+    return out[cores][0], cores, sample, out[1][0]
 
 
 def run_reference(args):
@@ -237,6 +255,7 @@ def run_reference(args):
     import oracle
 
     o = oracle.Oracle(c)
+    cores = o.set_threads(os.cpu_count() or 1)
     o.set_particles(pos, vel)
     o.step(args.warmup)
     upd, t = 0, 0.0
@@ -247,13 +266,13 @@ def run_reference(args):
         t += time.perf_counter() - t0
         upd += m
     value = upd / t if t > 0 else 0.0
-    sample = (f"oracle (FP64, 1 thread) on a {c['n'][0]}x{c['n'][1]}-cell window of the "
+    sample = (f"oracle (FP64, per-cell loop on {cores} threads) on a {c['n'][0]}x{c['n'][1]}-cell window of the "
               f"{workload_name(args.scale)} grid from a uniform freestream start, {len(vel[0])} particles")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(args.scale), "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -277,58 +296,93 @@ def rank_seed(rank):
     return 1 + rank
 
 
-def bench_batch(sp, torch, stream, steps):
+def bench_batch(sp, torch, stream, steps, dist=None, device="cuda"):
+    """256 independent 1-D instances of uneven size.  Four legs: FP32 (FP64
+    per-cell arithmetic) and plain FP64, each as one batched context
+    (autotuned schedule; one set of launches per step) and as 256 separate
+    contexts stepped one after another.  Under torchrun the instances are
+    partitioned over the ranks (rank r: i = r mod N, no collective in the
+    step); times are the slowest rank's, updates the sum over ranks."""
+    from paper_2506_23917_gb300 import ensemble
     from paper_2506_23917_gb300 import workloads as W
 
     insts = W.batch(n_inst=256, seed=1, n_steady=0)
-    M = sum(v.shape[1] for _, _, v in insts)
+    world = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    mine = [insts[i] for i in ensemble.owned(len(insts), world, rank)]
+    M = sum(v.shape[1] for _, _, v in mine)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    sim = sp.Sim([c for c, _, _ in insts], sp.FP32, capacity=int(1.3 * M) + 10000)
-    for i, (c, p, v) in enumerate(insts):
-        sim.set_particles(i, p, v)
-    sim.step(5)
-    sim.sync()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    sim.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    sim.sync()
-    t32 = e0.elapsed_time(e1)
-    launches32 = sim.launches_per_step()
-    sim.close()
-    sims = []
-    for c, p, v in insts:
-        s = sp.Sim(c, sp.FP64, capacity=int(1.3 * v.shape[1]) + 1000)
-        s.set_particles(0, p, v)
-        s.step(5)
-        sims.append(s)
-    for s in sims:
-        s.sync()
-    k64 = max(5, steps // 10)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(k64):
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def batched(prec, k):
+        sim = sp.Sim([c for c, _, _ in mine], prec, capacity=int(1.3 * M) + 10000)
+        if prec != sp.FP64:
+            sim.set_reproducible(False)
+        for i, (c, p, v) in enumerate(mine):
+            sim.set_particles(i, p, v)
+        sim.step(5)
+        sched = sim.autotune(steps_per_trial=3)
+        sim.step(3)
+        sim.sync()
+        t = timed(sim.step, k)
+        sim.sync()
+        launches = sim.launches_per_step()
+        sim.close()
+        return t, launches, sched
+
+    def separate(prec, k):
+        sims = []
+        for c, p, v in mine:
+            s = sp.Sim(c, prec, capacity=int(1.3 * v.shape[1]) + 1000)
+            if prec != sp.FP64:
+                s.set_reproducible(False)
+            s.set_particles(0, p, v)
+            s.step(5)
+            sims.append(s)
         for s in sims:
-            s.step(1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    for s in sims:
-        s.sync()
-    t64 = e0.elapsed_time(e1)
-    launches64 = sum(s.launches_per_step() for s in sims)
-    for s in sims:
-        s.close()
-    v32 = steps * M / (t32 * 1e-3)
-    v64 = k64 * M / (t64 * 1e-3)
+            s.sync()
+
+        def run(n):
+            for _ in range(n):
+                for s in sims:
+                    s.step(1)
+
+        t = timed(run, k)
+        for s in sims:
+            s.sync()
+        launches = sum(s.launches_per_step() for s in sims)
+        for s in sims:
+            s.close()
+        return t, launches
+
+    ks = max(5, steps // 10)
+    legs = {}
+    for name, prec, k, fn in (("fp32_batched", sp.FP32, steps, batched), ("fp64_batched", sp.FP64, ks, batched),
+                              ("fp32_separate", sp.FP32, ks, separate), ("fp64_separate", sp.FP64, ks, separate)):
+        r = fn(prec, k)
+        t, upd = reduce_timing(r[0], k * M, dist, device)
+        legs[name] = {"value": upd / (t * 1e-3), "unit": UNIT, "ms_per_step": t / k, "steps": k,
+                      "launches_per_step": r[1]}
+        if fn is batched and r[2]:
+            legs[name]["schedule"] = {"cap": r[2][0], "warps_per_block": r[2][1]}
+    v = {k2: legs[k2]["value"] for k2 in legs}
     return {"workload": "256 x 1-D (even: Sod, nx = 2N/112.5; odd: homogeneous relaxation), "
-                        "N log-uniform 1e3..5e5, Kn log-uniform 1e-4..1", "particles": M,
-            "fp32_batched": {"value": v32, "unit": UNIT, "ms_per_step": t32 / steps, "steps": steps,
-                             "launches_per_step": launches32},
-            "fp64_separate": {"value": v64, "unit": UNIT, "ms_per_step": t64 / k64, "steps": k64,
-                              "launches_per_step": launches64},
-            "speedup": v32 / v64}
+                        "N log-uniform 1e3..5e5, Kn log-uniform 1e-4..1",
+            "particles": int(sum(v_.shape[1] for _, _, v_ in insts)), "ranks": world,
+            "partition": "rank r advances instances i = r mod N (strong scaling: fixed total work)",
+            **legs,
+            "batching_gain_fp32": v["fp32_batched"] / v["fp32_separate"],
+            "batching_gain_fp64": v["fp64_batched"] / v["fp64_separate"],
+            "precision_gain_batched": v["fp32_batched"] / v["fp64_batched"],
+            "speedup": v["fp32_batched"] / v["fp64_separate"]}
 
 
 def main():
@@ -364,9 +418,9 @@ def main():
     M_init = vel.shape[1]
     cap = int(1.5 * M_init) + 200000
     stream = torch.cuda.current_stream()
-    prec = sp.FP32 if args.precision == "fp32" else sp.FP64
+    prec = {"fp32": sp.FP32, "fp32c": sp.FP32_CELL32, "fp64": sp.FP64}[args.precision]
     sim = sp.Sim(cfg, prec, capacity=cap)
-    if prec == sp.FP32 and not args.reproducible:
+    if prec != sp.FP64 and not args.reproducible:
         sim.set_reproducible(False)  # FP32 mode is checked statistically
     sim.set_particles(0, pos, vel)
     sim.step(args.develop)
@@ -405,7 +459,7 @@ def main():
     # --- the same workload with the within-cell order restored every step
     # (bit-reproducible runs; FP64 mode always runs this way)
     repro = None
-    if prec == sp.FP32 and not args.reproducible:
+    if prec != sp.FP64 and not args.reproducible:
         sim.set_reproducible(True)
         sim.step(5)
         sim.sync()
@@ -428,14 +482,16 @@ def main():
     prof = sim.step_profiled(args.profile_steps)
     sim.sync()
     Mp = sim.count(0)
-    S = 4 * (cfg["dim"] + 3) if prec == sp.FP32 else 8 * (cfg["dim"] + 3)
+    S = 4 * (cfg["dim"] + 3) if prec != sp.FP64 else 8 * (cfg["dim"] + 3)
     collide_ms = prof[0] / args.profile_steps
     bytes_collide = (2 * S + 4) * Mp  # state read + state write + new key
     peak, peak_kind = load_peaks()
     achieved = bytes_collide / (collide_ms * 1e-3) / 1e9
     src_hash = kernel_source_hash()
     # the committed ncu figure covers the FP32 cylinder only
-    tpp = collide_traffic(src_hash) if (args.config == "cylinder" and prec == sp.FP32) else None
+    # the committed ncu figures cover the FP32 cylinder only
+    prof_pp = collide_profile(src_hash) if (args.config == "cylinder" and prec == sp.FP32) else {}
+    tpp = prof_pp.get("bytes_per_particle")
     step_ms = sum(prof) / args.profile_steps
     step_bytes = (2 * S + 8) * Mp
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -448,14 +504,30 @@ def main():
                                       zip(["collide", "inject", "scan", "scatter"], prof)},
                 "step_frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak,
                 "step_bytes_per_particle": 2 * S + 8}
+    # instruction-issue roof of the same kernel: warp-instructions per
+    # particle (ncu) x particles / kernel time, against SMs x 4 schedulers x
+    # the SM clock under load (one warp-instruction per scheduler per cycle)
+    ipp = prof_pp.get("inst_per_particle")
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_mhz = clk.get("sm_mhz") or 2070.0
+    issue_peak = nsm * 4 * clk_mhz * 1e6
+    roofline["issue"] = {"inst_per_particle": ipp, "unit": "warp-inst/s", "peak": issue_peak,
+                         "achieved": (ipp * Mp / (collide_ms * 1e-3)) if ipp else None,
+                         "frac": (ipp * Mp / (collide_ms * 1e-3) / issue_peak) if ipp else None,
+                         "source": "ncu smsp__inst_executed.sum of the committed profile" if ipp else
+                                   "no profile of the current kernel source"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == sp.FP32 else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if prec != sp.FP64 else "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.scale, args.config),
                        "cells": int(np.prod(cfg["n"][:cfg["dim"]])),
                        "particles_per_rank": int(0.5 * (M0 + M1)), "developed_steps": args.develop,
-                       "state": "FP32 particles, FP64 per-cell moments" if prec == sp.FP32 else "FP64",
+                       "state": {sp.FP32: "FP32 particles; per-cell sums accumulated to FP64 accuracy "
+                                          "and all per-cell arithmetic in FP64",
+                                 sp.FP32_CELL32: "FP32 particles, FP32 per-cell sums and arithmetic "
+                                                 "(opt-in variant)",
+                                 sp.FP64: "FP64"}[prec],
                        "l2": "inputs larger than L2 (state 2 x %.0f MB)" % (S * M0 / 1e6),
                        "graph": "one CUDA graph per step", "parallelism": f"replicas{world}",
                        "schedule": {"cap": sched[0], "warps_per_block": sched[1]} if sched else "default"},
@@ -466,7 +538,7 @@ def main():
         line["fp32_reproducible_order"] = repro
 
     # --- plain FP64 form of the same workload
-    if not args.no_fp64 and prec == sp.FP32:
+    if not args.no_fp64 and prec != sp.FP64:
         sim64 = sp.Sim(cfg, sp.FP64, capacity=cap)
         sim64.set_particles(0, pos, vel)
         sim64.step(args.develop)
@@ -489,6 +561,27 @@ def main():
                               "collide_ms": p64[0] / 10, "fp32_over_fp64": value / (v64 * world)}
         sim64.close()
 
+    # --- Sod shock tube in FP64: 200 cells, 500 / 62.5 particles per cell
+    # (56 250 particles), 400 steps at CFL 0.5 (L2-resident and latency bound)
+    if not args.no_sod and rank == 0:
+        cs, ps, vs = make_workload(W, "sod", 1.0, 1)
+        s1 = sp.Sim(cs, sp.FP64, capacity=4 * vs.shape[1])
+        s1.set_particles(0, ps, vs)
+        s1.step(3)
+        s1.sync()
+        n_sod = 400
+        m0 = s1.count(0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s1.step(n_sod)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s1.sync()
+        ts = e0.elapsed_time(e1)
+        line["sod_fp64"] = {"workload": workload_name(1.0, "sod"), "value": n_sod * 0.5 * (m0 + s1.count(0)) / (ts * 1e-3),
+                            "unit": UNIT, "ms_per_step": ts / n_sod, "steps": n_sod, "particles": m0}
+        s1.close()
+
     # --- the same workload with one collision sub-step forced everywhere
     # (pure DSMC and pure stochastic-particle Shakhov), the method's two
     # limits, in the headline's precision and schedule
@@ -497,7 +590,7 @@ def main():
         for name, mode in (("dsmc", W.MODE_DSMC), ("shakhov", W.MODE_SHAKHOV)):
             cfg_m = dict(cfg, mode=mode)
             sm = sp.Sim(cfg_m, prec, capacity=cap)
-            if prec == sp.FP32 and not args.reproducible:
+            if prec != sp.FP64 and not args.reproducible:
                 sm.set_reproducible(False)
             sm.set_particles(0, pos, vel)
             if sched:
@@ -526,10 +619,10 @@ def main():
         po, vo, _ = sim.particles(0)
         n_e2e = po.shape[1]
         # the context's own precision on the host side (FP32 state: FP32 input)
-        hdt = np.float32 if prec == sp.FP32 else np.float64
+        hdt = np.float32 if prec != sp.FP64 else np.float64
         hp = torch.from_numpy(np.ascontiguousarray(po, dtype=hdt)).pin_memory()
         hv = torch.from_numpy(np.ascontiguousarray(vo, dtype=hdt)).pin_memory()
-        upload = sim.set_particles_ptr_f32 if prec == sp.FP32 else sim.set_particles_ptr
+        upload = sim.set_particles_ptr_f32 if prec != sp.FP64 else sim.set_particles_ptr
         out = torch.empty((len(sp.FIELDS), sim.ncells[0]), dtype=torch.float64).pin_memory()
         K2 = 20
         for it in range(K2 + 2):
@@ -549,14 +642,15 @@ def main():
     # --- batched ensemble: 256 independent 1-D Sod / relaxation instances of
     # uneven size, FP32 in one context (one set of launches per step) vs the
     # plain FP64 form as 256 separate contexts stepped one after another
-    if not args.no_batch and rank == 0:
-        line["batch256"] = bench_batch(sp, torch, stream, args.batch_steps)
+    if not args.no_batch:
+        line["batch256"] = bench_batch(sp, torch, stream, args.batch_steps, dist, "cuda")
 
     # --- CPU oracle on a bounded sample of the same (developed) state
     if rank == 0 and world >= 1 and not args.no_cpu and args.config == "cylinder":
         po, vo, _ = sim.particles(0)
-        v_cpu, sample = cpu_sample(cfg, po, vo)
-        line["cpu_baseline"] = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        v_cpu, cores, sample, v_cpu1 = cpu_sample(cfg, po, vo)
+        line["cpu_baseline"] = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                                "single_thread": v_cpu1}
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

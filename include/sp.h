@@ -54,7 +54,19 @@ typedef enum {
   SP_ERR_STATE = -5     /* call out of order (e.g. sp_step before particles) */
 } sp_status;
 
-typedef enum { SP_FP64 = 0, SP_FP32 = 1 } sp_precision;
+/* Precision modes (sp_init):
+ *   SP_FP64         particle state and all arithmetic in FP64 (matches the
+ *                   CPU oracle particle for particle);
+ *   SP_FP32         particle state and per-particle arithmetic (free flight,
+ *                   pair collisions, Maxwellian sampling) in FP32; per-cell
+ *                   sums accumulated in FP64, and the per-cell arithmetic
+ *                   (U, T, q, tau, dt_c, the split, N_col, exp(-dt/tau), the
+ *                   conservation rescale) and the time averages in FP64;
+ *   SP_FP32_CELL32  opt-in variant of SP_FP32 whose per-cell sums and
+ *                   per-cell arithmetic are FP32 too (only the exp(-dt/tau)
+ *                   weight, the rescale factor and the time averages stay
+ *                   FP64).  Faster; checked statistically like SP_FP32. */
+typedef enum { SP_FP64 = 0, SP_FP32 = 1, SP_FP32_CELL32 = 2 } sp_precision;
 typedef enum { SP_BC_SPECULAR = 0, SP_BC_DIFFUSE = 1, SP_BC_OUTFLOW = 2, SP_BC_INFLOW = 3 } sp_bc;
 typedef enum { SP_BODY_NONE = 0, SP_BODY_CIRCLE = 1, SP_BODY_SPHERE = 2 } sp_body;
 typedef enum { SP_MODE_HYBRID = 0, SP_MODE_DSMC = 1, SP_MODE_SHAKHOV = 2 } sp_mode;
@@ -116,10 +128,10 @@ enum {
 };
 
 /* Create a context holding n_instances independent flows (cfgs[0..n)), all
- * with the same dim, stored and advanced in one set of kernels.
- * precision: SP_FP64 (state and arithmetic in FP64) or SP_FP32 (particle
- * state and per-particle arithmetic in FP32; per-cell moments, relaxation
- * weights, rescale factors and time averages in FP64).
+ * with the same dim, stored and advanced in one set of kernels.  This is the
+ * set-up part of Step 1 of Sec. III.B (the input data: grid, gas, boundary
+ * conditions); the particles of Step 1 come with sp_set_particles().
+ * precision: an sp_precision mode (SP_FP64, SP_FP32, SP_FP32_CELL32).
  * capacity: device particle slots over all instances (<= 2^31).
  * stream: a cudaStream_t or NULL.  Errors: SP_ERR_ARG for an invalid
  * config, SP_ERR_CUDA if device memory cannot be had. */
@@ -143,7 +155,12 @@ sp_status sp_set_particles(sp_ctx* ctx, int inst, const double* pos, const doubl
  * In an FP64 context the values are widened exactly. */
 sp_status sp_set_particles_f32(sp_ctx* ctx, int inst, const float* pos, const float* vel, int64_t n);
 
-/* Advance all instances by n_steps global steps (asynchronous). */
+/* Advance all instances by n_steps global steps (asynchronous): each step
+ * is Steps 2-5 of Sec. III.B -- per cell the Step 3 moments, the Step 4
+ * collision split into the DSMC part (Sec. II.A) and the Shakhov part
+ * (Sec. II.B) with the rescale, the Step 5 sampling, then the free flight
+ * of Step 2 and the indexing of Step 3 for the next step -- launched as one
+ * CUDA graph per step. */
 sp_status sp_step(sp_ctx* ctx, int n_steps);
 
 /* kind 0: moments of the current state (fields SP_F_*); kind 1: time-
@@ -171,6 +188,17 @@ sp_status sp_set_record(sp_ctx* ctx, int on);
 sp_status sp_get_step_record(sp_ctx* ctx, int inst, int64_t* cell4, uint8_t* resampled,
                              uint32_t* perm, int64_t* n_old);
 
+/* Conservation record of the last step of instance inst (record mode, FP64
+ * and FP32 modes): out host double [6][ncells].  For every cell whose
+ * velocities were rescaled (Sec. II.B: after a Shakhov resampling all
+ * velocities of the cell are mapped to c' = U + (c - U_p) sqrt(T / T_p)),
+ * with U, T the cell's Step 3 moments and the sums taken in FP64 over the
+ * rescaled velocities before they are stored in the state's precision:
+ * [0..2] sum c'_d - N U_d, [3] sum |c' - U|^2 - 3 R (N-1) T,
+ * [4] 3 R (N-1) T (> 0; the energy scale), [5] N sqrt(|U|^2 + 3 R T) (the
+ * momentum scale).  Cells without a rescale hold zeros.  SP_ERR_STATE
+ * unless recording was on during the step (sp_set_record). */
+sp_status sp_get_conservation(sp_ctx* ctx, int inst, double* out);
 /* Cell offsets of the current state of instance inst: host uint32
  * [ncells+1], relative to the instance's first particle. */
 sp_status sp_get_cell_start(sp_ctx* ctx, int inst, uint32_t* start);
@@ -244,6 +272,9 @@ sp_status sp_autotune(sp_ctx* ctx, int steps_per_trial, int* cap_out, int* warps
 sp_status sp_sync(sp_ctx* ctx);
 /* Number of kernel launches one sp_step() issues (for launch accounting). */
 int sp_launches_per_step(sp_ctx* ctx);
+/* Release a context: waits for its stream, frees its device memory and
+ * graphs.  (The end of the run of Sec. III.B: the fields of Step 6 are read
+ * with sp_moments() before this call.) */
 sp_status sp_free(sp_ctx* ctx);
 
 /* Stable counting sort of cell keys that allocates no device memory.  The
@@ -261,7 +292,10 @@ sp_status sp_free(sp_ctx* ctx);
  *   stream  cudaStream_t or NULL; the call is asynchronous on it.
  * Scratch lives in a file-scope __device__ array sized for ncells <=
  * 1,048,576 (8 MiB, held by every GPU that loads the library until exit);
- * larger ncells return SP_ERR_CAPACITY with a message.  The first call on a
+ * larger ncells, or n > 2^30 keys, return SP_ERR_CAPACITY with a message.
+ * Cells of up to 1024 entries are put in order by one warp each, larger
+ * ones by a block each (a cell of 2^20 entries takes a few tenths of a
+ * second).  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  Every call shares the one
  * array and clears the counters it needs, so calls whose work overlaps on

@@ -18,7 +18,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsp.so")
 
-FP64, FP32 = 0, 1
+# precision modes (sp_precision): FP64 state and arithmetic; FP32 state with
+# FP64 per-cell sums and arithmetic; FP32 state with FP32 per-cell sums and
+# arithmetic (opt-in)
+FP64, FP32, FP32_CELL32 = 0, 1, 2
 FIELDS = ["N", "n", "ux", "uy", "uz", "T", "qx", "qy", "qz", "tau", "dtc", "ratio"]
 ERRORS = ["capacity", "cell_cap", "bounce_cap", "ar_cap", "ncol_cap"]
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "capacity exceeded",
@@ -52,7 +55,7 @@ SYMBOLS = ["sp_init", "sp_set_particles", "sp_step", "sp_moments", "sp_get_parti
            "sp_set_record", "sp_get_step_record", "sp_get_cell_start", "sp_get_sigc_max",
            "sp_get_dt", "sp_get_surface", "sp_errors", "sp_sync", "sp_step_profiled", "sp_set_schedule", "sp_set_reproducible", "sp_autotune", "sp_launches_per_step", "sp_free",
            "sp_status_str", "sp_sort_cells_static", "sp_surface_coefficients",
-           "sp_set_particles_f32"]
+           "sp_set_particles_f32", "sp_get_conservation"]
 
 _lib = None
 
@@ -74,6 +77,7 @@ def lib():
         L.sp_set_record.argtypes = [P, C.c_int]
         L.sp_get_step_record.argtypes = [P, C.c_int, P, P, P, P]
         L.sp_get_cell_start.argtypes = [P, C.c_int, P]
+        L.sp_get_conservation.argtypes = [P, C.c_int, P]
         L.sp_get_sigc_max.argtypes = [P, C.c_int, P]
         L.sp_get_dt.argtypes = [P, C.c_int, P, P]
         L.sp_errors.argtypes = [P, P]
@@ -285,6 +289,15 @@ class Sim:
         perm = np.zeros(max(M, 1), dtype=np.uint32)
         _chk("sp_get_step_record", lib().sp_get_step_record(self.h, inst, None, _ptr(res), _ptr(perm), None))
         return cell4, res[: int(n_old[0])], perm[:M]
+
+    def conservation(self, inst=0):
+        """Rescale conservation record of the last recorded step, [6][ncells]:
+        sum c'_d - N U_d (d = x, y, z), sum |c' - U|^2 - 3 R (N-1) T, the
+        energy scale 3 R (N-1) T and the momentum scale N sqrt(|U|^2 + 3 R T),
+        summed in FP64 before the store (zeros where nothing was rescaled)."""
+        out = np.zeros((6, self.ncells[inst]))
+        _chk("sp_get_conservation", lib().sp_get_conservation(self.h, inst, _ptr(out)))
+        return out
 
     def cell_start(self, inst=0):
         st = np.zeros(self.ncells[inst] + 1, dtype=np.uint32)

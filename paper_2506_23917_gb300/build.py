@@ -13,7 +13,20 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsp.so")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["sp_api.cu", "sp_common.cu", "sp_kern_f64.cu", "sp_kern_f32.cu", "sp_noalloc.cu"]
+# (source, object, extra flags): sp_kern.cu is compiled once per precision
+# mode.  The FP64 mode is compiled without FMA contraction (-fmad=false), so
+# that every product and sum rounds as in the oracle (built with
+# -ffp-contract=off) and no cell index or accept decision can differ by a
+# fused rounding.
+KERN = "sp_kern.cu"
+SOURCES = [
+    ("sp_api.cu", "sp_api.o", []),
+    ("sp_common.cu", "sp_common.o", []),
+    ("sp_noalloc.cu", "sp_noalloc.o", []),
+    (KERN, "sp_kern_f64.o", ["-DSP_KT=double", "-DSP_KA=double", "-DSP_TAG=f64", "-fmad=false"]),
+    (KERN, "sp_kern_f32.o", ["-DSP_KT=float", "-DSP_KA=double", "-DSP_TAG=f32"]),
+    (KERN, "sp_kern_f32c.o", ["-DSP_KT=float", "-DSP_KA=float", "-DSP_TAG=f32c"]),
+]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -32,9 +45,10 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     extra = list(extra or [])
 
-    def cc(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    def cc(item):
+        src, o, flags = item
+        obj = os.path.join(BUILD, o)
+        cmd = [NVCC, *ARCH, *FLAGS, *flags, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

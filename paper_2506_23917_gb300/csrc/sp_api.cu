@@ -31,15 +31,16 @@ void launch_order_cells(const uint32_t* start, int64_t ncells, uint32_t* perm, c
 using namespace sp;
 
 namespace {
-// Staging capacity (particles) of the big-cell launch: one warp, 227 KB of
-// shared memory at 32 B (FP64) or 20 B (FP32) per particle, a power of two.
-constexpr int kBigCap64 = 4096, kBigCap32 = 8192;
 constexpr double kPiHost = 3.14159265358979323846;
+// Blocks of the big-cell launches (one warp per cell up to kHugeCell
+// particles; one block per larger cell), persistent over the big-cell list.
+constexpr int kBigGridPerSm = 2;
 }  // namespace
 
 struct sp_ctx {
   int n_inst = 0, dim = 0, prec = 0;
   size_t tsize = 8;
+  const KernelSet* K = nullptr;  // the kernels of this precision mode
   std::vector<InstParams> hP;
   std::vector<sp_config> cfg;
   InstParams* dP = nullptr;
@@ -66,6 +67,7 @@ struct sp_ctx {
   double* mom = nullptr;  // [SP_NFIELDS][largest instance] output of sp_moments kind 0
   int64_t mom_cells = 0;
   int32_t* rec = nullptr;
+  double* cons = nullptr;  // [6][NC] rescale conservation record
   uint8_t* resamp = nullptr;
   double* dt_cur = nullptr;
   unsigned long long* dt_min = nullptr;
@@ -81,8 +83,10 @@ struct sp_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_ok = false;
   cudaStream_t side = nullptr;       // capture-time branches of the step graph (injection,
-  cudaStream_t side2 = nullptr;      // big-cell launch)
+  cudaStream_t side2 = nullptr;      // big-cell launch, huge-cell launch)
+  cudaStream_t side3 = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr, fork2_ev = nullptr, join2_ev = nullptr;
+  cudaEvent_t fork3_ev = nullptr, join3_ev = nullptr;
   int launches = 0;
   std::vector<double*> dstage;    // per instance: FP64 [dim][n] then [3][n], device
   std::vector<int64_t> stage_n, stage_cap;
@@ -156,6 +160,11 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
   P->ncells = (int64_t)P->n[0] * P->n[1] * P->n[2];
   P->n_surf = (c.body != SP_BODY_NONE && c.n_surf > 0) ? c.n_surf : 0;
   P->FnM = c.Fn * c.m;
+  P->inv3R = 1.0 / (3.0 * c.R);
+  P->sqrt_gamma = sqrt(c.gamma);
+  P->tau_k = c.mu_ref * pow(c.T_ref, -c.omega) / (c.m * c.R);
+  P->inv_Lmin = 1.0 / P->Lmin;
+  P->inv_Fn = 1.0 / c.Fn;
   for (int d = 0; d < 3; ++d) {
     P->g64.lo[d] = P->lo[d];
     P->g64.hi[d] = P->hi[d];
@@ -290,6 +299,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.rem = c->rem;
   a.samp = c->samp;
   a.rec = c->record ? c->rec : nullptr;
+  a.cons = c->record ? c->cons : nullptr;
   a.resamp = c->record ? c->resamp : nullptr;
   a.P = c->dP;
   a.dt_cur = c->dt_cur;
@@ -305,7 +315,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.err = c->err;
   a.NC = c->NC;
   a.cap = c->cap;
-  a.big_cap = c->prec == SP_FP64 ? kBigCap64 : kBigCap32;
+  a.big_cap = kHugeCell;
   a.cap_small = c->sched_cap;
   a.stable = c->stable;
   a.surf = c->n_surf_tot > 0 ? c->surf : nullptr;
@@ -346,21 +356,19 @@ int small_grid(const sp_ctx* c) {
 
 void launch_collide_p(sp_ctx* c, const StepArgs& a, bool big, int grid, cudaStream_t s) {
   const int warps = big ? 1 : c->sched_warps;
-  if (c->prec == SP_FP64) launch_collide_f64(c->dim, a, big, grid, warps, s);
-  else launch_collide_f32(c->dim, a, big, grid, warps, s);
+  c->K->collide(c->dim, a, big, grid, warps, s);
 }
 
 // Collision-kernel schedule: staging capacity per warp and warps per block.
 // Returns false if it does not fit the shared memory or the block limits.
 bool apply_schedule(sp_ctx* c, int cap, int warps) {
-  if (cap < 32 || cap > (c->prec == SP_FP64 ? kBigCap64 : kBigCap32) || warps < 1 ||
+  if (cap < 32 || cap > kHugeCell || warps < 1 ||
       warps > kMaxWarpsPerBlock)
     return false;
-  const size_t smem = c->prec == SP_FP64 ? collide_smem_f64(warps, cap) : collide_smem_f32(warps, cap);
+  const size_t smem = c->K->collide_smem(warps, cap);
   if (smem > (size_t)kMaxDynSmem) return false;
   const bool one = c->n_inst == 1;
-  const int per_sm = c->prec == SP_FP64 ? collide_blocks_per_sm_f64(c->dim, warps, cap, one)
-                                        : collide_blocks_per_sm_f32(c->dim, warps, cap, one);
+  const int per_sm = c->K->collide_blocks_per_sm(c->dim, warps, cap, one);
   if (per_sm < 1) return false;
   c->sched_cap = cap;
   c->sched_warps = warps;
@@ -385,11 +393,9 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     cudaEventRecord(c->fork_ev, c->stream);
     cudaStreamWaitEvent(c->side, c->fork_ev, 0);
     const InjectArgs ia = make_inject_args(c, par);
-    if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 0, c->side);
-    else launch_inject_f32(c->dim, ia, 0, c->side);
+    c->K->inject(c->dim, ia, 0, c->side);
     launch_scan(c->gcount, c->goff, c->n_ghost, c->gscan_part, c->side);
-    if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 1, c->side);
-    else launch_inject_f32(c->dim, ia, 1, c->side);
+    c->K->inject(c->dim, ia, 1, c->side);
     cudaEventRecord(c->join_ev, c->side);
     n += 4;
   }
@@ -401,24 +407,27 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     // the main launch instead of after all of it
     cudaEventRecord(c->fork2_ev, c->stream);
     cudaStreamWaitEvent(c->side2, c->fork2_ev, 0);
-    launch_collide_p(c, a, true, 2 * 152, c->side2); ++n;
+    cudaStreamWaitEvent(c->side3, c->fork2_ev, 0);
+    launch_collide_p(c, a, true, kBigGridPerSm * c->nsm, c->side2); ++n;
     cudaEventRecord(c->join2_ev, c->side2);
+    c->K->collide_huge(c->dim, a, kBigGridPerSm * c->nsm, c->side3); ++n;
+    cudaEventRecord(c->join3_ev, c->side3);
     launch_collide_p(c, a, false, small_grid(c), c->stream); ++n;
     cudaStreamWaitEvent(c->stream, c->join2_ev, 0);
+    cudaStreamWaitEvent(c->stream, c->join3_ev, 0);
   } else {
     launch_collide_p(c, a, false, small_grid(c), c->stream); ++n;
-    launch_collide_p(c, a, true, 2 * 152, c->stream); ++n;
+    launch_collide_p(c, a, true, kBigGridPerSm * c->nsm, c->stream); ++n;
+    c->K->collide_huge(c->dim, a, kBigGridPerSm * c->nsm, c->stream); ++n;
   }
   if (ev) cudaEventRecord(ev[1], c->stream);
   if (fork) {
     cudaStreamWaitEvent(c->stream, c->join_ev, 0);
   } else if (c->n_ghost > 0) {
     const InjectArgs ia = make_inject_args(c, par);
-    if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 0, c->stream);
-    else launch_inject_f32(c->dim, ia, 0, c->stream);
+    c->K->inject(c->dim, ia, 0, c->stream);
     launch_scan(c->gcount, c->goff, c->n_ghost, c->gscan_part, c->stream);
-    if (c->prec == SP_FP64) launch_inject_f64(c->dim, ia, 1, c->stream);
-    else launch_inject_f32(c->dim, ia, 1, c->stream);
+    c->K->inject(c->dim, ia, 1, c->stream);
     n += 4;
   }
   if (ev) cudaEventRecord(ev[2], c->stream);
@@ -450,6 +459,9 @@ sp_status build_graphs(sp_ctx* c) {
     CK(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->fork2_ev, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->join2_ev, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&c->side3, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->fork3_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->join3_ev, cudaEventDisableTiming));
   }
   for (int par = 0; par < 2; ++par) {
     cudaStream_t cs;
@@ -494,27 +506,18 @@ sp_status upload(sp_ctx* c) {
     if (n > 0) {
       const double* sp = c->dstage[i];
       const float* sf = (const float*)c->dstage[i];
-      if (c->stage_f32[i]) {
-        if (c->prec == SP_FP64)
-          launch_stage_in32_f64(dim, sf, sf + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
-                                (uint32_t)i, c->stream);
-        else
-          launch_stage_in32_f32(dim, sf, sf + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
-                                (uint32_t)i, c->stream);
-      } else if (c->prec == SP_FP64) {
-        launch_stage_in_f64(dim, sp, sp + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
-                            (uint32_t)i, c->stream);
-      } else {
-        launch_stage_in_f32(dim, sp, sp + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
-                            (uint32_t)i, c->stream);
-      }
+      if (c->stage_f32[i])
+        c->K->stage_in32(dim, sf, sf + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
+                         (uint32_t)i, c->stream);
+      else
+        c->K->stage_in(dim, sp, sp + dim * n, n, c->pos[c->cur], c->vel[c->cur], off, c->part_inst,
+                       (uint32_t)i, c->stream);
     }
     off += n;
   }
   CK(cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * c->NC, c->stream));
   const void* P3[3] = {c->pos[c->cur][0], c->pos[c->cur][1], c->pos[c->cur][2]};
-  if (c->prec == SP_FP64) launch_keys_f64(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
-  else launch_keys_f32(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
+  c->K->keys(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
   launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream);
   c->hM = (uint32_t)M;
   CK(cudaMemcpyAsync(c->Mtot, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
@@ -528,8 +531,7 @@ sp_status upload(sp_ctx* c) {
   for (int i = 0; i < c->n_inst; ++i) c->hinf[i] = 0x7FF0000000000000ull;
   CK(cudaMemcpyAsync(c->dt_min, c->hinf.data(), 8 * c->n_inst, cudaMemcpyHostToDevice, c->stream));
   StepArgs a = make_step_args(c, c->cur);
-  if (c->prec == SP_FP64) launch_moments_f64(a, 0, c->NC, nullptr, c->stream);
-  else launch_moments_f32(a, 0, c->NC, nullptr, c->stream);
+  c->K->moments(a, 0, c->NC, nullptr, c->stream);
   CK(cudaMemcpyAsync(c->hmin.data(), c->dt_min, 8 * c->n_inst, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   for (int i = 0; i < c->n_inst; ++i) {
@@ -600,7 +602,7 @@ const char* sp_status_str(int s) {
 sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t capacity,
                   void* stream, sp_ctx** out) {
   if (!cfgs || n_instances < 1 || !out || capacity < 1 || capacity > (int64_t(1) << 31)) return SP_ERR_ARG;
-  if (precision != SP_FP64 && precision != SP_FP32) return SP_ERR_ARG;
+  if (precision != SP_FP64 && precision != SP_FP32 && precision != SP_FP32_CELL32) return SP_ERR_ARG;
   const int dim = cfgs[0].dim;
   for (int i = 0; i < n_instances; ++i)
     if (!valid(cfgs[i], dim)) return SP_ERR_ARG;
@@ -610,6 +612,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
   c->dim = dim;
   c->prec = precision;
   c->tsize = precision == SP_FP64 ? 8 : 4;
+  c->K = precision == SP_FP64 ? &kernels_f64() : precision == SP_FP32 ? &kernels_f32() : &kernels_f32c();
   c->stream = (cudaStream_t)stream;
   c->cap = capacity;
   c->cfg.assign(cfgs, cfgs + n_instances);
@@ -636,7 +639,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
   c->n_ghost = (int64_t)gh.size();
 
   sp_status st = [&]() -> sp_status {
-    CK(precision == SP_FP64 ? configure_f64(kBigCap64) : configure_f32(kBigCap32));
+    CK(c->K->configure());
     const int64_t NC = c->NC, cap = c->cap;
     for (int b = 0; b < 2; ++b)
       for (int d = 0; d < 3; ++d) {
@@ -771,6 +774,7 @@ sp_status sp_set_record(sp_ctx* c, int on) {
   const bool want = on != 0;
   if (want && !c->rec) {
     CK(dalloc(&c->rec, 4 * 4 * c->NC));
+    CK(dalloc(&c->cons, 8 * 6 * c->NC));
     CK(dalloc(&c->resamp, c->cap));
   }
   if (want != c->record) {
@@ -793,6 +797,7 @@ sp_status sp_step(sp_ctx* c, int n_steps) {
       c->prev_start.resize(c->NC + 1);
       CK(cudaMemcpyAsync(c->prev_start.data(), c->start, 4 * (c->NC + 1), cudaMemcpyDeviceToHost, c->stream));
       CK(cudaMemsetAsync(c->resamp, 0, c->cap, c->stream));
+      CK(cudaMemsetAsync(c->cons, 0, 8 * 6 * c->NC, c->stream));
       CK(cudaStreamSynchronize(c->stream));
     }
     CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
@@ -940,8 +945,7 @@ sp_status sp_moments(sp_ctx* c, int inst, int kind, double* out, int n_fields) {
     // same order, so this changes no later result)
     if (c->stable) launch_order_cells(c->start, c->NC, c->perm, c->stream);
     StepArgs a = make_step_args(c, c->cur);
-    if (c->prec == SP_FP64) launch_moments_f64(a, P.cell_off, P.cell_off + nc, d, c->stream);
-    else launch_moments_f32(a, P.cell_off, P.cell_off + nc, d, c->stream);
+    c->K->moments(a, P.cell_off, P.cell_off + nc, d, c->stream);
     CK(cudaMemcpyAsync(out, d, 8 * nf * nc, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   } else {
@@ -1002,8 +1006,7 @@ sp_status sp_get_particles(sp_ctx* c, int inst, double* pos, double* vel, uint32
   if (M > 0) CK(cudaMemcpyAsync(dperm, pm.data(), 4 * M, cudaMemcpyHostToDevice, c->stream));
   const void* Ap[3] = {c->pos[c->cur][0], c->pos[c->cur][1], c->pos[c->cur][2]};
   const void* Av[3] = {c->vel[c->cur][0], c->vel[c->cur][1], c->vel[c->cur][2]};
-  if (c->prec == SP_FP64) launch_gather_f64(c->dim, Ap, Av, dperm, 0, M, dpos, dvel, c->stream);
-  else launch_gather_f32(c->dim, Ap, Av, dperm, 0, M, dpos, dvel, c->stream);
+  c->K->gather(c->dim, Ap, Av, dperm, 0, M, dpos, dvel, c->stream);
   if (pos && M > 0) CK(cudaMemcpyAsync(pos, dpos, 8 * c->dim * M, cudaMemcpyDeviceToHost, c->stream));
   if (vel && M > 0) CK(cudaMemcpyAsync(vel, dvel, 8 * 3 * M, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -1037,6 +1040,18 @@ sp_status sp_get_step_record(sp_ctx* c, int inst, int64_t* cell4, uint8_t* resam
     if (s != SP_OK) return s;
     std::copy(pm.begin(), pm.end(), perm);
   }
+  return SP_OK;
+}
+
+sp_status sp_get_conservation(sp_ctx* c, int inst, double* out) {
+  if (!c || inst < 0 || inst >= c->n_inst || !out) return SP_ERR_ARG;
+  if (!c->record || !c->cons) return SP_ERR_STATE;
+  const InstParams& P = c->hP[inst];
+  const int64_t nc = P.ncells;
+  for (int f = 0; f < 6; ++f)
+    CK(cudaMemcpyAsync(out + f * nc, c->cons + f * c->NC + P.cell_off, 8 * nc, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return SP_OK;
 }
 
@@ -1179,6 +1194,9 @@ sp_status sp_free(sp_ctx* c) {
     cudaStreamDestroy(c->side2);
     cudaEventDestroy(c->fork2_ev);
     cudaEventDestroy(c->join2_ev);
+    cudaStreamDestroy(c->side3);
+    cudaEventDestroy(c->fork3_ev);
+    cudaEventDestroy(c->join3_ev);
   }
   for (int b = 0; b < 2; ++b)
     for (int d = 0; d < 3; ++d) {
@@ -1186,7 +1204,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->mom, c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->cons, c->mom, c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->rem, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

@@ -8,6 +8,7 @@
 // averages) are always FP64; per-particle arithmetic runs in T.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "sp_internal.h"
 
@@ -499,9 +500,18 @@ __device__ __forceinline__ double dsmc_ratio(const InstParams& P, int N, const C
   return m.tau / m.dtc;
 }
 
+// Precision modes of the collision kernel: T = particle state and
+// per-particle arithmetic, A = per-cell sums and per-cell arithmetic.
+// T == A: FP64 mode (double) or the opt-in all-FP32 mode (float).
+// T = float, A = double: FP32 state with FP64 per-cell sums and arithmetic.
+template <class T, class A>
+__host__ __device__ constexpr bool mixed_prec() {
+  return sizeof(T) < sizeof(A);
+}
+
 // Per-cell constants of a batch that the particle-parallel phases read
 // (one warp's batch of at most 32 cells).
-template <class T>
+template <class T, class A>
 struct __align__(16) CellTab {
   int off[33];   // slot range of cell i: [off[i], off[i+1])
   int inst[32];
@@ -514,14 +524,20 @@ struct __align__(16) CellTab {
   T U[3][32];
   T q[3][32];
   T RT[32], s2RT[32], Amax[32], Pres[32], omp[32], dt[32];
+  // Conservation rescale c' = U + (c - U_p) f, applied slot by slot.
+  // T == A: Up = U_p and f.  Mixed precision: the same map written as
+  // c' = c f + K with f = f[] + fl[] and K = Up[] + Kl[] as FP32 pairs
+  // (high part + rounding remainder of the FP64 values).  The mean-shift
+  // of the second moment pass uses Up / Kl the same way (U = Up + Kl).
   T Up[3][32];
+  T Kl[3][32];
   T f[32];
-  T acc[7][32];  // per-cell sums of the current reduction
+  T fl[32];
   T smax[32];    // (sigma_T c_r)_max while candidates run
 };
 
 // Staging per particle: velocities (3 T), source index, clash tag, cell.
-// In FP32 mode the source indices live in the x-velocity array until the
+// In FP32 modes the source indices live in the x-velocity array until the
 // gather overwrites them slot by slot (the free flight re-reads them from
 // perm), which saves 4 bytes per particle and raises the resident warps.
 template <class T>
@@ -532,47 +548,83 @@ template <class T>
 __host__ __device__ constexpr size_t stage_bytes_per_particle() {
   return 3 * sizeof(T) + (idx_in_velocity<T>() ? 0 : 4) + 4 + 1;
 }
-template <class T>
+template <class T, class A>
 __host__ __device__ constexpr size_t warp_stage_bytes(int cap) {
-  return (sizeof(CellTab<T>) + (size_t)cap * stage_bytes_per_particle<T>() + 15) / 16 * 16;
+  return (sizeof(CellTab<T, A>) + (size_t)cap * stage_bytes_per_particle<T>() + 15) / 16 * 16;
 }
 
-// Per-cell sums over all M slots of a batch in one pass: slots are grouped
-// by cell (sseg is nondecreasing), so a lane-ordered segmented scan of each
-// 32-slot chunk leaves the chunk's partial sum of a cell in the last lane
-// holding that cell, which adds it to acc[k][cell].  Chunks are aligned to
-// multiples of 32 of the global slot index (p0 is the batch's first slot),
-// so the order of additions of a cell depends only on its own slots, not on
-// how cells were grouped into batches.  acc must be zero on entry.
-template <class T, int K, class F>
-__device__ __forceinline__ void seg_sums(int M, uint32_t p0, const uint8_t* sseg, T (*acc)[32], F f) {
-  const int lane = threadIdx.x & 31;
-  for (int base = -(int)(p0 & 31u); base < M; base += 32) {
-    const int s = base + lane;
-    const bool valid = s >= 0 && s < M;
-    const int c = valid ? (int)sseg[s] : 255;
-    T v[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = 0;
-    if (valid) f(s, v);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int co = __shfl_up_sync(kFull, c, o);
-      const bool same = lane >= o && co == c;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const T y = __shfl_up_sync(kFull, v[k], o);
-        if (same) v[k] += y;
-      }
-    }
-    const int cn = __shfl_down_sync(kFull, c, 1);
-    if (valid && (lane == 31 || cn != c)) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) acc[k][c] += v[k];
-    }
-    __syncwarp();
-  }
+// ---------------------------------------------------------------------------
+// Error-free transformations in FP32 (Knuth's two-sum; Dekker's product,
+// here with a fused multiply-add): a + b = s + e and a * b = p + e exactly.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float two_sum(float a, float b, float* e) {
+  const float s = a + b;
+  const float bv = s - a;
+  const float av = s - bv;
+  *e = (a - av) + (b - bv);
+  return s;
 }
+__device__ __forceinline__ float two_prod(float a, float b, float* e) {
+  const float p = a * b;
+  *e = fmaf(a, b, -p);
+  return p;
+}
+
+// Accumulators of a lane's run of terms.  Each term comes as x plus an
+// exact low part lo (zero for plain terms; the remainder of an exact
+// product).
+//   PlainSum<T>: x added in T (lo is zero in the modes that use it).
+//   ExactSum: FP32 terms carried without rounding loss: every addition is
+//   split by two_sum, and the remainders (with the low parts) collect in e,
+//   whose own rounding is of order eps^2 of the total; s + e, formed in
+//   FP64, is the run's sum to FP64 accuracy.  On GB300 an FP64 add (and the
+//   FP32 -> FP64 conversion of its operand) goes through the FP64 pipe at
+//   about 1/56 of the FP32 rate, so these seven FP32 operations per term
+//   are several times cheaper than widening each term and adding in FP64.
+// combine(o) adds another accumulator's run; shfl_xor(o) is the lane
+// o-apart copy (for butterflies across a warp).
+template <class T>
+struct PlainSum {
+  using term = T;
+  using result = T;
+  static constexpr bool kExact = false;
+  T s;
+  __device__ __forceinline__ void init() { s = 0; }
+  __device__ __forceinline__ void add(T x, T) { s += x; }
+  __device__ __forceinline__ void combine(const PlainSum& o) { s += o.s; }
+  __device__ __forceinline__ PlainSum shfl_xor(int o) const {
+    PlainSum r;
+    r.s = __shfl_xor_sync(kFull, s, o);
+    return r;
+  }
+  __device__ __forceinline__ T get() const { return s; }
+};
+struct ExactSum {
+  using term = float;
+  using result = double;
+  static constexpr bool kExact = true;
+  float s, e;
+  __device__ __forceinline__ void init() { s = 0.0f; e = 0.0f; }
+  __device__ __forceinline__ void add(float x, float lo) {
+    float r;
+    s = two_sum(s, x, &r);
+    e += r + lo;
+  }
+  __device__ __forceinline__ void combine(const ExactSum& o) {
+    float r;
+    s = two_sum(s, o.s, &r);
+    e += o.e + r;
+  }
+  __device__ __forceinline__ ExactSum shfl_xor(int o) const {
+    ExactSum r;
+    r.s = __shfl_xor_sync(kFull, s, o);
+    r.e = __shfl_xor_sync(kFull, e, o);
+    return r;
+  }
+  __device__ __forceinline__ double get() const { return (double)s + (double)e; }
+};
+template <class T, class A>
+using CellAcc = typename std::conditional<mixed_prec<T, A>(), ExactSum, PlainSum<T>>::type;
 
 // Parameters of instance i.  With a single instance (ONE) they come from
 // the copy in the kernel's parameter space, so that the geometry and gas
@@ -597,74 +649,355 @@ __device__ __forceinline__ const InstParams& inst_params(const StepArgs& a, uint
 // Per-cell sums with an order fixed by the cell alone (so results do not
 // depend on how cells are grouped into batches): a cell of at most
 // kLaneSumMax particles is summed by its own lane (lane i <-> cell i) in
-// slot order, with no shuffles; the cells above it by the warp (FP64: the
-// segmented scan; FP32: a share of slots per lane and a butterfly).  Writes
-// acc[k][i] for every own cell i.
+// slot order, with no shuffles; a larger cell by the warp, one contiguous
+// share of its slots per lane, then a butterfly over the lanes (the order
+// again fixed by the cell's particle count).  f(s, c, v, lo) gives the K
+// terms of slot s of cell c (and their exact low parts); lane i receives
+// the sums of its own cell i in out[] (cells with own false are skipped).
 constexpr int kLaneSumMax = 256;
+constexpr int kLaneSumMaxExact = 256;
+// Cells above kHugeCell particles (sp_internal.h) are collided by one
+// block of kHugeThreads threads each (k_collide_huge).
+constexpr int kHugeThreads = 256;
+constexpr int kHugeWarps = kHugeThreads / 32;
 // NTC candidates up to which a cell runs its collision loop on its own lane:
 // in 3-D (sphere: +18 %; thresholds 8-32 gave -7 % to +9 %); not in 2-D,
 // where the flattened loop is as fast or faster (cylinder: -1 % to -3 %)
 template <int DIM>
 constexpr int kLaneNtcMax = DIM == 3 ? 256 : 0;
-template <class T, int K, class F>
-__device__ __forceinline__ void cell_sums(int M, uint32_t p0, const uint8_t* sseg, T (*acc)[32], bool own,
-                                          int offi, int Ni, F f) {
+// Cells above lane_sum_max<Acc> particles are summed by the whole warp.
+// (With the error-free accumulator, thresholds of 32 / 64 / 128 were 60 /
+// 26 / 6 % slower on the cylinder than 256: the warp's error-free butterfly
+// costs more than the lanes a dense cell leaves idle.)
+template <class Acc>
+constexpr int lane_sum_max = Acc::kExact ? kLaneSumMaxExact : kLaneSumMax;
+template <class Acc, int K, class F>
+__device__ __forceinline__ void cell_sums(bool own, int offi, int Ni, typename Acc::result (&out)[K], F f) {
+  using Tm = typename Acc::term;
   const int lane = threadIdx.x & 31;
-  const bool small = own && Ni <= kLaneSumMax;
+  const bool small = own && Ni <= lane_sum_max<Acc>;
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = 0;
   if (small) {
-    T a[K];
+    Acc acc[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) a[k] = 0;
+    for (int k = 0; k < K; ++k) acc[k].init();
     for (int s = offi; s < offi + Ni; ++s) {
-      T v[K];
-      f(s, lane, v);
+      Tm v[K], lo[K];
+      f(s, lane, v, lo);
 #pragma unroll
-      for (int k = 0; k < K; ++k) a[k] += v[k];
+      for (int k = 0; k < K; ++k) acc[k].add(v[k], lo[k]);
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k][lane] = a[k];
-  } else if (own) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k][lane] = 0;
+    for (int k = 0; k < K; ++k) out[k] = acc[k].get();
   }
-  const unsigned bigs = __ballot_sync(kFull, own && !small);
+  for (unsigned b = __ballot_sync(kFull, own && !small); b; b &= b - 1) {
+    const int c = __ffs(b) - 1;
+    const int o0 = __shfl_sync(kFull, offi, c), n = __shfl_sync(kFull, Ni, c);
+    const int per = (n + 31) / 32;
+    const int s0 = o0 + lane * per;
+    const int s1 = s0 + per < o0 + n ? s0 + per : o0 + n;
+    Acc acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k].init();
+    for (int s = s0; s < s1; ++s) {
+      Tm v[K], lo[K];
+      f(s, c, v, lo);
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k].add(v[k], lo[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k].combine(acc[k].shfl_xor(o));
+    if (lane == c)
+#pragma unroll
+      for (int k = 0; k < K; ++k) out[k] = acc[k].get();
+  }
   __syncwarp();
-  if (bigs) {
-    if constexpr (sizeof(T) == 4) {
-      // FP32: each big cell by the whole warp, one contiguous share of its
-      // slots per lane, then a butterfly over the lanes (the order depends
-      // only on the cell's particle count)
-      for (unsigned b = bigs; b; b &= b - 1) {
-        const int c = __ffs(b) - 1;
-        const int o0 = __shfl_sync(kFull, offi, c), n = __shfl_sync(kFull, Ni, c);
-        const int per = (n + 31) / 32;
-        const int s0 = o0 + lane * per;
-        const int s1 = s0 + per < o0 + n ? s0 + per : o0 + n;
-        T a[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) a[k] = 0;
-        for (int s = s0; s < s1; ++s) {
-          T v[K];
-          f(s, c, v);
-#pragma unroll
-          for (int k = 0; k < K; ++k) a[k] += v[k];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int k = 0; k < K; ++k) a[k] += __shfl_xor_sync(kFull, a[k], o);
-        if (lane == c)
-#pragma unroll
-          for (int k = 0; k < K; ++k) acc[k][c] += a[k];
-      }
+}
+
+// c f + K for an FP32 c, with f = fh + fl and K = Kh + Kl given as FP32
+// pairs (the splits of FP64 values): the product c fh is split exactly, the
+// small parts are added in FP32, and s + *lo (s returned) is the FP64 value
+// to about 2^-48 relative.
+__device__ __forceinline__ float affine_ff(float c, float fh, float fl, float Kh, float Kl, float* lo) {
+  float pe, se;
+  const float p = two_prod(c, fh, &pe);
+  const float s = two_sum(p, Kh, &se);
+  *lo = se + (pe + fmaf(c, fl, Kl));
+  return s;
+}
+
+// Record mode: conservation of the rescale in FP64, per cell:
+// cons[0..2] = sum c'_d - N U_d, cons[3] = sum |c' - U|^2 - 3 R (N-1) T,
+// cons[4] = 3 R (N-1) T, cons[5] = N sqrt(|U|^2 + 3 R T) (momentum scale),
+// with U, T the Step 3 moments and r = (sum c'_x, sum c'_y, sum c'_z,
+// sum |c'|^2) of the rescaled velocities before the FP32 store, summed in
+// FP64 (sum |c' - U|^2 = sum |c'|^2 - 2 U . sum c' + N |U|^2).
+template <class A>
+__device__ __forceinline__ void record_conservation(const StepArgs& a, int64_t kc, int Ni, const InstParams& P,
+                                                    const A* U, A T, const double* r) {
+  const int64_t NC = a.NC;
+  const double N = (double)Ni;
+  double uu = 0, us = 0;
+  for (int d = 0; d < 3; ++d) {
+    a.cons[d * NC + kc] = r[d] - N * (double)U[d];
+    uu += (double)U[d] * (double)U[d];
+    us += (double)U[d] * r[d];
+  }
+  const double E = 3.0 * P.R * (N - 1.0) * (double)T;
+  a.cons[3 * NC + kc] = (r[3] - 2.0 * us + N * uu) - E;
+  a.cons[4 * NC + kc] = E;
+  a.cons[5 * NC + kc] =
+      N * sqrt((double)U[0] * U[0] + (double)U[1] * U[1] + (double)U[2] * U[2] + 3.0 * P.R * (double)T);
+}
+
+// Step 3 scalars and the Step 4 split of one cell, in A (Sec. III.B): from
+// the cell's sums (m = sum c, mS2 = sum |C|^2, mS3 = sum |C|^2 C about the
+// mean) to U, n, the unbiased T and q_s, tau = mu / p with the VHS
+// viscosity, dt_c (Eq. "local time step"), the DSMC ratio and the sub-step
+// durations (Eqs. "tDSMC", "tShakhov"), the NTC candidate count (Eq.
+// "Ncol_DSMC", fractional part by stochastic rounding or the carried
+// remainder), the resampling probability 1 - exp(-dt_SBGK / tau) (FP64) and
+// the Shakhov sampling constants (A_max at |C| = 5 sqrt(RT), C parallel to
+// q_s).  FP64 mode: the oracle's expressions in its order.
+template <class A>
+struct CellMath {
+  A U[3], T, q[3], n, tau, dtc, ratio, dtG;
+  A RT, s2RT, Amax, omp;  // Shakhov sampling constants (shk)
+  double Pres;            // resampling probability (shk)
+  int64_t ncol;
+  unsigned long long dtbits;  // dt_c as ordered bits (~0: not a candidate)
+  bool shk;
+  __device__ __forceinline__ void clear() {
+    U[0] = U[1] = U[2] = 0;
+    T = 0;
+    q[0] = q[1] = q[2] = 0;
+    n = 0;
+    tau = dtc = tinf<A>();
+    ratio = 1;
+    dtG = 0;
+    RT = s2RT = Amax = omp = 0;
+    Pres = 0;
+    ncol = 0;
+    dtbits = ~0ull;
+    shk = false;
+  }
+};
+
+// The same quantities in FP64 for the FP32-state mode, with fewer FP64
+// instructions (the FP64 pipe of GB300 runs at 1/56 of the FP32 rate, and an
+// instruction costs the same whether one lane or 32 execute it): the
+// reciprocals 1/N, 1/(N-1), 1/(N-2), 1/V once; one square root sqrt(R T)
+// for the sound speed, sqrt(2RT) and (RT)^(3/2); and the viscosity power
+// through tau = tau_k T^(omega-1) / n = tau_k exp((omega-1) ln T) / n with
+// tau_k = mu_ref T_ref^-omega / (m R) from the host (one logarithm and one
+// exponential instead of pow).  FP64 throughout; the rounding differs from
+// the oracle's order by a few ulps (this mode is checked statistically).
+template <class T>
+__device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstParams& Pi, int64_t kc, uint32_t kl,
+                                               int Ni, double m0, double m1, double m2, double mS2, double mS3x,
+                                               double mS3y, double mS3z, double vol_k, T smaxT, double dt_cur,
+                                               uint32_t step, CellMath<double>& o) {
+  o.dtG = dt_cur;
+  o.ratio = Pi.mode == 2 ? 0.0 : 1.0;  // cells without a split: the forced mode, else DSMC
+  if (Ni <= 0) return;
+  const double fN = (double)Ni, iN = 1.0 / fN, iV = 1.0 / vol_k;
+  o.U[0] = m0 * iN;
+  o.U[1] = m1 * iN;
+  o.U[2] = m2 * iN;
+  const double nt = fN * Pi.Fn * iV;
+  o.n = nt;
+  if (Ni < 2) return;
+  const double iN1 = 1.0 / (fN - 1.0);
+  const double Tt = mS2 * iN1 * Pi.inv3R;
+  if (Ni >= 3) {
+    const double fq = 0.5 * fN * iN1 / (fN - 2.0);
+    o.q[0] = fq * mS3x;
+    o.q[1] = fq * mS3y;
+    o.q[2] = fq * mS3z;
+  }
+  o.T = Tt;
+  const double umag = sqrt(o.U[0] * o.U[0] + o.U[1] * o.U[1] + o.U[2] * o.U[2]);
+  double taut = tinf<double>(), dtct = tinf<double>(), itau = 0, sRT = 0;
+  if (Tt > 0.0) {
+    sRT = sqrt(Pi.R * Tt);
+    // 1/tau = n T^(1-omega) / tau_k
+    itau = nt * exp((1.0 - Pi.omega) * log(Tt)) / Pi.tau_k;
+    taut = 1.0 / itau;
+    dtct = Pi.Lmin / (umag + Pi.sqrt_gamma * sRT);
+  } else if (umag > 0.0) {
+    dtct = Pi.Lmin / umag;
+  }
+  if (dtct < tinf<double>()) o.dtbits = (unsigned long long)__double_as_longlong(dtct);
+  o.tau = taut;
+  o.dtc = dtct;
+  // r = tau / dt_c = tau (|U| + c_s) / L_min
+  const double r = (Tt > 0.0) ? taut * (umag + Pi.sqrt_gamma * sRT) * Pi.inv_Lmin : 1.0;
+  if (Pi.mode == 1) o.ratio = 1;
+  else if (Pi.mode == 2) o.ratio = 0;
+  else if (!(Tt > 0.0) || dtct <= taut) o.ratio = 1;
+  else o.ratio = r;
+  if (!(Tt > 0.0)) return;
+  const double dtG = dt_cur;
+  double dsmc, sbgk;
+  if (Pi.mode == 1) { dsmc = dtG; sbgk = 0; }
+  else if (Pi.mode == 2) { dsmc = 0; sbgk = dtG; }
+  else if (dtct <= taut) { dsmc = dtG; sbgk = 0; }
+  else { dsmc = r * dtG; sbgk = (1.0 - r) * dtG; }
+  if (dsmc > 0.0) {
+    const double ncr = 0.5 * fN * (fN - 1.0) * Pi.Fn * (double)smaxT * dsmc * iV;
+    if (Pi.ntc_carry) {
+      const double x = ncr + a.rem[kc];
+      o.ncol = (int64_t)floor(x);
+      a.rem[kc] = x - (double)o.ncol;
     } else {
-      seg_sums<T, K>(M, p0, sseg, acc, [&](int s, T* v) {
-        const int c = sseg[s];
-        if ((bigs >> c) & 1u) f(s, c, v);
-      });
+      Uni<T> rr(step, kl, kSentinel, kPurpNtc << 24, Pi.key0, Pi.key1);
+      o.ncol = (int64_t)floor(ncr + (double)rr.get(0));
+    }
+    if (o.ncol > kNcolCap) {
+      o.ncol = kNcolCap;
+      atomicAdd(&a.err[kErrNcol], 1ull);
     }
   }
-  __syncwarp();
+  if (sbgk > 0.0 && Ni >= 3) {
+    o.shk = true;
+    const double RTt = Pi.R * Tt;
+    const double qn = sqrt(o.q[0] * o.q[0] + o.q[1] * o.q[1] + o.q[2] * o.q[2]);
+    o.RT = RTt;
+    o.s2RT = 1.4142135623730950488 * sRT;
+    o.Amax = 1.0 + 20.0 * (1.0 - Pi.Pr) * qn / (RTt * sRT);
+    o.omp = 1.0 - Pi.Pr;
+    o.Pres = 1.0 - exp(-sbgk * itau);
+  }
+}
+
+template <class T, class A>
+__device__ __forceinline__ void cell_math(const StepArgs& a, const InstParams& Pi, int64_t kc, uint32_t kl, int Ni,
+                                          A m0, A m1, A m2, A mS2, A mS3x, A mS3y, A mS3z, double vol_k,
+                                          T smaxT, double dt_cur, uint32_t step, CellMath<A>& o) {
+  if constexpr (mixed_prec<T, A>()) {
+    cell_math_lean<T>(a, Pi, kc, kl, Ni, m0, m1, m2, mS2, mS3x, mS3y, mS3z, vol_k, smaxT, dt_cur, step, o);
+    return;
+  }
+  const A V = (A)vol_k;
+  A Tt = 0, qt[3] = {0, 0, 0}, nt = 0;
+  A taut = tinf<A>(), dtct = tinf<A>();
+  if (Ni > 0) {
+    o.U[0] = cdiv(m0, (A)Ni);
+    o.U[1] = cdiv(m1, (A)Ni);
+    o.U[2] = cdiv(m2, (A)Ni);
+    nt = cdiv((A)Ni * (A)Pi.Fn, V);
+  }
+  if (Ni >= 2) {
+    Tt = cdiv(mS2, (A)3.0 * (A)Pi.R * (A)(Ni - 1));
+    if (Ni >= 3) {
+      const A den = (A)(Ni - 1) * (A)(Ni - 2);
+      qt[0] = cdiv((A)0.5 * (A)Ni * mS3x, den);
+      qt[1] = cdiv((A)0.5 * (A)Ni * mS3y, den);
+      qt[2] = cdiv((A)0.5 * (A)Ni * mS3z, den);
+    }
+    const A umag = tsqrt(o.U[0] * o.U[0] + o.U[1] * o.U[1] + o.U[2] * o.U[2]);
+    if (Tt > (A)0) {
+      const A p = nt * (A)Pi.m * (A)Pi.R * Tt;
+      const A mu = (A)Pi.mu_ref * cpow(cdiv(Tt, (A)Pi.T_ref), (A)Pi.omega);
+      taut = cdiv(mu, p);
+      dtct = cdiv((A)Pi.Lmin, umag + tsqrt((A)Pi.gamma * (A)Pi.R * Tt));
+    } else if (umag > (A)0) {
+      dtct = cdiv((A)Pi.Lmin, umag);
+    }
+    if (dtct < tinf<A>()) o.dtbits = (unsigned long long)__double_as_longlong((double)dtct);
+  }
+  o.T = Tt;
+  o.q[0] = qt[0];
+  o.q[1] = qt[1];
+  o.q[2] = qt[2];
+  o.n = nt;
+  o.tau = taut;
+  o.dtc = dtct;
+  // DSMC ratio of the split (Eqs. tDSMC, tShakhov)
+  if (Pi.mode == 1) o.ratio = 1;
+  else if (Pi.mode == 2) o.ratio = 0;
+  else if (Ni < 2 || !(Tt > (A)0) || dtct <= taut) o.ratio = 1;
+  else o.ratio = cdiv(taut, dtct);
+  const A dtG = (A)dt_cur;
+  o.dtG = dtG;
+  if (Ni >= 2 && Tt > (A)0) {
+    A dsmc, sbgk;
+    if (Pi.mode == 1) { dsmc = dtG; sbgk = 0; }
+    else if (Pi.mode == 2) { dsmc = 0; sbgk = dtG; }
+    else if (dtct <= taut) { dsmc = dtG; sbgk = 0; }
+    else {
+      const A r = cdiv(taut, dtct);
+      dsmc = r * dtG;
+      sbgk = ((A)1.0 - r) * dtG;
+    }
+    if (dsmc > (A)0) {
+      const A ncr = cdiv((A)0.5 * (A)Ni * (A)(Ni - 1) * (A)Pi.Fn * (A)smaxT * dsmc, V);
+      if (Pi.ntc_carry) {  // Bird's carried remainder (FP64 state per cell)
+        const double x = (double)ncr + a.rem[kc];
+        o.ncol = (int64_t)floor(x);
+        a.rem[kc] = x - (double)o.ncol;
+      } else {
+        Uni<T> rr(step, kl, kSentinel, kPurpNtc << 24, Pi.key0, Pi.key1);
+        o.ncol = (int64_t)tfloor(ncr + (A)rr.get(0));
+      }
+      if (o.ncol > kNcolCap) {
+        o.ncol = kNcolCap;
+        atomicAdd(&a.err[kErrNcol], 1ull);
+      }
+    }
+    if (sbgk > (A)0 && Ni >= 3) {
+      o.shk = true;
+      const A RTt = (A)Pi.R * Tt;
+      const A qn = tsqrt(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2]);
+      o.RT = RTt;
+      o.s2RT = tsqrt((A)2.0 * RTt);
+      o.Amax = (A)1.0 + cdiv((A)20.0 * ((A)1.0 - (A)Pi.Pr) * qn, RTt * tsqrt(RTt));
+      o.omp = (A)1.0 - (A)Pi.Pr;
+      o.Pres = 1.0 - exp(-(double)sbgk / (double)taut);
+    }
+  }
+}
+
+// One acceptance-rejection attempt t of the Shakhov resampling of a slot
+// (Sec. II.B, Eqs. "Maxwell" and "A_cal"): a Box-Muller Maxwellian C at RT
+// from the slot's stream r, accepted when R5 A_max < A(C) with
+// A = 1 + (1 - Pr) (q_s . C) / (5 (RT)^2) (|C|^2 / RT - 5).  FP64 mode: five
+// uniforms 1 + 5t .. 5 + 5t of the stream (the oracle's layout).  FP32
+// modes: one Philox block per attempt (block 1 + t; block 0 holds the
+// Bernoulli draw), the two angles sharing a word, 16 bits each, and A formed
+// with the per-particle constants kA = (1 - Pr) / (5 (RT)^2), iRT = 1 / RT.
+template <class T>
+__device__ __forceinline__ bool shakhov_attempt(const Uni<T>& r, int t, T s2RT, T Amax, T omp, T RT, T kA, T iRT,
+                                                T q0, T q1, T q2, T* C0, T* C1, T* C2) {
+  T R1, R2, R3, R4, R5;
+  if constexpr (sizeof(T) == 4) {
+    const uint4 w = philox10(r.c0, r.c1, r.c2, r.c3 + 1u + (uint32_t)t, r.k0, r.k1);
+    R2 = u01f(w.x);
+    R4 = u01f(w.y);
+    R1 = (float)(2u * (w.z >> 16) + 1u) * 7.62939453125e-6f;
+    R3 = (float)(2u * (w.z & 0xFFFFu) + 1u) * 7.62939453125e-6f;
+    R5 = u01f(w.w);
+  } else {
+    T Rt[5];
+    uni_run<T, 5>(r, 1 + 5 * t, Rt);
+    R1 = Rt[0]; R2 = Rt[1]; R3 = Rt[2]; R4 = Rt[3]; R5 = Rt[4];
+  }
+  // (max: near R = 1 the approximate logarithm may round above 0)
+  const T r2 = csqrt(tmax0(-clog(R2))), r4 = csqrt(tmax0(-clog(R4)));
+  T sn3, cs3;
+  sincos2pi(R3, &sn3, &cs3);
+  *C0 = s2RT * cos2pi(R1) * r2;
+  *C1 = s2RT * cs3 * r4;
+  *C2 = s2RT * sn3 * r4;
+  const T qC = q0 * *C0 + q1 * *C1 + q2 * *C2;
+  const T CC = *C0 * *C0 + *C1 * *C1 + *C2 * *C2;
+  T A;
+  if constexpr (sizeof(T) == 4) A = (T)1.0 + kA * qC * (CC * iRT - (T)5.0);
+  else A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
+  return R5 * Amax < A;
 }
 
 // ---------------------------------------------------------------------------
@@ -674,9 +1007,11 @@ __device__ __forceinline__ void cell_sums(int M, uint32_t p0, const uint8_t* sse
 // histogram.  Particle work is spread over the lanes across the whole
 // batch; per-cell FP64 arithmetic runs lane-per-cell (lane i <-> cell i).
 // ---------------------------------------------------------------------------
-template <class T, int DIM, bool ONE>
-__device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* ct, uint32_t* sidx,
+template <class T, class A, int DIM, bool ONE>
+__device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A>* ct, uint32_t* sidx,
                               int* stag, uint8_t* sseg, T* svx, T* svy, T* svz) {
+  using Acc = CellAcc<T, A>;
+  constexpr bool kMixed = mixed_prec<T, A>();
   const int lane = threadIdx.x & 31;
   const int64_t NC = a.NC;
   const uint32_t step = *a.step;
@@ -803,15 +1138,18 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
     cp_async_wait_all();
   }
   __syncwarp();
-  // ---- 3. moment sums per cell (segmented, one pass each), kept by lane i.
-  // FP32 mode, cells of at most kLaneSumMax particles: one pass, shifted by
-  // the velocity D = c - c_1 of the cell's first particle (close to the
-  // mean, so FP32 loses nothing to cancellation): sums of D, of D D^T and of
+  // ---- 3. moment sums per cell, kept by lane i (lane i <-> cell i).
+  // All-FP32 mode, cells of at most kLaneSumMax particles: one pass, shifted
+  // by the velocity D = c - c_1 of the cell's first particle (close to the
+  // mean, so FP32 loses little to cancellation): sums of D, of D D^T and of
   // |D|^2 D, from which the central sums follow exactly (below).  All other
-  // cells: two passes, the second shifted by the cell mean.
+  // cases: two passes, the second about the cell mean U (FP64 mode: C = c - U
+  // in FP64, the oracle's sums; FP32 state with FP64 cells: C = (c - U_h) -
+  // U_l in FP32, with U = U_h + U_l the FP64 mean split into an FP32 pair, and
+  // both passes summed without loss into FP64).
   bool one_pass = false;
-  T m0 = 0, m1 = 0, m2 = 0, mS2 = 0, mS3x = 0, mS3y = 0, mS3z = 0;
-  if constexpr (sizeof(T) == 4) {
+  A m0 = 0, m1 = 0, m2 = 0, mS2 = 0, mS3x = 0, mS3y = 0, mS3z = 0;
+  if constexpr (sizeof(A) == 4) {
     one_pass = own && Ni > 0 && Ni <= kLaneSumMax;
     if (one_pass) {
       const T c0x = svx[offi], c0y = svy[offi], c0z = svz[offi];
@@ -854,148 +1192,82 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   }
   const bool two_pass = own && !one_pass;
   if (__any_sync(kFull, two_pass)) {
-    if (two_pass)
-      for (int k = 0; k < 7; ++k) ct->acc[k][lane] = 0;
-    __syncwarp();
-    cell_sums<T, 3>(M, p0, sseg, ct->acc, two_pass, offi, Ni, [&](int s, int c, T* v) {
+    A r1[3];
+    cell_sums<Acc, 3>(two_pass, offi, Ni, r1, [&](int s, int c, T* v, T* lo) {
       v[0] = svx[s];
       v[1] = svy[s];
       v[2] = svz[s];
+      lo[0] = lo[1] = lo[2] = 0;
     });
     if (two_pass && Ni > 0) {  // the shift of the central sums: the cell mean
-      ct->U[0][lane] = cdiv(ct->acc[0][lane], (T)Ni);
-      ct->U[1][lane] = cdiv(ct->acc[1][lane], (T)Ni);
-      ct->U[2][lane] = cdiv(ct->acc[2][lane], (T)Ni);
+      const A iN = kMixed ? (A)1 / (A)Ni : (A)0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const A Ud = kMixed ? r1[d] * iN : cdiv(r1[d], (A)Ni);
+        ct->Up[d][lane] = (T)Ud;
+        if constexpr (kMixed) ct->Kl[d][lane] = (T)(Ud - (A)(T)Ud);
+      }
     }
     __syncwarp();
-    cell_sums<T, 4>(M, p0, sseg, ct->acc + 3, two_pass, offi, Ni, [&](int s, int c, T* v) {
-      const T C0 = svx[s] - ct->U[0][c], C1 = svy[s] - ct->U[1][c], C2 = svz[s] - ct->U[2][c];
+    A r2[4];
+    cell_sums<Acc, 4>(two_pass, offi, Ni, r2, [&](int s, int c, T* v, T* lo) {
+      T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
+      if constexpr (kMixed) {
+        C0 -= ct->Kl[0][c];
+        C1 -= ct->Kl[1][c];
+        C2 -= ct->Kl[2][c];
+      }
       const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
       v[0] = c2;
       v[1] = c2 * C0;
       v[2] = c2 * C1;
       v[3] = c2 * C2;
+      lo[0] = lo[1] = lo[2] = lo[3] = 0;
     });
     if (two_pass) {
-      m0 = ct->acc[0][lane];
-      m1 = ct->acc[1][lane];
-      m2 = ct->acc[2][lane];
+      m0 = r1[0];
+      m1 = r1[1];
+      m2 = r1[2];
       if (Ni >= 2) {
-        mS2 = ct->acc[3][lane];
-        mS3x = ct->acc[4][lane];
-        mS3y = ct->acc[5][lane];
-        mS3z = ct->acc[6][lane];
+        mS2 = r2[0];
+        mS3x = r2[1];
+        mS3y = r2[2];
+        mS3z = r2[3];
       }
     }
+    __syncwarp();
   }
-  // ---- 4. per-cell arithmetic, lane i <-> cell i.  FP64 mode: all in FP64
-  // (the oracle's expressions).  FP32 mode: the cell scalars in FP32, with
-  // FP64 kept for the exp(-dt/tau) split weight (below), the rescale factor
-  // and the time-average accumulators.
+  // ---- 4. per-cell arithmetic in A, lane i <-> cell i (cell_math)
   const InstParams& Pi = inst_params<ONE>(a, inst);
-  CellMoments m;
-  m.T = 0;
-  m.q[0] = m.q[1] = m.q[2] = 0;
-  m.n = 0;
-  m.U[0] = m.U[1] = m.U[2] = 0;
-  m.tau = __longlong_as_double(0x7FF0000000000000ll);
-  m.dtc = m.tau;
-  int64_t ncol = 0;
+  CellMath<A> cm;
+  cm.clear();
   T smaxT = 0;
-  T ratioT = 1;
-  T sbgkT = 0, tauT = 0;
-  bool shk = false;
   bool sample = false;
-  unsigned long long dtbits = ~0ull;  // the cell's Delta t_c (positive: bits order as values)
   if (own) {
     sample = (int64_t)step >= (int64_t)Pi.n_steady;
-    const T V = (T)vol_k;
-    T Ut[3] = {0, 0, 0}, Tt = 0, qt[3] = {0, 0, 0}, nt = 0;
-    T taut = tinf<T>(), dtct = tinf<T>();
-    if (Ni > 0) {
-      Ut[0] = cdiv(m0, (T)Ni);
-      Ut[1] = cdiv(m1, (T)Ni);
-      Ut[2] = cdiv(m2, (T)Ni);
-      nt = cdiv((T)Ni * (T)Pi.Fn, V);
-    }
-    if (Ni >= 2) {
-      Tt = cdiv(mS2, (T)3.0 * (T)Pi.R * (T)(Ni - 1));
-      if (Ni >= 3) {
-        const T den = (T)(Ni - 1) * (T)(Ni - 2);
-        qt[0] = cdiv((T)0.5 * (T)Ni * mS3x, den);
-        qt[1] = cdiv((T)0.5 * (T)Ni * mS3y, den);
-        qt[2] = cdiv((T)0.5 * (T)Ni * mS3z, den);
-      }
-      const T umag = tsqrt(Ut[0] * Ut[0] + Ut[1] * Ut[1] + Ut[2] * Ut[2]);
-      if (Tt > (T)0) {
-        const T p = nt * (T)Pi.m * (T)Pi.R * Tt;
-        const T mu = (T)Pi.mu_ref * cpow(cdiv(Tt, (T)Pi.T_ref), (T)Pi.omega);
-        taut = cdiv(mu, p);
-        dtct = cdiv((T)Pi.Lmin, umag + tsqrt((T)Pi.gamma * (T)Pi.R * Tt));
-      } else if (umag > (T)0) {
-        dtct = cdiv((T)Pi.Lmin, umag);
-      }
-      if (dtct < tinf<T>()) dtbits = (unsigned long long)__double_as_longlong((double)dtct);
-    }
-    m.U[0] = Ut[0]; m.U[1] = Ut[1]; m.U[2] = Ut[2];
-    m.T = Tt;
-    m.q[0] = qt[0]; m.q[1] = qt[1]; m.q[2] = qt[2];
-    m.n = nt;
-    m.tau = taut;
-    m.dtc = dtct;
-    // DSMC ratio of the split (Eqs. tDSMC, tShakhov)
-    if (Pi.mode == 1) ratioT = 1;
-    else if (Pi.mode == 2) ratioT = 0;
-    else if (Ni < 2 || !(Tt > (T)0) || dtct <= taut) ratioT = 1;
-    else ratioT = cdiv(taut, dtct);
-    const T dtG = (T)a.dt_cur[inst];
-    ct->dt[lane] = dtG;
+    smaxT = (T)smax_k;
+    cell_math<T, A>(a, Pi, kc, (uint32_t)ct->kl[lane], Ni, m0, m1, m2, mS2, mS3x, mS3y, mS3z, vol_k, smaxT,
+                    a.dt_cur[inst], step, cm);
+    ct->dt[lane] = (T)cm.dtG;
     ct->Pres[lane] = 0;
-    if (Ni >= 2 && Tt > (T)0) {
-      T dsmc, sbgk;
-      if (Pi.mode == 1) { dsmc = dtG; sbgk = 0; }
-      else if (Pi.mode == 2) { dsmc = 0; sbgk = dtG; }
-      else if (dtct <= taut) { dsmc = dtG; sbgk = 0; }
-      else {
-        const T r = cdiv(taut, dtct);
-        dsmc = r * dtG;
-        sbgk = ((T)1.0 - r) * dtG;
-      }
-      if (dsmc > (T)0) {
-        smaxT = (T)smax_k;
-        const T ncr = cdiv((T)0.5 * (T)Ni * (T)(Ni - 1) * (T)Pi.Fn * smaxT * dsmc, V);
-        if (Pi.ntc_carry) {  // Bird's carried remainder (FP64 state per cell)
-          const double x = (double)ncr + a.rem[kc];
-          ncol = (int64_t)floor(x);
-          a.rem[kc] = x - (double)ncol;
-        } else {
-          Uni<T> rr(step, (uint32_t)ct->kl[lane], kSentinel, kPurpNtc << 24, Pi.key0, Pi.key1);
-          ncol = (int64_t)tfloor(ncr + rr.get(0));
-        }
-        if (ncol > kNcolCap) {
-          ncol = kNcolCap;
-          atomicAdd(&a.err[kErrNcol], 1ull);
-        }
-      }
-      if (sbgk > (T)0 && Ni >= 3) {
-        shk = true;
-        sbgkT = sbgk;
-        tauT = taut;
-        const T RTt = (T)Pi.R * Tt;
-        const T qn = tsqrt(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2]);
-        ct->RT[lane] = RTt;
-        ct->s2RT[lane] = tsqrt((T)2.0 * RTt);
-        ct->Amax[lane] = (T)1.0 + cdiv((T)20.0 * ((T)1.0 - (T)Pi.Pr) * qn, RTt * tsqrt(RTt));
-        ct->omp[lane] = (T)1.0 - (T)Pi.Pr;
-      }
+    if (cm.shk) {
+      ct->RT[lane] = (T)cm.RT;
+      ct->s2RT[lane] = (T)cm.s2RT;
+      ct->Amax[lane] = (T)cm.Amax;
+      ct->omp[lane] = (T)cm.omp;
     }
-    ct->U[0][lane] = Ut[0];
-    ct->U[1][lane] = Ut[1];
-    ct->U[2][lane] = Ut[2];
-    ct->q[0][lane] = qt[0];
-    ct->q[1][lane] = qt[1];
-    ct->q[2][lane] = qt[2];
+    ct->U[0][lane] = (T)cm.U[0];
+    ct->U[1][lane] = (T)cm.U[1];
+    ct->U[2][lane] = (T)cm.U[2];
+    ct->q[0][lane] = (T)cm.q[0];
+    ct->q[1][lane] = (T)cm.q[1];
+    ct->q[2][lane] = (T)cm.q[2];
   }
+  const int64_t ncol = cm.ncol;
+  const bool shk = cm.shk;
+  const unsigned long long dtbits = cm.dtbits;
+  A* UA = cm.U;
+  const A TA = cm.T;
   // the instance's minimum Delta t_c: with one instance the warp's minimum
   // goes in one atomic (32 atomics per batch on one address otherwise)
   if constexpr (ONE) {
@@ -1011,9 +1283,8 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   }
   // resampling probability 1 - exp(-dt_SBGK/tau) in FP64, only when a cell
   // of the batch has a Shakhov part
-  if (__any_sync(kFull, shk) && shk)
-    ct->Pres[lane] = (T)(1.0 - exp(-(double)sbgkT / (double)tauT));
-  const double ratio = (double)ratioT;
+  if (__any_sync(kFull, shk) && shk) ct->Pres[lane] = (T)cm.Pres;
+  const double ratio = (double)cm.ratio;
   __syncwarp();
   // ---- 5. DSMC sub-step.  In 3-D a cell with at most kLaneNtcMax
   // candidates runs its NTC loop on its own lane (lane i <-> cell i),
@@ -1268,34 +1539,8 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
       while (__any_sync(kFull, s >= 0)) {
         bool done = false;
         if (s >= 0) {
-          T R1, R2, R3, R4, R5;
-          if constexpr (sizeof(T) == 4) {
-            // FP32: one Philox block per attempt (block 1 + t; block 0 holds
-            // the Bernoulli draw); the two angles share a word, 16 bits each
-            const uint4 w = philox10(r.c0, r.c1, r.c2, r.c3 + 1u + (uint32_t)t, r.k0, r.k1);
-            R2 = u01f(w.x);
-            R4 = u01f(w.y);
-            R1 = (float)(2u * (w.z >> 16) + 1u) * 7.62939453125e-6f;
-            R3 = (float)(2u * (w.z & 0xFFFFu) + 1u) * 7.62939453125e-6f;
-            R5 = u01f(w.w);
-          } else {
-            T Rt[5];
-            uni_run<T, 5>(r, 1 + 5 * t, Rt);
-            R1 = Rt[0]; R2 = Rt[1]; R3 = Rt[2]; R4 = Rt[3]; R5 = Rt[4];
-          }
-          // (max: near R = 1 the approximate logarithm may round above 0)
-          const T r2 = csqrt(tmax0(-clog(R2))), r4 = csqrt(tmax0(-clog(R4)));
-          T sn3, cs3;
-          sincos2pi(R3, &sn3, &cs3);
-          const T C0 = s2RT * cos2pi(R1) * r2;
-          const T C1 = s2RT * cs3 * r4;
-          const T C2 = s2RT * sn3 * r4;
-          const T qC = q0 * C0 + q1 * C1 + q2 * C2;
-          const T CC = C0 * C0 + C1 * C1 + C2 * C2;
-          T A;
-          if constexpr (sizeof(T) == 4) A = (T)1.0 + kA * qC * (CC * iRT - (T)5.0);
-          else A = (T)1.0 + omp * qC / ((T)5.0 * RT * RT) * (CC / RT - (T)5.0);
-          const bool acc = R5 * Amax < A;
+          T C0, C1, C2;
+          const bool acc = shakhov_attempt<T>(r, t, s2RT, Amax, omp, RT, kA, iRT, q0, q1, q2, &C0, &C1, &C2);
           if (acc || t == armax - 1) {
             if (!acc) atomicAdd(&a.err[kErrAr], 1ull);
             atomicAdd(&ct->nar[c], t + 1);
@@ -1322,69 +1567,188 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   if (idx_in_velocity<T>()) {
     for (int s = lane; s < M; s += 32) cp_async<4>(&stag[s], &a.perm[p0 + s]);
   }
-  // ---- 7. conservation rescale c' = U + (c_p - U_p) sqrt(T/T_p)
+  // ---- 7. conservation rescale c' = U + (c_p - U_p) sqrt(T/T_p) of every
+  // particle of a cell with a resampled particle; U, T are the Step 3
+  // moments (the targets), U_p, T_p those after the Shakhov sub-step.
   const int nres_i = own ? ct->nres[lane] : 0;
   const unsigned rcells = __ballot_sync(kFull, nres_i > 0);
+  const bool rown = own && nres_i > 0;
+  // Step 5 squares of the post-collision velocities of a rescaled cell
+  // (mixed precision: exact from the rescale's sums; else phase 8's pass)
+  A bsq[3] = {0, 0, 0};
   if (rcells) {
-    if (own)
-      for (int k = 0; k < 4; ++k) ct->acc[k][lane] = 0;
-    __syncwarp();
-    cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, int c, T* v) {
-      v[0] = svx[s];
-      v[1] = svy[s];
-      v[2] = svz[s];
-    });
-    if (nres_i > 0) {
-      ct->Up[0][lane] = ct->acc[0][lane] / (T)Ni;
-      ct->Up[1][lane] = ct->acc[1][lane] / (T)Ni;
-      ct->Up[2][lane] = ct->acc[2][lane] / (T)Ni;
+    if constexpr (!kMixed) {
+      // the U_p pass, then T_p about U_p (the oracle's order)
+      A r1[3];
+      cell_sums<Acc, 3>(rown, offi, Ni, r1, [&](int s, int c, T* v, T* lo) {
+        v[0] = svx[s];
+        v[1] = svy[s];
+        v[2] = svz[s];
+        lo[0] = lo[1] = lo[2] = 0;
+      });
+      if (rown) {
+        ct->Up[0][lane] = (T)(r1[0] / (A)Ni);
+        ct->Up[1][lane] = (T)(r1[1] / (A)Ni);
+        ct->Up[2][lane] = (T)(r1[2] / (A)Ni);
+      }
+      __syncwarp();
+      A r2[1];
+      cell_sums<Acc, 1>(rown, offi, Ni, r2, [&](int s, int c, T* v, T* lo) {
+        const T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
+        v[0] = C0 * C0 + C1 * C1 + C2 * C2;
+        lo[0] = 0;
+      });
+      if (rown) {
+        const double Tp = (double)r2[0] / (3.0 * Pi.R * (double)(Ni - 1));
+        ct->f[lane] = Tp > 0 ? (T)sqrt((double)TA / Tp) : (T)-1;
+      }
+      __syncwarp();
+      for (int s = lane; s < M; s += 32) {
+        const int c = sseg[s];
+        if (!((rcells >> c) & 1u)) continue;
+        const T f = ct->f[c];
+        if (!(f > (T)0)) continue;
+        svx[s] = ct->U[0][c] + (svx[s] - ct->Up[0][c]) * f;
+        svy[s] = ct->U[1][c] + (svy[s] - ct->Up[1][c]) * f;
+        svz[s] = ct->U[2][c] + (svz[s] - ct->Up[2][c]) * f;
+      }
+      __syncwarp();
+    } else {
+      // FP32 state, FP64 cells: one pass of exact sums of the deviations
+      // d = c - U_h from the Step 3 mean U_h (as stored in FP32) and of
+      // their squares; two_sum gives each deviation exactly as d_h + d_l
+      // and two_prod its square, so that in FP64 U_p = U_h + sum d / N and
+      // sum (c_i - U_p,i)^2 = sum d_i^2 - N (sum d_i / N)^2 are accurate to
+      // a few 1e-13 (the deviations are thermal-sized: no cancellation).
+      // The map is then applied as c' = c f + K, K = U - U_p f, with f and
+      // K as FP32 pairs.
+      A r[6];
+      cell_sums<Acc, 6>(rown, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
+        const T x[3] = {svx[s], svy[s], svz[s]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          float dl;
+          const float dh = two_sum(x[d], -ct->U[d][c], &dl);
+          v[d] = dh;
+          lo[d] = dl;
+          float pe;
+          v[3 + d] = two_prod(dh, dh, &pe);
+          lo[3 + d] = fmaf(2.0f * dh, dl, pe);
+        }
+      });
+      if (rown) {
+        A Upd[3], Sii[3], Sp = 0;
+        const A iN = (A)1 / (A)Ni;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const A e = r[d] * iN;
+          Upd[d] = (A)ct->U[d][lane] + e;
+          Sii[d] = r[3 + d] - r[d] * e;
+          Sp += Sii[d];
+        }
+        if (Sp > 0) {
+          // f = sqrt(T / T_p), T_p = sum |c - U_p|^2 / (3 R (N - 1))
+          const A f = sqrt(TA * (A)3.0 * (A)Pi.R * (A)(Ni - 1) / Sp);
+          ct->f[lane] = (T)f;
+          ct->fl[lane] = (T)(f - (A)(T)f);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const A K = UA[d] - Upd[d] * f;
+            ct->Up[d][lane] = (T)K;
+            ct->Kl[d][lane] = (T)(K - (A)(T)K);
+            // sum (c'_d)^2 = f^2 sum (c_d - U_p,d)^2 + N U_d^2, since
+            // sum (c'_d - U_d) = f sum (c_d - U_p,d) = 0
+            bsq[d] = f * f * Sii[d] + (A)Ni * UA[d] * UA[d];
+          }
+        } else {
+          ct->f[lane] = (T)-1;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) bsq[d] = Sii[d] + (A)Ni * Upd[d] * Upd[d];
+        }
+      }
+      __syncwarp();
+      if (a.cons) {
+        // record mode: the FP64 values of the rescaled velocities (before
+        // they are rounded to FP32) summed in FP64, against the targets
+        const bool chk = rown && ct->f[lane] > (T)0;
+        double r3[4];
+        cell_sums<PlainSum<double>, 4>(chk, offi, Ni, r3, [&](int s, int c, double* v, double* lo) {
+          const T x[3] = {svx[s], svy[s], svz[s]};
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            float l;
+            const float h = affine_ff(x[d], ct->f[c], ct->fl[c], ct->Up[d][c], ct->Kl[d][c], &l);
+            v[d] = (double)h + (double)l;
+            lo[d] = 0;
+          }
+          v[3] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+          lo[3] = 0;
+        });
+        if (chk) record_conservation(a, kc, Ni, Pi, UA, TA, r3);
+      }
+      for (int s = lane; s < M; s += 32) {
+        const int c = sseg[s];
+        if (!((rcells >> c) & 1u)) continue;
+        const T f = ct->f[c];
+        if (!(f > (T)0)) continue;
+        float l;
+        float h = affine_ff(svx[s], f, ct->fl[c], ct->Up[0][c], ct->Kl[0][c], &l);
+        svx[s] = h + l;
+        h = affine_ff(svy[s], f, ct->fl[c], ct->Up[1][c], ct->Kl[1][c], &l);
+        svy[s] = h + l;
+        h = affine_ff(svz[s], f, ct->fl[c], ct->Up[2][c], ct->Kl[2][c], &l);
+        svz[s] = h + l;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    cell_sums<T, 1>(M, p0, sseg, ct->acc + 3, own, offi, Ni, [&](int s, int c, T* v) {
-      const T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
-      v[0] = C0 * C0 + C1 * C1 + C2 * C2;
-    });
-    const T rS2 = own ? ct->acc[3][lane] : (T)0;
-    if (nres_i > 0) {
-      const double Tp = (double)rS2 / (3.0 * Pi.R * (double)(Ni - 1));
-      ct->f[lane] = Tp > 0 ? (T)sqrt(m.T / Tp) : (T)-1;
+    if constexpr (sizeof(T) == 8) {
+      if (a.cons) {
+        // record mode, FP64 mode: the rescaled velocities summed in FP64
+        const bool chk = rown && ct->f[lane] > (T)0;
+        double r3[4];
+        cell_sums<PlainSum<double>, 4>(chk, offi, Ni, r3, [&](int s, int c, double* v, double* lo) {
+          v[0] = svx[s];
+          v[1] = svy[s];
+          v[2] = svz[s];
+          v[3] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+          lo[0] = lo[1] = lo[2] = lo[3] = 0;
+        });
+        if (chk) record_conservation(a, kc, Ni, Pi, UA, TA, r3);
+      }
     }
-    __syncwarp();
-    for (int s = lane; s < M; s += 32) {
-      const int c = sseg[s];
-      if (!((rcells >> c) & 1u)) continue;
-      const T f = ct->f[c];
-      if (!(f > (T)0)) continue;
-      svx[s] = ct->U[0][c] + (svx[s] - ct->Up[0][c]) * f;
-      svy[s] = ct->U[1][c] + (svy[s] - ct->Up[1][c]) * f;
-      svz[s] = ct->U[2][c] + (svz[s] - ct->Up[2][c]) * f;
-    }
-    __syncwarp();
   }
   // ---- 8. time-averaged sums (Step 5).  Both collision sub-steps conserve
   // each cell's momentum (the DSMC pair rule and the rescale to U), so the
-  // momentum sums are those of Step 3 up to rounding; only the per-component
-  // squares need a pass over the post-collision velocities.
-  const bool anys = __any_sync(kFull, sample && Ni > 0);
-  const T a0 = m0, a1 = m1, a2 = m2;
-  T b0 = 0, b1 = 0, b2 = 0;
+  // momentum sums are those of Step 3 up to rounding; the per-component
+  // squares need a pass over the post-collision velocities, except for the
+  // rescaled cells of the mixed mode (exact from the rescale's sums).
+  const bool need_sq = own && sample && Ni > 0 && !(kMixed && nres_i > 0);
+  const A a0 = m0, a1 = m1, a2 = m2;
+  A b0 = bsq[0], b1 = bsq[1], b2 = bsq[2];
   double sv[8];  // the accumulators, requested before the sums
   if (own && sample) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) sv[k] = a.samp[k * NC + kc];
   }
-  if (anys) {
-    if (own)
-      for (int k = 0; k < 3; ++k) ct->acc[k][lane] = 0;
-    __syncwarp();
-    cell_sums<T, 3>(M, p0, sseg, ct->acc, own, offi, Ni, [&](int s, int c, T* v) {
+  if (__any_sync(kFull, need_sq)) {
+    A r[3];
+    cell_sums<Acc, 3>(need_sq, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
-      v[0] = x0 * x0;
-      v[1] = x1 * x1;
-      v[2] = x2 * x2;
+      if constexpr (kMixed) {
+        v[0] = two_prod(x0, x0, &lo[0]);
+        v[1] = two_prod(x1, x1, &lo[1]);
+        v[2] = two_prod(x2, x2, &lo[2]);
+      } else {
+        v[0] = x0 * x0;
+        v[1] = x1 * x1;
+        v[2] = x2 * x2;
+        lo[0] = lo[1] = lo[2] = 0;
+      }
     });
-    if (own) {
-      b0 = ct->acc[0][lane]; b1 = ct->acc[1][lane]; b2 = ct->acc[2][lane];
+    if (need_sq) {
+      b0 = r[0];
+      b1 = r[1];
+      b2 = r[2];
     }
   }
   if (own) {
@@ -1532,24 +1896,15 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T>* 
   __syncwarp();
 }
 
-// Drops every particle of a cell that exceeds even the big-cell staging
-// area (flagged; the run reports SP_ERR_CAPACITY).
-__device__ inline void drop_cell(const StepArgs& a, int64_t k) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t s0 = a.start[k], s1 = a.start[k + 1];
-  if (lane == 0) atomicAdd(&a.err[kErrCellCap], 1ull);
-  for (uint32_t s = s0 + lane; s < s1; s += 32) a.key[s] = kSentinel;
-}
-
-template <class T, int DIM, bool ONE>
+template <class T, class A, int DIM, bool ONE>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs a, int big) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cap = big ? a.big_cap : a.cap_small;
   if (big && warp != 0) return;
-  unsigned char* base = smem + (size_t)(big ? 0 : warp) * warp_stage_bytes<T>(cap);
-  CellTab<T>* ct = (CellTab<T>*)base;
-  T* svx = (T*)(base + sizeof(CellTab<T>));
+  unsigned char* base = smem + (size_t)(big ? 0 : warp) * warp_stage_bytes<T, A>(cap);
+  CellTab<T, A>* ct = (CellTab<T, A>*)base;
+  T* svx = (T*)(base + sizeof(CellTab<T, A>));
   T* svy = svx + cap;
   T* svz = svy + cap;
   unsigned char* tail = (unsigned char*)(svz + cap);
@@ -1599,13 +1954,10 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
       k0 = (int64_t)a.big_list[it];
       it += gridDim.x;
       G = 1;
-      if ((int)(a.start[k0 + 1] - a.start[k0]) > cap) {
-        drop_cell(a, k0);
-        continue;
-      }
+      if ((int)(a.start[k0 + 1] - a.start[k0]) > kHugeCell) continue;  // k_collide_huge's cell
     }
     const long long t0 = clock64();
-    process_batch<T, DIM, ONE>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
+    process_batch<T, A, DIM, ONE>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
     if (!big) {
       // the batch's cost steers the next step's plan (no effect on results):
       // hot if it cost more than the threshold per particle, counting at
@@ -1622,6 +1974,568 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
       const uint8_t h = (thr != ~0ull && cyc > thr * Mq) ? 1 : 0;
       if (lane < G) a.hot[k0 + lane] = h;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cells above kHugeCell particles: one block of kHugeThreads threads per
+// cell (the big-cell list is shared with the one-warp launch, which takes
+// the cells up to kHugeCell).  The threshold is fixed, not the schedule's
+// staging capacity, so that which code runs a cell depends on the cell
+// alone (results do not depend on the schedule).  The block stages the
+// cell in shared memory when it fits the launch's staging area and
+// otherwise in the cell's own output slots in global memory (velocities in
+// the B velocity arrays, source indices in the key array, clash tags in the
+// first B position array; the free flight overwrites all three last), so
+// no cell size is refused.  The steps are those of process_batch for one
+// cell: stable order, gather, two-pass moments, cell_math, the NTC loop
+// with exactly the one-by-one outcome (candidates of a round evaluated as
+// soon as their pair is final, decided against the prefix maximum of
+// sigma c), Shakhov resampling, the conservation rescale, Step 5 sums and
+// the free flight.
+// ---------------------------------------------------------------------------
+template <class T, class A>
+struct __align__(16) HugeTab {
+  using acc_t = A;
+  A red[kHugeWarps][8];  // per-warp partial sums
+  A sum[8];              // the block's sums
+  T wpm[kHugeWarps];     // prefix scans across warps (NTC passes)
+  int wall[kHugeWarps];
+  T U[3], q[3], RT, s2RT, Amax, Pres, omp, dt, f, fl, Kh[3], Kl[3], smax;
+  A UA[3], TA;
+  int ncol, nacc, nres, nar;
+  double ratio;
+  int shk;
+};
+
+// Bytes of staging per particle in shared memory: velocities, source
+// index, clash tag.
+template <class T>
+__host__ __device__ constexpr size_t huge_bytes_per_particle() {
+  return 3 * sizeof(T) + 4 + 4;
+}
+// Particles staged in shared memory by the huge-cell launch.
+template <class T>
+__host__ __device__ constexpr int huge_smem_cap() {
+  return sizeof(T) == 4 ? 4096 : 2048;
+}
+template <class T, class A>
+__host__ __device__ constexpr size_t huge_smem_bytes() {
+  return (sizeof(HugeTab<T, A>) + 15) / 16 * 16 + (size_t)huge_smem_cap<T>() * huge_bytes_per_particle<T>();
+}
+
+// Block-wide sums over n slots with an order fixed by n and the block size:
+// thread t sums its contiguous share (the accumulator Acc), a butterfly
+// combines each warp, and thread 0 adds the warp totals in warp order.
+// Every thread returns the sums in out[].
+template <class Acc, int K, class TabT, class F>
+__device__ __forceinline__ void block_sums(TabT* tb, int n, typename Acc::result (&out)[K], F f) {
+  using Tm = typename Acc::term;
+  using R = typename Acc::result;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = (n + kHugeThreads - 1) / kHugeThreads;
+  const int s0 = tid * per;
+  const int s1 = s0 + per < n ? s0 + per : n;
+  Acc acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k].init();
+  for (int s = s0; s < s1; ++s) {
+    Tm v[K], lo[K];
+    f(s, v, lo);
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k].add(v[k], lo[k]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k].combine(acc[k].shfl_xor(o));
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) tb->red[w][k] = (typename TabT::acc_t)acc[k].get();
+  __syncthreads();
+  if (tid == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      R t = 0;
+      for (int i = 0; i < kHugeWarps; ++i) t += (R)tb->red[i][k];
+      tb->sum[k] = (typename TabT::acc_t)t;
+    }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = (R)tb->sum[k];
+  __syncthreads();
+}
+
+// In-place sorting network whose comparators all point one way, over n
+// slots by the whole block (slots past n act as +infinity).
+__device__ __forceinline__ void block_sort_u32(uint32_t* p, int n) {
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < n; t += kHugeThreads) {
+        const int q = (j == (k >> 1)) ? (t ^ (k - 1)) : (t ^ j);
+        if (q > t && q < n) {
+          const uint32_t x = p[t], y = p[q];
+          if (x > y) {
+            p[t] = y;
+            p[q] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <class T, class A, int DIM, bool ONE>
+__global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
+  using Acc = CellAcc<T, A>;
+  constexpr bool kMixed = mixed_prec<T, A>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  HugeTab<T, A>* tb = (HugeTab<T, A>*)smem;
+  unsigned char* stage = smem + (sizeof(HugeTab<T, A>) + 15) / 16 * 16;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t step = *a.step;
+  const uint32_t nb = *a.big_count;
+  for (uint32_t it = blockIdx.x; it < nb; it += gridDim.x) {
+    const int64_t k = (int64_t)a.big_list[it];
+    const uint32_t p0 = a.start[k];
+    const int N = (int)(a.start[k + 1] - p0);
+    if (N <= kHugeCell) continue;  // the one-warp launch's cell
+    const uint32_t inst = a.cell_inst[k];
+    const InstParams& Pi = inst_params<ONE>(a, inst);
+    const uint32_t kl = (uint32_t)(k - Pi.cell_off);
+    // ---- staging: shared memory, else the cell's own output slots
+    T *svx, *svy, *svz;
+    uint32_t* sidx;
+    int* stag;
+    if (N <= huge_smem_cap<T>()) {
+      const int cap = huge_smem_cap<T>();
+      svx = (T*)stage;
+      svy = svx + cap;
+      svz = svy + cap;
+      sidx = (uint32_t*)(svz + cap);
+      stag = (int*)(sidx + cap);
+    } else {
+      svx = (T*)a.Bvel[0] + p0;
+      svy = (T*)a.Bvel[1] + p0;
+      svz = (T*)a.Bvel[2] + p0;
+      sidx = a.key + p0;
+      stag = (int*)((T*)a.Bpos[0] + p0);
+    }
+    // ---- 1. source indices in stable (source) order
+    for (int s = tid; s < N; s += kHugeThreads) sidx[s] = a.perm[p0 + s];
+    __syncthreads();
+    if (a.stable) {
+      int uns = 0;
+      for (int s = tid; s + 1 < N; s += kHugeThreads) uns |= sidx[s] > sidx[s + 1];
+      if (__syncthreads_or(uns)) block_sort_u32(sidx, N);
+    }
+    // ---- 2. gather
+    {
+      const T* Av0 = (const T*)a.Avel[0];
+      const T* Av1 = (const T*)a.Avel[1];
+      const T* Av2 = (const T*)a.Avel[2];
+      for (int s = tid; s < N; s += kHugeThreads) {
+        const uint32_t o = sidx[s];
+        svx[s] = Av0[o];
+        svy[s] = Av1[o];
+        svz[s] = Av2[o];
+        stag[s] = 0x7FFFFFFF;
+      }
+    }
+    __syncthreads();
+    // ---- 3. moments: the mean, then the central sums about it
+    A r1[3];
+    block_sums<Acc, 3>(tb, N, r1, [&](int s, auto* v, auto* lo) {
+      v[0] = svx[s];
+      v[1] = svy[s];
+      v[2] = svz[s];
+      lo[0] = lo[1] = lo[2] = 0;
+    });
+    T sh[3], shl[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const A Ud = cdiv(r1[d], (A)N);
+      sh[d] = (T)Ud;
+      if constexpr (kMixed) shl[d] = (T)(Ud - (A)(T)Ud);
+    }
+    A r2[4];
+    block_sums<Acc, 4>(tb, N, r2, [&](int s, auto* v, auto* lo) {
+      T C0 = svx[s] - sh[0], C1 = svy[s] - sh[1], C2 = svz[s] - sh[2];
+      if constexpr (kMixed) {
+        C0 -= shl[0];
+        C1 -= shl[1];
+        C2 -= shl[2];
+      }
+      const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+      v[0] = c2;
+      v[1] = c2 * C0;
+      v[2] = c2 * C1;
+      v[3] = c2 * C2;
+      lo[0] = lo[1] = lo[2] = lo[3] = 0;
+    });
+    // ---- 4. per-cell arithmetic (thread 0)
+    const bool sample = (int64_t)step >= (int64_t)Pi.n_steady;
+    if (tid == 0) {
+      CellMath<A> cm;
+      cm.clear();
+      const T smaxT = (T)a.smax[k];
+      cell_math<T, A>(a, Pi, k, kl, N, r1[0], r1[1], r1[2], r2[0], r2[1], r2[2], r2[3], a.vol[k], smaxT,
+                      a.dt_cur[inst], step, cm);
+      if (cm.dtbits != ~0ull) atomicMin(&a.dt_min[inst], cm.dtbits);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        tb->U[d] = (T)cm.U[d];
+        tb->q[d] = (T)cm.q[d];
+        tb->UA[d] = cm.U[d];
+      }
+      tb->TA = cm.T;
+      tb->RT = (T)cm.RT;
+      tb->s2RT = (T)cm.s2RT;
+      tb->Amax = (T)cm.Amax;
+      tb->omp = (T)cm.omp;
+      tb->Pres = cm.shk ? (T)cm.Pres : (T)0;
+      tb->dt = (T)cm.dtG;
+      tb->smax = smaxT;
+      tb->ncol = (int)cm.ncol;
+      tb->nacc = 0;
+      tb->nres = 0;
+      tb->nar = 0;
+      tb->ratio = (double)cm.ratio;
+      tb->shk = cm.shk ? 1 : 0;
+    }
+    __syncthreads();
+    // ---- 5. DSMC: rounds of kHugeThreads consecutive candidates
+    const int ncol = tb->ncol;
+    if (ncol > 0) {
+      const T coef = geo<T>(Pi).sigc_coef, ex = geo<T>(Pi).sigc_exp;
+      T smx = tb->smax;
+      for (int base = 0; base < ncol; base += kHugeThreads) {
+        const int g = base + tid;
+        const bool valid = g < ncol;
+        int ci = 0, cj = 0;
+        T u3 = 0, u4 = 0, u5 = 0;
+        if (valid) {
+          const NtcDraw<T> dr = ntc_draw((T)0, step, kl, (uint32_t)g, Pi.key0, Pi.key1);
+          u3 = dr.u3;
+          u4 = dr.u4;
+          u5 = dr.u5;
+          ci = (int)(dr.u1 * (T)N);
+          if (ci > N - 1) ci = N - 1;
+          cj = (int)(dr.u2 * (T)(N - 1));
+          if (cj > N - 2) cj = N - 2;
+          if (cj >= ci) cj += 1;
+        }
+        bool pending = valid, known = false;
+        T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;
+        for (;;) {
+          if (pending) {
+            atomicMin(&stag[ci], tid);
+            atomicMin(&stag[cj], tid);
+          }
+          __syncthreads();
+          const bool ev = pending && stag[ci] == tid && stag[cj] == tid;
+          __syncthreads();
+          if (pending) {
+            stag[ci] = 0x7FFFFFFF;
+            stag[cj] = 0x7FFFFFFF;
+          }
+          if (ev && !known) {
+            ax = svx[ci]; ay = svy[ci]; az = svz[ci];
+            bx = svx[cj]; by = svy[cj]; bz = svz[cj];
+            const T g0 = ax - bx, g1 = ay - by, g2 = az - bz;
+            cr = csqrt(g0 * g0 + g1 * g1 + g2 * g2);
+            sc = coef * cpow(cr, ex);
+            known = true;
+          }
+          // inclusive prefix over the candidates: maximum of the evaluated
+          // sigma c, and whether every earlier one is evaluated
+          T pm = known ? sc : (T)-1;
+          int all = known || !valid;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(kFull, pm, o);
+            const int ya = __shfl_up_sync(kFull, all, o);
+            if (lane >= o) {
+              if (y > pm) pm = y;
+              all = all && ya;
+            }
+          }
+          if (lane == 31) {
+            tb->wpm[w] = pm;
+            tb->wall[w] = all;
+          }
+          __syncthreads();
+          for (int i = 0; i < w; ++i) {
+            if (tb->wpm[i] > pm) pm = tb->wpm[i];
+            all = all && tb->wall[i];
+          }
+          const T smL = pm > smx ? pm : smx;
+          bool pass;
+          if constexpr (sizeof(T) == 4) pass = ev && u3 * smL < sc;
+          else pass = ev && u3 < sc / smL;
+          const bool decided = ev && (all || !pass);
+          if (decided && pass) {
+            atomicAdd(&tb->nacc, 1);
+            const T cchi = (T)2.0 * u4 - (T)1.0;
+            const T schi = csqrt((T)1.0 - cchi * cchi);
+            T sn, cs;
+            sincos2pi(u5, &sn, &cs);
+            const T w0 = cchi, w1 = schi * cs, w2 = schi * sn;
+            const T q0 = ax + bx, q1 = ay + by, q2 = az + bz;
+            svx[ci] = (T)0.5 * (q0 - cr * w0);
+            svy[ci] = (T)0.5 * (q1 - cr * w1);
+            svz[ci] = (T)0.5 * (q2 - cr * w2);
+            svx[cj] = (T)0.5 * (q0 + cr * w0);
+            svy[cj] = (T)0.5 * (q1 + cr * w1);
+            svz[cj] = (T)0.5 * (q2 + cr * w2);
+          }
+          if (decided) pending = false;
+          if (!__syncthreads_or(pending)) break;
+        }
+        // the round's candidates raise (sigma c)_max
+        T mx = sc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T y = __shfl_xor_sync(kFull, mx, o);
+          if (y > mx) mx = y;
+        }
+        if (lane == 0) tb->wpm[w] = mx;
+        __syncthreads();
+        for (int i = 0; i < kHugeWarps; ++i)
+          if (tb->wpm[i] > smx) smx = tb->wpm[i];
+        __syncthreads();
+      }
+      if (tid == 0) a.smax[k] = (double)smx;
+    }
+    // ---- 6. Shakhov resampling, slot by slot
+    if (tb->shk) {
+      const T Pres = tb->Pres;
+      const T RT = tb->RT, s2RT = tb->s2RT, Amax = tb->Amax, omp = tb->omp;
+      const T q0 = tb->q[0], q1 = tb->q[1], q2 = tb->q[2];
+      T kA = 0, iRT = 0;
+      if constexpr (sizeof(T) == 4) {
+        kA = omp / ((T)5.0 * RT * RT);
+        iRT = (T)1.0 / RT;
+      }
+      int nres = 0, nar = 0;
+      for (int s = tid; s < N; s += kHugeThreads) {
+        const Uni<T> r0(step, kl, (uint32_t)s, kPurpShk << 24, Pi.key0, Pi.key1);
+        Uni<T> r = r0;
+        if (!(r.get(0) < Pres)) continue;
+        ++nres;
+        if (a.resamp) a.resamp[p0 + s] = 1;
+        for (int t = 0;; ++t) {
+          T C0, C1, C2;
+          const bool acc = shakhov_attempt<T>(r0, t, s2RT, Amax, omp, RT, kA, iRT, q0, q1, q2, &C0, &C1, &C2);
+          if (acc || t == Pi.ar_max - 1) {
+            if (!acc) atomicAdd(&a.err[kErrAr], 1ull);
+            nar += t + 1;
+            svx[s] = tb->U[0] + C0;
+            svy[s] = tb->U[1] + C1;
+            svz[s] = tb->U[2] + C2;
+            break;
+          }
+        }
+      }
+      if (nres) {
+        atomicAdd(&tb->nres, nres);
+        atomicAdd(&tb->nar, nar);
+      }
+    }
+    __syncthreads();
+    // ---- 7. conservation rescale (as process_batch)
+    const int nres = tb->nres;
+    A bsq[3] = {0, 0, 0};
+    bool bsq_ok = false;
+    if (nres > 0) {
+      if constexpr (!kMixed) {
+        A u[3];
+        block_sums<Acc, 3>(tb, N, u, [&](int s, auto* v, auto* lo) {
+          v[0] = svx[s];
+          v[1] = svy[s];
+          v[2] = svz[s];
+          lo[0] = lo[1] = lo[2] = 0;
+        });
+        const T Up0 = (T)(u[0] / (A)N), Up1 = (T)(u[1] / (A)N), Up2 = (T)(u[2] / (A)N);
+        A e[1];
+        block_sums<Acc, 1>(tb, N, e, [&](int s, auto* v, auto* lo) {
+          const T C0 = svx[s] - Up0, C1 = svy[s] - Up1, C2 = svz[s] - Up2;
+          v[0] = C0 * C0 + C1 * C1 + C2 * C2;
+          lo[0] = 0;
+        });
+        const double Tp = (double)e[0] / (3.0 * Pi.R * (double)(N - 1));
+        const T f = Tp > 0 ? (T)sqrt((double)tb->TA / Tp) : (T)-1;
+        if (f > (T)0)
+          for (int s = tid; s < N; s += kHugeThreads) {
+            svx[s] = tb->U[0] + (svx[s] - Up0) * f;
+            svy[s] = tb->U[1] + (svy[s] - Up1) * f;
+            svz[s] = tb->U[2] + (svz[s] - Up2) * f;
+          }
+        __syncthreads();
+        if constexpr (sizeof(T) == 8) {
+          if (a.cons && f > (T)0) {
+            double r3[4];
+            block_sums<PlainSum<double>, 4>(tb, N, r3, [&](int s, double* v, double* lo) {
+              v[0] = svx[s];
+              v[1] = svy[s];
+              v[2] = svz[s];
+              v[3] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+              lo[0] = lo[1] = lo[2] = lo[3] = 0;
+            });
+            if (tid == 0) record_conservation(a, k, N, Pi, tb->UA, tb->TA, r3);
+          }
+        }
+      } else {
+        A r[6];
+        const T uh0 = tb->U[0], uh1 = tb->U[1], uh2 = tb->U[2];
+        block_sums<Acc, 6>(tb, N, r, [&](int s, auto* v, auto* lo) {
+          const T x[3] = {svx[s], svy[s], svz[s]};
+          const T u[3] = {uh0, uh1, uh2};
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            float dl;
+            const float dh = two_sum(x[d], -u[d], &dl);
+            v[d] = dh;
+            lo[d] = dl;
+            float pe;
+            v[3 + d] = two_prod(dh, dh, &pe);
+            lo[3 + d] = fmaf(2.0f * dh, dl, pe);
+          }
+        });
+        if (tid == 0) {
+          A Upd[3], Sii[3], Sp = 0;
+          const A iN = (A)1 / (A)N;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const A e = r[d] * iN;
+            Upd[d] = (A)tb->U[d] + e;
+            Sii[d] = r[3 + d] - r[d] * e;
+            Sp += Sii[d];
+          }
+          tb->f = (T)-1;
+          if (Sp > 0) {
+            const A f = sqrt(tb->TA * (A)3.0 * (A)Pi.R * (A)(N - 1) / Sp);
+            tb->f = (T)f;
+            tb->fl = (T)(f - (A)(T)f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              const A K = tb->UA[d] - Upd[d] * f;
+              tb->Kh[d] = (T)K;
+              tb->Kl[d] = (T)(K - (A)(T)K);
+              tb->red[0][d] = f * f * Sii[d] + (A)N * tb->UA[d] * tb->UA[d];
+            }
+          } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) tb->red[0][d] = Sii[d] + (A)N * Upd[d] * Upd[d];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int d = 0; d < 3; ++d) bsq[d] = tb->red[0][d];
+        bsq_ok = true;
+        const T f = tb->f;
+        __syncthreads();
+        if (f > (T)0) {
+          const T fl = tb->fl;
+          if (a.cons) {
+            double r3[4];
+            block_sums<PlainSum<double>, 4>(tb, N, r3, [&](int s, double* v, double* lo) {
+              const T x[3] = {svx[s], svy[s], svz[s]};
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                float l;
+                const float h = affine_ff(x[d], f, fl, tb->Kh[d], tb->Kl[d], &l);
+                v[d] = (double)h + (double)l;
+                lo[d] = 0;
+              }
+              v[3] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+              lo[3] = 0;
+            });
+            if (tid == 0) record_conservation(a, k, N, Pi, tb->UA, tb->TA, r3);
+          }
+          for (int s = tid; s < N; s += kHugeThreads) {
+            float l;
+            float h = affine_ff(svx[s], f, fl, tb->Kh[0], tb->Kl[0], &l);
+            svx[s] = h + l;
+            h = affine_ff(svy[s], f, fl, tb->Kh[1], tb->Kl[1], &l);
+            svy[s] = h + l;
+            h = affine_ff(svz[s], f, fl, tb->Kh[2], tb->Kl[2], &l);
+            svz[s] = h + l;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // ---- 8. Step 5 sums
+    if (sample) {
+      if (!bsq_ok) {
+        block_sums<Acc, 3>(tb, N, bsq, [&](int s, auto* v, auto* lo) {
+          const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
+          if constexpr (kMixed) {
+            v[0] = two_prod(x0, x0, &lo[0]);
+            v[1] = two_prod(x1, x1, &lo[1]);
+            v[2] = two_prod(x2, x2, &lo[2]);
+          } else {
+            v[0] = x0 * x0;
+            v[1] = x1 * x1;
+            v[2] = x2 * x2;
+            lo[0] = lo[1] = lo[2] = 0;
+          }
+        });
+      }
+      if (tid == 0) {
+        double* S = a.samp;
+        const int64_t NC = a.NC;
+        S[0 * NC + k] += (double)N;
+        S[1 * NC + k] += (double)r1[0];
+        S[2 * NC + k] += (double)r1[1];
+        S[3 * NC + k] += (double)r1[2];
+        S[4 * NC + k] += (double)bsq[0];
+        S[5 * NC + k] += (double)bsq[1];
+        S[6 * NC + k] += (double)bsq[2];
+        S[7 * NC + k] += tb->ratio;
+      }
+    }
+    if (tid == 0 && a.rec) {
+      const int64_t NC = a.NC;
+      a.rec[0 * NC + k] = tb->ncol;
+      a.rec[1 * NC + k] = tb->nacc;
+      a.rec[2 * NC + k] = tb->nres;
+      a.rec[3 * NC + k] = tb->nar;
+    }
+    // ---- 9. free flight of the next interval, key and histogram (every
+    // thread reads its slot's source index and velocity before it writes
+    // the slot's key, position and velocity)
+    {
+      T* Bx[3] = {(T*)a.Bpos[0], (T*)a.Bpos[1], (T*)a.Bpos[2]};
+      T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
+      const T dt = tb->dt;
+      __syncthreads();  // the clash tags (in the first B position array) are dead
+      for (int sb = 0; sb < N; sb += kHugeThreads) {
+        const int s = sb + tid;
+        uint32_t key = kSentinel;
+        if (s < N) {
+          const uint32_t o = sidx[s];
+          T x[3] = {0, 0, 0};
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) x[d] = ((const T*)a.Apos[d])[o];
+          T v[3] = {svx[s], svy[s], svz[s]};
+          const bool gone = move_particle<T, DIM>(Pi, a.surf, x, v, dt, step, kPurpWall, kl, (uint32_t)s, 0u, a.err);
+          if (!gone) key = (uint32_t)Pi.cell_off + cell_of<T, DIM>(Pi, x);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) Bx[d][p0 + s] = x[d];
+          Bv[0][p0 + s] = v[0];
+          Bv[1][p0 + s] = v[1];
+          Bv[2][p0 + s] = v[2];
+          a.key[p0 + s] = key;
+        }
+        warp_count(key, a.count);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1733,9 +2647,13 @@ __global__ void k_inject(InjectArgs a, int pass) {
 // ---------------------------------------------------------------------------
 // Observability / initialisation kernels
 // ---------------------------------------------------------------------------
-// Moments of the current state for cells [c0, c1) (warp per cell, unsorted
-// sums).  With out == nullptr only dt_min is updated.
-template <class T>
+// Moments of the current state for cells [c0, c1) (warp per cell, in the
+// cells' current slot order).  With out == nullptr only dt_min is updated.
+// The sums run in A (FP64 in the FP64 and FP32 modes: each velocity is
+// widened and added in FP64 -- this kernel runs only at upload and for
+// sp_moments, so the FP64 rate does not matter; FP32 in the all-FP32 mode),
+// the per-cell scalars in FP64.
+template <class T, class A>
 __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
   // sums warp per cell, 32 cells in a row; then the FP64 scalars lane per
   // cell (lane j <-> cell kb + j), so each FP64 instruction serves 32 cells
@@ -1749,7 +2667,7 @@ __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
        kb += 32 * nw) {
     int myN = 0;
     double myU[3] = {0, 0, 0};
-    T myS2 = 0, myS3[3] = {0, 0, 0};
+    A myS2 = 0, myS3[3] = {0, 0, 0};
     const int nj = (int)((c1 - kb) < 32 ? (c1 - kb) : 32);
     for (int j = 0; j < nj; ++j) {
       const int64_t k = kb + j;
@@ -1757,21 +2675,21 @@ __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
       const int N = (int)(a.start[k + 1] - s0);
       double U[3] = {0, 0, 0};
       {
-        T s0x = 0, s1x = 0, s2x = 0;
+        A s0x = 0, s1x = 0, s2x = 0;
         for (int s = lane; s < N; s += 32) {
           const uint32_t o = a.perm[s0 + s];
-          s0x += Av0[o]; s1x += Av1[o]; s2x += Av2[o];
+          s0x += (A)Av0[o]; s1x += (A)Av1[o]; s2x += (A)Av2[o];
         }
         s0x = warp_sum(s0x); s1x = warp_sum(s1x); s2x = warp_sum(s2x);
         if (N > 0) { U[0] = (double)s0x / N; U[1] = (double)s1x / N; U[2] = (double)s2x / N; }
       }
-      T S2 = 0, S3x = 0, S3y = 0, S3z = 0;
+      A S2 = 0, S3x = 0, S3y = 0, S3z = 0;
       if (N >= 2) {
-        const T Ux = (T)U[0], Uy = (T)U[1], Uz = (T)U[2];
+        const A Ux = (A)U[0], Uy = (A)U[1], Uz = (A)U[2];
         for (int s = lane; s < N; s += 32) {
           const uint32_t o = a.perm[s0 + s];
-          const T C0 = Av0[o] - Ux, C1 = Av1[o] - Uy, C2 = Av2[o] - Uz;
-          const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+          const A C0 = (A)Av0[o] - Ux, C1 = (A)Av1[o] - Uy, C2 = (A)Av2[o] - Uz;
+          const A c2 = C0 * C0 + C1 * C1 + C2 * C2;
           S2 += c2; S3x += c2 * C0; S3y += c2 * C1; S3z += c2 * C2;
         }
         S2 = warp_sum(S2); S3x = warp_sum(S3x); S3y = warp_sum(S3y); S3z = warp_sum(S3z);

@@ -15,6 +15,10 @@ constexpr int kMaxWarpsPerBlock = 8;         // collide kernel block size limit
 constexpr int kCapSmall = 512;               // default per-warp staging capacity (particles)
 constexpr int kWarpsDefault = 4;             // default warps per block
 constexpr int kMaxDynSmem = 232448;          // 227 KB per block (opt-in maximum)
+// Cells above kHugeCell particles are collided by one block each (the
+// huge-cell launch); the other launches stage at most kHugeCell particles
+// per warp, so which code collides a cell depends on the cell alone.
+constexpr int kHugeCell = 1024;
 
 // Philox stream purposes (high byte of counter word 3).
 constexpr uint32_t kPurpNtc = 1, kPurpShk = 2, kPurpWall = 3, kPurpInj = 4, kPurpInjWall = 5;
@@ -57,6 +61,12 @@ struct InstParams {
   int n_surf;        // surface elements of the body (0: no tallies)
   int64_t surf_off;  // first element in the context's tally array
   double FnM;        // F_N m: weight of one hit in the tallies
+  // constants of the FP64 per-cell arithmetic of the FP32 modes
+  double inv3R;      // 1 / (3 R)
+  double sqrt_gamma; // sqrt(gamma)
+  double tau_k;      // tau = tau_k T^(omega - 1) / n, tau_k = mu_ref T_ref^-omega / (m R)
+  double inv_Lmin;   // 1 / L_min
+  double inv_Fn;     // 1 / F_N
   Geo<double> g64;
   Geo<float> g32;
 };
@@ -89,6 +99,7 @@ struct StepArgs {
   double* rem;          // [NC] carried NTC remainder
   double* samp;         // [8][NC]
   int32_t* rec;         // [4][NC] or null
+  double* cons;         // [6][NC] rescale conservation record (record mode) or null
   uint8_t* resamp;      // [cap] or null
   const InstParams* P;  // [n_inst]
   const double* dt_cur; // [n_inst]
@@ -130,28 +141,29 @@ struct InjectArgs {
   double* surf;
 };
 
-// Launch wrappers, one set per precision (sp_kern_f64.cu, sp_kern_f32.cu).
-#define SP_DECLARE_LAUNCHERS(tag)                                                                  \
-  void launch_collide_##tag(int dim, const StepArgs& a, bool big, int grid, int warps,           \
-                            cudaStream_t s);                                                     \
-  void launch_inject_##tag(int dim, const InjectArgs& a, int pass, cudaStream_t s);               \
-  void launch_moments_##tag(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s); \
-  void launch_keys_##tag(int dim, const void* const pos[3], int64_t M, const uint32_t* part_inst, \
-                         const InstParams* P, uint32_t* key, uint32_t* count, cudaStream_t s);   \
-  void launch_gather_##tag(int dim, const void* const Apos[3], const void* const Avel[3],        \
-                           const uint32_t* perm, int64_t s0, int64_t n, double* out_pos,          \
-                           double* out_vel, cudaStream_t s);                                      \
-  void launch_stage_in32_##tag(int dim, const float* pos, const float* vel, int64_t n,              \
-                               void* const dpos[3], void* const dvel[3], int64_t off,            \
-                               uint32_t* part_inst, uint32_t inst, cudaStream_t s);              \
-  void launch_stage_in_##tag(int dim, const double* pos, const double* vel, int64_t n,             \
-                             void* const dpos[3], void* const dvel[3], int64_t off,              \
-                             uint32_t* part_inst, uint32_t inst, cudaStream_t s);                \
-  int collide_blocks_per_sm_##tag(int dim, int warps, int cap, bool one);                                 \
-  size_t collide_smem_##tag(int warps, int cap);                                                \
-  cudaError_t configure_##tag(int big_cap);
-SP_DECLARE_LAUNCHERS(f64)
-SP_DECLARE_LAUNCHERS(f32)
+// Launch wrappers of one precision mode (sp_kern.cu, compiled once per mode:
+// f64 = FP64 state and arithmetic; f32 = FP32 state, FP64 per-cell sums and
+// arithmetic; f32c = FP32 state and FP32 per-cell sums and arithmetic).
+struct KernelSet {
+  void (*collide)(int dim, const StepArgs& a, bool big, int grid, int warps, cudaStream_t s);
+  void (*collide_huge)(int dim, const StepArgs& a, int grid, cudaStream_t s);
+  size_t (*collide_smem)(int warps, int cap);
+  int (*collide_blocks_per_sm)(int dim, int warps, int cap, bool one);
+  cudaError_t (*configure)();
+  void (*inject)(int dim, const InjectArgs& a, int pass, cudaStream_t s);
+  void (*moments)(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s);
+  void (*keys)(int dim, const void* const pos[3], int64_t M, const uint32_t* part_inst, const InstParams* P,
+               uint32_t* key, uint32_t* count, cudaStream_t s);
+  void (*gather)(int dim, const void* const Apos[3], const void* const Avel[3], const uint32_t* perm,
+                 int64_t s0, int64_t n, double* out_pos, double* out_vel, cudaStream_t s);
+  void (*stage_in)(int dim, const double* pos, const double* vel, int64_t n, void* const dpos[3],
+                   void* const dvel[3], int64_t off, uint32_t* part_inst, uint32_t inst, cudaStream_t s);
+  void (*stage_in32)(int dim, const float* pos, const float* vel, int64_t n, void* const dpos[3],
+                     void* const dvel[3], int64_t off, uint32_t* part_inst, uint32_t inst, cudaStream_t s);
+};
+const KernelSet& kernels_f64();
+const KernelSet& kernels_f32();
+const KernelSet& kernels_f32c();
 
 // Precision-independent kernels (sp_common.cu).
 void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s);

@@ -463,6 +463,25 @@ def homogeneous_box(N, Kn, seed=1, Tx=2.0, Tyz=1.0, skew=0.05, ppc=56.25, n_stea
     return cfg, pos, vel
 
 
+def huge_cells(counts=(20000, 6000, 1500, 300), seed=5):
+    """A 1-D tube of len(counts) unit cells holding the given particle
+    counts (each a bi-Maxwellian with a heat-flux skew), specular ends, the
+    gas dense enough in the first cell that both collision sub-steps run.
+    Returns (cfg, pos, vel)."""
+    nc = len(counts)
+    cfg = base_config(1, [nc], [0.0], [float(nc)])
+    T = (2.0 + 2 * 1.0) / 3.0
+    d = d_for_mfp(0.05, 1.0, 1.0, T, 0.5)
+    cfg.update(omega=0.5, T_ref=1.0, d_ref=d, mu_ref=vhs_mu_ref(1.0, d, 1.0, 0.5, kB=1.0),
+               Fn=1.0 / counts[0], sigc_T0=T, seed=seed, n_steady=1)
+    ps, vs = [], []
+    for k, N in enumerate(counts):
+        p, v = homogeneous_particles(cfg, N, Tx=2.0, skew=0.1, seed=seed + k)
+        ps.append(p + k)
+        vs.append(v)
+    return cfg, np.ascontiguousarray(np.concatenate(ps, axis=1)), np.ascontiguousarray(np.concatenate(vs, axis=1))
+
+
 def batch(n_inst=256, seed=1, Nmin=1e3, Nmax=5e5, Kn_min=1e-4, Kn_max=1.0, n_steady=10**9):
     """Ensemble of independent 1-D instances: even i a Sod tube with
     nx = round(2 N_i / 112.5) cells, odd i a spatially homogeneous

@@ -57,12 +57,13 @@ def _batch_fields(sim, cfg, nbatch, per, R):
     return out
 
 
-def _compare(sp, cfg, pos, vel, warm, nbatch, per, min_frac=0.95, reproducible=True, min_n=0.0):
+def _compare(sp, cfg, pos, vel, warm, nbatch, per, min_frac=0.95, reproducible=True, min_n=0.0, prec32=None):
     res = {}
-    for prec in (sp.FP64, sp.FP32):
+    prec32 = sp.FP32 if prec32 is None else prec32
+    for prec in (sp.FP64, prec32):
         c = dict(cfg, n_steady=warm)
         s = sp.Sim(c, prec, capacity=4 * vel.shape[1] + 10000)
-        if prec == sp.FP32 and not reproducible:
+        if prec != sp.FP64 and not reproducible:
             s.set_reproducible(False)
         s.set_particles(0, pos, vel)
         s.step(warm)
@@ -76,7 +77,7 @@ def _compare(sp, cfg, pos, vel, warm, nbatch, per, min_frac=0.95, reproducible=T
     dense = np.array([x[0] for x in res[sp.FP64]]).mean(axis=0) >= min_n
     for fi, name in enumerate(("n", "ux", "T")):
         a = np.array([x[fi] for x in res[sp.FP64]])
-        b = np.array([x[fi] for x in res[sp.FP32]])
+        b = np.array([x[fi] for x in res[prec32]])
         ok = np.all(np.isfinite(a), axis=0) & np.all(np.isfinite(b), axis=0) & dense
         ma, mb = a[:, ok].mean(axis=0), b[:, ok].mean(axis=0)
         se = np.sqrt(a[:, ok].var(axis=0, ddof=1) / len(a) + b[:, ok].var(axis=0, ddof=1) / len(b))
@@ -89,13 +90,16 @@ def _compare(sp, cfg, pos, vel, warm, nbatch, per, min_frac=0.95, reproducible=T
     return stats
 
 
+@pytest.mark.parametrize("mode", ["FP32", "FP32_CELL32"])
 @pytest.mark.parametrize("reproducible", [True, False])
-def test_fp32_channel_time_averages_match_fp64(sp, reproducible):
-    """Also with the scatter's arrival order kept inside cells (FP32 only):
-    the statistics must not change."""
+def test_fp32_channel_time_averages_match_fp64(sp, reproducible, mode):
+    """Both FP32-state modes (FP64 per-cell arithmetic, and the opt-in
+    all-FP32 variant), also with the scatter's arrival order kept inside
+    cells: the statistics must not change."""
     cfg, regions = W.box2d(nx=24, ny=12, ppc=200.0, Kn=0.02)
     pos, vel = W.fill_regions(cfg, regions, 3)
-    _compare(sp, cfg, pos, vel, warm=300, nbatch=20, per=100, reproducible=reproducible)
+    _compare(sp, cfg, pos, vel, warm=300, nbatch=20, per=100, reproducible=reproducible,
+             prec32=getattr(sp, mode))
 
 
 def test_fp32_sod_ensemble_profile_matches_fp64(sp):
@@ -134,11 +138,15 @@ def test_fp32_sod_ensemble_profile_matches_fp64(sp):
         assert within >= 0.95, (name, within)
 
 
-def test_fp32_closed_box_conserves_energy(sp):
+@pytest.mark.parametrize("mode", ["FP32", "FP32_CELL32"])
+def test_fp32_closed_box_conserves_energy(sp, mode):
+    """Energy of the FP32 state over 50 steps of a closed homogeneous cell
+    (the FP32 store of every collided velocity rounds it: drift at the FP32
+    level only)."""
     N = 3000
     cfg = W.homogeneous(N=N, Kn=0.05, omega=0.81)
     pos, vel = W.homogeneous_particles(cfg, N, Tx=2.0, skew=0.1, seed=3)
-    s = sp.Sim(cfg, sp.FP32, capacity=2 * N)
+    s = sp.Sim(cfg, getattr(sp, mode), capacity=2 * N)
     s.set_particles(0, pos, vel)
     e0 = (vel.astype(np.float32).astype(np.float64) ** 2).sum()
     for _ in range(10):
