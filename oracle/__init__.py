@@ -35,6 +35,7 @@ class OrConfig(C.Structure):
         ("sigc_T0", C.c_double), ("n_steady", C.c_int32), ("seed", C.c_uint64),
         ("mode", C.c_int32), ("ar_max", C.c_int32), ("n_surf", C.c_int32),
         ("win_lo", (C.c_double * 2) * 6), ("win_hi", (C.c_double * 2) * 6), ("ntc_carry", C.c_int32),
+        ("subcells", C.c_int32),
     ]
 
 
@@ -64,6 +65,8 @@ def lib():
         L.or_step_index.restype = C.c_int64
         L.or_get_totals.argtypes = [P, P]
         L.or_set_threads.argtypes = [P, C.c_int]
+        L.or_select_pair.argtypes = [C.c_int64, P, C.c_double, C.c_double, P, P]
+        L.or_subcell_order.argtypes = [C.POINTER(OrConfig), C.c_int64, P, C.c_int64, P, P]
         L.or_get_threads.argtypes = [P]
         L.or_get_surface.argtypes = [P, P, P]
         L.or_free.argtypes = [P]
@@ -118,6 +121,7 @@ def make_config(cfg: dict):
             s.win_lo[f][i] = cfg.get("win_lo", [[0.0, 0.0]] * 6)[f][i]
             s.win_hi[f][i] = cfg.get("win_hi", [[0.0, 0.0]] * 6)[f][i]
     s.ntc_carry = int(cfg.get("ntc_carry", 0))
+    s.subcells = int(cfg.get("subcells", 0))
     return s, keep
 
 
@@ -136,6 +140,31 @@ def u01(a, b):
 def sigc(cfg, cr):
     s, _ = make_config(cfg)
     return lib().or_sigc(C.byref(s), cr)
+
+
+def select_pair(N, u1, u2, soff=None):
+    """The (i, j) slots of one NTC candidate from its uniforms u1, u2."""
+    i = np.zeros(1, dtype=np.int64)
+    j = np.zeros(1, dtype=np.int64)
+    so = None if soff is None else np.ascontiguousarray(soff, dtype=np.int64)
+    rc = lib().or_select_pair(int(N), _ptr(so), float(u1), float(u2), _ptr(i), _ptr(j))
+    if rc != 0:
+        raise ValueError("or_select_pair failed")
+    return int(i[0]), int(j[0])
+
+
+def subcell_order(cfg, cell, pos):
+    """(order, soff): the stable order by sub-cell of particles pos [dim][N]
+    of cell `cell` and the sub-cell offsets (cfg["subcells"] >= 2)."""
+    s, keep = make_config(cfg)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    N = pos.shape[1]
+    order = np.zeros(max(N, 1), dtype=np.int64)
+    soff = np.zeros(9, dtype=np.int64)
+    rc = lib().or_subcell_order(C.byref(s), int(cell), _ptr(pos), N, _ptr(order), _ptr(soff))
+    if rc != 0:
+        raise ValueError("or_subcell_order failed")
+    return order[:N], soff
 
 
 def collide_cell(cfg, step, cell, volume, dt_G, sigc_max, vel):

@@ -227,11 +227,88 @@ static double ratio_of(const or_config* g, const mom* mm) {
 }
 
 /* ---------------------------------------------------------------------
+ * Bird's sub-cells (option).  The sub-cell of a particle of cell k: on each
+ * axis the cell coordinate u = (x - lo) n / L (the expression of cell_of),
+ * its fractional part within the cell split into s equal parts.  Before its
+ * step, a cell's particles are put in a stable order by sub-cell, so that
+ * every sub-cell is a run of consecutive slots: soff[t] .. soff[t+1].
+ * ------------------------------------------------------------------- */
+static int nsub_of(const or_config* g) {
+  int ns = g->subcells > 1 ? g->subcells : 1, m = 1;
+  for (int d = 0; d < g->dim; ++d) m *= ns;
+  return m;
+}
+
+static int subcell_of(const or_ctx* c, int64_t k, const double* x) {
+  const or_config* g = &c->cfg;
+  const int ns = g->subcells;
+  int64_t kk = k;
+  int sub = 0, mul = 1;
+  for (int d = 0; d < g->dim; ++d) {
+    int64_t id = kk % g->n[d];
+    kk /= g->n[d];
+    double u = (x[d] - g->lo[d]) * c->inv_d[d];
+    double f = floor((u - (double)id) * (double)ns);
+    int t = (int)f;
+    if (f < 0) t = 0;
+    if (t > ns - 1) t = ns - 1;
+    sub += mul * t;
+    mul *= ns;
+  }
+  return sub;
+}
+
+/* The pair of an NTC candidate (Sec. II.A: "selected randomly within the
+ * cell"): i uniform over the N slots, j uniform over the other N - 1; with
+ * sub-cells, j uniform over the other particles of i's sub-cell (slots
+ * soff[t] .. soff[t+1]) when it holds one. */
+static void select_pair(int64_t N, const int64_t* soff, double u1, double u2, int64_t* pi, int64_t* pj) {
+  int64_t i = (int64_t)(u1 * (double)N);
+  if (i > N - 1) i = N - 1;
+  int64_t a0 = 0, b0 = N;
+  if (soff) {
+    int t = 0;
+    while (soff[t + 1] <= i) ++t;
+    if (soff[t + 1] - soff[t] >= 2) {
+      a0 = soff[t];
+      b0 = soff[t + 1];
+    }
+  }
+  int64_t j = a0 + (int64_t)(u2 * (double)(b0 - a0 - 1));
+  if (j > b0 - 2) j = b0 - 2;
+  if (j >= i) j += 1;
+  *pi = i;
+  *pj = j;
+}
+
+static void order_by_subcell(const or_ctx* c, int64_t k, part* ps, int64_t N, int64_t* soff) {
+  const int m = nsub_of(&c->cfg);
+  int64_t cnt[9] = {0};
+  if (N == 0) { /* an empty cell: nothing to order (ps is the next cell's) */
+    for (int t = 0; t <= m; ++t) soff[t] = 0;
+    return;
+  }
+  int* sub = (int*)malloc(sizeof(int) * N);
+  part* tmp = (part*)malloc(sizeof(part) * N);
+  for (int64_t i = 0; i < N; ++i) {
+    sub[i] = subcell_of(c, k, ps[i].x);
+    cnt[sub[i] + 1] += 1;
+  }
+  for (int t = 0; t < m; ++t) cnt[t + 1] += cnt[t];
+  for (int t = 0; t <= m; ++t) soff[t] = cnt[t];
+  for (int64_t i = 0; i < N; ++i) tmp[cnt[sub[i]]++] = ps[i];
+  memcpy(ps, tmp, sizeof(part) * N);
+  free(tmp);
+  free(sub);
+}
+
+/* ---------------------------------------------------------------------
  * Step 4 on one cell: NTC DSMC part, Shakhov part, rescale.
  * ps[0..N) are the cell's particles in slot order; k is the cell's index.
  * ------------------------------------------------------------------- */
 static void collide_cell(or_ctx* c, int64_t k, double V, part* ps, int64_t N, const mom* mm,
-                         double dtG, double* smax, double* rem, int64_t rec[4], uint8_t* res) {
+                         double dtG, double* smax, double* rem, int64_t rec[4], uint8_t* res,
+                         const int64_t* soff) {
   const or_config* g = &c->cfg;
   rec[0] = rec[1] = rec[2] = rec[3] = 0;
   if (N < 2 || !(mm->T > 0)) return;
@@ -259,11 +336,8 @@ static void collide_cell(or_ctx* c, int64_t k, double V, part* ps, int64_t N, co
       double u3 = uq(c, kc, (uint32_t)kk, PURP_NTC, 0, 2);
       double u4 = uq(c, kc, (uint32_t)kk, PURP_NTC, 0, 3);
       double u5 = uq(c, kc, (uint32_t)kk, PURP_NTC, 0, 4);
-      int64_t i = (int64_t)(u1 * (double)N);
-      if (i > N - 1) i = N - 1;
-      int64_t j = (int64_t)(u2 * (double)(N - 1));
-      if (j > N - 2) j = N - 2;
-      if (j >= i) j += 1;
+      int64_t i, j;
+      select_pair(N, soff, u1, u2, &i, &j);
       double* a = ps[i].v;
       double* b = ps[j].v;
       double g0 = a[0] - b[0], g1 = a[1] - b[1], g2 = a[2] - b[2];
@@ -513,6 +587,10 @@ int or_init(const or_config* cfg, or_ctx** out) {
   or_ctx* c = (or_ctx*)calloc(1, sizeof *c);
   c->cfg = *cfg;
   c->nthreads = 1;
+  if (nsub_of(cfg) > 8) {
+    free(c);
+    return OR_ERR_ARG;
+  }
   or_config* g = &c->cfg;
   for (int d = 0; d < 3; ++d) {
     if (d >= g->dim) { g->n[d] = 1; }
@@ -747,11 +825,17 @@ int or_step(or_ctx* c, int nsteps) {
 #endif
     for (int64_t k = 0; k < c->ncells; ++k) {
       int64_t s0 = c->start[k], N = c->start[k + 1] - s0;
+      int64_t soff[9];
+      const int64_t* so = NULL;
+      if (g->subcells > 1) {
+        order_by_subcell(c, k, c->p + s0, N, soff);
+        so = soff;
+      }
       mom mm;
       moments_of(c, k, c->p + s0, N, &mm);
       if (N >= 2 && mm.dtc < mn) mn = mm.dtc;
       int64_t rec[4];
-      collide_cell(c, k, c->vol[k], c->p + s0, N, &mm, dtG, &c->smax[k], &c->rem[k], rec, c->resamp + s0);
+      collide_cell(c, k, c->vol[k], c->p + s0, N, &mm, dtG, &c->smax[k], &c->rem[k], rec, c->resamp + s0, so);
       for (int i = 0; i < 4; ++i) c->rec[i * c->ncells + k] = rec[i];
       if (sample) {
         double* S = c->samp;
@@ -894,6 +978,28 @@ int or_set_threads(or_ctx* c, int n) {
 
 int or_get_threads(const or_ctx* c) { return c ? c->nthreads : 0; }
 
+int or_select_pair(int64_t N, const int64_t* soff, double u1, double u2, int64_t* i, int64_t* j) {
+  if (N < 2 || !i || !j) return OR_ERR_ARG;
+  select_pair(N, soff, u1, u2, i, j);
+  return OR_OK;
+}
+
+int or_subcell_order(const or_config* cfg, int64_t cell, const double* pos, int64_t N, int64_t* order,
+                     int64_t* soff) {
+  or_ctx* c;
+  if (or_init(cfg, &c) != OR_OK || cfg->subcells < 2) return OR_ERR_ARG;
+  part* ps = (part*)calloc(N ? N : 1, sizeof(part));
+  for (int64_t i = 0; i < N; ++i) {
+    for (int d = 0; d < cfg->dim; ++d) ps[i].x[d] = pos[d * N + i];
+    ps[i].v[0] = (double)i; /* carries the input index through the reorder */
+  }
+  order_by_subcell(c, cell, ps, N, soff);
+  for (int64_t i = 0; i < N; ++i) order[i] = (int64_t)ps[i].v[0];
+  free(ps);
+  or_free(c);
+  return OR_OK;
+}
+
 int or_get_totals(const or_ctx* c, int64_t* out4) {
   memcpy(out4, c->totals, sizeof c->totals);
   return OR_OK;
@@ -917,7 +1023,7 @@ int or_collide_cell(const or_config* cfg, int64_t step, uint32_t cell, double vo
   /* the homogeneous cell uses its own volume and index for the draw stream */
   moments_of(c, 0, ps, N, &mm);
   double rem = 0.0;
-  collide_cell(c, (int64_t)cell, volume, ps, N, &mm, dt_G, sigc_max, &rem, rec, resampled);
+  collide_cell(c, (int64_t)cell, volume, ps, N, &mm, dt_G, sigc_max, &rem, rec, resampled, NULL);
   for (int64_t i = 0; i < N; ++i)
     for (int d = 0; d < 3; ++d) vel[d * N + i] = ps[i].v[d];
   free(ps);

@@ -63,6 +63,11 @@ typedef struct or_config {
    * fraction is kept per cell, starting at 0, and added to the next step's
    * count). */
   int32_t ntc_carry;
+  /* Bird's sub-cells (an option; Sec. II.A selects pairs anywhere in the
+   * cell): 0 or 1 = off; s >= 2 splits each cell into s parts per axis
+   * (s^dim sub-cells, at most 8) and takes a candidate's partner from the
+   * first particle's sub-cell when it holds another particle. */
+  int32_t subcells;
 } or_config;
 
 typedef struct or_ctx or_ctx;
@@ -106,6 +111,14 @@ int or_get_totals(const or_ctx* c, int64_t* out4);
  * independent, so any count gives results identical to 1 (the default).
  * Without OpenMP the count stays 1. */
 int or_set_threads(or_ctx* c, int n);
+/* The pair of one NTC candidate from its two uniforms (the selection the
+ * step uses): soff = NULL, or the sub-cell offsets of the cell's slots. */
+int or_select_pair(int64_t N, const int64_t* soff, double u1, double u2, int64_t* i, int64_t* j);
+/* The stable order by sub-cell of N particles of cell `cell` (pos [dim][N])
+ * that a step with cfg->subcells >= 2 uses: order[r] = input index of slot
+ * r, soff[0..nsub] the sub-cell offsets. */
+int or_subcell_order(const or_config* cfg, int64_t cell, const double* pos, int64_t N, int64_t* order,
+                     int64_t* soff);
 int or_get_threads(const or_ctx* c);
 void or_free(or_ctx* c);
 
