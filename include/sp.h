@@ -117,6 +117,14 @@ typedef struct sp_config {
    * 1 = Bird's carried remainder, kept per cell from 0 and added to the
    * next step's count (deterministic; no draw). */
   int32_t ntc_carry;
+  /* Bird's sub-cells (Sec. II.A selects a candidate pair anywhere in the
+   * cell; this is the usual DSMC refinement, off by default): 0 or 1 = off;
+   * s >= 2 splits every cell into s equal parts per axis (s^dim sub-cells,
+   * at most 8).  A cell's particles are then ordered by sub-cell (stable)
+   * before its step, the first particle of a candidate pair is uniform over
+   * the cell and its partner uniform over the other particles of the first
+   * one's sub-cell (over the cell when it is alone there). */
+  int32_t subcells;
 } sp_config;
 
 typedef struct sp_ctx sp_ctx;

@@ -48,6 +48,7 @@ class SpConfig(C.Structure):
         ("sigc_T0", C.c_double), ("n_steady", C.c_int32), ("seed", C.c_uint64),
         ("mode", C.c_int32), ("ar_max", C.c_int32), ("n_surf", C.c_int32),
         ("win_lo", (C.c_double * 2) * 6), ("win_hi", (C.c_double * 2) * 6), ("ntc_carry", C.c_int32),
+        ("subcells", C.c_int32),
     ]
 
 
@@ -142,6 +143,7 @@ def make_config(cfg: dict):
             s.win_lo[f][i] = cfg.get("win_lo", [[0.0, 0.0]] * 6)[f][i]
             s.win_hi[f][i] = cfg.get("win_hi", [[0.0, 0.0]] * 6)[f][i]
     s.ntc_carry = int(cfg.get("ntc_carry", 0))
+    s.subcells = int(cfg.get("subcells", 0))
     return s, keep
 
 

@@ -63,6 +63,7 @@ struct sp_ctx {
   double* surf_time = nullptr;  // [n_inst] sampled time
   int64_t n_surf_tot = 0;
   double *vol = nullptr, *smax = nullptr, *samp = nullptr;
+  double *ivol = nullptr, *rcp = nullptr;  // 1 / vol per cell; 1 / k for k <= kHugeCell
   double* rem = nullptr;  // [NC] carried NTC remainders
   double* mom = nullptr;  // [SP_NFIELDS][largest instance] output of sp_moments kind 0
   int64_t mom_cells = 0;
@@ -156,6 +157,9 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
   P->mode = c.mode;
   P->ar_max = c.ar_max < 1 ? 1 : c.ar_max;
   P->ntc_carry = c.ntc_carry ? 1 : 0;
+  P->subcells = c.subcells > 1 ? c.subcells : 1;
+  P->nsub = 1;
+  for (int d = 0; d < c.dim; ++d) P->nsub *= P->subcells;
   P->cell_off = cell_off;
   P->ncells = (int64_t)P->n[0] * P->n[1] * P->n[2];
   P->n_surf = (c.body != SP_BODY_NONE && c.n_surf > 0) ? c.n_surf : 0;
@@ -163,6 +167,7 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
   P->inv3R = 1.0 / (3.0 * c.R);
   P->sqrt_gamma = sqrt(c.gamma);
   P->tau_k = c.mu_ref * pow(c.T_ref, -c.omega) / (c.m * c.R);
+  P->inv_tau_k = 1.0 / P->tau_k;
   P->inv_Lmin = 1.0 / P->Lmin;
   P->inv_Fn = 1.0 / c.Fn;
   for (int d = 0; d < 3; ++d) {
@@ -211,6 +216,11 @@ bool valid(const sp_config& c, int dim) {
   }
   if (!(c.R > 0) || !(c.m > 0) || !(c.Fn > 0) || !(c.mu_ref > 0) || !(c.T_ref > 0)) return false;
   if (c.body == SP_BODY_CIRCLE && c.dim != 2) return false;
+  if (c.subcells > 1) {
+    int64_t m = 1;
+    for (int d = 0; d < c.dim; ++d) m *= c.subcells;
+    if (m > kMaxSub) return false;
+  }
   if (c.body == SP_BODY_SPHERE && c.dim != 3) return false;
   return true;
 }
@@ -295,6 +305,8 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.count = c->count;
   a.cell_inst = c->cell_inst;
   a.vol = c->vol;
+  a.ivol = c->ivol;
+  a.rcp = c->rcp;
   a.smax = c->smax;
   a.rem = c->rem;
   a.samp = c->samp;
@@ -661,6 +673,8 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->hot, std::max<int64_t>(NC, 1)));
     CK(dalloc(&c->cyc, 24));
     CK(dalloc(&c->vol, 8 * NC));
+    CK(dalloc(&c->ivol, 8 * NC));
+    CK(dalloc(&c->rcp, 8 * (kHugeCell + 1)));
     CK(dalloc(&c->smax, 8 * NC));
     CK(dalloc(&c->rem, 8 * std::max<int64_t>(NC, 1)));
     CK(dalloc(&c->samp, 8 * 8 * NC));
@@ -682,7 +696,8 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     if (c->n_ghost)
       CK(cudaMemcpyAsync(c->ghosts, gh.data(), sizeof(GhostCell) * c->n_ghost, cudaMemcpyHostToDevice, s));
     std::vector<uint32_t> ci(NC);
-    std::vector<double> vol(NC), sm(NC);
+    std::vector<double> vol(NC), ivol(NC), sm(NC), rcp(kHugeCell + 1, 0.0);
+    for (int k = 1; k <= kHugeCell; ++k) rcp[k] = 1.0 / (double)k;
     for (int i = 0; i < n_instances; ++i) {
       const InstParams& P = c->hP[i];
       const sp_config& g = cfgs[i];
@@ -692,11 +707,14 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
       for (int64_t k = 0; k < P.ncells; ++k) {
         ci[P.cell_off + k] = (uint32_t)i;
         vol[P.cell_off + k] = g.cell_volume ? g.cell_volume[k] : v0;
+        ivol[P.cell_off + k] = 1.0 / vol[P.cell_off + k];
         sm[P.cell_off + k] = s0;
       }
     }
     CK(cudaMemcpyAsync(c->cell_inst, ci.data(), 4 * NC, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->vol, vol.data(), 8 * NC, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->ivol, ivol.data(), 8 * NC, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->rcp, rcp.data(), 8 * (kHugeCell + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->smax, sm.data(), 8 * NC, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(c->rem, 0, 8 * std::max<int64_t>(NC, 1), s));
     CK(cudaMemsetAsync(c->samp, 0, 8 * 8 * NC, s));
@@ -1204,7 +1222,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->cons, c->mom, c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->ivol, c->rcp, c->cons, c->mom, c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->rem, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

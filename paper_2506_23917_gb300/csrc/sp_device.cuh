@@ -256,6 +256,56 @@ __device__ __forceinline__ bool face_open(const Geo<T>& G, int f, const T* x) {
   return true;
 }
 
+// Bird's sub-cells (option): the sub-cell of a particle at x in the
+// instance-local cell kl -- on each axis the cell coordinate
+// u = (x - lo) n / L (cell_of's expression) minus the cell's index, split
+// into P.subcells equal parts (clamped).
+template <class T, int DIM>
+__device__ __forceinline__ int subcell_of(const InstParams& P, int64_t kl, const T* x) {
+  const Geo<T>& G = geo<T>(P);
+  const int ns = P.subcells;
+  int64_t kk = kl;
+  int sub = 0, mul = 1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int64_t id = kk % P.n[d];
+    kk /= P.n[d];
+    const T u = (x[d] - G.lo[d]) * G.inv_d[d];
+    const T f = tfloor((u - (T)id) * (T)ns);
+    int t = (int)f;
+    if (f < (T)0) t = 0;
+    if (t > ns - 1) t = ns - 1;
+    sub += mul * t;
+    mul *= ns;
+  }
+  return sub;
+}
+
+// The pair of an NTC candidate (Sec. II.A: "selected randomly within the
+// cell") from its uniforms u1, u2: i uniform over the N slots, j uniform
+// over the other N - 1; with sub-cells (so = the cell's sub-cell offsets,
+// nsub > 1) j uniform over the other particles of i's sub-cell when it
+// holds one.  Slots relative to the cell.
+template <class T, class O>
+__device__ __forceinline__ void select_pair(int N, T u1, T u2, const O* so, int nsub, int* pi, int* pj) {
+  int i = (int)(u1 * (T)N);
+  if (i > N - 1) i = N - 1;
+  int a0 = 0, b0 = N;
+  if (nsub > 1) {
+    int t = 0;
+    while ((int)so[t + 1] <= i) ++t;
+    if ((int)so[t + 1] - (int)so[t] >= 2) {
+      a0 = so[t];
+      b0 = so[t + 1];
+    }
+  }
+  int j = a0 + (int)(u2 * (T)(b0 - a0 - 1));
+  if (j > b0 - 2) j = b0 - 2;
+  if (j >= i) j += 1;
+  *pi = i;
+  *pj = j;
+}
+
 // Diffuse re-emission at a wall with R T_w = RTw: normal speed
 // c_n = sqrt(-2 R T_w ln R1), tangential Box-Muller pair (R3, R4).
 template <class T>
@@ -521,6 +571,7 @@ struct __align__(16) CellTab {
   int nacc[32];
   int coff[33];  // candidate offsets of the flattened NTC loop
   int pad[2];
+  uint16_t soff[32][kMaxSub + 1];  // sub-cell offsets within each cell (sub-cells on)
   T U[3][32];
   T q[3][32];
   T RT[32], s2RT[32], Amax[32], Pres[32], omp[32], dt[32];
@@ -672,24 +723,19 @@ constexpr int kLaneNtcMax = DIM == 3 ? 256 : 0;
 template <class Acc>
 constexpr int lane_sum_max = Acc::kExact ? kLaneSumMaxExact : kLaneSumMax;
 template <class Acc, int K, class F>
-__device__ __forceinline__ void cell_sums(bool own, int offi, int Ni, typename Acc::result (&out)[K], F f) {
+__device__ __forceinline__ void cell_sums_acc(bool own, int offi, int Ni, Acc (&out)[K], F f) {
   using Tm = typename Acc::term;
   const int lane = threadIdx.x & 31;
   const bool small = own && Ni <= lane_sum_max<Acc>;
 #pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = 0;
+  for (int k = 0; k < K; ++k) out[k].init();
   if (small) {
-    Acc acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k].init();
     for (int s = offi; s < offi + Ni; ++s) {
       Tm v[K], lo[K];
       f(s, lane, v, lo);
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k].add(v[k], lo[k]);
+      for (int k = 0; k < K; ++k) out[k].add(v[k], lo[k]);
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = acc[k].get();
   }
   for (unsigned b = __ballot_sync(kFull, own && !small); b; b &= b - 1) {
     const int c = __ffs(b) - 1;
@@ -712,9 +758,17 @@ __device__ __forceinline__ void cell_sums(bool own, int offi, int Ni, typename A
       for (int k = 0; k < K; ++k) acc[k].combine(acc[k].shfl_xor(o));
     if (lane == c)
 #pragma unroll
-      for (int k = 0; k < K; ++k) out[k] = acc[k].get();
+      for (int k = 0; k < K; ++k) out[k] = acc[k];
   }
   __syncwarp();
+}
+
+template <class Acc, int K, class F>
+__device__ __forceinline__ void cell_sums(bool own, int offi, int Ni, typename Acc::result (&out)[K], F f) {
+  Acc acc[K];
+  cell_sums_acc<Acc, K>(own, offi, Ni, acc, f);
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = acc[k].get();
 }
 
 // c f + K for an FP32 c, with f = fh + fl and K = Kh + Kl given as FP32
@@ -803,17 +857,20 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   o.dtG = dt_cur;
   o.ratio = Pi.mode == 2 ? 0.0 : 1.0;  // cells without a split: the forced mode, else DSMC
   if (Ni <= 0) return;
-  const double fN = (double)Ni, iN = 1.0 / fN, iV = 1.0 / vol_k;
+  // 1/N, 1/(N-1), 1/(N-2) from the table of reciprocals (cells of the
+  // warp launches) and 1/V from the per-cell array: no FP64 division
+  const bool tab = Ni <= kHugeCell;
+  const double fN = (double)Ni, iN = tab ? a.rcp[Ni] : 1.0 / fN, iV = a.ivol[kc];
   o.U[0] = m0 * iN;
   o.U[1] = m1 * iN;
   o.U[2] = m2 * iN;
   const double nt = fN * Pi.Fn * iV;
   o.n = nt;
   if (Ni < 2) return;
-  const double iN1 = 1.0 / (fN - 1.0);
+  const double iN1 = tab ? a.rcp[Ni - 1] : 1.0 / (fN - 1.0);
   const double Tt = mS2 * iN1 * Pi.inv3R;
   if (Ni >= 3) {
-    const double fq = 0.5 * fN * iN1 / (fN - 2.0);
+    const double fq = 0.5 * fN * iN1 * (tab ? a.rcp[Ni - 2] : 1.0 / (fN - 2.0));
     o.q[0] = fq * mS3x;
     o.q[1] = fq * mS3y;
     o.q[2] = fq * mS3z;
@@ -824,7 +881,7 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   if (Tt > 0.0) {
     sRT = sqrt(Pi.R * Tt);
     // 1/tau = n T^(1-omega) / tau_k
-    itau = nt * exp((1.0 - Pi.omega) * log(Tt)) / Pi.tau_k;
+    itau = nt * exp((1.0 - Pi.omega) * log(Tt)) * Pi.inv_tau_k;
     taut = 1.0 / itau;
     dtct = Pi.Lmin / (umag + Pi.sqrt_gamma * sRT);
   } else if (umag > 0.0) {
@@ -1110,11 +1167,44 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       }
     }
   }
+  // ---- 1b. Bird's sub-cells (option): each cell's slots in a stable order
+  // by sub-cell (the sub-cell of a slot from its particle's position), so
+  // that every sub-cell is a run of slots; offsets in ct->soff
+  const int nsub_i = own ? inst_params<ONE>(a, inst).nsub : 1;
+  const unsigned subs = __ballot_sync(kFull, nsub_i > 1);
+  if (subs) {
+    for (int s = lane; s < M; s += 32) {
+      const int c = sseg[s];
+      int sub = 0;
+      if ((subs >> c) & 1u) {
+        const InstParams& P = inst_params<ONE>(a, ct->inst[c]);
+        T x[3] = {0, 0, 0};
+        const uint32_t o = sidx[s];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) x[d] = ((const T*)a.Apos[d])[o];
+        sub = subcell_of<T, DIM>(P, ct->kl[c], x);
+      }
+      stag[s] = sub;
+    }
+    __syncwarp();
+    if (nsub_i > 1) {  // lane i: a counting sort of cell i's slots (stable)
+      uint16_t* so = ct->soff[lane];
+      for (int t = 0; t <= nsub_i; ++t) so[t] = 0;
+      for (int s = offi; s < offi + Ni; ++s) so[stag[s] + 1] += 1;
+      for (int t = 0; t < nsub_i; ++t) so[t + 1] += so[t];
+      uint32_t* tmp = (uint32_t*)svy;  // free until the gather
+      for (int s = offi; s < offi + Ni; ++s) tmp[offi + so[stag[s]]++] = sidx[s];
+      for (int t = nsub_i; t > 0; --t) so[t] = so[t - 1];
+      so[0] = 0;
+      for (int s = offi; s < offi + Ni; ++s) sidx[s] = tmp[s];
+    }
+    __syncwarp();
+  }
   // the free flight re-reads the source indices from perm when they share
-  // the x-velocity array: store the restored order there
-  if (idx_in_velocity<T>() && uns) {
+  // the x-velocity array: store the restored (and sub-cell) order there
+  if (idx_in_velocity<T>() && (uns | subs)) {
     for (int s = lane; s < M; s += 32)
-      if ((uns >> sseg[s]) & 1u) a.perm[p0 + s] = sidx[s];
+      if (((uns | subs) >> sseg[s]) & 1u) a.perm[p0 + s] = sidx[s];
   }
   // ---- 2. gather velocities (with the indices in the x-velocity array,
   // each lane reads slot s's index before it writes slot s's velocity)
@@ -1193,19 +1283,31 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   const bool two_pass = own && !one_pass;
   if (__any_sync(kFull, two_pass)) {
     A r1[3];
-    cell_sums<Acc, 3>(two_pass, offi, Ni, r1, [&](int s, int c, T* v, T* lo) {
+    Acc a1[3];
+    cell_sums_acc<Acc, 3>(two_pass, offi, Ni, a1, [&](int s, int c, T* v, T* lo) {
       v[0] = svx[s];
       v[1] = svy[s];
       v[2] = svz[s];
       lo[0] = lo[1] = lo[2] = 0;
     });
-    if (two_pass && Ni > 0) {  // the shift of the central sums: the cell mean
-      const A iN = kMixed ? (A)1 / (A)Ni : (A)0;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const A Ud = kMixed ? r1[d] * iN : cdiv(r1[d], (A)Ni);
-        ct->Up[d][lane] = (T)Ud;
-        if constexpr (kMixed) ct->Kl[d][lane] = (T)(Ud - (A)(T)Ud);
+    for (int d = 0; d < 3; ++d) r1[d] = a1[d].get();
+    if (two_pass && Ni > 0) {  // the shift of the central sums: the cell mean
+      if constexpr (kMixed) {
+        // U = (s + e) / N as an FP32 pair U_h + U_l without FP64 work: the
+        // residual s - U_h N is exact (an FMA), so U_h + U_l is the mean to
+        // ~eps^2 relative
+        const float fN = (float)Ni, rN = 1.0f / fN;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float uh = a1[d].s * rN;
+          const float r = fmaf(-uh, fN, a1[d].s) + a1[d].e;
+          ct->Up[d][lane] = uh;
+          ct->Kl[d][lane] = r * rN;
+        }
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ct->Up[d][lane] = (T)cdiv(r1[d], (A)Ni);
       }
     }
     __syncwarp();
@@ -1256,9 +1358,15 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       ct->Amax[lane] = (T)cm.Amax;
       ct->omp[lane] = (T)cm.omp;
     }
-    ct->U[0][lane] = (T)cm.U[0];
-    ct->U[1][lane] = (T)cm.U[1];
-    ct->U[2][lane] = (T)cm.U[2];
+    if constexpr (kMixed) {  // the FP32 mean of the shift (U_h), no conversion
+      ct->U[0][lane] = ct->Up[0][lane];
+      ct->U[1][lane] = ct->Up[1][lane];
+      ct->U[2][lane] = ct->Up[2][lane];
+    } else {
+      ct->U[0][lane] = (T)cm.U[0];
+      ct->U[1][lane] = (T)cm.U[1];
+      ct->U[2][lane] = (T)cm.U[2];
+    }
     ct->q[0][lane] = (T)cm.q[0];
     ct->q[1][lane] = (T)cm.q[1];
     ct->q[2][lane] = (T)cm.q[2];
@@ -1317,11 +1425,8 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
         if (lane_ntc && k < (int)ncol) {
           const int N = Ni;
           const NtcDraw<T> dr = ntc_draw((T)0, step, (uint32_t)ct->kl[lane], (uint32_t)k, Pi.key0, Pi.key1);
-          int ci = (int)(dr.u1 * (T)N);
-          if (ci > N - 1) ci = N - 1;
-          int cj = (int)(dr.u2 * (T)(N - 1));
-          if (cj > N - 2) cj = N - 2;
-          if (cj >= ci) cj += 1;
+          int ci, cj;
+          select_pair(N, dr.u1, dr.u2, ct->soff[lane], nsub_i, &ci, &cj);
           ci += offi;
           cj += offi;
           const T ax = svx[ci], ay = svy[ci], az = svz[ci];
@@ -1376,11 +1481,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       u3 = dr.u3;
       u4 = dr.u4;
       u5 = dr.u5;
-      ci = (int)(dr.u1 * (T)N);
-      if (ci > N - 1) ci = N - 1;
-      cj = (int)(dr.u2 * (T)(N - 1));
-      if (cj > N - 2) cj = N - 2;
-      if (cj >= ci) cj += 1;
+      select_pair(N, dr.u1, dr.u2, ct->soff[c], P.nsub, &ci, &cj);
       ci += ct->off[c];
       cj += ct->off[c];
     }
@@ -2006,6 +2107,7 @@ struct __align__(16) HugeTab {
   int ncol, nacc, nres, nar;
   double ratio;
   int shk;
+  int soff[kMaxSub + 1];  // sub-cell offsets (sub-cells on)
 };
 
 // Bytes of staging per particle in shared memory: velocities, source
@@ -2132,6 +2234,31 @@ __global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
       for (int s = tid; s + 1 < N; s += kHugeThreads) uns |= sidx[s] > sidx[s + 1];
       if (__syncthreads_or(uns)) block_sort_u32(sidx, N);
     }
+    // Bird's sub-cells (option): the slots in a stable order by sub-cell
+    const int nsub = Pi.nsub;
+    if (nsub > 1) {
+      for (int s = tid; s < N; s += kHugeThreads) {
+        T x[3] = {0, 0, 0};
+        const uint32_t o = sidx[s];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) x[d] = ((const T*)a.Apos[d])[o];
+        stag[s] = subcell_of<T, DIM>(Pi, kl, x);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int* so = tb->soff;
+        for (int t = 0; t <= nsub; ++t) so[t] = 0;
+        for (int s = 0; s < N; ++s) so[stag[s] + 1] += 1;
+        for (int t = 0; t < nsub; ++t) so[t + 1] += so[t];
+        uint32_t* tmp = (uint32_t*)svy;  // free until the gather
+        for (int s = 0; s < N; ++s) tmp[so[stag[s]]++] = sidx[s];
+        for (int t = nsub; t > 0; --t) so[t] = so[t - 1];
+        so[0] = 0;
+      }
+      __syncthreads();
+      for (int s = tid; s < N; s += kHugeThreads) sidx[s] = ((const uint32_t*)svy)[s];
+      __syncthreads();
+    }
     // ---- 2. gather
     {
       const T* Av0 = (const T*)a.Avel[0];
@@ -2222,11 +2349,7 @@ __global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
           u3 = dr.u3;
           u4 = dr.u4;
           u5 = dr.u5;
-          ci = (int)(dr.u1 * (T)N);
-          if (ci > N - 1) ci = N - 1;
-          cj = (int)(dr.u2 * (T)(N - 1));
-          if (cj > N - 2) cj = N - 2;
-          if (cj >= ci) cj += 1;
+          select_pair(N, dr.u1, dr.u2, tb->soff, nsub, &ci, &cj);
         }
         bool pending = valid, known = false;
         T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cr = 0, sc = (T)-1;

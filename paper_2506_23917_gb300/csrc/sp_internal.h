@@ -19,6 +19,7 @@ constexpr int kMaxDynSmem = 232448;          // 227 KB per block (opt-in maximum
 // huge-cell launch); the other launches stage at most kHugeCell particles
 // per warp, so which code collides a cell depends on the cell alone.
 constexpr int kHugeCell = 1024;
+constexpr int kMaxSub = 8;                   // sub-cells per cell
 
 // Philox stream purposes (high byte of counter word 3).
 constexpr uint32_t kPurpNtc = 1, kPurpShk = 2, kPurpWall = 3, kPurpInj = 4, kPurpInjWall = 5;
@@ -56,6 +57,8 @@ struct InstParams {
   int mode;
   int ar_max;
   int ntc_carry;     // carried NTC remainder instead of stochastic rounding
+  int subcells;      // sub-cells per axis (1: off)
+  int nsub;          // sub-cells per cell (subcells^dim, at most kMaxSub)
   int64_t cell_off;  // first global cell of the instance
   int64_t ncells;
   int n_surf;        // surface elements of the body (0: no tallies)
@@ -65,6 +68,7 @@ struct InstParams {
   double inv3R;      // 1 / (3 R)
   double sqrt_gamma; // sqrt(gamma)
   double tau_k;      // tau = tau_k T^(omega - 1) / n, tau_k = mu_ref T_ref^-omega / (m R)
+  double inv_tau_k;  // 1 / tau_k
   double inv_Lmin;   // 1 / L_min
   double inv_Fn;     // 1 / F_N
   Geo<double> g64;
@@ -95,6 +99,8 @@ struct StepArgs {
   uint32_t* count;      // [NC]    next-state histogram (atomics)
   const uint32_t* cell_inst;  // [NC]
   const double* vol;    // [NC]
+  const double* ivol;   // [NC] 1 / vol
+  const double* rcp;    // [kHugeCell + 1] rcp[k] = 1 / k (rcp[0] = 0)
   double* smax;         // [NC]
   double* rem;          // [NC] carried NTC remainder
   double* samp;         // [8][NC]

@@ -74,7 +74,7 @@ def base_config(dim, n, lo, hi):
         body=BODY_NONE, body_c=[0.0, 0.0, 0.0], body_r=0.0, body_Tw=1.0,
         cell_volume=None, sigc_T0=1.0, n_steady=0, seed=1, mode=MODE_HYBRID, ar_max=64,
         n_surf=0, win_lo=[[0.0, 0.0] for _ in range(6)], win_hi=[[0.0, 0.0] for _ in range(6)],
-        ntc_carry=0,
+        ntc_carry=0, subcells=0,
     )
 
 

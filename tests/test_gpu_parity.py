@@ -317,3 +317,27 @@ def test_huge_cells_match_oracle(sp):
     assert tot[0] > 1000 and tot[1] > 0 and tot[2] > 1000
     assert np.diff(o.cell_start().astype(np.int64)).max() > 4096  # still above every staging area
     _close(s.moments(0, 1), o.moments(1), what="averaged moments")
+
+
+@pytest.mark.parametrize("case", ["channel2d", "sphere3d", "huge1d"])
+def test_subcells_match_oracle(sp, case):
+    """Bird's sub-cells (option; 2 x 2 in 2-D, 2 x 2 x 2 in 3-D, 4 in the 1-D
+    tube with cells of 20 000 / 6000 / 1500 / 300 particles): the cells'
+    slots ordered by sub-cell and each candidate's partner drawn from the
+    first particle's sub-cell -- bit-exact integers, 1e-12 floats."""
+    if case == "channel2d":
+        cfg, regions = W.box2d(nx=24, ny=12, ppc=40.0)
+        cfg["subcells"] = 2
+        pos, vel = W.fill_regions(cfg, regions, 3)
+        steps = 8
+    elif case == "sphere3d":
+        cfg, regions = W.box3d(n=(12, 8, 8), ppc=16.0)
+        cfg["subcells"] = 2
+        pos, vel = W.fill_regions(cfg, regions, 5)
+        steps = 5
+    else:
+        cfg, pos, vel = W.huge_cells()
+        cfg["subcells"] = 4
+        steps = 4
+    o, s, tot = run_pair(sp, cfg, pos, vel, steps=steps)
+    assert tot[0] > 0 and tot[1] > 0
