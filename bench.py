@@ -61,6 +61,9 @@ def parse():
                    help="FP32: restore the source order inside cells in the timed run")
     p.add_argument("--batch-steps", type=int, default=200)
     p.add_argument("--no-sod", action="store_true", help="skip the FP64 Sod shock-tube leg")
+    p.add_argument("--state-file", default=None,
+                   help="developed particle state (.npz): loaded when the file exists, else written after "
+                        "the development steps (lets a profiler start at the developed flow)")
     return p.parse_args()
 
 
@@ -422,9 +425,18 @@ def main():
     sim = sp.Sim(cfg, prec, capacity=cap)
     if prec != sp.FP64 and not args.reproducible:
         sim.set_reproducible(False)  # FP32 mode is checked statistically
-    sim.set_particles(0, pos, vel)
-    sim.step(args.develop)
-    sim.sync()
+    developed = args.develop
+    if args.state_file and os.path.exists(args.state_file):
+        z = np.load(args.state_file)
+        sim.set_particles(0, z["pos"], z["vel"])
+        developed = int(z["steps"])
+    else:
+        sim.set_particles(0, pos, vel)
+        sim.step(args.develop)
+        sim.sync()
+        if args.state_file:
+            ps, vs, _ = sim.particles(0)
+            np.savez(args.state_file, pos=ps, vel=vs, steps=args.develop)
     if args.schedule:
         sched = tuple(int(x) for x in args.schedule.split(","))
         sim.set_schedule(*sched)
@@ -522,7 +534,7 @@ def main():
             "vs_baseline": None, "dtype": "f32" if prec != sp.FP64 else "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.scale, args.config),
                        "cells": int(np.prod(cfg["n"][:cfg["dim"]])),
-                       "particles_per_rank": int(0.5 * (M0 + M1)), "developed_steps": args.develop,
+                       "particles_per_rank": int(0.5 * (M0 + M1)), "developed_steps": developed,
                        "state": {sp.FP32: "FP32 particles; per-cell sums accumulated to FP64 accuracy "
                                           "and all per-cell arithmetic in FP64",
                                  sp.FP32_CELL32: "FP32 particles, FP32 per-cell sums and arithmetic "
@@ -560,6 +572,31 @@ def main():
         line["fp64_plain"] = {"value": v64 * world, "unit": UNIT, "ms_per_step": t64 / k64, "steps": k64,
                               "collide_ms": p64[0] / 10, "fp32_over_fp64": value / (v64 * world)}
         sim64.close()
+
+    # --- the opt-in all-FP32 per-cell variant on the same developed state
+    if not args.no_modes and prec == sp.FP32 and rank == 0:
+        po, vo, _ = sim.particles(0)
+        sv = sp.Sim(cfg, sp.FP32_CELL32, capacity=cap)
+        if not args.reproducible:
+            sv.set_reproducible(False)
+        sv.set_particles(0, po, vo)
+        if sched:
+            sv.set_schedule(*sched)
+        sv.step(args.warmup + 20)
+        sv.sync()
+        kv = max(200, args.steps // 5)
+        m0 = sv.count(0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sv.step(kv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sv.sync()
+        tv = e0.elapsed_time(e1)
+        line["precision_variants"] = {"fp32_cell32": {
+            "value": kv * 0.5 * (m0 + sv.count(0)) / (tv * 1e-3), "unit": UNIT, "ms_per_step": tv / kv,
+            "steps": kv, "note": "FP32 per-cell sums and arithmetic (opt-in), same state and schedule"}}
+        sv.close()
 
     # --- Sod shock tube in FP64: 200 cells, 500 / 62.5 particles per cell
     # (56 250 particles), 400 steps at CFL 0.5 (L2-resident and latency bound)

@@ -32,8 +32,8 @@
  *    sp_init() and frees it in sp_free().
  *  - Device work is enqueued on the CUDA stream given to sp_init() (NULL
  *    selects the legacy default stream of the current device).
- *  - A device-side failure (capacity overflow, a cell above the staging
- *    capacity, a bounce or acceptance-rejection cap) sets a sticky flag that
+ *  - A device-side failure (particle capacity overflow, a bounce or
+ *    acceptance-rejection cap) sets a sticky flag that
  *    the next synchronising call reports as SP_ERR_DEVICE or
  *    SP_ERR_CAPACITY; sp_errors() reads the individual counters.
  */
@@ -49,7 +49,7 @@ typedef enum {
   SP_OK = 0,
   SP_ERR_ARG = -1,      /* invalid argument or configuration              */
   SP_ERR_CUDA = -2,     /* a CUDA runtime call failed                      */
-  SP_ERR_CAPACITY = -3, /* particle capacity or per-cell capacity exceeded */
+  SP_ERR_CAPACITY = -3, /* particle capacity (or a static-sort limit) exceeded */
   SP_ERR_DEVICE = -4,   /* sticky device error flag set                    */
   SP_ERR_STATE = -5     /* call out of order (e.g. sp_step before particles) */
 } sp_status;
@@ -245,8 +245,9 @@ sp_status sp_get_surface(sp_ctx* ctx, int inst, double* out, double* time);
 sp_status sp_surface_coefficients(const sp_config* cfg, const double* tallies, double time,
                                   double rho_inf, double u_inf, double p_inf, double* elem,
                                   double* body);
-/* Device error counters: [0] capacity overflow, [1] cell above staging
- * capacity, [2] bounce cap, [3] AR cap, [4] NTC candidate cap.
+/* Device error counters: [0] capacity overflow, [1] reserved (always 0:
+ * cells of any occupancy are processed, those above 1024 particles by one
+ * thread block each), [2] bounce cap, [3] AR cap, [4] NTC candidate cap.
  * Clears nothing. */
 sp_status sp_errors(sp_ctx* ctx, int64_t* out5);
 /* Advance n_steps steps launched one kernel at a time (no CUDA graph) with
