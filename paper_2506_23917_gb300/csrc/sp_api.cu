@@ -168,6 +168,7 @@ void fill_params(const sp_config& c, InstParams* P, int64_t cell_off) {
   P->sqrt_gamma = sqrt(c.gamma);
   P->tau_k = c.mu_ref * pow(c.T_ref, -c.omega) / (c.m * c.R);
   P->inv_tau_k = 1.0 / P->tau_k;
+  P->omf = (float)(1.0 - c.omega);
   P->inv_Lmin = 1.0 / P->Lmin;
   P->inv_Fn = 1.0 / c.Fn;
   for (int d = 0; d < 3; ++d) {

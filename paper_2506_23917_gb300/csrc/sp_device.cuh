@@ -632,6 +632,7 @@ __device__ __forceinline__ float two_prod(float a, float b, float* e) {
 //   FP32 -> FP64 conversion of its operand) goes through the FP64 pipe at
 //   about 1/56 of the FP32 rate, so these seven FP32 operations per term
 //   are several times cheaper than widening each term and adding in FP64.
+// add1(x) takes a term without a low part (one FP32 add fewer);
 // combine(o) adds another accumulator's run; shfl_xor(o) is the lane
 // o-apart copy (for butterflies across a warp).
 template <class T>
@@ -642,6 +643,7 @@ struct PlainSum {
   T s;
   __device__ __forceinline__ void init() { s = 0; }
   __device__ __forceinline__ void add(T x, T) { s += x; }
+  __device__ __forceinline__ void add1(T x) { s += x; }
   __device__ __forceinline__ void combine(const PlainSum& o) { s += o.s; }
   __device__ __forceinline__ PlainSum shfl_xor(int o) const {
     PlainSum r;
@@ -660,6 +662,11 @@ struct ExactSum {
     float r;
     s = two_sum(s, x, &r);
     e += r + lo;
+  }
+  __device__ __forceinline__ void add1(float x) {  // a term without a low part
+    float r;
+    s = two_sum(s, x, &r);
+    e += r;
   }
   __device__ __forceinline__ void combine(const ExactSum& o) {
     float r;
@@ -722,7 +729,8 @@ constexpr int kLaneNtcMax = DIM == 3 ? 256 : 0;
 // costs more than the lanes a dense cell leaves idle.)
 template <class Acc>
 constexpr int lane_sum_max = Acc::kExact ? kLaneSumMaxExact : kLaneSumMax;
-template <class Acc, int K, class F>
+// kLo: the terms come with exact low parts (else lo is ignored).
+template <class Acc, int K, bool kLo = false, class F>
 __device__ __forceinline__ void cell_sums_acc(bool own, int offi, int Ni, Acc (&out)[K], F f) {
   using Tm = typename Acc::term;
   const int lane = threadIdx.x & 31;
@@ -734,7 +742,10 @@ __device__ __forceinline__ void cell_sums_acc(bool own, int offi, int Ni, Acc (&
       Tm v[K], lo[K];
       f(s, lane, v, lo);
 #pragma unroll
-      for (int k = 0; k < K; ++k) out[k].add(v[k], lo[k]);
+      for (int k = 0; k < K; ++k) {
+        if constexpr (kLo) out[k].add(v[k], lo[k]);
+        else out[k].add1(v[k]);
+      }
     }
   }
   for (unsigned b = __ballot_sync(kFull, own && !small); b; b &= b - 1) {
@@ -750,7 +761,10 @@ __device__ __forceinline__ void cell_sums_acc(bool own, int offi, int Ni, Acc (&
       Tm v[K], lo[K];
       f(s, c, v, lo);
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k].add(v[k], lo[k]);
+      for (int k = 0; k < K; ++k) {
+        if constexpr (kLo) acc[k].add(v[k], lo[k]);
+        else acc[k].add1(v[k]);
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -763,10 +777,10 @@ __device__ __forceinline__ void cell_sums_acc(bool own, int offi, int Ni, Acc (&
   __syncwarp();
 }
 
-template <class Acc, int K, class F>
+template <class Acc, int K, bool kLo = false, class F>
 __device__ __forceinline__ void cell_sums(bool own, int offi, int Ni, typename Acc::result (&out)[K], F f) {
   Acc acc[K];
-  cell_sums_acc<Acc, K>(own, offi, Ni, acc, f);
+  cell_sums_acc<Acc, K, kLo>(own, offi, Ni, acc, f);
 #pragma unroll
   for (int k = 0; k < K; ++k) out[k] = acc[k].get();
 }
@@ -847,12 +861,16 @@ struct CellMath {
 // for the sound speed, sqrt(2RT) and (RT)^(3/2); and the viscosity power
 // through tau = tau_k T^(omega-1) / n = tau_k exp((omega-1) ln T) / n with
 // tau_k = mu_ref T_ref^-omega / (m R) from the host (one logarithm and one
-// exponential instead of pow).  FP64 throughout; the rounding differs from
-// the oracle's order by a few ulps (this mode is checked statistically).
+// exponential instead of pow).  tau enters a result only through the split:
+// where an FP32 bound of Delta t_c / tau is below 0.99 (its error is below
+// 1e-5, so Delta t_c <= tau holds exactly) the cell is pure DSMC and tau is
+// not formed; q_s and the Shakhov constants only in cells with a Shakhov
+// part.  FP64 throughout; the rounding differs from the oracle's order by a
+// few ulps (this mode is checked statistically).  ivol_k = 1 / V.
 template <class T>
 __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstParams& Pi, int64_t kc, uint32_t kl,
                                                int Ni, double m0, double m1, double m2, double mS2, double mS3x,
-                                               double mS3y, double mS3z, double vol_k, T smaxT, double dt_cur,
+                                               double mS3y, double mS3z, double ivol_k, T smaxT, double dt_cur,
                                                uint32_t step, CellMath<double>& o) {
   o.dtG = dt_cur;
   o.ratio = Pi.mode == 2 ? 0.0 : 1.0;  // cells without a split: the forced mode, else DSMC
@@ -860,7 +878,7 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   // 1/N, 1/(N-1), 1/(N-2) from the table of reciprocals (cells of the
   // warp launches) and 1/V from the per-cell array: no FP64 division
   const bool tab = Ni <= kHugeCell;
-  const double fN = (double)Ni, iN = tab ? a.rcp[Ni] : 1.0 / fN, iV = a.ivol[kc];
+  const double fN = (double)Ni, iN = tab ? a.rcp[Ni] : 1.0 / fN, iV = ivol_k;
   o.U[0] = m0 * iN;
   o.U[1] = m1 * iN;
   o.U[2] = m2 * iN;
@@ -869,21 +887,28 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   if (Ni < 2) return;
   const double iN1 = tab ? a.rcp[Ni - 1] : 1.0 / (fN - 1.0);
   const double Tt = mS2 * iN1 * Pi.inv3R;
-  if (Ni >= 3) {
-    const double fq = 0.5 * fN * iN1 * (tab ? a.rcp[Ni - 2] : 1.0 / (fN - 2.0));
-    o.q[0] = fq * mS3x;
-    o.q[1] = fq * mS3y;
-    o.q[2] = fq * mS3z;
-  }
   o.T = Tt;
   const double umag = sqrt(o.U[0] * o.U[0] + o.U[1] * o.U[1] + o.U[2] * o.U[2]);
   double taut = tinf<double>(), dtct = tinf<double>(), itau = 0, sRT = 0;
+  bool dsmc_only = true;  // Delta t_c <= tau (or no split: T = 0, DSMC forced)
   if (Tt > 0.0) {
     sRT = sqrt(Pi.R * Tt);
-    // 1/tau = n T^(1-omega) / tau_k
-    itau = nt * exp((1.0 - Pi.omega) * log(Tt)) * Pi.inv_tau_k;
-    taut = 1.0 / itau;
     dtct = Pi.Lmin / (umag + Pi.sqrt_gamma * sRT);
+    if (Pi.mode != 1) {
+      // Delta t_c / tau = Delta t_c n T^(1-omega) / tau_k; the FP32 power has
+      // a relative error below 1e-5 for T in [1e-30, 1e30]
+      bool sure = false;
+      if (Pi.mode == 0 && Tt > 1e-30 && Tt < 1e30) {
+        const double k = dtct * nt * Pi.inv_tau_k;
+        sure = k * (double)__powf((float)Tt, Pi.omf) < 0.99;
+      }
+      if (!sure) {
+        // 1/tau = n T^(1-omega) / tau_k
+        itau = nt * exp((1.0 - Pi.omega) * log(Tt)) * Pi.inv_tau_k;
+        taut = 1.0 / itau;
+        dsmc_only = Pi.mode == 0 && dtct <= taut;
+      }
+    }
   } else if (umag > 0.0) {
     dtct = Pi.Lmin / umag;
   }
@@ -891,17 +916,15 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   o.tau = taut;
   o.dtc = dtct;
   // r = tau / dt_c = tau (|U| + c_s) / L_min
-  const double r = (Tt > 0.0) ? taut * (umag + Pi.sqrt_gamma * sRT) * Pi.inv_Lmin : 1.0;
+  const double r = dsmc_only ? 1.0 : taut * (umag + Pi.sqrt_gamma * sRT) * Pi.inv_Lmin;
   if (Pi.mode == 1) o.ratio = 1;
   else if (Pi.mode == 2) o.ratio = 0;
-  else if (!(Tt > 0.0) || dtct <= taut) o.ratio = 1;
   else o.ratio = r;
   if (!(Tt > 0.0)) return;
   const double dtG = dt_cur;
   double dsmc, sbgk;
-  if (Pi.mode == 1) { dsmc = dtG; sbgk = 0; }
-  else if (Pi.mode == 2) { dsmc = 0; sbgk = dtG; }
-  else if (dtct <= taut) { dsmc = dtG; sbgk = 0; }
+  if (Pi.mode == 2) { dsmc = 0; sbgk = dtG; }
+  else if (dsmc_only) { dsmc = dtG; sbgk = 0; }
   else { dsmc = r * dtG; sbgk = (1.0 - r) * dtG; }
   if (dsmc > 0.0) {
     const double ncr = 0.5 * fN * (fN - 1.0) * Pi.Fn * (double)smaxT * dsmc * iV;
@@ -920,6 +943,10 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   }
   if (sbgk > 0.0 && Ni >= 3) {
     o.shk = true;
+    const double fq = 0.5 * fN * iN1 * (tab ? a.rcp[Ni - 2] : 1.0 / (fN - 2.0));
+    o.q[0] = fq * mS3x;
+    o.q[1] = fq * mS3y;
+    o.q[2] = fq * mS3z;
     const double RTt = Pi.R * Tt;
     const double qn = sqrt(o.q[0] * o.q[0] + o.q[1] * o.q[1] + o.q[2] * o.q[2]);
     o.RT = RTt;
@@ -930,6 +957,7 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   }
 }
 
+// vol_k: the cell volume V (FP64 and all-FP32 modes) or 1/V (mixed).
 template <class T, class A>
 __device__ __forceinline__ void cell_math(const StepArgs& a, const InstParams& Pi, int64_t kc, uint32_t kl, int Ni,
                                           A m0, A m1, A m2, A mS2, A mS3x, A mS3y, A mS3z, double vol_k,
@@ -1079,9 +1107,10 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   const int64_t kc = k0 + (own ? lane : 0);
   int Ni = 0, offi = 0;
   uint32_t inst = 0;
-  double vol_k = 1.0, smax_k = 0.0;  // loaded early: used by the cell math
+  // loaded early: used by the cell math (mixed precision: 1/V)
+  double vol_k = 1.0, smax_k = 0.0;
   if (own) {
-    vol_k = a.vol[kc];
+    vol_k = kMixed ? a.ivol[kc] : a.vol[kc];
     smax_k = a.smax[kc];
     const uint32_t s0 = a.start[kc];
     Ni = (int)(a.start[kc + 1] - s0);
@@ -1367,9 +1396,11 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       ct->U[1][lane] = (T)cm.U[1];
       ct->U[2][lane] = (T)cm.U[2];
     }
-    ct->q[0][lane] = (T)cm.q[0];
-    ct->q[1][lane] = (T)cm.q[1];
-    ct->q[2][lane] = (T)cm.q[2];
+    if (cm.shk) {  // the Shakhov sampling reads q_s in these cells only
+      ct->q[0][lane] = (T)cm.q[0];
+      ct->q[1][lane] = (T)cm.q[1];
+      ct->q[2][lane] = (T)cm.q[2];
+    }
   }
   const int64_t ncol = cm.ncol;
   const bool shk = cm.shk;
@@ -1724,7 +1755,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       // The map is then applied as c' = c f + K, K = U - U_p f, with f and
       // K as FP32 pairs.
       A r[6];
-      cell_sums<Acc, 6>(rown, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
+      cell_sums<Acc, 6, true>(rown, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
         const T x[3] = {svx[s], svy[s], svz[s]};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -1833,7 +1864,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   }
   if (__any_sync(kFull, need_sq)) {
     A r[3];
-    cell_sums<Acc, 3>(need_sq, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
+    cell_sums<Acc, 3, true>(need_sq, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
       if constexpr (kMixed) {
         v[0] = two_prod(x0, x0, &lo[0]);
@@ -2130,7 +2161,7 @@ __host__ __device__ constexpr size_t huge_smem_bytes() {
 // thread t sums its contiguous share (the accumulator Acc), a butterfly
 // combines each warp, and thread 0 adds the warp totals in warp order.
 // Every thread returns the sums in out[].
-template <class Acc, int K, class TabT, class F>
+template <class Acc, int K, bool kLo = false, class TabT, class F>
 __device__ __forceinline__ void block_sums(TabT* tb, int n, typename Acc::result (&out)[K], F f) {
   using Tm = typename Acc::term;
   using R = typename Acc::result;
@@ -2145,7 +2176,10 @@ __device__ __forceinline__ void block_sums(TabT* tb, int n, typename Acc::result
     Tm v[K], lo[K];
     f(s, v, lo);
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k].add(v[k], lo[k]);
+    for (int k = 0; k < K; ++k) {
+      if constexpr (kLo) acc[k].add(v[k], lo[k]);
+      else acc[k].add1(v[k]);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
@@ -2309,7 +2343,8 @@ __global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
       CellMath<A> cm;
       cm.clear();
       const T smaxT = (T)a.smax[k];
-      cell_math<T, A>(a, Pi, k, kl, N, r1[0], r1[1], r1[2], r2[0], r2[1], r2[2], r2[3], a.vol[k], smaxT,
+      cell_math<T, A>(a, Pi, k, kl, N, r1[0], r1[1], r1[2], r2[0], r2[1], r2[2], r2[3],
+                      mixed_prec<T, A>() ? a.ivol[k] : a.vol[k], smaxT,
                       a.dt_cur[inst], step, cm);
       if (cm.dtbits != ~0ull) atomicMin(&a.dt_min[inst], cm.dtbits);
 #pragma unroll
@@ -2514,7 +2549,7 @@ __global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
       } else {
         A r[6];
         const T uh0 = tb->U[0], uh1 = tb->U[1], uh2 = tb->U[2];
-        block_sums<Acc, 6>(tb, N, r, [&](int s, auto* v, auto* lo) {
+        block_sums<Acc, 6, true>(tb, N, r, [&](int s, auto* v, auto* lo) {
           const T x[3] = {svx[s], svy[s], svz[s]};
           const T u[3] = {uh0, uh1, uh2};
 #pragma unroll
@@ -2595,7 +2630,7 @@ __global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
     // ---- 8. Step 5 sums
     if (sample) {
       if (!bsq_ok) {
-        block_sums<Acc, 3>(tb, N, bsq, [&](int s, auto* v, auto* lo) {
+        block_sums<Acc, 3, true>(tb, N, bsq, [&](int s, auto* v, auto* lo) {
           const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
           if constexpr (kMixed) {
             v[0] = two_prod(x0, x0, &lo[0]);
@@ -2779,7 +2814,12 @@ __global__ void k_inject(InjectArgs a, int pass) {
 template <class T, class A>
 __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
   // sums warp per cell, 32 cells in a row; then the FP64 scalars lane per
-  // cell (lane j <-> cell kb + j), so each FP64 instruction serves 32 cells
+  // cell (lane j <-> cell kb + j), so each FP64 instruction serves 32 cells.
+  // The sums use the collision kernel's accumulator (FP32 state with FP64
+  // cells: FP32 terms carried without loss, the mean as an FP32 pair), so
+  // no per-particle work lands on the narrow FP64 pipe.
+  using Acc = CellAcc<T, A>;
+  constexpr bool kMixed = mixed_prec<T, A>();
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nc = c1 - c0;
@@ -2790,32 +2830,69 @@ __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
        kb += 32 * nw) {
     int myN = 0;
     double myU[3] = {0, 0, 0};
-    A myS2 = 0, myS3[3] = {0, 0, 0};
+    double myS2 = 0, myS3[3] = {0, 0, 0};
     const int nj = (int)((c1 - kb) < 32 ? (c1 - kb) : 32);
     for (int j = 0; j < nj; ++j) {
       const int64_t k = kb + j;
       const uint32_t s0 = a.start[k];
       const int N = (int)(a.start[k + 1] - s0);
       double U[3] = {0, 0, 0};
+      T Uh[3] = {0, 0, 0}, Ul[3] = {0, 0, 0};
       {
-        A s0x = 0, s1x = 0, s2x = 0;
+        Acc sx[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sx[d].init();
         for (int s = lane; s < N; s += 32) {
           const uint32_t o = a.perm[s0 + s];
-          s0x += (A)Av0[o]; s1x += (A)Av1[o]; s2x += (A)Av2[o];
+          sx[0].add(Av0[o], (T)0);
+          sx[1].add(Av1[o], (T)0);
+          sx[2].add(Av2[o], (T)0);
         }
-        s0x = warp_sum(s0x); s1x = warp_sum(s1x); s2x = warp_sum(s2x);
-        if (N > 0) { U[0] = (double)s0x / N; U[1] = (double)s1x / N; U[2] = (double)s2x / N; }
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) sx[d].combine(sx[d].shfl_xor(m));
+        if (N > 0) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            U[d] = (double)sx[d].get() / N;
+            if constexpr (kMixed) {
+              const float fN = (float)N, rN = 1.0f / fN;
+              Uh[d] = sx[d].s * rN;
+              Ul[d] = (fmaf(-Uh[d], fN, sx[d].s) + sx[d].e) * rN;
+            } else {
+              Uh[d] = (T)U[d];
+            }
+          }
+        }
       }
-      A S2 = 0, S3x = 0, S3y = 0, S3z = 0;
+      double S2 = 0, S3x = 0, S3y = 0, S3z = 0;
       if (N >= 2) {
-        const A Ux = (A)U[0], Uy = (A)U[1], Uz = (A)U[2];
+        Acc r[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) r[d].init();
         for (int s = lane; s < N; s += 32) {
           const uint32_t o = a.perm[s0 + s];
-          const A C0 = (A)Av0[o] - Ux, C1 = (A)Av1[o] - Uy, C2 = (A)Av2[o] - Uz;
-          const A c2 = C0 * C0 + C1 * C1 + C2 * C2;
-          S2 += c2; S3x += c2 * C0; S3y += c2 * C1; S3z += c2 * C2;
+          T C0 = Av0[o] - Uh[0], C1 = Av1[o] - Uh[1], C2 = Av2[o] - Uh[2];
+          if constexpr (kMixed) {
+            C0 -= Ul[0];
+            C1 -= Ul[1];
+            C2 -= Ul[2];
+          }
+          const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+          r[0].add(c2, (T)0);
+          r[1].add(c2 * C0, (T)0);
+          r[2].add(c2 * C1, (T)0);
+          r[3].add(c2 * C2, (T)0);
         }
-        S2 = warp_sum(S2); S3x = warp_sum(S3x); S3y = warp_sum(S3y); S3z = warp_sum(S3z);
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+          for (int d = 0; d < 4; ++d) r[d].combine(r[d].shfl_xor(m));
+        S2 = (double)r[0].get();
+        S3x = (double)r[1].get();
+        S3y = (double)r[2].get();
+        S3z = (double)r[3].get();
       }
       if (lane == j) {
         myN = N;

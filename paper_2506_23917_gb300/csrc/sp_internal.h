@@ -71,6 +71,7 @@ struct InstParams {
   double inv_tau_k;  // 1 / tau_k
   double inv_Lmin;   // 1 / L_min
   double inv_Fn;     // 1 / F_N
+  float omf;         // 1 - omega in FP32 (the bound that certifies a pure DSMC split)
   Geo<double> g64;
   Geo<float> g32;
 };
