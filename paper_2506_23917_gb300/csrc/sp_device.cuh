@@ -866,8 +866,9 @@ struct CellMath {
 // 1e-5, so Delta t_c <= tau holds exactly) the cell is pure DSMC and tau is
 // not formed; q_s and the Shakhov constants only in cells with a Shakhov
 // part.  FP64 throughout; the rounding differs from the oracle's order by a
-// few ulps (this mode is checked statistically).  ivol_k = 1 / V.
-template <class T>
+// few ulps (this mode is checked statistically).  ivol_k = 1 / V.  kQ
+// false: q_s and A_max are left to shakhov_q_amax.
+template <class T, bool kQ = true>
 __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstParams& Pi, int64_t kc, uint32_t kl,
                                                int Ni, double m0, double m1, double m2, double mS2, double mS3x,
                                                double mS3y, double mS3z, double ivol_k, T smaxT, double dt_cur,
@@ -943,27 +944,48 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   }
   if (sbgk > 0.0 && Ni >= 3) {
     o.shk = true;
-    const double fq = 0.5 * fN * iN1 * (tab ? a.rcp[Ni - 2] : 1.0 / (fN - 2.0));
-    o.q[0] = fq * mS3x;
-    o.q[1] = fq * mS3y;
-    o.q[2] = fq * mS3z;
     const double RTt = Pi.R * Tt;
-    const double qn = sqrt(o.q[0] * o.q[0] + o.q[1] * o.q[1] + o.q[2] * o.q[2]);
     o.RT = RTt;
     o.s2RT = 1.4142135623730950488 * sRT;
-    o.Amax = 1.0 + 20.0 * (1.0 - Pi.Pr) * qn / (RTt * sRT);
     o.omp = 1.0 - Pi.Pr;
     o.Pres = 1.0 - exp(-sbgk * itau);
+    if constexpr (kQ) {
+      const double fq = 0.5 * fN * iN1 * (tab ? a.rcp[Ni - 2] : 1.0 / (fN - 2.0));
+      o.q[0] = fq * mS3x;
+      o.q[1] = fq * mS3y;
+      o.q[2] = fq * mS3z;
+      const double qn = sqrt(o.q[0] * o.q[0] + o.q[1] * o.q[1] + o.q[2] * o.q[2]);
+      o.Amax = 1.0 + 20.0 * (1.0 - Pi.Pr) * qn / (RTt * sRT);
+    }
   }
 }
 
+// q_s = N/(2 (N-1)(N-2)) sum |C|^2 C and A_max = 1 + 20 (1 - Pr) |q_s| /
+// (RT)^(3/2) of a Shakhov cell (Step 3, Sec. II.B), from o.RT and o.s2RT
+// of cell_math_lean (mixed precision: the sums are taken after Step 4,
+// in the Shakhov cells only).
+__device__ __forceinline__ void shakhov_q_amax(const StepArgs& a, const InstParams& Pi, int Ni, double S3x,
+                                               double S3y, double S3z, CellMath<double>& o) {
+  const double fN = (double)Ni;
+  const bool tab = Ni <= kHugeCell;
+  const double fq = 0.5 * fN * (tab ? a.rcp[Ni - 1] * a.rcp[Ni - 2] : 1.0 / ((fN - 1.0) * (fN - 2.0)));
+  o.q[0] = fq * S3x;
+  o.q[1] = fq * S3y;
+  o.q[2] = fq * S3z;
+  const double qn = sqrt(o.q[0] * o.q[0] + o.q[1] * o.q[1] + o.q[2] * o.q[2]);
+  const double sRT = o.s2RT * 0.70710678118654752440;
+  o.Amax = 1.0 + 20.0 * (1.0 - Pi.Pr) * qn / (o.RT * sRT);
+}
+
 // vol_k: the cell volume V (FP64 and all-FP32 modes) or 1/V (mixed).
-template <class T, class A>
+// kQ false (mixed precision): sum |C|^2 C is not given; q_s and A_max come
+// later from shakhov_q_amax.
+template <class T, class A, bool kQ = true>
 __device__ __forceinline__ void cell_math(const StepArgs& a, const InstParams& Pi, int64_t kc, uint32_t kl, int Ni,
                                           A m0, A m1, A m2, A mS2, A mS3x, A mS3y, A mS3z, double vol_k,
                                           T smaxT, double dt_cur, uint32_t step, CellMath<A>& o) {
   if constexpr (mixed_prec<T, A>()) {
-    cell_math_lean<T>(a, Pi, kc, kl, Ni, m0, m1, m2, mS2, mS3x, mS3y, mS3z, vol_k, smaxT, dt_cur, step, o);
+    cell_math_lean<T, kQ>(a, Pi, kc, kl, Ni, m0, m1, m2, mS2, mS3x, mS3y, mS3z, vol_k, smaxT, dt_cur, step, o);
     return;
   }
   const A V = (A)vol_k;
@@ -1340,8 +1362,11 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       }
     }
     __syncwarp();
-    A r2[4];
-    cell_sums<Acc, 4>(two_pass, offi, Ni, r2, [&](int s, int c, T* v, T* lo) {
+    // the second pass: sum |C|^2 and sum |C|^2 C (mixed precision: sum |C|^2
+    // only; sum |C|^2 C, needed by the Shakhov cells alone, after Step 4)
+    constexpr int K2 = kMixed ? 1 : 4;
+    A r2[K2];
+    cell_sums<Acc, K2>(two_pass, offi, Ni, r2, [&](int s, int c, T* v, T* lo) {
       T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
       if constexpr (kMixed) {
         C0 -= ct->Kl[0][c];
@@ -1350,10 +1375,13 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       }
       const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
       v[0] = c2;
-      v[1] = c2 * C0;
-      v[2] = c2 * C1;
-      v[3] = c2 * C2;
-      lo[0] = lo[1] = lo[2] = lo[3] = 0;
+      lo[0] = 0;
+      if constexpr (K2 == 4) {
+        v[1] = c2 * C0;
+        v[2] = c2 * C1;
+        v[3] = c2 * C2;
+        lo[1] = lo[2] = lo[3] = 0;
+      }
     });
     if (two_pass) {
       m0 = r1[0];
@@ -1361,9 +1389,11 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       m2 = r1[2];
       if (Ni >= 2) {
         mS2 = r2[0];
-        mS3x = r2[1];
-        mS3y = r2[2];
-        mS3z = r2[3];
+        if constexpr (K2 == 4) {
+          mS3x = r2[1];
+          mS3y = r2[2];
+          mS3z = r2[3];
+        }
       }
     }
     __syncwarp();
@@ -1377,15 +1407,15 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   if (own) {
     sample = (int64_t)step >= (int64_t)Pi.n_steady;
     smaxT = (T)smax_k;
-    cell_math<T, A>(a, Pi, kc, (uint32_t)ct->kl[lane], Ni, m0, m1, m2, mS2, mS3x, mS3y, mS3z, vol_k, smaxT,
-                    a.dt_cur[inst], step, cm);
+    cell_math<T, A, !kMixed>(a, Pi, kc, (uint32_t)ct->kl[lane], Ni, m0, m1, m2, mS2, mS3x, mS3y, mS3z, vol_k,
+                             smaxT, a.dt_cur[inst], step, cm);
     ct->dt[lane] = (T)cm.dtG;
     ct->Pres[lane] = 0;
     if (cm.shk) {
       ct->RT[lane] = (T)cm.RT;
       ct->s2RT[lane] = (T)cm.s2RT;
-      ct->Amax[lane] = (T)cm.Amax;
       ct->omp[lane] = (T)cm.omp;
+      if constexpr (!kMixed) ct->Amax[lane] = (T)cm.Amax;
     }
     if constexpr (kMixed) {  // the FP32 mean of the shift (U_h), no conversion
       ct->U[0][lane] = ct->Up[0][lane];
@@ -1396,10 +1426,35 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       ct->U[1][lane] = (T)cm.U[1];
       ct->U[2][lane] = (T)cm.U[2];
     }
-    if (cm.shk) {  // the Shakhov sampling reads q_s in these cells only
+    if (!kMixed && cm.shk) {  // the Shakhov sampling reads q_s in these cells only
       ct->q[0][lane] = (T)cm.q[0];
       ct->q[1][lane] = (T)cm.q[1];
       ct->q[2][lane] = (T)cm.q[2];
+    }
+  }
+  if constexpr (kMixed) {
+    // sum |C|^2 C about the Step 3 mean (the pair U_h + U_l), in the cells
+    // with a Shakhov part only, before the DSMC sub-step moves any velocity
+    const bool qsh = own && cm.shk;
+    if (__any_sync(kFull, qsh)) {
+      A r3[3];
+      cell_sums<Acc, 3>(qsh, offi, Ni, r3, [&](int s, int c, T* v, T* lo) {
+        const T C0 = (svx[s] - ct->Up[0][c]) - ct->Kl[0][c];
+        const T C1 = (svy[s] - ct->Up[1][c]) - ct->Kl[1][c];
+        const T C2 = (svz[s] - ct->Up[2][c]) - ct->Kl[2][c];
+        const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+        v[0] = c2 * C0;
+        v[1] = c2 * C1;
+        v[2] = c2 * C2;
+        lo[0] = lo[1] = lo[2] = 0;
+      });
+      if (qsh) {
+        shakhov_q_amax(a, Pi, Ni, r3[0], r3[1], r3[2], cm);
+        ct->q[0][lane] = (T)cm.q[0];
+        ct->q[1][lane] = (T)cm.q[1];
+        ct->q[2][lane] = (T)cm.q[2];
+        ct->Amax[lane] = (T)cm.Amax;
+      }
     }
   }
   const int64_t ncol = cm.ncol;
