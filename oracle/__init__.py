@@ -35,7 +35,8 @@ class OrConfig(C.Structure):
         ("sigc_T0", C.c_double), ("n_steady", C.c_int32), ("seed", C.c_uint64),
         ("mode", C.c_int32), ("ar_max", C.c_int32), ("n_surf", C.c_int32),
         ("win_lo", (C.c_double * 2) * 6), ("win_hi", (C.c_double * 2) * 6), ("ntc_carry", C.c_int32),
-        ("subcells", C.c_int32),
+        ("subcells", C.c_int32), ("mesh", C.c_int32), ("mesh_r_out", C.c_double),
+        ("mesh_growth", C.c_double),
     ]
 
 
@@ -69,6 +70,9 @@ def lib():
         L.or_subcell_order.argtypes = [C.POINTER(OrConfig), C.c_int64, P, C.c_int64, P, P]
         L.or_get_threads.argtypes = [P]
         L.or_get_surface.argtypes = [P, P, P]
+        L.or_mesh_locate.argtypes = [P, P, C.c_int64, P]
+        L.or_mesh_geometry.argtypes = [P, P, P, P]
+        L.or_get_volumes.argtypes = [P, P]
         L.or_free.argtypes = [P]
         L.or_philox4x32_10.argtypes = [P, P, P]
         L.or_u01_from_words.argtypes = [C.c_uint32, C.c_uint32]
@@ -122,6 +126,9 @@ def make_config(cfg: dict):
             s.win_hi[f][i] = cfg.get("win_hi", [[0.0, 0.0]] * 6)[f][i]
     s.ntc_carry = int(cfg.get("ntc_carry", 0))
     s.subcells = int(cfg.get("subcells", 0))
+    s.mesh = int(cfg.get("mesh", 0))
+    s.mesh_r_out = float(cfg.get("mesh_r_out", 0.0))
+    s.mesh_growth = float(cfg.get("mesh_growth", 1.0))
     return s, keep
 
 
@@ -283,3 +290,30 @@ class Oracle:
         lib().or_get_totals(self.h, _ptr(out))
         return dict(removed=int(out[0]), injected=int(out[1]), move_capped=int(out[2]),
                     ar_capped=int(out[3]))
+
+    def volumes(self):
+        out = np.zeros(self.ncells)
+        lib().or_get_volumes(self.h, _ptr(out))
+        return out
+
+    def mesh_locate(self, pos):
+        """O-grid: the cell of each point of pos [2][n] (face-crossing walk), -1 outside."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        n = pos.shape[1]
+        out = np.zeros(max(n, 1), dtype=np.int64)
+        rc = lib().or_mesh_locate(self.h, _ptr(pos), n, _ptr(out))
+        if rc != 0:
+            raise ValueError("not an O-grid context")
+        return out[:n]
+
+    def mesh_geometry(self):
+        """O-grid: (nodes [(nr + ghost_layers + 1) * nt][2], faces [ncells][4][3], L [ncells])."""
+        nr, nt = self.cfg["n"][0], self.cfg["n"][1]
+        nn = (nr + max(int(self.cfg["ghost_layers"]), 0) + 1) * nt
+        nodes = np.zeros((nn, 2))
+        faces = np.zeros((self.ncells, 4, 3))
+        L = np.zeros(self.ncells)
+        rc = lib().or_mesh_geometry(self.h, _ptr(nodes), _ptr(faces), _ptr(L))
+        if rc != 0:
+            raise ValueError("not an O-grid context")
+        return nodes, faces, L

@@ -102,6 +102,13 @@ struct or_ctx {
   double surf_time;
   int sampling_now;
   int nthreads; /* threads of the per-cell loop of a step (OpenMP; 1 = sequential) */
+  double *Lc;   /* [ncells] cell size L of Delta t_c (uniform grid: L_min) */
+  /* body-fitted O-grid (cfg.mesh == 1) */
+  int mnr, mnt, mnl; /* radial layers, sectors, reservoir layers */
+  double *mrad;      /* [mnr + mnl + 1] node radii */
+  double *mnode;     /* [(mnr + mnl + 1) * mnt][2] node coordinates */
+  double *mrel;      /* the same relative to the body centre (areas) */
+  double *mface;     /* [ncells][4][3] outward unit normal, offset */
 };
 
 /* ---------------------------------------------------------------------
@@ -203,9 +210,9 @@ static void moments_of(const or_ctx* c, int64_t k, const part* ps, int64_t N, mo
     o->p = o->n * g->m * g->R * o->T;
     double mu = g->mu_ref * pow(o->T / g->T_ref, g->omega);
     o->tau = mu / o->p;
-    o->dtc = c->Lmin / (umag + sqrt(g->gamma * g->R * o->T));
+    o->dtc = c->Lc[k] / (umag + sqrt(g->gamma * g->R * o->T));
   } else if (umag > 0) {
-    o->dtc = c->Lmin / umag;
+    o->dtc = c->Lc[k] / umag;
   }
 }
 
@@ -453,6 +460,49 @@ static int face_open(const or_config* g, int f, const double* x) {
   return 1;
 }
 
+/* Surface tallies of one body hit (Step 5 sampling of the wall fluxes):
+ * the momentum and energy the wall receives, binned by the polar angle of
+ * the inward normal nv at the hit point. */
+static void tally_hit(or_ctx* c, const double* nv, const double* vin, const double* v) {
+  const or_config* g = &c->cfg;
+  if (!(c->sampling_now && g->n_surf > 0)) return;
+  int ns = g->n_surf;
+  double th, frac;
+  if (g->body == OR_BODY_CIRCLE) {
+    th = atan2(nv[1], nv[0]);
+    frac = (th + M_PI) / (2.0 * M_PI);
+  } else {
+    double cx = nv[0] < -1.0 ? -1.0 : (nv[0] > 1.0 ? 1.0 : nv[0]);
+    th = acos(cx);
+    frac = th / M_PI;
+  }
+  int bin = (int)floor(frac * (double)ns);
+  if (bin < 0) bin = 0;
+  if (bin > ns - 1) bin = ns - 1;
+  double w = g->Fn * g->m;
+  double ein = vin[0] * vin[0] + vin[1] * vin[1] + vin[2] * vin[2];
+  double eout = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double dp[3], et[3] = {0, 0, 0};
+  for (int d = 0; d < 3; ++d) dp[d] = w * (vin[d] - v[d]);
+  /* direction of increasing polar angle at the hit point */
+  if (g->body == OR_BODY_CIRCLE) {
+    et[0] = -nv[1];
+    et[1] = nv[0];
+  } else {
+    double sn = sqrt(nv[1] * nv[1] + nv[2] * nv[2]);
+    if (sn > 0) {
+      et[0] = -sn;
+      et[1] = nv[0] * nv[1] / sn;
+      et[2] = nv[0] * nv[2] / sn;
+    }
+  }
+  c->surf[0 * ns + bin] += 1.0;
+  for (int d = 0; d < 3; ++d) c->surf[(1 + d) * ns + bin] += dp[d];
+  c->surf[4 * ns + bin] += 0.5 * w * (ein - eout);
+  c->surf[5 * ns + bin] -= dp[0] * nv[0] + dp[1] * nv[1] + dp[2] * nv[2];
+  c->surf[6 * ns + bin] += dp[0] * et[0] + dp[1] * et[1] + dp[2] * et[2];
+}
+
 static int move_particle(or_ctx* c, double* x, double* v, double trem, uint32_t purpose, uint32_t a,
                          uint32_t b, uint32_t subbase) {
   const or_config* g = &c->cfg;
@@ -518,44 +568,7 @@ static int move_particle(or_ctx* c, double* x, double* v, double trem, uint32_t 
       diffuse_sample(c, g->body_Tw, purpose, a, b, sub, &cn, &t1, &t2);
       double vin[3] = {v[0], v[1], v[2]};
       for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
-      if (c->sampling_now && g->n_surf > 0) {
-        /* momentum and energy the wall receives from this hit */
-        int ns = g->n_surf;
-        double th, frac;
-        if (g->body == OR_BODY_CIRCLE) {
-          th = atan2(nv[1], nv[0]);
-          frac = (th + M_PI) / (2.0 * M_PI);
-        } else {
-          double cx = nv[0] < -1.0 ? -1.0 : (nv[0] > 1.0 ? 1.0 : nv[0]);
-          th = acos(cx);
-          frac = th / M_PI;
-        }
-        int bin = (int)floor(frac * (double)ns);
-        if (bin < 0) bin = 0;
-        if (bin > ns - 1) bin = ns - 1;
-        double w = g->Fn * g->m;
-        double ein = vin[0] * vin[0] + vin[1] * vin[1] + vin[2] * vin[2];
-        double eout = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        double dp[3], et[3] = {0, 0, 0};
-        for (int d = 0; d < 3; ++d) dp[d] = w * (vin[d] - v[d]);
-        /* direction of increasing polar angle at the hit point */
-        if (g->body == OR_BODY_CIRCLE) {
-          et[0] = -nv[1];
-          et[1] = nv[0];
-        } else {
-          double sn = sqrt(nv[1] * nv[1] + nv[2] * nv[2]);
-          if (sn > 0) {
-            et[0] = -sn;
-            et[1] = nv[0] * nv[1] / sn;
-            et[2] = nv[0] * nv[2] / sn;
-          }
-        }
-        c->surf[0 * ns + bin] += 1.0;
-        for (int d = 0; d < 3; ++d) c->surf[(1 + d) * ns + bin] += dp[d];
-        c->surf[4 * ns + bin] += 0.5 * w * (ein - eout);
-        c->surf[5 * ns + bin] -= dp[0] * nv[0] + dp[1] * nv[1] + dp[2] * nv[2];
-        c->surf[6 * ns + bin] += dp[0] * et[0] + dp[1] * et[1] + dp[2] * et[2];
-      }
+      tally_hit(c, nv, vin, v);
       continue;
     }
     for (int d = 0; d < g->dim; ++d)
@@ -578,6 +591,202 @@ static int move_particle(or_ctx* c, double* x, double* v, double trem, uint32_t 
     }
   }
 }
+
+/* ---------------------------------------------------------------------
+ * Body-fitted O-grid (option, 2-D): straight-edged quadrilaterals between
+ * the body polygon and the outer polygon.  A particle carries its cell and
+ * finds the next one by face crossing: from its position it leaves the
+ * cell through the face whose line its straight path meets first among
+ * the faces it moves towards (exit times below zero count as zero, so a
+ * point that rounding left just outside a face leaves at once), crosses
+ * into the neighbour, and repeats until the remaining time ends inside the
+ * current cell.
+ * ------------------------------------------------------------------- */
+#define MESH_TWO_PI (2.0 * 3.14159265358979323846)
+#define MAX_CROSS 4096
+
+static const double* mesh_node(const or_ctx* c, int i, int j) {
+  int jj = j % c->mnt;
+  return c->mnode + 2 * ((int64_t)i * c->mnt + jj);
+}
+static const double* mesh_rel(const or_ctx* c, int i, int j) {
+  int jj = j % c->mnt;
+  return c->mrel + 2 * ((int64_t)i * c->mnt + jj);
+}
+
+/* Shoelace area of the quadrilateral p0 p1 p2 p3 (counter-clockwise). */
+static double quad_area(const double* p0, const double* p1, const double* p2, const double* p3) {
+  return 0.5 * ((p0[0] * p1[1] - p1[0] * p0[1]) + (p1[0] * p2[1] - p2[0] * p1[1]) +
+                (p2[0] * p3[1] - p3[0] * p2[1]) + (p3[0] * p0[1] - p0[0] * p3[1]));
+}
+static double tri_area(const double* p0, const double* p1, const double* p2) {
+  return 0.5 * ((p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]));
+}
+
+/* Unit outward normal and offset (n.x = d on the line) of the edge p -> q
+ * of a counter-clockwise cell; returns the edge length. */
+static double edge_line(const double* p, const double* q, double* f) {
+  double tx = q[0] - p[0], ty = q[1] - p[1];
+  double len = sqrt(tx * tx + ty * ty);
+  f[0] = ty / len;
+  f[1] = -tx / len;
+  f[2] = f[0] * p[0] + f[1] * p[1];
+  return len;
+}
+
+static int mesh_build(or_ctx* c) {
+  or_config* g = &c->cfg;
+  if (g->dim != 2 || g->body != OR_BODY_CIRCLE || g->n[0] < 1 || g->n[1] < 3 || !(g->body_r > 0) ||
+      !(g->mesh_r_out > g->body_r) || !(g->mesh_growth > 0) || g->subcells > 1)
+    return OR_ERR_ARG;
+  int nr = g->n[0], nt = g->n[1], nl = g->ghost_layers > 0 ? g->ghost_layers : 0;
+  c->mnr = nr;
+  c->mnt = nt;
+  c->mnl = nl;
+  int nrad = nr + nl + 1;
+  c->mrad = (double*)malloc(sizeof(double) * nrad);
+  /* spacing dr_0 with dr_0 (1 + q + ... + q^(nr-1)) = r_out - r_0 */
+  double q = g->mesh_growth, geo = 0.0, qp = 1.0;
+  for (int i = 0; i < nr; ++i) {
+    geo += qp;
+    qp *= q;
+  }
+  double dr = (g->mesh_r_out - g->body_r) / geo;
+  c->mrad[0] = g->body_r;
+  for (int i = 0; i + 1 < nrad; ++i) {
+    c->mrad[i + 1] = c->mrad[i] + dr;
+    dr *= q;
+  }
+  c->mnode = (double*)malloc(sizeof(double) * 2 * (size_t)nrad * nt);
+  c->mrel = (double*)malloc(sizeof(double) * 2 * (size_t)nrad * nt);
+  for (int i = 0; i < nrad; ++i)
+    for (int j = 0; j < nt; ++j) {
+      double th = MESH_TWO_PI * (double)j / (double)nt;
+      double rx = c->mrad[i] * cos(th), ry = c->mrad[i] * sin(th);
+      int64_t o = 2 * ((int64_t)i * nt + j);
+      c->mrel[o] = rx;
+      c->mrel[o + 1] = ry;
+      c->mnode[o] = g->body_c[0] + rx;
+      c->mnode[o + 1] = g->body_c[1] + ry;
+    }
+  c->mface = (double*)malloc(sizeof(double) * 12 * (size_t)c->ncells);
+  double depth = g->hi[2] - g->lo[2];
+  for (int j = 0; j < nt; ++j)
+    for (int i = 0; i < nr; ++i) {
+      int64_t k = i + (int64_t)nr * j;
+      const double *A = mesh_node(c, i, j), *B = mesh_node(c, i + 1, j);
+      const double *C = mesh_node(c, i + 1, j + 1), *D = mesh_node(c, i, j + 1);
+      double* f = c->mface + 12 * k;
+      double l0 = edge_line(D, A, f + 0);  /* inner */
+      double l1 = edge_line(B, C, f + 3);  /* outer */
+      double l2 = edge_line(A, B, f + 6);  /* theta_j */
+      double l3 = edge_line(C, D, f + 9);  /* theta_j+1 */
+      double L = l0;
+      if (l1 < L) L = l1;
+      if (l2 < L) L = l2;
+      if (l3 < L) L = l3;
+      c->Lc[k] = L;
+      c->vol[k] = quad_area(mesh_rel(c, i, j), mesh_rel(c, i + 1, j), mesh_rel(c, i + 1, j + 1),
+                            mesh_rel(c, i, j + 1)) * depth;
+    }
+  return OR_OK;
+}
+
+/* Walk of one particle of cell *k for time trem (O-grid): interior faces
+ * hand it to the neighbour, the body polygon re-emits it diffusely at
+ * body_Tw, the outer polygon removes it (inflow, outflow), reflects it
+ * (specular) or re-emits it (diffuse at face_T[1]).  locate != 0: the
+ * point location walk (boundary faces end it with -1 instead).  Draws of
+ * wall event b: (step, a, bb, purpose<<24 | subbase + 2b), as for the
+ * Cartesian walls.  Returns 1 when the particle left the domain. */
+static int mesh_walk(or_ctx* c, int64_t* k, double* x, double* v, double trem, uint32_t purpose,
+                     uint32_t a, uint32_t bb, uint32_t subbase, int locate) {
+  const or_config* g = &c->cfg;
+  int nr = c->mnr, nt = c->mnt, bounce = 0;
+  for (int cross = 0;; ++cross) {
+    if (cross >= MAX_CROSS) {
+      if (locate) return 1;
+      c->totals[2] += 1;
+      return 0;
+    }
+    const double* f = c->mface + 12 * *k;
+    double tmin = INFINITY;
+    int fm = -1;
+    for (int e = 0; e < 4; ++e) {
+      double nvv = f[3 * e] * v[0] + f[3 * e + 1] * v[1];
+      if (nvv > 0) {
+        double t = (f[3 * e + 2] - (f[3 * e] * x[0] + f[3 * e + 1] * x[1])) / nvv;
+        if (t < 0) t = 0;
+        if (t < tmin) {
+          tmin = t;
+          fm = e;
+        }
+      }
+    }
+    if (!(tmin < trem)) {
+      x[0] += v[0] * trem;
+      x[1] += v[1] * trem;
+      return 0;
+    }
+    x[0] += v[0] * tmin;
+    x[1] += v[1] * tmin;
+    trem -= tmin;
+    int i = (int)(*k % nr), j = (int)(*k / nr);
+    if (fm == 2) { *k = i + (int64_t)nr * ((j + nt - 1) % nt); continue; }
+    if (fm == 3) { *k = i + (int64_t)nr * ((j + 1) % nt); continue; }
+    if (fm == 0 && i > 0) { *k -= 1; continue; }
+    if (fm == 1 && i < nr - 1) { *k += 1; continue; }
+    if (locate) return 1;
+    if (bounce >= MAX_BOUNCE) { c->totals[2] += 1; return 0; }
+    uint32_t sub = subbase + 2u * (uint32_t)bounce;
+    ++bounce;
+    /* a boundary face: normal into the domain */
+    double nv[3] = {-f[3 * fm], -f[3 * fm + 1], 0};
+    double Tw;
+    if (fm == 1) {
+      int bc = g->face_bc[1];
+      if (bc == OR_BC_OUTFLOW || bc == OR_BC_INFLOW) return 1;
+      if (bc == OR_BC_SPECULAR) {
+        double vn = f[3] * v[0] + f[4] * v[1];
+        v[0] -= 2.0 * vn * f[3];
+        v[1] -= 2.0 * vn * f[4];
+        continue;
+      }
+      Tw = g->face_T[1];
+    } else {
+      Tw = g->body_Tw;
+    }
+    double e1[3] = {-nv[1], nv[0], 0}, e2[3] = {0, 0, 1};
+    double cn, t1, t2;
+    diffuse_sample(c, Tw, purpose, a, bb, sub, &cn, &t1, &t2);
+    double vin[3] = {v[0], v[1], v[2]};
+    for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
+    if (fm == 0) tally_hit(c, nv, vin, v);
+  }
+}
+
+/* The cell of point x (O-grid): a first guess from the point's polar
+ * coordinates, then the walk from that cell's centroid to x; -1 outside. */
+static int64_t mesh_locate(const or_ctx* c, const double* x) {
+  const or_config* g = &c->cfg;
+  int nr = c->mnr, nt = c->mnt;
+  double dx = x[0] - g->body_c[0], dy = x[1] - g->body_c[1];
+  double r = sqrt(dx * dx + dy * dy), th = atan2(dy, dx);
+  if (th < 0) th += MESH_TWO_PI;
+  int j = (int)floor(th * (double)nt / MESH_TWO_PI);
+  if (j < 0) j = 0;
+  if (j > nt - 1) j = nt - 1;
+  int i = 0;
+  while (i < nr - 1 && c->mrad[i + 1] <= r) ++i;
+  int64_t k = i + (int64_t)nr * j;
+  const double *A = mesh_node(c, i, j), *B = mesh_node(c, i + 1, j);
+  const double *C = mesh_node(c, i + 1, j + 1), *D = mesh_node(c, i, j + 1);
+  double p[2] = {0.25 * (A[0] + B[0] + C[0] + D[0]), 0.25 * (A[1] + B[1] + C[1] + D[1])};
+  double w[3] = {x[0] - p[0], x[1] - p[1], 0};
+  if (mesh_walk((or_ctx*)c, &k, p, w, 1.0, 0, 0, 0, 0, 1)) return -1;
+  return k;
+}
+
 
 /* ---------------------------------------------------------------------
  * Context
@@ -603,9 +812,22 @@ int or_init(const or_config* cfg, or_ctx** out) {
     if (c->dl[d] < c->Lmin) c->Lmin = c->dl[d];
   c->ncells = (int64_t)g->n[0] * g->n[1] * g->n[2];
   c->vol = (double*)malloc(sizeof(double) * c->ncells);
+  c->Lc = (double*)malloc(sizeof(double) * (c->ncells > 0 ? c->ncells : 1));
   double v0 = c->dl[0] * c->dl[1] * c->dl[2];
-  for (int64_t k = 0; k < c->ncells; ++k) c->vol[k] = cfg->cell_volume ? cfg->cell_volume[k] : v0;
+  for (int64_t k = 0; k < c->ncells; ++k) {
+    c->vol[k] = cfg->cell_volume ? cfg->cell_volume[k] : v0;
+    c->Lc[k] = c->Lmin;
+  }
   g->cell_volume = NULL;
+  if (g->mesh == 1) {
+    if (mesh_build(c) != OR_OK) {
+      or_free(c);
+      return OR_ERR_ARG;
+    }
+  } else if (g->mesh != 0) {
+    or_free(c);
+    return OR_ERR_ARG;
+  }
   c->sigc_coef = M_PI * g->d_ref * g->d_ref * pow(4.0 * g->R * g->T_ref, g->omega - 0.5) /
                  tgamma(2.5 - g->omega);
   c->sigc_exp = 2.0 - 2.0 * g->omega;
@@ -631,6 +853,7 @@ void or_free(or_ctx* c) {
   if (!c) return;
   free(c->vol); free(c->p); free(c->start); free(c->smax); free(c->rem); free(c->samp);
   free(c->rec); free(c->resamp); free(c->perm); free(c->surf);
+  free(c->Lc); free(c->mrad); free(c->mnode); free(c->mrel); free(c->mface);
   free(c);
 }
 
@@ -677,7 +900,12 @@ int or_set_particles(or_ctx* c, const double* pos, const double* vel, int64_t M)
   for (int64_t i = 0; i < M; ++i) {
     for (int d = 0; d < g->dim; ++d) src[i].x[d] = pos[d * M + i];
     for (int d = 0; d < 3; ++d) src[i].v[d] = vel[d * M + i];
-    keys[i] = (uint32_t)cell_of(c, src[i].x);
+    if (g->mesh) {
+      int64_t k = mesh_locate(c, src[i].x);
+      keys[i] = k < 0 ? SENTINEL : (uint32_t)k;
+    } else {
+      keys[i] = (uint32_t)cell_of(c, src[i].x);
+    }
   }
   sort_into_cells(c, src, keys, M);
   free(src);
@@ -806,6 +1034,90 @@ static void inject(or_ctx* c, part** buf, uint32_t** keys, int64_t* n, int64_t* 
   }
 }
 
+/* Reservoir injection through the outer polygon of the O-grid (face 1 an
+ * inflow boundary): ghost_layers rings of reservoir quadrilaterals beyond
+ * it, continuing the radial spacing, refilled each step with
+ * floor(n V / F_N + u) particles at the face state, uniform in each
+ * quadrilateral (its two triangles A B C and A C D chosen by area).  A
+ * particle whose straight path enters the outer polygon within the step
+ * through one of the ghost_layers + 1 outer edges on either side of its
+ * sector (the same truncation as the Cartesian reservoir's depth) enters
+ * at the crossing and walks the rest of the step.  Order: layer, sector,
+ * particle. */
+static void inject_mesh(or_ctx* c, part** buf, uint32_t** keys, int64_t* n, int64_t* cap) {
+  const or_config* g = &c->cfg;
+  if (g->face_bc[1] != OR_BC_INFLOW) return;
+  int nr = c->mnr, nt = c->mnt, nl = c->mnl, w = nl + 1;
+  double dt = c->dt, depth = g->hi[2] - g->lo[2];
+  double RT = g->R * g->face_T[1];
+  double s2RT = sqrt(2.0 * RT);
+  uint32_t sb = 1u * 16u;
+  for (int64_t gc = 0; gc < (int64_t)nl * nt; ++gc) {
+    int L = (int)(gc / nt), j = (int)(gc % nt), i0 = nr + L;
+    double a1 = tri_area(mesh_rel(c, i0, j), mesh_rel(c, i0 + 1, j), mesh_rel(c, i0 + 1, j + 1));
+    double a2 = tri_area(mesh_rel(c, i0, j), mesh_rel(c, i0 + 1, j + 1), mesh_rel(c, i0, j + 1));
+    const double *A = mesh_node(c, i0, j), *B = mesh_node(c, i0 + 1, j);
+    const double *C = mesh_node(c, i0 + 1, j + 1), *D = mesh_node(c, i0, j + 1);
+    double lam = g->face_n[1] * (a1 + a2) * depth / g->Fn;
+    int64_t ng = (int64_t)floor(lam + uq(c, (uint32_t)gc, SENTINEL, PURP_INJ, sb, 0));
+    for (int64_t m = 0; m < ng; ++m) {
+      part q;
+      memset(&q, 0, sizeof q);
+      double u0 = uq(c, (uint32_t)gc, (uint32_t)m, PURP_INJ, sb, 0);
+      double s = uq(c, (uint32_t)gc, (uint32_t)m, PURP_INJ, sb, 1);
+      double t = uq(c, (uint32_t)gc, (uint32_t)m, PURP_INJ, sb, 2);
+      if (s + t > 1.0) {
+        s = 1.0 - s;
+        t = 1.0 - t;
+      }
+      const double* P1 = B;
+      const double* P2 = C;
+      if (!(u0 * (a1 + a2) < a1)) {
+        P1 = C;
+        P2 = D;
+      }
+      q.x[0] = A[0] + s * (P1[0] - A[0]) + t * (P2[0] - A[0]);
+      q.x[1] = A[1] + s * (P1[1] - A[1]) + t * (P2[1] - A[1]);
+      double R1 = uq(c, (uint32_t)gc, (uint32_t)m, PURP_INJ, sb, 3);
+      double R2 = uq(c, (uint32_t)gc, (uint32_t)m, PURP_INJ, sb, 4);
+      double R3 = uq(c, (uint32_t)gc, (uint32_t)m, PURP_INJ, sb, 5);
+      double R4 = uq(c, (uint32_t)gc, (uint32_t)m, PURP_INJ, sb, 6);
+      double r2 = sqrt(-log(R2)), r4 = sqrt(-log(R4));
+      q.v[0] = g->face_u[1][0] + s2RT * cos(2.0 * M_PI * R1) * r2;
+      q.v[1] = g->face_u[1][1] + s2RT * cos(2.0 * M_PI * R3) * r4;
+      q.v[2] = g->face_u[1][2] + s2RT * sin(2.0 * M_PI * R3) * r4;
+      /* first crossing of an outer edge within the step */
+      double best = INFINITY;
+      int jb = -1;
+      for (int o = -w; o <= w; ++o) {
+        int jj = ((j + o) % nt + nt) % nt;
+        const double* f = c->mface + 12 * ((nr - 1) + (int64_t)nr * jj) + 3;
+        double nvv = f[0] * q.v[0] + f[1] * q.v[1];
+        if (!(nvv < 0)) continue;
+        double sx = f[0] * q.x[0] + f[1] * q.x[1];
+        if (!(sx > f[2])) continue;
+        double te = (f[2] - sx) / nvv;
+        if (!(te < dt) || !(te < best)) continue;
+        const double *E0 = mesh_node(c, nr, jj), *E1 = mesh_node(c, nr, jj + 1);
+        double ex = E1[0] - E0[0], ey = E1[1] - E0[1];
+        double xc = q.x[0] + q.v[0] * te, yc = q.x[1] + q.v[1] * te;
+        double u = ((xc - E0[0]) * ex + (yc - E0[1]) * ey) / (ex * ex + ey * ey);
+        if (u < 0.0 || u > 1.0) continue;
+        best = te;
+        jb = jj;
+      }
+      if (jb < 0) continue;
+      q.x[0] += q.v[0] * best;
+      q.x[1] += q.v[1] * best;
+      int64_t k = (nr - 1) + (int64_t)nr * jb;
+      if (mesh_walk(c, &k, q.x, q.v, dt - best, PURP_INJWALL, (uint32_t)gc, (uint32_t)m, 1u << 16, 0))
+        continue;
+      append(buf, keys, n, cap, &q, (uint32_t)k);
+      c->totals[1] += 1;
+    }
+  }
+}
+
 int or_step(or_ctx* c, int nsteps) {
   const or_config* g = &c->cfg;
   for (int it = 0; it < nsteps; ++it) {
@@ -867,13 +1179,24 @@ int or_step(or_ctx* c, int nsteps) {
       int64_t s0 = c->start[k], N = c->start[k + 1] - s0;
       for (int64_t s = 0; s < N; ++s) {
         part q = c->p[s0 + s];
-        int gone = move_particle(c, q.x, q.v, dtG, PURP_WALL, (uint32_t)k, (uint32_t)s, 0);
-        uint32_t key = gone ? SENTINEL : (uint32_t)cell_of(c, q.x);
+        int gone;
+        uint32_t key;
+        if (g->mesh) {
+          int64_t k2 = k;
+          gone = mesh_walk(c, &k2, q.x, q.v, dtG, PURP_WALL, (uint32_t)k, (uint32_t)s, 0, 0);
+          key = gone ? SENTINEL : (uint32_t)k2;
+        } else {
+          gone = move_particle(c, q.x, q.v, dtG, PURP_WALL, (uint32_t)k, (uint32_t)s, 0);
+          key = gone ? SENTINEL : (uint32_t)cell_of(c, q.x);
+        }
         if (gone) c->totals[0] += 1;
         append(&buf, &keys, &n, &cap, &q, key);
       }
     }
-    inject(c, &buf, &keys, &n, &cap);
+    if (g->mesh)
+      inject_mesh(c, &buf, &keys, &n, &cap);
+    else
+      inject(c, &buf, &keys, &n, &cap);
     sort_into_cells(c, buf, keys, n);
     free(buf);
     free(keys);
@@ -1028,5 +1351,29 @@ int or_collide_cell(const or_config* cfg, int64_t step, uint32_t cell, double vo
     for (int d = 0; d < 3; ++d) vel[d * N + i] = ps[i].v[d];
   free(ps);
   or_free(c);
+  return OR_OK;
+}
+
+int or_mesh_locate(const or_ctx* c, const double* pos, int64_t n, int64_t* cell) {
+  if (!c || c->cfg.mesh != 1 || n < 0) return OR_ERR_ARG;
+  for (int64_t i = 0; i < n; ++i) {
+    double x[2] = {pos[i], pos[n + i]};
+    cell[i] = mesh_locate(c, x);
+  }
+  return OR_OK;
+}
+
+int or_mesh_geometry(const or_ctx* c, double* nodes, double* faces, double* L) {
+  if (!c || c->cfg.mesh != 1) return OR_ERR_ARG;
+  int64_t nn = (int64_t)(c->mnr + c->mnl + 1) * c->mnt;
+  if (nodes) memcpy(nodes, c->mnode, sizeof(double) * 2 * nn);
+  if (faces) memcpy(faces, c->mface, sizeof(double) * 12 * c->ncells);
+  if (L) memcpy(L, c->Lc, sizeof(double) * c->ncells);
+  return OR_OK;
+}
+
+int or_get_volumes(const or_ctx* c, double* vol) {
+  if (!c) return OR_ERR_ARG;
+  memcpy(vol, c->vol, sizeof(double) * c->ncells);
   return OR_OK;
 }

@@ -10,7 +10,8 @@
  * smoke check and the benchmark's CPU-baseline leg may load it.  It shares
  * no code, header or constant table with the CUDA library.
  *
- * One context = one flow instance on a uniform Cartesian grid.
+ * One context = one flow instance on a uniform Cartesian grid or a
+ * body-fitted O-grid (the mesh option below).
  */
 #ifndef SP_ORACLE_H
 #define SP_ORACLE_H
@@ -68,6 +69,20 @@ typedef struct or_config {
    * (s^dim sub-cells, at most 8) and takes a candidate's partner from the
    * first particle's sub-cell when it holds another particle. */
   int32_t subcells;
+  /* Body-fitted O-grid about a circular body (an option, 2-D only; the
+   * paper's cylinder meshes are body-fitted, Sec. IV.B).  0 = the Cartesian
+   * grid above.  1 = n[0] radial layers x n[1] sectors of straight-edged
+   * quadrilaterals between the body polygon (nodes on the circle of radius
+   * body_r about body_c) and the outer polygon (radius about mesh_r_out):
+   * node radii r_0 = body_r, r_{i+1} = r_i + dr_i with dr_{i+1} =
+   * mesh_growth * dr_i, the sum of the first n[0] spacings being
+   * mesh_r_out - body_r; node angles 2 pi j / n[1].  Cell k = i + n[0] j.
+   * The body polygon is a diffuse wall at body_Tw; the outer polygon is
+   * face 1 (face_bc[1], and for an inflow boundary face_n/T/u[1] and
+   * ghost_layers reservoir layers continuing the radial spacing).  Particles
+   * find their cell by face crossing.  lo/hi[2] give the depth. */
+  int32_t mesh;
+  double mesh_r_out, mesh_growth;
 } or_config;
 
 typedef struct or_ctx or_ctx;
@@ -120,6 +135,17 @@ int or_select_pair(int64_t N, const int64_t* soff, double u1, double u2, int64_t
 int or_subcell_order(const or_config* cfg, int64_t cell, const double* pos, int64_t N, int64_t* order,
                      int64_t* soff);
 int or_get_threads(const or_ctx* c);
+/* O-grid option: the cell containing each of n points (pos [2][n]) found
+ * by face crossing from a first guess, -1 outside the mesh (inside the
+ * body polygon or beyond the outer polygon). */
+int or_mesh_locate(const or_ctx* c, const double* pos, int64_t n, int64_t* cell);
+/* O-grid option: node coordinates [(n[0] + ghost_layers + 1) * n[1]][2]
+ * (node (i, j) at row i * n[1] + j), per-cell faces [ncells][4][3] (unit
+ * outward normal and offset n.x = d of faces inner, outer, theta_j,
+ * theta_j+1) and per-cell size L (the shortest edge). */
+int or_mesh_geometry(const or_ctx* c, double* nodes, double* faces, double* L);
+/* Cell volumes [ncells] (O-grid: quadrilateral area x depth). */
+int or_get_volumes(const or_ctx* c, double* vol);
 void or_free(or_ctx* c);
 
 /* Building blocks exported for the pin tests. */

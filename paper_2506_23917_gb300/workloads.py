@@ -74,7 +74,7 @@ def base_config(dim, n, lo, hi):
         body=BODY_NONE, body_c=[0.0, 0.0, 0.0], body_r=0.0, body_Tw=1.0,
         cell_volume=None, sigc_T0=1.0, n_steady=0, seed=1, mode=MODE_HYBRID, ar_max=64,
         n_surf=0, win_lo=[[0.0, 0.0] for _ in range(6)], win_hi=[[0.0, 0.0] for _ in range(6)],
-        ntc_carry=0, subcells=0,
+        ntc_carry=0, subcells=0, mesh=0, mesh_r_out=0.0, mesh_growth=1.0,
     )
 
 
@@ -332,6 +332,65 @@ def cylinder(scale=1.0, ppc=40.0, Kn=0.01, Ma=5.0, seed=1, n_steady=1000, T_inf=
     cfg["face_u"] = [[U, 0.0, 0.0] for _ in range(6)]
     cfg["cell_volume"] = circle_cut_volumes(cfg)
     regions = [dict(lo=[-3.0 * Rb, 0.0], hi=[3.0 * Rb, 3.0 * Rb], n=n_inf, T=T_inf, u=[U, 0, 0])]
+    return cfg, regions
+
+
+def cylinder_ogrid(nr=96, nt=192, r_out=4.0, growth=1.03, ppc=40.0, Kn=0.05, Ma=5.0, seed=1,
+                   n_steady=1000, T_inf=273.0, ghost_layers=2):
+    """2-D hypersonic argon flow past a cylinder on a body-fitted O-grid.
+
+    The cylinder case on a synthetic body-fitted mesh (the paper's own
+    cylinder meshes are body-fitted and not available): nr radial layers x
+    nt sectors of straight-edged quadrilaterals from the body (radius R = 1 m,
+    diffuse at T_inf) to radius r_out R, radial spacing growing by ``growth``
+    per layer.  The whole outer polygon is a freestream boundary (reservoir
+    of ghost_layers rings at n_inf, T_inf, U): it feeds the upstream side and
+    absorbs what leaves downstream.  Argon VHS as in ``cylinder``; Kn =
+    lambda_inf / R; F_N sets ppc particles in a cell of the mean area.
+    """
+    gas = ARGON
+    m, d_ref, T_ref, omega = gas["m"], gas["d_ref"], gas["T_ref"], gas["omega"]
+    R_gas = KB / m
+    Rb = 1.0
+    cfg = base_config(2, [nr, nt], [-r_out * Rb, -r_out * Rb], [r_out * Rb, r_out * Rb])
+    n_inf = n_for_kn(Kn, Rb, d_ref, T_ref, T_inf, omega)
+    U = Ma * math.sqrt(5.0 / 3.0 * R_gas * T_inf)
+    depth = cfg["hi"][2] - cfg["lo"][2]
+    mean_area = math.pi * ((r_out * Rb) ** 2 - Rb ** 2) / (nr * nt)
+    cfg.update(m=m, R=R_gas, omega=omega, T_ref=T_ref, d_ref=d_ref,
+               mu_ref=vhs_mu_ref(m, d_ref, T_ref, omega), Fn=n_inf * mean_area * depth / ppc, cfl=0.5,
+               sigc_T0=T_inf, seed=seed, n_steady=n_steady, ghost_layers=ghost_layers,
+               body=BODY_CIRCLE, body_c=[0.0, 0.0, 0.0], body_r=Rb, body_Tw=T_inf,
+               mesh=1, mesh_r_out=r_out * Rb, mesh_growth=growth)
+    fb = [BC_OUTFLOW, BC_INFLOW, BC_OUTFLOW, BC_OUTFLOW, BC_SPECULAR, BC_SPECULAR]
+    cfg["face_bc"] = fb
+    cfg["face_T"] = [T_inf] * 6
+    cfg["face_n"] = [0.0, n_inf, 0.0, 0.0, 0.0, 0.0]
+    cfg["face_u"] = [[U, 0.0, 0.0] for _ in range(6)]
+    regions = [dict(lo=[-r_out * Rb, -r_out * Rb], hi=[r_out * Rb, r_out * Rb], n=n_inf, T=T_inf,
+                    u=[U, 0, 0])]
+    return cfg, regions
+
+
+def ogrid_box(nr=12, nt=24, r_out=3.0, growth=1.08, ppc=30.0, seed=3, T=1.0, U=2.0, Kn=0.05,
+              outer=BC_INFLOW, mode=MODE_HYBRID, body_r=1.0, n_steady=0):
+    """Small nondimensional O-grid about a unit-radius body (parity and pin
+    cases): freestream (T, U along x) at Kn = lambda / body_r through the
+    outer polygon (``outer``: inflow, specular or diffuse at T), body
+    diffuse at T."""
+    cfg = base_config(2, [nr, nt], [-r_out, -r_out], [r_out, r_out])
+    n = 1.0
+    d = d_for_mfp(Kn * body_r, n, 1.0, T, 0.5)
+    mean_area = math.pi * (r_out ** 2 - body_r ** 2) / (nr * nt)
+    cfg.update(omega=0.5, T_ref=1.0, d_ref=d, mu_ref=vhs_mu_ref(1.0, d, 1.0, 0.5, kB=1.0),
+               Fn=n * mean_area / ppc, sigc_T0=T, seed=seed, n_steady=n_steady, ghost_layers=2,
+               body=BODY_CIRCLE, body_c=[0.0, 0.0, 0.0], body_r=body_r, body_Tw=T, mode=mode,
+               mesh=1, mesh_r_out=r_out, mesh_growth=growth)
+    cfg["face_bc"] = [BC_OUTFLOW, outer, BC_OUTFLOW, BC_OUTFLOW, BC_SPECULAR, BC_SPECULAR]
+    cfg["face_T"] = [T] * 6
+    cfg["face_n"] = [0.0, n if outer == BC_INFLOW else 0.0, 0.0, 0.0, 0.0, 0.0]
+    cfg["face_u"] = [[U, 0.0, 0.0] for _ in range(6)]
+    regions = [dict(lo=[-r_out, -r_out], hi=[r_out, r_out], n=n, T=T, u=[U, 0, 0])]
     return cfg, regions
 
 
