@@ -125,6 +125,22 @@ typedef struct sp_config {
    * the cell and its partner uniform over the other particles of the first
    * one's sub-cell (over the cell when it is alone there). */
   int32_t subcells;
+  /* Body-fitted O-grid about a circular body (2-D; the paper's cylinder
+   * meshes are body-fitted, Sec. IV.B).  0 = the uniform Cartesian grid
+   * above.  1 = n[0] radial layers x n[1] angular sectors (n[1] >= 3) of
+   * straight-edged quadrilaterals between the body polygon (nodes on the
+   * circle body_r about body_c; a diffuse wall at body_Tw) and the outer
+   * polygon (radius mesh_r_out): node radii r_0 = body_r,
+   * r_{i+1} = r_i + dr_i with dr_{i+1} = mesh_growth * dr_i and the first
+   * n[0] spacings summing to mesh_r_out - body_r; node angles 2 pi j / n[1];
+   * cell k = i + n[0] j.  The outer polygon is face 1: face_bc[1] (inflow =
+   * a freestream reservoir of ghost_layers rings continuing the radial
+   * spacing, at face_n/T/u[1]; outflow; specular; diffuse at face_T[1]).
+   * Particles find their cell by face crossing; the local observation time
+   * uses each cell's shortest edge; lo/hi[0..1] are ignored, hi[2] - lo[2]
+   * is the depth.  Requires body = SP_BODY_CIRCLE, subcells <= 1. */
+  int32_t mesh;
+  double mesh_r_out, mesh_growth;
 } sp_config;
 
 typedef struct sp_ctx sp_ctx;

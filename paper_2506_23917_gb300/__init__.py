@@ -48,7 +48,8 @@ class SpConfig(C.Structure):
         ("sigc_T0", C.c_double), ("n_steady", C.c_int32), ("seed", C.c_uint64),
         ("mode", C.c_int32), ("ar_max", C.c_int32), ("n_surf", C.c_int32),
         ("win_lo", (C.c_double * 2) * 6), ("win_hi", (C.c_double * 2) * 6), ("ntc_carry", C.c_int32),
-        ("subcells", C.c_int32),
+        ("subcells", C.c_int32), ("mesh", C.c_int32), ("mesh_r_out", C.c_double),
+        ("mesh_growth", C.c_double),
     ]
 
 
@@ -144,6 +145,9 @@ def make_config(cfg: dict):
             s.win_hi[f][i] = cfg.get("win_hi", [[0.0, 0.0]] * 6)[f][i]
     s.ntc_carry = int(cfg.get("ntc_carry", 0))
     s.subcells = int(cfg.get("subcells", 0))
+    s.mesh = int(cfg.get("mesh", 0))
+    s.mesh_r_out = float(cfg.get("mesh_r_out", 0.0))
+    s.mesh_growth = float(cfg.get("mesh_growth", 1.0))
     return s, keep
 
 

@@ -223,6 +223,7 @@ bool valid(const sp_config& c, int dim) {
     if (m > kMaxSub) return false;
   }
   if (c.body == SP_BODY_SPHERE && c.dim != 3) return false;
+  if (c.mesh != 0) return false;  // the O-grid path is not built yet
   return true;
 }
 
