@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--develop", type=int, default=600)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--scale", type=float, default=1.0)
-    p.add_argument("--config", default="cylinder", choices=["cylinder", "sphere", "sod", "jet"])
+    p.add_argument("--config", default="cylinder", choices=["cylinder", "sphere", "sod", "jet", "ogrid"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp32c", "fp64"],
                    help="fp32: FP32 state, FP64 per-cell sums and arithmetic; fp32c: the opt-in "
                         "all-FP32 variant; fp64: FP64 everything")
@@ -76,6 +76,9 @@ def workload_name(scale, config="cylinder"):
     if config == "jet":
         nc = max(8, int(round(512 * scale)))
         return f"jet2d_{nc}x{nc}_orifice_ppc500_plenum4x_Ma1_Kn0.02_n2like_vhs"
+    if config == "ogrid":
+        nr, nt = max(4, int(round(150 * scale))), max(8, int(round(600 * scale)))
+        return f"cylinder2d_ogrid_{nr}x{nt}_rout4_growth1.01_ppc40_Ma5_Kn0.01_argon_vhs"
     nx, ny = max(4, int(round(600 * scale))), max(2, int(round(300 * scale)))
     return f"cylinder2d_{nx}x{ny}_ppc40_Ma5_Kn0.01_argon_vhs"
 
@@ -87,6 +90,9 @@ def make_workload(W, config, scale, seed):
         cfg, regions = W.jet(scale=scale, seed=seed, n_steady=0)
     elif config == "sod":
         cfg, regions = W.sod(ncell=200, ppc_left=500.0, lam_left=1e-3, seed=seed, n_steady=0)
+    elif config == "ogrid":
+        cfg, regions = W.cylinder_ogrid(nr=max(4, int(round(150 * scale))), nt=max(8, int(round(600 * scale))),
+                                        r_out=4.0, growth=1.01, ppc=40.0, Kn=0.01, seed=seed, n_steady=0)
     else:
         cfg, regions = W.cylinder(scale=scale, seed=seed, n_steady=0)
     pos, vel = W.fill_regions(cfg, regions, seed)

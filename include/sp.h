@@ -169,7 +169,9 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
  * until the next synchronising call).  At the next sp_step / query every
  * instance's staged particles are converted to the context's precision,
  * indexed and stably sorted by cell (input order within a cell), and
- * Delta t of the next step is set to cfl * min dt_c of that state.  Calling
+ * Delta t of the next step is set to cfl * min dt_c of that state (on an
+ * O-grid, particles outside the mesh -- inside the body polygon or beyond
+ * the outer polygon -- are dropped).  Calling
  * it again restarts every instance from its staged particles; sampling sums
  * and the step counter are kept.  Errors: SP_ERR_CAPACITY if n exceeds the
  * capacity. */

@@ -49,6 +49,11 @@
  *   - A face may be open only on a window (an orifice); the rest of it is a
  *     diffuse wall at the face temperature, and the reservoir of a windowed
  *     inflow face spans the window plus ghost_layers cells on each side.
+ *   - Body-fitted meshes (Sec. IV.B-E, not available) are stood in for by a
+ *     synthetic O-grid of straight-edged quadrilaterals about the body
+ *     polygon; particles find their cell by crossing faces; the local
+ *     observation time uses each cell's shortest edge; the freestream
+ *     enters from reservoir rings beyond the outer polygon.
  */
 #define _GNU_SOURCE
 #include "oracle.h"

@@ -29,7 +29,10 @@ SOURCES = [
 ]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Host code without FMA contraction (as the oracle): the O-grid's node
+# coordinates and face lines, built on the host, must match the oracle's.
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", f"-I{os.path.join(ROOT, 'include')}"]
 
 

@@ -97,6 +97,10 @@ struct sp_ctx {
   std::vector<unsigned long long> hinf, hmin;  // host mirrors used by upload()
   std::vector<double> hdt;
   uint32_t hM = 0;
+  // body-fitted O-grid instances (all instances share the mesh kind)
+  int mesh = 0;
+  double *Lc = nullptr, *iLc = nullptr, *mrad = nullptr;  // [NC], [NC], radii
+  void *mface = nullptr, *mnode = nullptr;                 // state type
 };
 
 namespace {
@@ -223,8 +227,126 @@ bool valid(const sp_config& c, int dim) {
     if (m > kMaxSub) return false;
   }
   if (c.body == SP_BODY_SPHERE && c.dim != 3) return false;
-  if (c.mesh != 0) return false;  // the O-grid path is not built yet
+  if (c.mesh != 0) {
+    if (c.mesh != 1 || c.dim != 2 || c.body != SP_BODY_CIRCLE || c.n[1] < 3 || !(c.body_r > 0) ||
+        !(c.mesh_r_out > c.body_r) || !(c.mesh_growth > 0) || c.subcells > 1)
+      return false;
+  }
   return true;
+}
+
+// Body-fitted O-grid of one instance (sp_config.mesh = 1): node radii r_0 =
+// body_r, r_{i+1} = r_i + dr_i, dr_{i+1} = q dr_i with the first n[0]
+// spacings summing to r_out - r_0, continued over the reservoir rings;
+// nodes at angles 2 pi j / n[1]; per cell k = i + n[0] j (corners A =
+// (i, j), B = (i+1, j), C = (i+1, j+1), D = (i, j+1), counter-clockwise)
+// the four face lines inner D->A, outer B->C, theta_j A->B, theta_j+1
+// C->D as unit outward normal and offset, the shortest edge L and the area
+// (shoelace on coordinates about the centre) times the depth.
+struct MeshHost {
+  std::vector<double> rad;    // [nr + nl + 1]
+  std::vector<double> node;   // [(nr + nl + 1) nt][2]
+  std::vector<double> rel;    // the same about the centre
+  std::vector<double> face;   // [ncells][12]
+  std::vector<double> L, vol; // [ncells]
+};
+
+double edge_line(const double* p, const double* q, double* f) {
+  const double tx = q[0] - p[0], ty = q[1] - p[1];
+  const double len = sqrt(tx * tx + ty * ty);
+  f[0] = ty / len;
+  f[1] = -tx / len;
+  f[2] = f[0] * p[0] + f[1] * p[1];
+  return len;
+}
+
+double quad_area(const double* p0, const double* p1, const double* p2, const double* p3) {
+  return 0.5 * ((p0[0] * p1[1] - p1[0] * p0[1]) + (p1[0] * p2[1] - p2[0] * p1[1]) +
+                (p2[0] * p3[1] - p3[0] * p2[1]) + (p3[0] * p0[1] - p0[0] * p3[1]));
+}
+
+double tri_area(const double* p0, const double* p1, const double* p2) {
+  return 0.5 * ((p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]));
+}
+
+void build_mesh(const sp_config& c, MeshHost& m) {
+  const int nr = c.n[0], nt = c.n[1], nl = c.ghost_layers > 0 ? c.ghost_layers : 0;
+  const int nrad = nr + nl + 1;
+  m.rad.assign(nrad, 0.0);
+  double q = c.mesh_growth, geo = 0.0, qp = 1.0;
+  for (int i = 0; i < nr; ++i) {
+    geo += qp;
+    qp *= q;
+  }
+  double dr = (c.mesh_r_out - c.body_r) / geo;
+  m.rad[0] = c.body_r;
+  for (int i = 0; i + 1 < nrad; ++i) {
+    m.rad[i + 1] = m.rad[i] + dr;
+    dr *= q;
+  }
+  m.node.assign(2 * (size_t)nrad * nt, 0.0);
+  m.rel.assign(2 * (size_t)nrad * nt, 0.0);
+  const double two_pi = 2.0 * 3.14159265358979323846;
+  for (int i = 0; i < nrad; ++i)
+    for (int j = 0; j < nt; ++j) {
+      const double th = two_pi * (double)j / (double)nt;
+      const double rx = m.rad[i] * cos(th), ry = m.rad[i] * sin(th);
+      const size_t o = 2 * ((size_t)i * nt + j);
+      m.rel[o] = rx;
+      m.rel[o + 1] = ry;
+      m.node[o] = c.body_c[0] + rx;
+      m.node[o + 1] = c.body_c[1] + ry;
+    }
+  auto nd = [&](const std::vector<double>& v, int i, int j) { return &v[2 * ((size_t)i * nt + j % nt)]; };
+  const int64_t ncell = (int64_t)nr * nt;
+  m.face.assign(12 * (size_t)ncell, 0.0);
+  m.L.assign(ncell, 0.0);
+  m.vol.assign(ncell, 0.0);
+  const double depth = c.hi[2] - c.lo[2];
+  for (int j = 0; j < nt; ++j)
+    for (int i = 0; i < nr; ++i) {
+      const int64_t k = i + (int64_t)nr * j;
+      const double *A = nd(m.node, i, j), *B = nd(m.node, i + 1, j);
+      const double *C = nd(m.node, i + 1, j + 1), *D = nd(m.node, i, j + 1);
+      double* f = &m.face[12 * (size_t)k];
+      const double l0 = edge_line(D, A, f + 0);
+      const double l1 = edge_line(B, C, f + 3);
+      const double l2 = edge_line(A, B, f + 6);
+      const double l3 = edge_line(C, D, f + 9);
+      double L = l0;
+      if (l1 < L) L = l1;
+      if (l2 < L) L = l2;
+      if (l3 < L) L = l3;
+      m.L[k] = L;
+      m.vol[k] = quad_area(nd(m.rel, i, j), nd(m.rel, i + 1, j), nd(m.rel, i + 1, j + 1),
+                           nd(m.rel, i, j + 1)) * depth;
+    }
+}
+
+// Reservoir quadrilaterals of an O-grid inflow boundary, in (ring, sector)
+// order: expected count n V / F_N with V the area times the depth.
+void build_ghosts_mesh(const sp_config& c, const MeshHost& m, int inst, std::vector<GhostCell>& out) {
+  if (c.face_bc[1] != SP_BC_INFLOW) return;
+  const int nr = c.n[0], nt = c.n[1], nl = c.ghost_layers > 0 ? c.ghost_layers : 0;
+  const double depth = c.hi[2] - c.lo[2];
+  const double s2RT = sqrt(2.0 * (c.R * c.face_T[1]));
+  auto rl = [&](int i, int j) { return &m.rel[2 * ((size_t)i * nt + j % nt)]; };
+  for (int64_t gc = 0; gc < (int64_t)nl * nt; ++gc) {
+    GhostCell G;
+    memset(&G, 0, sizeof G);
+    G.inst = inst;
+    G.face = 1;
+    G.gc = (uint32_t)gc;
+    G.mlay = (int)(gc / nt);
+    G.msec = (int)(gc % nt);
+    const int i0 = nr + G.mlay, j = G.msec;
+    G.a1 = tri_area(rl(i0, j), rl(i0 + 1, j), rl(i0 + 1, j + 1));
+    G.a2 = tri_area(rl(i0, j), rl(i0 + 1, j + 1), rl(i0, j + 1));
+    G.lam = c.face_n[1] * (G.a1 + G.a2) * depth / c.Fn;
+    G.s2RT = s2RT;
+    for (int d = 0; d < 3; ++d) G.u[d] = c.face_u[1][d];
+    out.push_back(G);
+  }
 }
 
 // Reservoir cells in (face, layer-major, tangential) order with the same
@@ -328,6 +450,12 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.cyc = c->cyc;
   a.err = c->err;
   a.NC = c->NC;
+  a.mesh = c->mesh;
+  a.Lc = c->Lc;
+  a.iLc = c->iLc;
+  a.mface = c->mface;
+  a.mnode = c->mnode;
+  a.mrad = c->mrad;
   a.cap = c->cap;
   a.big_cap = kHugeCell;
   a.cap_small = c->sched_cap;
@@ -358,6 +486,8 @@ InjectArgs make_inject_args(sp_ctx* c, int par) {
   a.err = c->err;
   a.cap = c->cap;
   a.surf = c->n_surf_tot > 0 ? c->surf : nullptr;
+  a.mface = c->mface;
+  a.mnode = c->mnode;
   return a;
 }
 
@@ -382,7 +512,7 @@ bool apply_schedule(sp_ctx* c, int cap, int warps) {
   const size_t smem = c->K->collide_smem(warps, cap);
   if (smem > (size_t)kMaxDynSmem) return false;
   const bool one = c->n_inst == 1;
-  const int per_sm = c->K->collide_blocks_per_sm(c->dim, warps, cap, one);
+  const int per_sm = c->K->collide_blocks_per_sm(c->dim, warps, cap, one, c->mesh != 0);
   if (per_sm < 1) return false;
   c->sched_cap = cap;
   c->sched_warps = warps;
@@ -531,11 +661,16 @@ sp_status upload(sp_ctx* c) {
   }
   CK(cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * c->NC, c->stream));
   const void* P3[3] = {c->pos[c->cur][0], c->pos[c->cur][1], c->pos[c->cur][2]};
-  c->K->keys(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
+  if (c->mesh)
+    c->K->keys_mesh(P3, M, c->part_inst, c->dP, c->mface, c->mnode, c->mrad, c->key, c->count, c->stream);
+  else
+    c->K->keys(dim, P3, M, c->part_inst, c->dP, c->key, c->count, c->stream);
   launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream);
   c->hM = (uint32_t)M;
   CK(cudaMemcpyAsync(c->Mtot, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->Mcur, &c->hM, 4, cudaMemcpyHostToDevice, c->stream));
+  // the state holds the located particles only: an O-grid drops those
+  // outside the mesh (sentinel keys), so its size is start[NC], not M
+  CK(cudaMemcpyAsync(c->Mcur, c->start + c->NC, 4, cudaMemcpyDeviceToDevice, c->stream));
   launch_scatter(c->key, c->start, c->count, c->perm, c->Mtot, c->cap, c->stream);
   // the scatter's atomics leave each cell's order arbitrary: reproducible
   // runs restore the source order, so that the moments below (and the first
@@ -648,8 +783,28 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
   c->hinf.assign(n_instances, 0x7FF0000000000000ull);
   c->hmin.assign(n_instances, 0);
   c->hdt.assign(n_instances, 0.0);
+  // body-fitted O-grid instances: every instance of a context has the same
+  // mesh kind (one kernel variant per launch)
+  c->mesh = cfgs[0].mesh;
+  for (int i = 0; i < n_instances; ++i)
+    if (cfgs[i].mesh != c->mesh) { delete c; return SP_ERR_ARG; }
+  std::vector<MeshHost> meshes(c->mesh ? n_instances : 0);
+  int64_t node_off = 0, rad_off = 0;
+  for (int i = 0; i < (int)meshes.size(); ++i) {
+    build_mesh(cfgs[i], meshes[i]);
+    InstParams& P = c->hP[i];
+    P.mesh = 1;
+    P.mnl = cfgs[i].ghost_layers > 0 ? cfgs[i].ghost_layers : 0;
+    P.mnode_off = node_off;
+    P.mrad_off = rad_off;
+    node_off += (int64_t)meshes[i].node.size() / 2;
+    rad_off += (int64_t)meshes[i].rad.size();
+  }
   std::vector<GhostCell> gh;
-  for (int i = 0; i < n_instances; ++i) build_ghosts(cfgs[i], c->hP[i], i, gh);
+  for (int i = 0; i < n_instances; ++i) {
+    if (c->mesh) build_ghosts_mesh(cfgs[i], meshes[i], i, gh);
+    else build_ghosts(cfgs[i], c->hP[i], i, gh);
+  }
   c->n_ghost = (int64_t)gh.size();
 
   sp_status st = [&]() -> sp_status {
@@ -708,7 +863,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
       const double s0 = 2.0 * (P.sigc_coef * pow(crb, P.sigc_exp));
       for (int64_t k = 0; k < P.ncells; ++k) {
         ci[P.cell_off + k] = (uint32_t)i;
-        vol[P.cell_off + k] = g.cell_volume ? g.cell_volume[k] : v0;
+        vol[P.cell_off + k] = c->mesh ? meshes[i].vol[k] : (g.cell_volume ? g.cell_volume[k] : v0);
         ivol[P.cell_off + k] = 1.0 / vol[P.cell_off + k];
         sm[P.cell_off + k] = s0;
       }
@@ -718,6 +873,37 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(cudaMemcpyAsync(c->ivol, ivol.data(), 8 * NC, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->rcp, rcp.data(), 8 * (kHugeCell + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->smax, sm.data(), 8 * NC, cudaMemcpyHostToDevice, s));
+    if (c->mesh) {
+      // faces and nodes in the state's type, cell sizes and radii in FP64
+      std::vector<double> L(NC), iL(NC), face(12 * (size_t)NC), node(2 * (size_t)node_off), rad(rad_off);
+      for (int i = 0; i < n_instances; ++i) {
+        const InstParams& P = c->hP[i];
+        const MeshHost& m = meshes[i];
+        for (int64_t k = 0; k < P.ncells; ++k) {
+          L[P.cell_off + k] = m.L[k];
+          iL[P.cell_off + k] = 1.0 / m.L[k];
+        }
+        std::copy(m.face.begin(), m.face.end(), face.begin() + 12 * P.cell_off);
+        std::copy(m.node.begin(), m.node.end(), node.begin() + 2 * P.mnode_off);
+        std::copy(m.rad.begin(), m.rad.end(), rad.begin() + P.mrad_off);
+      }
+      CK(dalloc(&c->Lc, 8 * NC));
+      CK(dalloc(&c->iLc, 8 * NC));
+      CK(dalloc(&c->mrad, 8 * std::max<int64_t>(rad_off, 1)));
+      CK(dalloc(&c->mface, c->tsize * face.size()));
+      CK(dalloc(&c->mnode, c->tsize * std::max<size_t>(node.size(), 1)));
+      CK(cudaMemcpy(c->Lc, L.data(), 8 * NC, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->iLc, iL.data(), 8 * NC, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->mrad, rad.data(), 8 * rad.size(), cudaMemcpyHostToDevice));
+      if (c->tsize == 8) {
+        CK(cudaMemcpy(c->mface, face.data(), 8 * face.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->mnode, node.data(), 8 * node.size(), cudaMemcpyHostToDevice));
+      } else {
+        std::vector<float> f32(face.begin(), face.end()), n32(node.begin(), node.end());
+        CK(cudaMemcpy(c->mface, f32.data(), 4 * f32.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->mnode, n32.data(), 4 * n32.size(), cudaMemcpyHostToDevice));
+      }
+    }
     CK(cudaMemsetAsync(c->rem, 0, 8 * std::max<int64_t>(NC, 1), s));
     CK(cudaMemsetAsync(c->samp, 0, 8 * 8 * NC, s));
     CK(cudaMemsetAsync(c->surf, 0, 8 * kSurfFields * std::max<int64_t>(c->n_surf_tot, 1), s));
@@ -1224,7 +1410,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->ivol, c->rcp, c->cons, c->mom, c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->Lc, c->iLc, c->mrad, c->mface, c->mnode, c->ivol, c->rcp, c->cons, c->mom, c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->rem, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

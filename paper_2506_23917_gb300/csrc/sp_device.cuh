@@ -359,6 +359,52 @@ __device__ __forceinline__ bool flight_fast(const InstParams& P, T* x, const T* 
   return ok;
 }
 
+// Wall tallies of one body hit while sampling (FP64 atomics): the momentum
+// and energy the wall receives, binned by the polar angle of the inward
+// normal nv at the hit point.
+template <class T>
+__device__ __forceinline__ void tally_hit(const InstParams& P, double* surf_all, uint32_t step, const T* nv,
+                                          T vin0, T vin1, T vin2, const T* v) {
+  if (!(surf_all != nullptr && P.n_surf > 0 && (int64_t)step >= (int64_t)P.n_steady)) return;
+  // momentum and energy the wall receives from this hit (FP64 tallies)
+  double frac;
+  if (P.body == 1) {
+    frac = ((double)atan2(nv[1], nv[0]) + kPi) / (2.0 * kPi);
+  } else {
+    const double cx = (double)nv[0] < -1.0 ? -1.0 : ((double)nv[0] > 1.0 ? 1.0 : (double)nv[0]);
+    frac = acos(cx) / kPi;
+  }
+  int bin = (int)floor(frac * (double)P.n_surf);
+  if (bin < 0) bin = 0;
+  if (bin > P.n_surf - 1) bin = P.n_surf - 1;
+  double* t = surf_all + kSurfFields * (P.surf_off + bin);
+  const double ein = (double)vin0 * vin0 + (double)vin1 * vin1 + (double)vin2 * vin2;
+  const double eout = (double)v[0] * v[0] + (double)v[1] * v[1] + (double)v[2] * v[2];
+  const double dp0 = P.FnM * ((double)vin0 - (double)v[0]);
+  const double dp1 = P.FnM * ((double)vin1 - (double)v[1]);
+  const double dp2 = P.FnM * ((double)vin2 - (double)v[2]);
+  // direction of increasing polar angle at the hit point
+  double et0 = 0, et1 = 0, et2 = 0;
+  if (P.body == 1) {
+    et0 = -(double)nv[1];
+    et1 = (double)nv[0];
+  } else {
+    const double sn = sqrt((double)nv[1] * nv[1] + (double)nv[2] * nv[2]);
+    if (sn > 0) {
+      et0 = -sn;
+      et1 = (double)nv[0] * nv[1] / sn;
+      et2 = (double)nv[0] * nv[2] / sn;
+    }
+  }
+  atomicAdd(t + 0, 1.0);
+  atomicAdd(t + 1, dp0);
+  atomicAdd(t + 2, dp1);
+  atomicAdd(t + 3, dp2);
+  atomicAdd(t + 4, 0.5 * P.FnM * (ein - eout));
+  atomicAdd(t + 5, -(dp0 * nv[0] + dp1 * nv[1] + dp2 * nv[2]));
+  atomicAdd(t + 6, dp0 * et0 + dp1 * et1 + dp2 * et2);
+}
+
 // Moves one particle for time trem.  Returns true when it left the domain.
 // Draw stream of bounce b: (step, sa, sb, purpose<<24 | subbase + 2b).
 template <class T, int DIM>
@@ -481,46 +527,129 @@ __device__ __forceinline__ bool move_particle(const InstParams& P, double* surf_
     const T vin0 = v[0], vin1 = v[1], vin2 = v[2];
 #pragma unroll
     for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
-    if (body_hit && surf_all != nullptr && P.n_surf > 0 && (int64_t)step >= (int64_t)P.n_steady) {
-      // momentum and energy the wall receives from this hit (FP64 tallies)
-      double frac;
-      if (P.body == 1) {
-        frac = ((double)atan2(nv[1], nv[0]) + kPi) / (2.0 * kPi);
-      } else {
-        const double cx = (double)nv[0] < -1.0 ? -1.0 : ((double)nv[0] > 1.0 ? 1.0 : (double)nv[0]);
-        frac = acos(cx) / kPi;
-      }
-      int bin = (int)floor(frac * (double)P.n_surf);
-      if (bin < 0) bin = 0;
-      if (bin > P.n_surf - 1) bin = P.n_surf - 1;
-      double* t = surf_all + kSurfFields * (P.surf_off + bin);
-      const double ein = (double)vin0 * vin0 + (double)vin1 * vin1 + (double)vin2 * vin2;
-      const double eout = (double)v[0] * v[0] + (double)v[1] * v[1] + (double)v[2] * v[2];
-      const double dp0 = P.FnM * ((double)vin0 - (double)v[0]);
-      const double dp1 = P.FnM * ((double)vin1 - (double)v[1]);
-      const double dp2 = P.FnM * ((double)vin2 - (double)v[2]);
-      // direction of increasing polar angle at the hit point
-      double et0 = 0, et1 = 0, et2 = 0;
-      if (P.body == 1) {
-        et0 = -(double)nv[1];
-        et1 = (double)nv[0];
-      } else {
-        const double sn = sqrt((double)nv[1] * nv[1] + (double)nv[2] * nv[2]);
-        if (sn > 0) {
-          et0 = -sn;
-          et1 = (double)nv[0] * nv[1] / sn;
-          et2 = (double)nv[0] * nv[2] / sn;
+    if (body_hit) tally_hit<T>(P, surf_all, step, nv, vin0, vin1, vin2, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Body-fitted O-grid (mesh = 1, 2-D): point location by face crossing.
+// ---------------------------------------------------------------------------
+// Walk of one particle of local cell kl for time trem.  In its cell it
+// leaves through the face whose line its straight path meets first among
+// the faces it moves towards (outward normal . v > 0; exit times below zero
+// count as zero, so a point that rounding left just outside a face leaves
+// at once); interior faces hand it to the neighbour (inner i-1, outer i+1,
+// sectors j-1, j+1), the body polygon (inner face of ring 0) re-emits it
+// diffusely at T_w, the outer polygon (outer face of the last ring) removes
+// it (inflow, outflow), reflects it (specular) or re-emits it (diffuse at
+// face_T[1]).  locate: the point location walk, where a boundary face ends
+// the walk as "outside".  Draws of wall event b: (step, sa, sb, purpose<<24
+// | subbase + 2b), as for the Cartesian walls.  Returns true when the
+// particle left the domain (or, locating, the point lies outside).
+template <class T>
+__device__ __forceinline__ bool mesh_walk(const InstParams& P, const T* mface, double* surf_all, int64_t& kl,
+                                          T* x, T* v, T trem, uint32_t step, uint32_t purpose, uint32_t sa,
+                                          uint32_t sb, uint32_t subbase, unsigned long long* err, bool locate) {
+  const Geo<T>& G = geo<T>(P);
+  const int nr = P.n[0], nt = P.n[1];
+  int bounce = 0;
+  for (int cross = 0;; ++cross) {
+    if (cross >= kMaxCross) {
+      if (locate) return true;
+      atomicAdd(&err[kErrBounce], 1ull);
+      return false;
+    }
+    const T* f = mface + 12 * (P.cell_off + kl);
+    T tmin = tinf<T>();
+    int fm = -1;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const T nvv = f[3 * e] * v[0] + f[3 * e + 1] * v[1];
+      if (nvv > (T)0) {
+        T t = (f[3 * e + 2] - (f[3 * e] * x[0] + f[3 * e + 1] * x[1])) / nvv;
+        if (t < (T)0) t = 0;
+        if (t < tmin) {
+          tmin = t;
+          fm = e;
         }
       }
-      atomicAdd(t + 0, 1.0);
-      atomicAdd(t + 1, dp0);
-      atomicAdd(t + 2, dp1);
-      atomicAdd(t + 3, dp2);
-      atomicAdd(t + 4, 0.5 * P.FnM * (ein - eout));
-      atomicAdd(t + 5, -(dp0 * nv[0] + dp1 * nv[1] + dp2 * nv[2]));
-      atomicAdd(t + 6, dp0 * et0 + dp1 * et1 + dp2 * et2);
     }
+    if (!(tmin < trem)) {
+      x[0] += v[0] * trem;
+      x[1] += v[1] * trem;
+      return false;
+    }
+    x[0] += v[0] * tmin;
+    x[1] += v[1] * tmin;
+    trem -= tmin;
+    const int i = (int)(kl % nr), j = (int)(kl / nr);
+    if (fm == 2) { kl = i + (int64_t)nr * ((j + nt - 1) % nt); continue; }
+    if (fm == 3) { kl = i + (int64_t)nr * ((j + 1) % nt); continue; }
+    if (fm == 0 && i > 0) { kl -= 1; continue; }
+    if (fm == 1 && i < nr - 1) { kl += 1; continue; }
+    if (locate) return true;
+    if (bounce >= kMaxBounce) {
+      atomicAdd(&err[kErrBounce], 1ull);
+      return false;
+    }
+    const uint32_t c3 = (purpose << 24) | (subbase + 2u * (uint32_t)bounce);
+    ++bounce;
+    // a boundary face: normal into the domain
+    T nv[3] = {-f[3 * fm], -f[3 * fm + 1], (T)0};
+    T RTw;
+    if (fm == 1) {
+      const int bc = P.face_bc[1];
+      if (bc >= 2) return true;  // outflow, inflow
+      if (bc == 0) {             // specular
+        const T vn = f[3] * v[0] + f[4] * v[1];
+        v[0] -= (T)2.0 * vn * f[3];
+        v[1] -= (T)2.0 * vn * f[4];
+        continue;
+      }
+      RTw = G.face_RT[1];
+    } else {
+      RTw = G.body_RT;
+    }
+    const T e1[3] = {-nv[1], nv[0], (T)0}, e2[3] = {(T)0, (T)0, (T)1};
+    Uni<T> r(step, sa, sb, c3, P.key0, P.key1);
+    T cn, t1, t2;
+    diffuse_sample<T>(RTw, r, &cn, &t1, &t2);
+    const T vin0 = v[0], vin1 = v[1], vin2 = v[2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[d] = cn * nv[d] + t1 * e1[d] + t2 * e2[d];
+    if (fm == 0) tally_hit<T>(P, surf_all, step, nv, vin0, vin1, vin2, v);
   }
+}
+
+// The local cell of point x (O-grid): a first guess from its polar
+// coordinates, then the walk from that cell's centroid to x; -1 outside
+// the mesh (inside the body polygon or beyond the outer polygon).
+template <class T>
+__device__ __forceinline__ int64_t mesh_locate(const InstParams& P, const T* mface, const T* mnode,
+                                               const double* mrad, const T* x) {
+  const int nr = P.n[0], nt = P.n[1];
+  const double kTwoPi = 2.0 * 3.14159265358979323846;
+  const double dx = (double)x[0] - P.body_c[0], dy = (double)x[1] - P.body_c[1];
+  const double r = sqrt(dx * dx + dy * dy);
+  double th = atan2(dy, dx);
+  if (th < 0) th += kTwoPi;
+  int j = (int)floor(th * (double)nt / kTwoPi);
+  if (j < 0) j = 0;
+  if (j > nt - 1) j = nt - 1;
+  const double* rad = mrad + P.mrad_off;
+  int i = 0;
+  while (i < nr - 1 && rad[i + 1] <= r) ++i;
+  int64_t kl = i + (int64_t)nr * j;
+  const T* nd = mnode + 2 * P.mnode_off;
+  const int j1 = (j + 1) % nt;
+  const T* A = nd + 2 * ((int64_t)i * nt + j);
+  const T* B = nd + 2 * ((int64_t)(i + 1) * nt + j);
+  const T* C = nd + 2 * ((int64_t)(i + 1) * nt + j1);
+  const T* D = nd + 2 * ((int64_t)i * nt + j1);
+  T p[2] = {(T)0.25 * (A[0] + B[0] + C[0] + D[0]), (T)0.25 * (A[1] + B[1] + C[1] + D[1])};
+  T w[3] = {x[0] - p[0], x[1] - p[1], (T)0};
+  if (mesh_walk<T>(P, mface, nullptr, kl, p, w, (T)1, 0u, 0u, 0u, 0u, 0u, nullptr, true)) return -1;
+  return kl;
 }
 
 // ---------------------------------------------------------------------------
@@ -880,6 +1009,7 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   // warp launches) and 1/V from the per-cell array: no FP64 division
   const bool tab = Ni <= kHugeCell;
   const double fN = (double)Ni, iN = tab ? a.rcp[Ni] : 1.0 / fN, iV = ivol_k;
+  const double Lk = a.Lc ? a.Lc[kc] : Pi.Lmin;  // the cell size of Delta t_c
   o.U[0] = m0 * iN;
   o.U[1] = m1 * iN;
   o.U[2] = m2 * iN;
@@ -894,7 +1024,7 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
   bool dsmc_only = true;  // Delta t_c <= tau (or no split: T = 0, DSMC forced)
   if (Tt > 0.0) {
     sRT = sqrt(Pi.R * Tt);
-    dtct = Pi.Lmin / (umag + Pi.sqrt_gamma * sRT);
+    dtct = Lk / (umag + Pi.sqrt_gamma * sRT);
     if (Pi.mode != 1) {
       // Delta t_c / tau = Delta t_c n T^(1-omega) / tau_k; the FP32 power has
       // a relative error below 1e-5 for T in [1e-30, 1e30]
@@ -911,13 +1041,13 @@ __device__ __forceinline__ void cell_math_lean(const StepArgs& a, const InstPara
       }
     }
   } else if (umag > 0.0) {
-    dtct = Pi.Lmin / umag;
+    dtct = Lk / umag;
   }
   if (dtct < tinf<double>()) o.dtbits = (unsigned long long)__double_as_longlong(dtct);
   o.tau = taut;
   o.dtc = dtct;
   // r = tau / dt_c = tau (|U| + c_s) / L_min
-  const double r = dsmc_only ? 1.0 : taut * (umag + Pi.sqrt_gamma * sRT) * Pi.inv_Lmin;
+  const double r = dsmc_only ? 1.0 : taut * (umag + Pi.sqrt_gamma * sRT) * (a.Lc ? a.iLc[kc] : Pi.inv_Lmin);
   if (Pi.mode == 1) o.ratio = 1;
   else if (Pi.mode == 2) o.ratio = 0;
   else o.ratio = r;
@@ -989,6 +1119,7 @@ __device__ __forceinline__ void cell_math(const StepArgs& a, const InstParams& P
     return;
   }
   const A V = (A)vol_k;
+  const double Lk = a.Lc ? a.Lc[kc] : Pi.Lmin;  // the cell size of Delta t_c
   A Tt = 0, qt[3] = {0, 0, 0}, nt = 0;
   A taut = tinf<A>(), dtct = tinf<A>();
   if (Ni > 0) {
@@ -1010,9 +1141,9 @@ __device__ __forceinline__ void cell_math(const StepArgs& a, const InstParams& P
       const A p = nt * (A)Pi.m * (A)Pi.R * Tt;
       const A mu = (A)Pi.mu_ref * cpow(cdiv(Tt, (A)Pi.T_ref), (A)Pi.omega);
       taut = cdiv(mu, p);
-      dtct = cdiv((A)Pi.Lmin, umag + tsqrt((A)Pi.gamma * (A)Pi.R * Tt));
+      dtct = cdiv((A)Lk, umag + tsqrt((A)Pi.gamma * (A)Pi.R * Tt));
     } else if (umag > (A)0) {
-      dtct = cdiv((A)Pi.Lmin, umag);
+      dtct = cdiv((A)Lk, umag);
     }
     if (dtct < tinf<A>()) o.dtbits = (unsigned long long)__double_as_longlong((double)dtct);
   }
@@ -1114,7 +1245,7 @@ __device__ __forceinline__ bool shakhov_attempt(const Uni<T>& r, int t, T s2RT, 
 // histogram.  Particle work is spread over the lanes across the whole
 // batch; per-cell FP64 arithmetic runs lane-per-cell (lane i <-> cell i).
 // ---------------------------------------------------------------------------
-template <class T, class A, int DIM, bool ONE>
+template <class T, class A, int DIM, bool ONE, bool MESH = false>
 __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A>* ct, uint32_t* sidx,
                               int* stag, uint8_t* sseg, T* svx, T* svy, T* svz) {
   using Acc = CellAcc<T, A>;
@@ -1967,6 +2098,35 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
   if (idx_in_velocity<T>()) cp_async_wait_all();
   __syncwarp();
+  if constexpr (MESH) {
+    // body-fitted mesh: the walk from the particle's cell gives its next
+    // cell (point location by face crossing)
+#pragma unroll 1
+    for (int sb = 0; sb < M; sb += 32) {
+      const int s = sb + lane;
+      uint32_t key = kSentinel;
+      if (s < M) {
+        const int c = sseg[s];
+        const InstParams& P = inst_params<ONE>(a, ct->inst[c]);
+        const uint32_t o = idx_in_velocity<T>() ? (uint32_t)stag[s] : sidx[s];
+        T x[3] = {((const T*)a.Apos[0])[o], ((const T*)a.Apos[1])[o], (T)0};
+        T v[3] = {svx[s], svy[s], svz[s]};
+        int64_t kl = ct->kl[c];
+        const bool gone = mesh_walk<T>(P, (const T*)a.mface, a.surf, kl, x, v, ct->dt[c], step, kPurpWall,
+                                       (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), 0u, a.err, false);
+        if (!gone) key = (uint32_t)(P.cell_off + kl);
+        Bx[0][p0 + s] = x[0];
+        Bx[1][p0 + s] = x[1];
+        Bv[0][p0 + s] = v[0];
+        Bv[1][p0 + s] = v[1];
+        Bv[2][p0 + s] = v[2];
+        a.key[p0 + s] = key;
+      }
+      warp_count(key, a.count);
+    }
+    __syncwarp();
+    return;
+  }
   constexpr int R = kFlightRounds<T>;
   for (int sb0 = 0; sb0 < M; sb0 += 32 * R) {
     T xr[R][DIM] = {};
@@ -2083,7 +2243,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   __syncwarp();
 }
 
-template <class T, class A, int DIM, bool ONE>
+template <class T, class A, int DIM, bool ONE, bool MESH = false>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs a, int big) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2144,7 +2304,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
       if ((int)(a.start[k0 + 1] - a.start[k0]) > kHugeCell) continue;  // k_collide_huge's cell
     }
     const long long t0 = clock64();
-    process_batch<T, A, DIM, ONE>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
+    process_batch<T, A, DIM, ONE, MESH>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
     if (!big) {
       // the batch's cost steers the next step's plan (no effect on results):
       // hot if it cost more than the threshold per particle, counting at
@@ -2279,7 +2439,7 @@ __device__ __forceinline__ void block_sort_u32(uint32_t* p, int n) {
   }
 }
 
-template <class T, class A, int DIM, bool ONE>
+template <class T, class A, int DIM, bool ONE, bool MESH = false>
 __global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
   using Acc = CellAcc<T, A>;
   constexpr bool kMixed = mixed_prec<T, A>();
@@ -2736,8 +2896,15 @@ __global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
 #pragma unroll
           for (int d = 0; d < DIM; ++d) x[d] = ((const T*)a.Apos[d])[o];
           T v[3] = {svx[s], svy[s], svz[s]};
-          const bool gone = move_particle<T, DIM>(Pi, a.surf, x, v, dt, step, kPurpWall, kl, (uint32_t)s, 0u, a.err);
-          if (!gone) key = (uint32_t)Pi.cell_off + cell_of<T, DIM>(Pi, x);
+          if constexpr (MESH) {
+            int64_t kn = kl;
+            const bool gone = mesh_walk<T>(Pi, (const T*)a.mface, a.surf, kn, x, v, dt, step, kPurpWall, kl,
+                                           (uint32_t)s, 0u, a.err, false);
+            if (!gone) key = (uint32_t)(Pi.cell_off + kn);
+          } else {
+            const bool gone = move_particle<T, DIM>(Pi, a.surf, x, v, dt, step, kPurpWall, kl, (uint32_t)s, 0u, a.err);
+            if (!gone) key = (uint32_t)Pi.cell_off + cell_of<T, DIM>(Pi, x);
+          }
 #pragma unroll
           for (int d = 0; d < DIM; ++d) Bx[d][p0 + s] = x[d];
           Bv[0][p0 + s] = v[0];
@@ -2857,15 +3024,146 @@ __global__ void k_inject(InjectArgs a, int pass) {
   if (pass == 0 && lane == 0) a.gcount[g] = nsurv;
 }
 
+// Reservoir injection through the outer polygon of an O-grid (face 1 an
+// inflow boundary), two passes as k_inject: the reservoir quadrilateral of
+// ghost cell g is ring mlay beyond the outer polygon, sector msec; its
+// particles are uniform in it (triangle A B C or A C D chosen by area),
+// Maxwellian at the face state; one whose straight path enters the outer
+// polygon within the step through one of the mnl + 1 outer edges on either
+// side of its sector enters at the first crossing and walks the rest of the
+// step from the boundary cell.
+template <class T>
+__global__ void k_inject_mesh(InjectArgs a, int pass) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (g >= a.n_ghost) return;
+  const GhostCell G = a.ghosts[g];
+  const InstParams& P = a.P[G.inst];
+  const uint32_t step = *a.step;
+  const T dt = (T)a.dt_cur[G.inst];
+  const int nr = P.n[0], nt = P.n[1], w = P.mnl + 1;
+  const T* mface = (const T*)a.mface;
+  const T* nd = (const T*)a.mnode + 2 * P.mnode_off;
+  const int i0 = nr + G.mlay, j = G.msec, j1 = (j + 1) % nt;
+  const T* A = nd + 2 * ((int64_t)i0 * nt + j);
+  const T* B = nd + 2 * ((int64_t)(i0 + 1) * nt + j);
+  const T* C = nd + 2 * ((int64_t)(i0 + 1) * nt + j1);
+  const T* D = nd + 2 * ((int64_t)i0 * nt + j1);
+  const double a1 = G.a1, a12 = G.a1 + G.a2;
+  const uint32_t sb = (uint32_t)G.face * 16u;
+  Uni<T> rc(step, G.gc, kSentinel, (kPurpInj << 24) | sb, P.key0, P.key1);
+  const int64_t ng = (int64_t)floor(G.lam + (double)rc.get(0));
+  uint32_t nsurv = 0;
+  const int64_t base = pass == 1 ? (int64_t)*a.Mcur + (int64_t)a.goff[g] : 0;
+  T* Bx[2] = {(T*)a.Bpos[0], (T*)a.Bpos[1]};
+  T* Bv[3] = {(T*)a.Bvel[0], (T*)a.Bvel[1], (T*)a.Bvel[2]};
+  const T s2RT = (T)G.s2RT;
+  const T u0[3] = {(T)G.u[0], (T)G.u[1], (T)G.u[2]};
+  for (int64_t m0 = 0; m0 < ng; m0 += 32) {
+    const int64_t m = m0 + lane;
+    bool ok = m < ng;
+    T x[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+    int64_t kl = 0;
+    if (ok) {
+      Uni<T> r(step, G.gc, (uint32_t)m, (kPurpInj << 24) | sb, P.key0, P.key1);
+      const T uu = r.get(0);
+      T s = r.get(1), t = r.get(2);
+      if (s + t > (T)1) {
+        s = (T)1 - s;
+        t = (T)1 - t;
+      }
+      const T* P1 = B;
+      const T* P2 = C;
+      if (!((double)uu * a12 < a1)) {
+        P1 = C;
+        P2 = D;
+      }
+      x[0] = A[0] + s * (P1[0] - A[0]) + t * (P2[0] - A[0]);
+      x[1] = A[1] + s * (P1[1] - A[1]) + t * (P2[1] - A[1]);
+      const T R1 = r.get(3), R2 = r.get(4), R3 = r.get(5), R4 = r.get(6);
+      const T r2 = tsqrt(-tlog(R2)), r4 = tsqrt(-tlog(R4));
+      T sn3, cs3;
+      sincos2pi(R3, &sn3, &cs3);
+      v[0] = u0[0] + s2RT * cos2pi(R1) * r2;
+      v[1] = u0[1] + s2RT * cs3 * r4;
+      v[2] = u0[2] + s2RT * sn3 * r4;
+      // first crossing of an outer edge within the step
+      T best = tinf<T>();
+      int jb = -1;
+      for (int o = -w; o <= w; ++o) {
+        const int jj = ((j + o) % nt + nt) % nt;
+        const T* f = mface + 12 * (P.cell_off + (nr - 1) + (int64_t)nr * jj) + 3;
+        const T nvv = f[0] * v[0] + f[1] * v[1];
+        if (!(nvv < (T)0)) continue;
+        const T sx = f[0] * x[0] + f[1] * x[1];
+        if (!(sx > f[2])) continue;
+        const T te = (f[2] - sx) / nvv;
+        if (!(te < dt) || !(te < best)) continue;
+        const T* E0 = nd + 2 * ((int64_t)nr * nt + jj);
+        const T* E1 = nd + 2 * ((int64_t)nr * nt + (jj + 1) % nt);
+        const T ex = E1[0] - E0[0], ey = E1[1] - E0[1];
+        const T xc = x[0] + v[0] * te, yc = x[1] + v[1] * te;
+        const T u = ((xc - E0[0]) * ex + (yc - E0[1]) * ey) / (ex * ex + ey * ey);
+        if (u < (T)0 || u > (T)1) continue;
+        best = te;
+        jb = jj;
+      }
+      ok = jb >= 0;
+      if (ok) {
+        x[0] += v[0] * best;
+        x[1] += v[1] * best;
+        kl = (nr - 1) + (int64_t)nr * jb;
+        ok = !mesh_walk<T>(P, mface, a.surf, kl, x, v, dt - best, step, kPurpInjWall, G.gc, (uint32_t)m,
+                           (uint32_t)G.face << 16, a.err, false);
+      }
+    }
+    const unsigned sv = __ballot_sync(kFull, ok);
+    if (pass == 1 && ok) {
+      const int64_t idx = base + nsurv + __popc(sv & ((1u << lane) - 1u));
+      if (idx >= a.cap) {
+        atomicAdd(&a.err[kErrCapacity], 1ull);
+      } else {
+        const uint32_t key = (uint32_t)(P.cell_off + kl);
+        Bx[0][idx] = x[0];
+        Bx[1][idx] = x[1];
+        Bv[0][idx] = v[0];
+        Bv[1][idx] = v[1];
+        Bv[2][idx] = v[2];
+        a.key[idx] = key;
+        atomicAdd(&a.count[key], 1u);
+      }
+    }
+    nsurv += __popc(sv);
+  }
+  if (pass == 0 && lane == 0) a.gcount[g] = nsurv;
+}
+
+// Cell keys of uploaded particles on O-grid instances (point location by
+// face crossing; outside the mesh: the sentinel), with the histogram.
+template <class T>
+__global__ void k_keys_mesh(const T* x0, const T* x1, int64_t M, const uint32_t* part_inst,
+                            const InstParams* Ps, const T* mface, const T* mnode, const double* mrad,
+                            uint32_t* key, uint32_t* count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t k = kSentinel;
+  if (i < M) {
+    const InstParams& P = Ps[part_inst[i]];
+    const T x[2] = {x0[i], x1[i]};
+    const int64_t kl = mesh_locate<T>(P, mface, mnode, mrad, x);
+    if (kl >= 0) k = (uint32_t)(P.cell_off + kl);
+    key[i] = k;
+  }
+  warp_count(k, count);
+}
+
 // ---------------------------------------------------------------------------
 // Observability / initialisation kernels
 // ---------------------------------------------------------------------------
 // Moments of the current state for cells [c0, c1) (warp per cell, in the
 // cells' current slot order).  With out == nullptr only dt_min is updated.
-// The sums run in A (FP64 in the FP64 and FP32 modes: each velocity is
-// widened and added in FP64 -- this kernel runs only at upload and for
-// sp_moments, so the FP64 rate does not matter; FP32 in the all-FP32 mode),
-// the per-cell scalars in FP64.
+// The sums use the collision kernel's accumulator (FP64 values in FP64
+// mode, FP32 terms carried without loss in FP32 mode, plain FP32 in the
+// all-FP32 mode); the per-cell scalars are FP64.
 template <class T, class A>
 __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
   // sums warp per cell, 32 cells in a row; then the FP64 scalars lane per
@@ -2959,6 +3257,7 @@ __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
     const int64_t k = kb + lane;
     const int N = myN;
     const InstParams& P = a.P[a.cell_inst[k]];
+    const double Lk = a.Lc ? a.Lc[k] : P.Lmin;
     CellMoments m;
     m.U[0] = myU[0]; m.U[1] = myU[1]; m.U[2] = myU[2];
     m.n = N > 0 ? (double)N * P.Fn / a.vol[k] : 0.0;
@@ -2975,9 +3274,9 @@ __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
       if (m.T > 0) {
         const double p = m.n * P.m * P.R * m.T;
         m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
-        m.dtc = P.Lmin / (umag + sqrt(P.gamma * P.R * m.T));
+        m.dtc = Lk / (umag + sqrt(P.gamma * P.R * m.T));
       } else if (umag > 0) {
-        m.dtc = P.Lmin / umag;
+        m.dtc = Lk / umag;
       }
     }
     if (out) {

@@ -8,6 +8,7 @@ namespace sp {
 
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // key of a removed particle
 constexpr int kMaxBounce = 16;               // wall events per particle per step
+constexpr int kMaxCross = 4096;              // face crossings per particle per step (O-grid)
 constexpr int kSurfFields = 7;  // wall tallies per surface element
 constexpr int64_t kNcolCap = int64_t(1) << 24;
 constexpr int kBatchClasses = 9;             // batch lists: hot, then 8 by particle count (largest first)
@@ -72,6 +73,12 @@ struct InstParams {
   double inv_Lmin;   // 1 / L_min
   double inv_Fn;     // 1 / F_N
   float omf;         // 1 - omega in FP32 (the bound that certifies a pure DSMC split)
+  // body-fitted O-grid (mesh = 1): n[0] radial layers x n[1] sectors, mnl
+  // reservoir rings; its nodes start at mnode_off (node (i, j) at
+  // mnode_off + i n[1] + j) and its radii at mrad_off
+  int mesh;
+  int mnl;
+  int64_t mnode_off, mrad_off;
   Geo<double> g64;
   Geo<float> g32;
 };
@@ -83,6 +90,10 @@ struct GhostCell {
   uint32_t gc;       // index within the face's reservoir (Philox counter)
   int pad;
   double blo[3], bhi[3];
+  // O-grid reservoir quadrilateral: ring mlay beyond the outer polygon,
+  // sector msec; a1, a2 the areas of its triangles (A B C), (A C D)
+  int mlay, msec;
+  double a1, a2;
   double lam;        // expected particles = n_face * V / Fn
   double s2RT;       // sqrt(2 R T_face)
   double u[3];       // reservoir drift
@@ -127,6 +138,16 @@ struct StepArgs {
   int stable;           // restore source order within cells (reproducible runs)
   double* surf;         // [elements][kSurfFields] wall tallies
   int one;              // a single instance: P0 is its parameter set
+  // body-fitted O-grid instances (mesh = 1; all instances of a context
+  // share the mesh kind): per-cell size L of Delta t_c and 1/L, faces
+  // (state type, [NC][4][3]: outward unit normal, offset), nodes (state
+  // type, [.][2]) and node radii of all instances; null without a mesh
+  int mesh;
+  const double* Lc;
+  const double* iLc;
+  const void* mface;
+  const void* mnode;
+  const double* mrad;
   InstParams P0;        // instance 0, by value (kernel parameter space)
 };
 
@@ -146,6 +167,8 @@ struct InjectArgs {
   unsigned long long* err;
   int64_t cap;
   double* surf;
+  const void* mface;    // O-grid faces and nodes (as in StepArgs) or null
+  const void* mnode;
 };
 
 // Launch wrappers of one precision mode (sp_kern.cu, compiled once per mode:
@@ -155,12 +178,15 @@ struct KernelSet {
   void (*collide)(int dim, const StepArgs& a, bool big, int grid, int warps, cudaStream_t s);
   void (*collide_huge)(int dim, const StepArgs& a, int grid, cudaStream_t s);
   size_t (*collide_smem)(int warps, int cap);
-  int (*collide_blocks_per_sm)(int dim, int warps, int cap, bool one);
+  int (*collide_blocks_per_sm)(int dim, int warps, int cap, bool one, bool mesh);
   cudaError_t (*configure)();
   void (*inject)(int dim, const InjectArgs& a, int pass, cudaStream_t s);
   void (*moments)(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s);
   void (*keys)(int dim, const void* const pos[3], int64_t M, const uint32_t* part_inst, const InstParams* P,
                uint32_t* key, uint32_t* count, cudaStream_t s);
+  void (*keys_mesh)(const void* const pos[3], int64_t M, const uint32_t* part_inst, const InstParams* P,
+                    const void* mface, const void* mnode, const double* mrad, uint32_t* key,
+                    uint32_t* count, cudaStream_t s);
   void (*gather)(int dim, const void* const Apos[3], const void* const Avel[3], const uint32_t* perm,
                  int64_t s0, int64_t n, double* out_pos, double* out_vel, cudaStream_t s);
   void (*stage_in)(int dim, const double* pos, const double* vel, int64_t n, void* const dpos[3],
