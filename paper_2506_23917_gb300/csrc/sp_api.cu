@@ -53,8 +53,8 @@ struct sp_ctx {
   uint32_t* ticket = nullptr;
   uint2* batches = nullptr;
   uint32_t* nbatch = nullptr;         // [kBatchClasses] batches of the plan per class
-  uint8_t* hot = nullptr;             // [NC] slow-batch flags of the last step
-  unsigned long long* cyc = nullptr;  // [3] batch-cycle sum, particle sum, hot threshold per particle
+  uint8_t* cost = nullptr;            // [NC] cost bytes of the last step (batch plan)
+  unsigned long long* cyc = nullptr;  // [3] batch-cycle sum, particle sum, cost unit per particle
   int collide_grid = 1;
   int nsm = 1;
   int sched_cap = kCapSmall, sched_warps = kWarpsDefault;
@@ -446,7 +446,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.ticket = c->ticket;
   a.batches = c->batches;
   a.nbatch = c->nbatch;
-  a.hot = c->hot;
+  a.cost = c->cost;
   a.cyc = c->cyc;
   a.err = c->err;
   a.NC = c->NC;
@@ -543,7 +543,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     cudaEventRecord(c->join_ev, c->side);
     n += 4;
   }
-  launch_plan(c->start, c->hot, c->NC, c->sched_cap, c->batches, c->nbatch, c->big_list, c->big_count,
+  launch_plan(c->start, c->cost, c->NC, c->sched_cap, c->batches, c->nbatch, c->big_list, c->big_count,
               c->stream); ++n;
   if (branch) {
     // the big-cell launch (cells disjoint from the batches') is a branch
@@ -827,7 +827,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->ticket, 4));
     CK(dalloc(&c->batches, sizeof(uint2) * kBatchClasses * NC));
     CK(dalloc(&c->nbatch, 4 * kBatchClasses));
-    CK(dalloc(&c->hot, std::max<int64_t>(NC, 1)));
+    CK(dalloc(&c->cost, std::max<int64_t>(NC, 1)));
     CK(dalloc(&c->cyc, 24));
     CK(dalloc(&c->vol, 8 * NC));
     CK(dalloc(&c->ivol, 8 * NC));
@@ -912,7 +912,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(cudaMemsetAsync(c->big_count, 0, 4, s));
     CK(cudaMemsetAsync(c->ticket, 0, 4, s));
     CK(cudaMemsetAsync(c->nbatch, 0, 4 * kBatchClasses, s));
-    CK(cudaMemsetAsync(c->hot, 0, std::max<int64_t>(c->NC, 1), s));
+    CK(cudaMemsetAsync(c->cost, 0, std::max<int64_t>(c->NC, 1), s));
     CK(cudaMemsetAsync(c->cyc, 0, 16, s));
     CK(cudaMemsetAsync(c->cyc + 2, 0xFF, 8, s));
     int dev = 0;
@@ -1410,7 +1410,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->Lc, c->iLc, c->mrad, c->mface, c->mnode, c->ivol, c->rcp, c->cons, c->mom, c->hot, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->Lc, c->iLc, c->mrad, c->mface, c->mnode, c->ivol, c->rcp, c->cons, c->mom, c->cost, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->rem, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

@@ -136,9 +136,10 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
     *big_count = 0u;
     *ticket = 0u;
     for (int k = 0; k < kBatchClasses; ++k) nbatch[k] = 0u;
-    // threshold of the hot flag: cycles per particle, 2.5 times
-    // this step's mean over all batches
-    cyc[2] = cyc[1] > 0 ? (cyc[0] * 5ull) / (2ull * cyc[1]) : ~0ull;
+    // unit of the cost bytes: 1/16 of this step's mean cycles per particle
+    // over all batches (at least 1)
+    const unsigned long long u = cyc[1] > 0 ? cyc[0] / (16ull * cyc[1]) : ~0ull;
+    cyc[2] = u > 0 ? u : 1ull;
     cyc[0] = 0ull;
     cyc[1] = 0ull;
   }
@@ -155,19 +156,21 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 }
 // Work plan of a step: consecutive cells are grouped into batches whose
 // particles fit a warp's staging area (at most 32 cells each); cells above
-// it go to the big-cell list.  One warp per 32-cell chunk.  Batches holding
-// a cell flagged hot (its batch cost more per particle than 2.5 times the
-// step's mean: cells where most particles are resampled with many
-// rejections, or with many collision candidates) form the first class, so
-// that they start first; the others are classed by
-// particle count in eighths of cap, largest first.  The collision kernel
-// hands out the classes in that order, longest first, so that the batches
-// still running when the list runs out are short ones and the SMs finish
-// the launch together.  A warp takes only a few batches per launch, so
-// without this the last large batches alone would keep a few SMs busy for a
-// third of the launch.  Class k's list is batches[k NC ...].  Batches are
-// independent: their order changes no result.
-__global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches,
+// it go to the big-cell list.  One warp per 32-cell chunk.  Each batch is
+// classed by its predicted cost, sum over its cells of N_c w_c, where w_c is
+// the cell's cost byte from the last step (its batch's cycles per particle
+// in units of 1/16 of the step's mean; 16 before any measurement): in units
+// of a full batch at the mean cost (16 cap), classes >= 4, [2, 4),
+// [1.5, 2), [1, 1.5), [3/4, 1), [1/2, 3/4), [1/4, 1/2), [1/8, 1/4) and
+// below, most expensive first.  The collision kernel hands out the classes
+// in that order (longest processing time first), so that the batches still
+// running when the list runs out are short ones and the SMs finish the
+// launch together: cells where most particles are resampled with many
+// rejections, or with many collision candidates, cost several times the
+// mean per particle, and a warp takes only a few batches per launch.
+// Class k's list is batches[k NC ...].  Batches are independent: their
+// order changes no result.
+__global__ void k_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, uint2* batches,
                        uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
   // per block: the batches of each class (shared atomics), then one global
   // atomic per class for the block's place in the class list
@@ -188,14 +191,19 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
     if (chunk < nchunks) {
       const int64_t c0 = chunk * 32;
       const int nc = (int)((NC - c0) < 32 ? (NC - c0) : 32);
-      const bool is_hot = lane < nc && hot[c0 + lane] != 0;
-      int64_t cum = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
+      // inclusive prefix sums of the particle counts and the predicted costs
+      const int64_t nl = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
+      const int64_t wl = lane < nc ? (cost[c0 + lane] ? (int64_t)cost[c0 + lane] : 16) : 0;
+      int64_t cum = nl, ccum = nl * wl;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int64_t y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
-        if (lane >= o) cum += y;
+        const int64_t z = __shfl_up_sync(0xFFFFFFFFu, ccum, o);
+        if (lane >= o) {
+          cum += y;
+          ccum += z;
+        }
       }
-      const unsigned hmask = __ballot_sync(0xFFFFFFFFu, is_hot);
       int kk = 0;
       while (kk < nc) {
         const int64_t before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
@@ -209,12 +217,22 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
           kk += 1;
           continue;
         }
-        const int np = (int)(__shfl_sync(0xFFFFFFFFu, cum, kk + G - 1) - before);
+        const int64_t cb = kk > 0 ? __shfl_sync(0xFFFFFFFFu, ccum, kk - 1) : 0;
+        const int64_t cst = __shfl_sync(0xFFFFFFFFu, ccum, kk + G - 1) - cb;
         if (lane == nb) {
           mine = make_uint2((uint32_t)(c0 + kk), (uint32_t)G);
-          const unsigned gm = G >= 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
-          const int eighths = (int)((8 * (int64_t)np) / cap);  // 0 .. 8
-          mine_cls = ((hmask >> kk) & gm) != 0u ? 0 : kBatchClasses - 1 - (eighths < 7 ? eighths : 7);
+          const int64_t u = 16 * (int64_t)cap;  // a full batch at the mean cost
+          int cls;
+          if (cst >= 4 * u) cls = 0;
+          else if (cst >= 2 * u) cls = 1;
+          else if (2 * cst >= 3 * u) cls = 2;
+          else if (cst >= u) cls = 3;
+          else if (4 * cst >= 3 * u) cls = 4;
+          else if (2 * cst >= u) cls = 5;
+          else if (4 * cst >= u) cls = 6;
+          else if (8 * cst >= u) cls = 7;
+          else cls = 8;
+          mine_cls = cls;
         }
         ++nb;
         kk += G;
@@ -232,13 +250,13 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, in
 
 }  // namespace
 
-void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+void launch_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
                  uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
   const int64_t chunks = (NC + 31) / 32;
   int64_t g = (chunks + 7) / 8;
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
-  k_plan<<<(unsigned)g, 256, 0, s>>>(start, hot, NC, cap, batches, nbatch, big_list, big_count);
+  k_plan<<<(unsigned)g, 256, 0, s>>>(start, cost, NC, cap, batches, nbatch, big_list, big_count);
 }
 
 int64_t scan_partial_size(int64_t n) { return (n + kTile - 1) / kTile + 1; }

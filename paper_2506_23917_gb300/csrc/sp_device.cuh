@@ -2307,19 +2307,22 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) k_collide(StepArgs 
     process_batch<T, A, DIM, ONE, MESH>(a, k0, G, ct, sidx, stag, sseg, svx, svy, svz);
     if (!big) {
       // the batch's cost steers the next step's plan (no effect on results):
-      // hot if it cost more than the threshold per particle, counting at
-      // least cap/4 particles so that the fixed cost of a small batch does
-      // not flag it
+      // its cycles per particle in units of cyc[2] (1/16 of the last step's
+      // mean), saturating at 255, as the cost byte of each of its cells
       const unsigned long long cyc = (unsigned long long)(clock64() - t0);
       const unsigned long long Mb = a.start[k0 + G] - a.start[k0];
       if (lane == 0) {
         atomicAdd(&a.cyc[0], cyc);
         atomicAdd(&a.cyc[1], Mb);
       }
-      const unsigned long long thr = a.cyc[2];
-      const unsigned long long Mq = Mb > (unsigned long long)(cap / 4) ? Mb : (unsigned long long)(cap / 4);
-      const uint8_t h = (thr != ~0ull && cyc > thr * Mq) ? 1 : 0;
-      if (lane < G) a.hot[k0 + lane] = h;
+      const unsigned long long unit = a.cyc[2];
+      unsigned long long w = 16;
+      if (unit != ~0ull && unit > 0 && Mb > 0) {
+        w = cyc / (unit * Mb);
+        if (w < 1) w = 1;
+        if (w > 255) w = 255;
+      }
+      if (lane < G) a.cost[k0 + lane] = (uint8_t)w;
     }
   }
 }

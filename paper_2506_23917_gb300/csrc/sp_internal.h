@@ -11,7 +11,7 @@ constexpr int kMaxBounce = 16;               // wall events per particle per ste
 constexpr int kMaxCross = 4096;              // face crossings per particle per step (O-grid)
 constexpr int kSurfFields = 7;  // wall tallies per surface element
 constexpr int64_t kNcolCap = int64_t(1) << 24;
-constexpr int kBatchClasses = 9;             // batch lists: hot, then 8 by particle count (largest first)
+constexpr int kBatchClasses = 9;             // batch lists by predicted cost (most expensive first)
 constexpr int kMaxWarpsPerBlock = 8;         // collide kernel block size limit
 constexpr int kCapSmall = 512;               // default per-warp staging capacity (particles)
 constexpr int kWarpsDefault = 4;             // default warps per block
@@ -128,8 +128,8 @@ struct StepArgs {
   uint32_t* ticket;     // work-stealing counter over the batch list
   const uint2* batches; // [kBatchClasses][NC] (first cell, cell count) of each batch, per class
   const uint32_t* nbatch;  // [kBatchClasses] batches per class (taken in class order)
-  uint8_t* hot;         // [NC] the cell's batch was slower than the threshold last step
-  unsigned long long* cyc;  // [3] batch cycles and particles this step (sums), hot threshold per particle
+  uint8_t* cost;        // [NC] cost byte: last step's cycles per particle of the cell's batch / cyc[2]
+  unsigned long long* cyc;  // [3] batch cycles and particles this step (sums), cost unit (cycles per particle)
   unsigned long long* err;  // [kNumErr]
   int64_t NC;
   int64_t cap;
@@ -200,7 +200,7 @@ const KernelSet& kernels_f32c();
 
 // Precision-independent kernels (sp_common.cu).
 void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s);
-void launch_plan(const uint32_t* start, const uint8_t* hot, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+void launch_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
                  uint32_t* big_list, uint32_t* big_count, cudaStream_t s);
 void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* count, uint32_t* perm,
                     const uint32_t* Mtot, int64_t cap, cudaStream_t s);
