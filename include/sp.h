@@ -287,8 +287,9 @@ sp_status sp_set_reproducible(sp_ctx* ctx, int on);
  * go to a one-warp-per-cell launch) and `warps` warps per block (1..8).
  * The schedule changes no result.  SP_ERR_ARG if it does not fit. */
 sp_status sp_set_schedule(sp_ctx* ctx, int cap, int warps);
-/* Autotuner: for each candidate schedule (cap in 128..1024, warps in 2, 4,
- * 8 that fit) advance one untimed step and then steps_per_trial ordinary
+/* Autotuner: for each candidate schedule (warps in 2, 4, 8; cap in 128,
+ * 256, 384, 512, 768, 1024 and, per block size, the largest cap at each
+ * number of resident blocks per SM; those that fit) advance one untimed step and then steps_per_trial ordinary
  * steps while timing the collision kernel with CUDA events; time the three
  * fastest once more the same way and keep the one with the least total.  The
  * trial steps are part of the run (results do not depend on the schedule);

@@ -1081,14 +1081,30 @@ sp_status sp_autotune(sp_ctx* c, int steps_per_trial, int* cap_out, int* warps_o
   };
   struct Cand { int cap, warps; float t; };
   std::vector<Cand> cand;
-  for (int ci : caps)
-    for (int wi : warps) {
-      if (!apply_schedule(c, ci, wi)) continue;
-      float t = 0;
-      sp_status st = trial(ci, wi, &t);
-      if (st != SP_OK) return st;
-      cand.push_back({ci, wi, t});
+  // the fixed capacities, and for each block size the largest capacity at
+  // each residency level (blocks per SM from the occupancy calculator):
+  // more resident warps with slightly smaller batches can win (on the
+  // developed cylinder 864 x 2 at 6 blocks beat 1024 x 2 at 5 by 2 %)
+  std::vector<std::pair<int, int>> sched;
+  for (int wi : warps) {
+    for (int ci : caps) sched.push_back({ci, wi});
+    int last = -1;
+    for (int ci = kHugeCell; ci >= 128; ci -= 32) {
+      const int per = c->K->collide_blocks_per_sm(c->dim, wi, ci, c->n_inst == 1, c->mesh != 0);
+      if (per != last && per > 0 &&
+          std::find(sched.begin(), sched.end(), std::make_pair(ci, wi)) == sched.end())
+        sched.push_back({ci, wi});
+      last = per;
     }
+  }
+  for (const auto& sw : sched) {
+    const int ci = sw.first, wi = sw.second;
+    if (!apply_schedule(c, ci, wi)) continue;
+    float t = 0;
+    sp_status st = trial(ci, wi, &t);
+    if (st != SP_OK) return st;
+    cand.push_back({ci, wi, t});
+  }
   // second pass over the three fastest: the flow drifts between trials
   std::sort(cand.begin(), cand.end(), [](const Cand& x, const Cand& y) { return x.t < y.t; });
   if (cand.size() > 3) cand.resize(3);
