@@ -66,6 +66,7 @@ struct sp_ctx {
   double *ivol = nullptr, *rcp = nullptr;  // 1 / vol per cell; 1 / k for k <= kHugeCell
   double* rem = nullptr;  // [NC] carried NTC remainders
   double* mom = nullptr;  // [SP_NFIELDS][largest instance] output of sp_moments kind 0
+  double* msum = nullptr; // [7][NC] scratch of the moments kernels
   int64_t mom_cells = 0;
   int32_t* rec = nullptr;
   double* cons = nullptr;  // [6][NC] rescale conservation record
@@ -456,6 +457,7 @@ StepArgs make_step_args(sp_ctx* c, int par) {
   a.mface = c->mface;
   a.mnode = c->mnode;
   a.mrad = c->mrad;
+  a.msum = c->msum;
   a.cap = c->cap;
   a.big_cap = kHugeCell;
   a.cap_small = c->sched_cap;
@@ -835,6 +837,7 @@ sp_status sp_init(const sp_config* cfgs, int n_instances, int precision, int64_t
     CK(dalloc(&c->smax, 8 * NC));
     CK(dalloc(&c->rem, 8 * std::max<int64_t>(NC, 1)));
     CK(dalloc(&c->samp, 8 * 8 * NC));
+    CK(dalloc(&c->msum, 8 * 7 * NC));
     CK(dalloc(&c->dP, sizeof(InstParams) * n_instances));
     CK(dalloc(&c->dt_cur, 8 * n_instances));
     CK(dalloc(&c->dt_min, 8 * n_instances));
@@ -1426,7 +1429,7 @@ sp_status sp_free(sp_ctx* c) {
       cudaFree(c->vel[b][d]);
     }
   for (double* p : c->dstage) cudaFree(p);
-  void* ptrs[] = {c->Lc, c->iLc, c->mrad, c->mface, c->mnode, c->ivol, c->rcp, c->cons, c->mom, c->cost, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
+  void* ptrs[] = {c->Lc, c->iLc, c->mrad, c->mface, c->mnode, c->ivol, c->rcp, c->cons, c->mom, c->msum, c->cost, c->cyc, c->surf, c->surf_time, c->batches, c->nbatch, c->ticket, c->part_inst, c->key, c->perm, c->count, c->start, c->cell_inst, c->scan_part, c->big_list,
                   c->big_count, c->vol, c->smax, c->rem, c->samp, c->rec, c->resamp, c->dP, c->dt_cur, c->dt_min,
                   c->step_d, c->Mcur, c->Mtot, c->err, c->ghosts, c->gcount, c->goff, c->gscan_part};
   for (void* p : ptrs) cudaFree(p);

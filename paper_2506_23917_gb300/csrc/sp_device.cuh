@@ -7,6 +7,7 @@
 // dt_c, the DSMC/Shakhov split, exp(-dt/tau), rescale factors, time
 // averages) are always FP64; per-particle arithmetic runs in T.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <type_traits>
 
@@ -546,12 +547,16 @@ __device__ __forceinline__ bool move_particle(const InstParams& P, double* surf_
 // the walk as "outside".  Draws of wall event b: (step, sa, sb, purpose<<24
 // | subbase + 2b), as for the Cartesian walls.  Returns true when the
 // particle left the domain (or, locating, the point lies outside).
+// f0: the starting cell's face record (12 values) where the caller staged
+// it (shared memory), or null.
 template <class T>
 __device__ __forceinline__ bool mesh_walk(const InstParams& P, const T* mface, double* surf_all, int64_t& kl,
                                           T* x, T* v, T trem, uint32_t step, uint32_t purpose, uint32_t sa,
-                                          uint32_t sb, uint32_t subbase, unsigned long long* err, bool locate) {
+                                          uint32_t sb, uint32_t subbase, unsigned long long* err, bool locate,
+                                          const T* f0 = nullptr) {
   const Geo<T>& G = geo<T>(P);
   const int nr = P.n[0], nt = P.n[1];
+  const int64_t k0 = kl;
   int bounce = 0;
   for (int cross = 0;; ++cross) {
     if (cross >= kMaxCross) {
@@ -559,7 +564,7 @@ __device__ __forceinline__ bool mesh_walk(const InstParams& P, const T* mface, d
       atomicAdd(&err[kErrBounce], 1ull);
       return false;
     }
-    const T* f = mface + 12 * (P.cell_off + kl);
+    const T* f = (f0 != nullptr && kl == k0) ? f0 : mface + 12 * (P.cell_off + kl);
     T tmin = tinf<T>();
     int fm = -1;
 #pragma unroll
@@ -2100,7 +2105,23 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   __syncwarp();
   if constexpr (MESH) {
     // body-fitted mesh: the walk from the particle's cell gives its next
-    // cell (point location by face crossing)
+    // cell (point location by face crossing).  The face records of the
+    // batch's cells (12 values each) are staged in the table's per-cell
+    // arrays that are dead by now (U and q for cells 0-15, Up and Kl for
+    // 16-31), so that each particle's first walk step reads shared memory.
+    using CT = CellTab<T, A>;
+    static_assert(offsetof(CT, q) == offsetof(CT, U) + 96 * sizeof(T) &&
+                      offsetof(CT, Kl) == offsetof(CT, Up) + 96 * sizeof(T),
+                  "U, q and Up, Kl must each be 16 x 12 contiguous values");
+    T* fst0 = &ct->U[0][0];
+    T* fst1 = &ct->Up[0][0];
+    if (own) {
+      const T* src = (const T*)a.mface + 12 * kc;
+      T* dst = lane < 16 ? fst0 + 12 * lane : fst1 + 12 * (lane - 16);
+#pragma unroll
+      for (int e = 0; e < 12; ++e) dst[e] = src[e];
+    }
+    __syncwarp();
 #pragma unroll 1
     for (int sb = 0; sb < M; sb += 32) {
       const int s = sb + lane;
@@ -2112,8 +2133,9 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
         T x[3] = {((const T*)a.Apos[0])[o], ((const T*)a.Apos[1])[o], (T)0};
         T v[3] = {svx[s], svy[s], svz[s]};
         int64_t kl = ct->kl[c];
+        const T* f0 = c < 16 ? fst0 + 12 * c : fst1 + 12 * (c - 16);
         const bool gone = mesh_walk<T>(P, (const T*)a.mface, a.surf, kl, x, v, ct->dt[c], step, kPurpWall,
-                                       (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), 0u, a.err, false);
+                                       (uint32_t)ct->kl[c], (uint32_t)(s - ct->off[c]), 0u, a.err, false, f0);
         if (!gone) key = (uint32_t)(P.cell_off + kl);
         Bx[0][p0 + s] = x[0];
         Bx[1][p0 + s] = x[1];
@@ -3162,18 +3184,18 @@ __global__ void k_keys_mesh(const T* x0, const T* x1, int64_t M, const uint32_t*
 // ---------------------------------------------------------------------------
 // Observability / initialisation kernels
 // ---------------------------------------------------------------------------
-// Moments of the current state for cells [c0, c1) (warp per cell, in the
-// cells' current slot order).  With out == nullptr only dt_min is updated.
-// The sums use the collision kernel's accumulator (FP64 values in FP64
-// mode, FP32 terms carried without loss in FP32 mode, plain FP32 in the
-// all-FP32 mode); the per-cell scalars are FP64.
+// Moments of the current state for cells [c0, c1), in the cells' current
+// slot order, in two kernels.  k_moment_sums: one warp per cell; lanes
+// stride over the cell's slots, a butterfly combines them, and lane 0
+// writes U (3) and the central sums sum |C|^2, sum |C|^2 C (3) of the cell
+// to sums[7][nc].  The sums use the collision kernel's accumulator (FP64
+// values in FP64 mode, FP32 terms carried without loss in FP32 mode, plain
+// FP32 in the all-FP32 mode).  k_moment_cells: one thread per cell forms the
+// FP64 scalars (n, T, q, tau, dt_c, the split ratio) from them, so that the
+// narrow FP64 pipe works on full warps, and writes the fields to out
+// [12][nc] or, with out == nullptr, takes the minimum dt_c into dt_min.
 template <class T, class A>
-__global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
-  // sums warp per cell, 32 cells in a row; then the FP64 scalars lane per
-  // cell (lane j <-> cell kb + j), so each FP64 instruction serves 32 cells.
-  // The sums use the collision kernel's accumulator (FP32 state with FP64
-  // cells: FP32 terms carried without loss, the mean as an FP32 pair), so
-  // no per-particle work lands on the narrow FP64 pipe.
+__global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) {
   using Acc = CellAcc<T, A>;
   constexpr bool kMixed = mixed_prec<T, A>();
   const int lane = threadIdx.x & 31;
@@ -3182,123 +3204,126 @@ __global__ void k_moments(StepArgs a, int64_t c0, int64_t c1, double* out) {
   const T* Av0 = (const T*)a.Avel[0];
   const T* Av1 = (const T*)a.Avel[1];
   const T* Av2 = (const T*)a.Avel[2];
-  for (int64_t kb = c0 + 32 * ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); kb < c1;
-       kb += 32 * nw) {
-    int myN = 0;
-    double myU[3] = {0, 0, 0};
-    double myS2 = 0, myS3[3] = {0, 0, 0};
-    const int nj = (int)((c1 - kb) < 32 ? (c1 - kb) : 32);
-    for (int j = 0; j < nj; ++j) {
-      const int64_t k = kb + j;
-      const uint32_t s0 = a.start[k];
-      const int N = (int)(a.start[k + 1] - s0);
-      double U[3] = {0, 0, 0};
-      T Uh[3] = {0, 0, 0}, Ul[3] = {0, 0, 0};
-      {
-        Acc sx[3];
+  for (int64_t k = c0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c1; k += nw) {
+    const uint32_t s0 = a.start[k];
+    const int N = (int)(a.start[k + 1] - s0);
+    double U[3] = {0, 0, 0};
+    T Uh[3] = {0, 0, 0}, Ul[3] = {0, 0, 0};
+    {
+      Acc sx[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) sx[d].init();
-        for (int s = lane; s < N; s += 32) {
-          const uint32_t o = a.perm[s0 + s];
-          sx[0].add(Av0[o], (T)0);
-          sx[1].add(Av1[o], (T)0);
-          sx[2].add(Av2[o], (T)0);
-        }
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) sx[d].combine(sx[d].shfl_xor(m));
-        if (N > 0) {
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            U[d] = (double)sx[d].get() / N;
-            if constexpr (kMixed) {
-              const float fN = (float)N, rN = 1.0f / fN;
-              Uh[d] = sx[d].s * rN;
-              Ul[d] = (fmaf(-Uh[d], fN, sx[d].s) + sx[d].e) * rN;
-            } else {
-              Uh[d] = (T)U[d];
-            }
-          }
-        }
+      for (int d = 0; d < 3; ++d) sx[d].init();
+      for (int s = lane; s < N; s += 32) {
+        const uint32_t o = a.perm[s0 + s];
+        sx[0].add1(Av0[o]);
+        sx[1].add1(Av1[o]);
+        sx[2].add1(Av2[o]);
       }
-      double S2 = 0, S3x = 0, S3y = 0, S3z = 0;
-      if (N >= 2) {
-        Acc r[4];
 #pragma unroll
-        for (int d = 0; d < 4; ++d) r[d].init();
-        for (int s = lane; s < N; s += 32) {
-          const uint32_t o = a.perm[s0 + s];
-          T C0 = Av0[o] - Uh[0], C1 = Av1[o] - Uh[1], C2 = Av2[o] - Uh[2];
+      for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sx[d].combine(sx[d].shfl_xor(m));
+      if (N > 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          U[d] = (double)sx[d].get() / N;
           if constexpr (kMixed) {
-            C0 -= Ul[0];
-            C1 -= Ul[1];
-            C2 -= Ul[2];
+            const float fN = (float)N, rN = 1.0f / fN;
+            Uh[d] = sx[d].s * rN;
+            Ul[d] = (fmaf(-Uh[d], fN, sx[d].s) + sx[d].e) * rN;
+          } else {
+            Uh[d] = (T)U[d];
           }
-          const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
-          r[0].add(c2, (T)0);
-          r[1].add(c2 * C0, (T)0);
-          r[2].add(c2 * C1, (T)0);
-          r[3].add(c2 * C2, (T)0);
         }
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1)
-#pragma unroll
-          for (int d = 0; d < 4; ++d) r[d].combine(r[d].shfl_xor(m));
-        S2 = (double)r[0].get();
-        S3x = (double)r[1].get();
-        S3y = (double)r[2].get();
-        S3z = (double)r[3].get();
-      }
-      if (lane == j) {
-        myN = N;
-        myU[0] = U[0]; myU[1] = U[1]; myU[2] = U[2];
-        myS2 = S2; myS3[0] = S3x; myS3[1] = S3y; myS3[2] = S3z;
       }
     }
-    if (lane >= nj) continue;
-    const int64_t k = kb + lane;
-    const int N = myN;
-    const InstParams& P = a.P[a.cell_inst[k]];
-    const double Lk = a.Lc ? a.Lc[k] : P.Lmin;
-    CellMoments m;
-    m.U[0] = myU[0]; m.U[1] = myU[1]; m.U[2] = myU[2];
-    m.n = N > 0 ? (double)N * P.Fn / a.vol[k] : 0.0;
-    m.T = 0; m.q[0] = m.q[1] = m.q[2] = 0;
-    m.tau = __longlong_as_double(0x7FF0000000000000ll);
-    m.dtc = m.tau;
+    double S2 = 0, S3x = 0, S3y = 0, S3z = 0;
     if (N >= 2) {
-      m.T = (double)myS2 / (3.0 * P.R * (double)(N - 1));
-      if (N >= 3) {
-        const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
-        m.q[0] = f * (double)myS3[0]; m.q[1] = f * (double)myS3[1]; m.q[2] = f * (double)myS3[2];
+      Acc r[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) r[d].init();
+      for (int s = lane; s < N; s += 32) {
+        const uint32_t o = a.perm[s0 + s];
+        T C0 = Av0[o] - Uh[0], C1 = Av1[o] - Uh[1], C2 = Av2[o] - Uh[2];
+        if constexpr (kMixed) {
+          C0 -= Ul[0];
+          C1 -= Ul[1];
+          C2 -= Ul[2];
+        }
+        const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
+        r[0].add1(c2);
+        r[1].add1(c2 * C0);
+        r[2].add1(c2 * C1);
+        r[3].add1(c2 * C2);
       }
-      const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
-      if (m.T > 0) {
-        const double p = m.n * P.m * P.R * m.T;
-        m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
-        m.dtc = Lk / (umag + sqrt(P.gamma * P.R * m.T));
-      } else if (umag > 0) {
-        m.dtc = Lk / umag;
-      }
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) r[d].combine(r[d].shfl_xor(m));
+      S2 = (double)r[0].get();
+      S3x = (double)r[1].get();
+      S3y = (double)r[2].get();
+      S3z = (double)r[3].get();
     }
-    if (out) {
+    if (lane == 0) {
       const int64_t i = k - c0;
-      out[0 * nc + i] = (double)N;
-      out[1 * nc + i] = m.n;
-      out[2 * nc + i] = m.U[0];
-      out[3 * nc + i] = m.U[1];
-      out[4 * nc + i] = m.U[2];
-      out[5 * nc + i] = m.T;
-      out[6 * nc + i] = m.q[0];
-      out[7 * nc + i] = m.q[1];
-      out[8 * nc + i] = m.q[2];
-      out[9 * nc + i] = m.tau;
-      out[10 * nc + i] = m.dtc;
-      out[11 * nc + i] = dsmc_ratio(P, N, m);
-    } else if (N >= 2 && m.dtc < __longlong_as_double(0x7FF0000000000000ll)) {
-      atomicMin(&a.dt_min[a.cell_inst[k]], (unsigned long long)__double_as_longlong(m.dtc));
+      sums[0 * nc + i] = U[0];
+      sums[1 * nc + i] = U[1];
+      sums[2 * nc + i] = U[2];
+      sums[3 * nc + i] = S2;
+      sums[4 * nc + i] = S3x;
+      sums[5 * nc + i] = S3y;
+      sums[6 * nc + i] = S3z;
     }
+  }
+}
+
+static __global__ void k_moment_cells(StepArgs a, int64_t c0, int64_t c1, const double* sums, double* out) {
+  const int64_t nc = c1 - c0;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  const int64_t k = c0 + i;
+  const int N = (int)(a.start[k + 1] - a.start[k]);
+  const InstParams& P = a.P[a.cell_inst[k]];
+  const double Lk = a.Lc ? a.Lc[k] : P.Lmin;
+  CellMoments m;
+  m.U[0] = N > 0 ? sums[0 * nc + i] : 0.0;
+  m.U[1] = N > 0 ? sums[1 * nc + i] : 0.0;
+  m.U[2] = N > 0 ? sums[2 * nc + i] : 0.0;
+  m.n = N > 0 ? (double)N * P.Fn / a.vol[k] : 0.0;
+  m.T = 0; m.q[0] = m.q[1] = m.q[2] = 0;
+  m.tau = __longlong_as_double(0x7FF0000000000000ll);
+  m.dtc = m.tau;
+  if (N >= 2) {
+    m.T = sums[3 * nc + i] / (3.0 * P.R * (double)(N - 1));
+    if (N >= 3) {
+      const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
+      m.q[0] = f * sums[4 * nc + i]; m.q[1] = f * sums[5 * nc + i]; m.q[2] = f * sums[6 * nc + i];
+    }
+    const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
+    if (m.T > 0) {
+      const double p = m.n * P.m * P.R * m.T;
+      m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
+      m.dtc = Lk / (umag + sqrt(P.gamma * P.R * m.T));
+    } else if (umag > 0) {
+      m.dtc = Lk / umag;
+    }
+  }
+  if (out) {
+    out[0 * nc + i] = (double)N;
+    out[1 * nc + i] = m.n;
+    out[2 * nc + i] = m.U[0];
+    out[3 * nc + i] = m.U[1];
+    out[4 * nc + i] = m.U[2];
+    out[5 * nc + i] = m.T;
+    out[6 * nc + i] = m.q[0];
+    out[7 * nc + i] = m.q[1];
+    out[8 * nc + i] = m.q[2];
+    out[9 * nc + i] = m.tau;
+    out[10 * nc + i] = m.dtc;
+    out[11 * nc + i] = dsmc_ratio(P, N, m);
+  } else if (N >= 2 && m.dtc < __longlong_as_double(0x7FF0000000000000ll)) {
+    atomicMin(&a.dt_min[a.cell_inst[k]], (unsigned long long)__double_as_longlong(m.dtc));
   }
 }
 

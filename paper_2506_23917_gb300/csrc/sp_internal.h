@@ -148,6 +148,7 @@ struct StepArgs {
   const void* mface;
   const void* mnode;
   const double* mrad;
+  double* msum;         // [7][NC] scratch of the moments kernels
   InstParams P0;        // instance 0, by value (kernel parameter space)
 };
 

@@ -77,10 +77,11 @@ void inject(int dim, const InjectArgs& a, int pass, cudaStream_t s) {
 
 void moments(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s) {
   const int64_t nc = c1 - c0;
-  int64_t g = (nc + 255) / 256;  // a warp per 32 cells, 8 warps per block
-  if (g > 4096) g = 4096;
-  if (g < 1) g = 1;
-  k_moments<T, A><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, out);
+  if (nc <= 0) return;
+  int64_t g = (nc + 7) / 8;  // a warp per cell, 8 warps per block, grid-stride
+  if (g > 65535) g = 65535;
+  k_moment_sums<T, A><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, a.msum);
+  k_moment_cells<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(a, c0, c1, a.msum, out);
 }
 
 template <int DIM>

@@ -212,3 +212,13 @@ def test_sphere_fp32_time_averages_match_fp64(sp):
     pos, vel = W.fill_regions(cfg, regions, 1)
     _compare(sp, cfg, pos, vel, warm=400, nbatch=20, per=60, reproducible=False,
              min_n=0.25 * cfg["face_n"][0])
+
+
+def test_full_size_o_grid_fp64_step_matches_oracle(sp):
+    """The O-grid bench workload (150 x 600 body-fitted cells about the
+    cylinder, ~4 M particles, freestream reservoir rings): upload location
+    and one step bit-exact against the oracle."""
+    cfg, regions = W.cylinder_ogrid(nr=150, nt=600, r_out=4.0, growth=1.01, ppc=40.0, Kn=0.01, n_steady=0)
+    pos, vel = W.fill_regions(cfg, regions, 1)
+    c = _one_step_parity(sp, cfg, pos, vel)
+    assert c[0].sum() > 0
