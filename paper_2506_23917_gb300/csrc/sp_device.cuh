@@ -817,6 +817,10 @@ struct ExactSum {
 };
 template <class T, class A>
 using CellAcc = typename std::conditional<mixed_prec<T, A>(), ExactSum, PlainSum<T>>::type;
+// An FP32 accumulator as the pair (s, e) whose FP64 sum is its value.
+__device__ __forceinline__ float2 acc_pair(const ExactSum& x) { return make_float2(x.s, x.e); }
+__device__ __forceinline__ float2 acc_pair(const PlainSum<float>& x) { return make_float2(x.s, 0.0f); }
+__device__ __forceinline__ float2 acc_pair(const PlainSum<double>&) { return make_float2(0.0f, 0.0f); }
 
 // Parameters of instance i.  With a single instance (ONE) they come from
 // the copy in the kernel's parameter space, so that the geometry and gas
@@ -3187,17 +3191,22 @@ __global__ void k_keys_mesh(const T* x0, const T* x1, int64_t M, const uint32_t*
 // Moments of the current state for cells [c0, c1), in the cells' current
 // slot order, in two kernels.  k_moment_sums: one warp per cell; lanes
 // stride over the cell's slots, a butterfly combines them, and lane 0
-// writes U (3) and the central sums sum |C|^2, sum |C|^2 C (3) of the cell
-// to sums[7][nc].  The sums use the collision kernel's accumulator (FP64
-// values in FP64 mode, FP32 terms carried without loss in FP32 mode, plain
-// FP32 in the all-FP32 mode).  k_moment_cells: one thread per cell forms the
-// FP64 scalars (n, T, q, tau, dt_c, the split ratio) from them, so that the
-// narrow FP64 pipe works on full warps, and writes the fields to out
-// [12][nc] or, with out == nullptr, takes the minimum dt_c into dt_min.
+// writes the cell's sums to sums[7][nc]: sum c (3), then sum |C|^2 and
+// sum |C|^2 C (3) about the mean.  The sums use the collision kernel's
+// accumulators (FP64 values in FP64 mode, FP32 terms carried without loss in
+// FP32 mode, plain FP32 in the all-FP32 mode).  With an FP32 state a sum is
+// stored as its FP32 pair (s, e) in the 8-byte slot, so that this kernel
+// issues no FP64 instruction: on GB300 one costs a whole warp ~67 cycles of
+// a scheduler's FP64 unit even with one lane active, and a warp per cell
+// would spend most of its time there.  k_moment_cells: one thread per cell
+// forms the FP64 values and scalars (U, n, T, q, tau, dt_c, the split
+// ratio) from them on full warps, and writes the fields to out [12][nc] or,
+// with out == nullptr, takes the minimum dt_c into dt_min.
 template <class T, class A>
 __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) {
   using Acc = CellAcc<T, A>;
   constexpr bool kMixed = mixed_prec<T, A>();
+  constexpr bool kPair = sizeof(T) == 4;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nc = c1 - c0;
@@ -3207,41 +3216,40 @@ __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) 
   for (int64_t k = c0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c1; k += nw) {
     const uint32_t s0 = a.start[k];
     const int N = (int)(a.start[k + 1] - s0);
-    double U[3] = {0, 0, 0};
+    Acc sx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sx[d].init();
+    for (int s = lane; s < N; s += 32) {
+      const uint32_t o = a.perm[s0 + s];
+      sx[0].add1(Av0[o]);
+      sx[1].add1(Av1[o]);
+      sx[2].add1(Av2[o]);
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) sx[d].combine(sx[d].shfl_xor(m));
+    // the shift of the central sums: the mean (FP32 state: the FP32 pair
+    // U_h + U_l of the exact sum, formed without FP64 work)
     T Uh[3] = {0, 0, 0}, Ul[3] = {0, 0, 0};
-    {
-      Acc sx[3];
+    if (N > 0) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) sx[d].init();
-      for (int s = lane; s < N; s += 32) {
-        const uint32_t o = a.perm[s0 + s];
-        sx[0].add1(Av0[o]);
-        sx[1].add1(Av1[o]);
-        sx[2].add1(Av2[o]);
-      }
-#pragma unroll
-      for (int m = 16; m > 0; m >>= 1)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) sx[d].combine(sx[d].shfl_xor(m));
-      if (N > 0) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          U[d] = (double)sx[d].get() / N;
-          if constexpr (kMixed) {
-            const float fN = (float)N, rN = 1.0f / fN;
-            Uh[d] = sx[d].s * rN;
-            Ul[d] = (fmaf(-Uh[d], fN, sx[d].s) + sx[d].e) * rN;
-          } else {
-            Uh[d] = (T)U[d];
-          }
+      for (int d = 0; d < 3; ++d) {
+        if constexpr (kMixed) {
+          const float fN = (float)N, rN = 1.0f / fN;
+          Uh[d] = sx[d].s * rN;
+          Ul[d] = (fmaf(-Uh[d], fN, sx[d].s) + sx[d].e) * rN;
+        } else if constexpr (kPair) {
+          Uh[d] = sx[d].get() * (1.0f / (float)N);
+        } else {
+          Uh[d] = (T)((double)sx[d].get() / N);
         }
       }
     }
-    double S2 = 0, S3x = 0, S3y = 0, S3z = 0;
-    if (N >= 2) {
-      Acc r[4];
+    Acc r[4];
 #pragma unroll
-      for (int d = 0; d < 4; ++d) r[d].init();
+    for (int d = 0; d < 4; ++d) r[d].init();
+    if (N >= 2) {
       for (int s = lane; s < N; s += 32) {
         const uint32_t o = a.perm[s0 + s];
         T C0 = Av0[o] - Uh[0], C1 = Av1[o] - Uh[1], C2 = Av2[o] - Uh[2];
@@ -3260,25 +3268,37 @@ __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) 
       for (int m = 16; m > 0; m >>= 1)
 #pragma unroll
         for (int d = 0; d < 4; ++d) r[d].combine(r[d].shfl_xor(m));
-      S2 = (double)r[0].get();
-      S3x = (double)r[1].get();
-      S3y = (double)r[2].get();
-      S3z = (double)r[3].get();
     }
     if (lane == 0) {
       const int64_t i = k - c0;
-      sums[0 * nc + i] = U[0];
-      sums[1 * nc + i] = U[1];
-      sums[2 * nc + i] = U[2];
-      sums[3 * nc + i] = S2;
-      sums[4 * nc + i] = S3x;
-      sums[5 * nc + i] = S3y;
-      sums[6 * nc + i] = S3z;
+      if constexpr (kPair) {
+        float2* sp2 = (float2*)sums;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sp2[d * nc + i] = acc_pair(sx[d]);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) sp2[(3 + d) * nc + i] = acc_pair(r[d]);
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sums[d * nc + i] = (double)sx[d].get();
+#pragma unroll
+        for (int d = 0; d < 4; ++d) sums[(3 + d) * nc + i] = (double)r[d].get();
+      }
     }
   }
 }
 
-static __global__ void k_moment_cells(StepArgs a, int64_t c0, int64_t c1, const double* sums, double* out) {
+template <bool kPair>
+__device__ __forceinline__ double moment_sum(const double* sums, int64_t idx) {
+  if constexpr (kPair) {
+    const float2 p = ((const float2*)sums)[idx];
+    return (double)p.x + (double)p.y;
+  } else {
+    return sums[idx];
+  }
+}
+
+template <bool kPair>
+__global__ void k_moment_cells(StepArgs a, int64_t c0, int64_t c1, const double* sums, double* out) {
   const int64_t nc = c1 - c0;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc) return;
@@ -3287,23 +3307,28 @@ static __global__ void k_moment_cells(StepArgs a, int64_t c0, int64_t c1, const 
   const InstParams& P = a.P[a.cell_inst[k]];
   const double Lk = a.Lc ? a.Lc[k] : P.Lmin;
   CellMoments m;
-  m.U[0] = N > 0 ? sums[0 * nc + i] : 0.0;
-  m.U[1] = N > 0 ? sums[1 * nc + i] : 0.0;
-  m.U[2] = N > 0 ? sums[2 * nc + i] : 0.0;
+  m.U[0] = m.U[1] = m.U[2] = 0;
+  if (N > 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) m.U[d] = moment_sum<kPair>(sums, d * nc + i) / N;
+  }
   m.n = N > 0 ? (double)N * P.Fn / a.vol[k] : 0.0;
   m.T = 0; m.q[0] = m.q[1] = m.q[2] = 0;
   m.tau = __longlong_as_double(0x7FF0000000000000ll);
   m.dtc = m.tau;
   if (N >= 2) {
-    m.T = sums[3 * nc + i] / (3.0 * P.R * (double)(N - 1));
-    if (N >= 3) {
+    m.T = moment_sum<kPair>(sums, 3 * nc + i) / (3.0 * P.R * (double)(N - 1));
+    if (N >= 3 && out) {
       const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
-      m.q[0] = f * sums[4 * nc + i]; m.q[1] = f * sums[5 * nc + i]; m.q[2] = f * sums[6 * nc + i];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) m.q[d] = f * moment_sum<kPair>(sums, (4 + d) * nc + i);
     }
     const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
     if (m.T > 0) {
-      const double p = m.n * P.m * P.R * m.T;
-      m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
+      if (out) {  // tau is an output field only (dt_c does not need it)
+        const double p = m.n * P.m * P.R * m.T;
+        m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
+      }
       m.dtc = Lk / (umag + sqrt(P.gamma * P.R * m.T));
     } else if (umag > 0) {
       m.dtc = Lk / umag;

@@ -81,7 +81,7 @@ void moments(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_
   int64_t g = (nc + 7) / 8;  // a warp per cell, 8 warps per block, grid-stride
   if (g > 65535) g = 65535;
   k_moment_sums<T, A><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, a.msum);
-  k_moment_cells<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(a, c0, c1, a.msum, out);
+  k_moment_cells<sizeof(T) == 4><<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(a, c0, c1, a.msum, out);
 }
 
 template <int DIM>
