@@ -2059,18 +2059,14 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   }
   if (__any_sync(kFull, need_sq)) {
     A r[3];
-    cell_sums<Acc, 3, true>(need_sq, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
+    // (mixed precision: the FP32 squares, each rounded as the FP32 state
+    // itself is, summed without loss; exact squares cost 1.6 %)
+    cell_sums<Acc, 3>(need_sq, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
-      if constexpr (kMixed) {
-        v[0] = two_prod(x0, x0, &lo[0]);
-        v[1] = two_prod(x1, x1, &lo[1]);
-        v[2] = two_prod(x2, x2, &lo[2]);
-      } else {
-        v[0] = x0 * x0;
-        v[1] = x1 * x1;
-        v[2] = x2 * x2;
-        lo[0] = lo[1] = lo[2] = 0;
-      }
+      v[0] = x0 * x0;
+      v[1] = x1 * x1;
+      v[2] = x2 * x2;
+      lo[0] = lo[1] = lo[2] = 0;
     });
     if (need_sq) {
       b0 = r[0];
@@ -2874,18 +2870,12 @@ __global__ void __launch_bounds__(kHugeThreads, 2) k_collide_huge(StepArgs a) {
     // ---- 8. Step 5 sums
     if (sample) {
       if (!bsq_ok) {
-        block_sums<Acc, 3, true>(tb, N, bsq, [&](int s, auto* v, auto* lo) {
+        block_sums<Acc, 3>(tb, N, bsq, [&](int s, auto* v, auto* lo) {
           const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
-          if constexpr (kMixed) {
-            v[0] = two_prod(x0, x0, &lo[0]);
-            v[1] = two_prod(x1, x1, &lo[1]);
-            v[2] = two_prod(x2, x2, &lo[2]);
-          } else {
-            v[0] = x0 * x0;
-            v[1] = x1 * x1;
-            v[2] = x2 * x2;
-            lo[0] = lo[1] = lo[2] = 0;
-          }
+          v[0] = x0 * x0;
+          v[1] = x1 * x1;
+          v[2] = x2 * x2;
+          lo[0] = lo[1] = lo[2] = 0;
         });
       }
       if (tid == 0) {
@@ -3189,44 +3179,50 @@ __global__ void k_keys_mesh(const T* x0, const T* x1, int64_t M, const uint32_t*
 // Observability / initialisation kernels
 // ---------------------------------------------------------------------------
 // Moments of the current state for cells [c0, c1), in the cells' current
-// slot order, in two kernels.  k_moment_sums: one warp per cell; lanes
-// stride over the cell's slots, a butterfly combines them, and lane 0
-// writes the cell's sums to sums[7][nc]: sum c (3), then sum |C|^2 and
-// sum |C|^2 C (3) about the mean.  The sums use the collision kernel's
-// accumulators (FP64 values in FP64 mode, FP32 terms carried without loss in
-// FP32 mode, plain FP32 in the all-FP32 mode).  With an FP32 state a sum is
-// stored as its FP32 pair (s, e) in the 8-byte slot, so that this kernel
-// issues no FP64 instruction: on GB300 one costs a whole warp ~67 cycles of
-// a scheduler's FP64 unit even with one lane active, and a warp per cell
-// would spend most of its time there.  k_moment_cells: one thread per cell
-// forms the FP64 values and scalars (U, n, T, q, tau, dt_c, the split
-// ratio) from them on full warps, and writes the fields to out [12][nc] or,
-// with out == nullptr, takes the minimum dt_c into dt_min.
+// slot order, in two kernels.  k_moment_sums: a half-warp (16 lanes) per
+// cell; lanes stride over the cell's slots, a butterfly combines them, and
+// the first lane writes the cell's sums to sums[7][nc]: sum c (3), then
+// sum |C|^2 and sum |C|^2 C (3) about the mean.  The sums use the
+// collision kernel's accumulators (FP64 values in FP64 mode, FP32 terms
+// carried without loss in FP32 mode, plain FP32 in the all-FP32 mode).
+// With an FP32 state a sum is stored as its FP32 pair (s, e) in the 8-byte
+// slot, so that this kernel issues no FP64 instruction: on GB300 one costs
+// a whole warp ~67 cycles of a scheduler's FP64 unit even with one lane
+// active, and a kernel with a few lanes per cell would spend most of its
+// time there.  k_moment_cells: one thread per cell forms the FP64 values and
+// scalars (U, n, T, q, tau, dt_c, the split ratio) from them on full warps,
+// and writes the fields to out [12][nc] or, with out == nullptr, takes the
+// minimum dt_c into dt_min.
 template <class T, class A>
 __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) {
   using Acc = CellAcc<T, A>;
   constexpr bool kMixed = mixed_prec<T, A>();
   constexpr bool kPair = sizeof(T) == 4;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  // a half-warp per cell (16 lanes, two cells per warp)
+  const int lane = threadIdx.x & 15;
+  const int64_t nh = (int64_t)gridDim.x * (blockDim.x >> 4);
   const int64_t nc = c1 - c0;
   const T* Av0 = (const T*)a.Avel[0];
   const T* Av1 = (const T*)a.Avel[1];
   const T* Av2 = (const T*)a.Avel[2];
-  for (int64_t k = c0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < c1; k += nw) {
-    const uint32_t s0 = a.start[k];
-    const int N = (int)(a.start[k + 1] - s0);
+  // the same trip count for both halves of a warp (the shuffles need all lanes)
+  const int64_t h0 = (int64_t)blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4);
+  for (int64_t kb = c0 + (h0 & ~(int64_t)1); kb < c1; kb += nh) {
+    const int64_t k = kb + (h0 & 1);
+    const bool valid = k < c1;
+    const uint32_t s0 = valid ? a.start[k] : 0u;
+    const int N = valid ? (int)(a.start[k + 1] - s0) : 0;
     Acc sx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) sx[d].init();
-    for (int s = lane; s < N; s += 32) {
+    for (int s = lane; s < N; s += 16) {
       const uint32_t o = a.perm[s0 + s];
       sx[0].add1(Av0[o]);
       sx[1].add1(Av1[o]);
       sx[2].add1(Av2[o]);
     }
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1)
+    for (int m = 8; m > 0; m >>= 1)
 #pragma unroll
       for (int d = 0; d < 3; ++d) sx[d].combine(sx[d].shfl_xor(m));
     // the shift of the central sums: the mean (FP32 state: the FP32 pair
@@ -3250,7 +3246,7 @@ __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) 
 #pragma unroll
     for (int d = 0; d < 4; ++d) r[d].init();
     if (N >= 2) {
-      for (int s = lane; s < N; s += 32) {
+      for (int s = lane; s < N; s += 16) {
         const uint32_t o = a.perm[s0 + s];
         T C0 = Av0[o] - Uh[0], C1 = Av1[o] - Uh[1], C2 = Av2[o] - Uh[2];
         if constexpr (kMixed) {
@@ -3264,12 +3260,12 @@ __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) 
         r[2].add1(c2 * C1);
         r[3].add1(c2 * C2);
       }
-#pragma unroll
-      for (int m = 16; m > 0; m >>= 1)
-#pragma unroll
-        for (int d = 0; d < 4; ++d) r[d].combine(r[d].shfl_xor(m));
     }
-    if (lane == 0) {
+#pragma unroll
+    for (int m = 8; m > 0; m >>= 1)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) r[d].combine(r[d].shfl_xor(m));
+    if (lane == 0 && valid) {
       const int64_t i = k - c0;
       if constexpr (kPair) {
         float2* sp2 = (float2*)sums;

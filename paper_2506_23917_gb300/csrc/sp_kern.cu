@@ -78,7 +78,7 @@ void inject(int dim, const InjectArgs& a, int pass, cudaStream_t s) {
 void moments(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_t s) {
   const int64_t nc = c1 - c0;
   if (nc <= 0) return;
-  int64_t g = (nc + 7) / 8;  // a warp per cell, 8 warps per block, grid-stride
+  int64_t g = (nc + 15) / 16;  // a half-warp per cell, 16 cells per block, grid-stride
   if (g > 65535) g = 65535;
   k_moment_sums<T, A><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, a.msum);
   k_moment_cells<sizeof(T) == 4><<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(a, c0, c1, a.msum, out);
