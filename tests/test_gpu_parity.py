@@ -372,3 +372,33 @@ def test_o_grid_dense_cells_match_oracle(sp):
     o, s, tot = run_pair(sp, cfg, pos, vel, steps=4)
     assert np.diff(o.cell_start().astype(np.int64)).max() > 1024
     assert tot[0] > 0
+
+
+def test_batched_o_grids_match_separate_oracles(sp):
+    """Three O-grid instances of different shape (sizes, growth, outer
+    boundary, body radius) in one context: each equals its own oracle run
+    bit for bit (node, face and radius offsets per instance)."""
+    specs = [dict(nr=8, nt=16, r_out=2.5, growth=1.1, outer=W.BC_INFLOW, seed=3),
+             dict(nr=5, nt=9, r_out=3.0, growth=1.0, outer=W.BC_DIFFUSE, seed=4, body_r=0.5),
+             dict(nr=12, nt=20, r_out=2.0, growth=1.05, outer=W.BC_SPECULAR, seed=5)]
+    insts = []
+    for sp_ in specs:
+        cfg, regions = W.ogrid_box(ppc=25.0, n_steady=2, **sp_)
+        pos, vel = W.fill_regions(cfg, regions, sp_["seed"])
+        insts.append((cfg, pos, vel))
+    s = sp.Sim([c for c, _, _ in insts], sp.FP64, capacity=60000)
+    s.set_record(True)
+    os_ = []
+    for i, (c, p, v) in enumerate(insts):
+        s.set_particles(i, p, v)
+        o = oracle.Oracle(c)
+        o.set_particles(p, v)
+        os_.append(o)
+    for n in range(6):
+        s.step(1)
+        for i, o in enumerate(os_):
+            o.step(1)
+            compare_record(o, s, inst=i, what=f"o-grid {i} step {n}")
+            compare_state(o, s, inst=i, what=f"o-grid {i} step {n}")
+    for i, o in enumerate(os_):
+        _close(s.moments(i, 1), o.moments(1), what=f"o-grid {i} averages")
