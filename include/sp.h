@@ -137,8 +137,10 @@ typedef struct sp_config {
    * a freestream reservoir of ghost_layers rings continuing the radial
    * spacing, at face_n/T/u[1]; outflow; specular; diffuse at face_T[1]).
    * Particles find their cell by face crossing; the local observation time
-   * uses each cell's shortest edge; lo/hi[0..1] are ignored, hi[2] - lo[2]
-   * is the depth.  Requires body = SP_BODY_CIRCLE, subcells <= 1. */
+   * uses each cell's shortest edge; lo/hi[0..1] must be a non-empty box but
+   * are not used (the bounding box of the outer polygon is customary), and
+   * hi[2] - lo[2] is the depth.  Requires body = SP_BODY_CIRCLE,
+   * subcells <= 1; SP_ERR_ARG otherwise. */
   int32_t mesh;
   double mesh_r_out, mesh_growth;
 } sp_config;
