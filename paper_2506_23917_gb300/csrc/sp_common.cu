@@ -170,7 +170,7 @@ __global__ void k_step_finalize(const InstParams* P, int n_inst, double* dt_cur,
 // mean per particle, and a warp takes only a few batches per launch.
 // Class k's list is batches[k NC ...].  Batches are independent: their
 // order changes no result.
-__global__ void k_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, uint2* batches,
+__global__ void k_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, int split, uint2* batches,
                        uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count) {
   // per block: the batches of each class (shared atomics), then one global
   // atomic per class for the block's place in the class list
@@ -194,20 +194,26 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, i
       // inclusive prefix sums of the particle counts and the predicted costs
       const int64_t nl = lane < nc ? (int64_t)(start[c0 + lane + 1] - start[c0 + lane]) : 0;
       const int64_t wl = lane < nc ? (cost[c0 + lane] ? (int64_t)cost[c0 + lane] : 16) : 0;
+      // lanes of the per-cell sums (split cells; at most 32 per batch)
+      int lcum = lane < nc ? cell_lanes((int)(nl < 0x7FFFFFFF ? nl : 0x7FFFFFFF), split) : 0;
       int64_t cum = nl, ccum = nl * wl;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int64_t y = __shfl_up_sync(0xFFFFFFFFu, cum, o);
         const int64_t z = __shfl_up_sync(0xFFFFFFFFu, ccum, o);
+        const int w = __shfl_up_sync(0xFFFFFFFFu, lcum, o);
         if (lane >= o) {
           cum += y;
           ccum += z;
+          lcum += w;
         }
       }
       int kk = 0;
       while (kk < nc) {
         const int64_t before = kk > 0 ? __shfl_sync(0xFFFFFFFFu, cum, kk - 1) : 0;
-        const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap);
+        const int lbefore = kk > 0 ? __shfl_sync(0xFFFFFFFFu, lcum, kk - 1) : 0;
+        const unsigned fit = __ballot_sync(0xFFFFFFFFu, lane >= kk && lane < nc && cum - before <= cap &&
+                                                          lcum - lbefore <= 32);
         const int G = __popc(fit);
         if (G == 0) {  // the cell alone exceeds the staging area: big-cell list
           if (lane == 0) {
@@ -250,13 +256,13 @@ __global__ void k_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, i
 
 }  // namespace
 
-void launch_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
-                 uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
+void launch_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, int split, uint2* batches,
+                 uint32_t* nbatch, uint32_t* big_list, uint32_t* big_count, cudaStream_t s) {
   const int64_t chunks = (NC + 31) / 32;
   int64_t g = (chunks + 7) / 8;
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
-  k_plan<<<(unsigned)g, 256, 0, s>>>(start, cost, NC, cap, batches, nbatch, big_list, big_count);
+  k_plan<<<(unsigned)g, 256, 0, s>>>(start, cost, NC, cap, split, batches, nbatch, big_list, big_count);
 }
 
 int64_t scan_partial_size(int64_t n) { return (n + kTile - 1) / kTile + 1; }

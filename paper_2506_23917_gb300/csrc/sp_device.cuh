@@ -705,6 +705,7 @@ struct __align__(16) CellTab {
   int nacc[32];
   int coff[33];  // candidate offsets of the flattened NTC loop
   int pad[2];
+  uint16_t hpart[32];  // helper lane -> (cell << 8 | part) of the split sums
   uint16_t soff[32][kMaxSub + 1];  // sub-cell offsets within each cell (sub-cells on)
   T U[3][32];
   T q[3][32];
@@ -784,6 +785,11 @@ struct PlainSum {
     r.s = __shfl_xor_sync(kFull, s, o);
     return r;
   }
+  __device__ __forceinline__ PlainSum shfl_from(int src) const {
+    PlainSum r;
+    r.s = __shfl_sync(kFull, s, src);
+    return r;
+  }
   __device__ __forceinline__ T get() const { return s; }
 };
 struct ExactSum {
@@ -811,6 +817,12 @@ struct ExactSum {
     ExactSum r;
     r.s = __shfl_xor_sync(kFull, s, o);
     r.e = __shfl_xor_sync(kFull, e, o);
+    return r;
+  }
+  __device__ __forceinline__ ExactSum shfl_from(int src) const {
+    ExactSum r;
+    r.s = __shfl_sync(kFull, s, src);
+    r.e = __shfl_sync(kFull, e, src);
     return r;
   }
   __device__ __forceinline__ double get() const { return (double)s + (double)e; }
@@ -843,22 +855,27 @@ __device__ __forceinline__ const InstParams& inst_params(const StepArgs& a, uint
 }
 
 // Per-cell sums with an order fixed by the cell alone (so results do not
-// depend on how cells are grouped into batches): a cell of at most
+// depend on how cells are grouped into batches).  A cell of at most
 // kLaneSumMax particles is summed by its own lane (lane i <-> cell i) in
-// slot order, with no shuffles; a larger cell by the warp, one contiguous
-// share of its slots per lane, then a butterfly over the lanes (the order
-// again fixed by the cell's particle count).  f(s, c, v, lo) gives the K
-// terms of slot s of cell c (and their exact low parts); lane i receives
-// the sums of its own cell i in out[] (cells with own false are skipped).
-constexpr int kLaneSumMax = 256;
-constexpr int kLaneSumMaxExact = 256;
+// slot order; with an FP32 state a cell above kSplitLanes particles is cut
+// into P = cell_lanes(N) contiguous parts of ceil(N / P) slots, part 0 on
+// its own lane and parts 1..P-1 on helper lanes of the batch (lanes G,
+// G+1, ... in cell order), and its lane adds the parts in part order -- so
+// that a dense batch's loops run over ~N / P slots instead of N.  A larger
+// cell is summed by the warp, one contiguous share of its slots per lane,
+// then a butterfly over the lanes (the order again fixed by the cell's
+// particle count).  f(s, c, v, lo) gives the K terms of slot s of cell c
+// (and their exact low parts); lane i receives the sums of its own cell i
+// in out[] (cells with own false are skipped).
+constexpr int kLaneSumMaxExact = kLaneSumMax;
 // Cells above kHugeCell particles (sp_internal.h) are collided by one
 // block of kHugeThreads threads each (k_collide_huge).
 constexpr int kHugeThreads = 256;
 constexpr int kHugeWarps = kHugeThreads / 32;
 // NTC candidates up to which a cell runs its collision loop on its own lane:
 // in 3-D (sphere: +18 %; thresholds 8-32 gave -7 % to +9 %); not in 2-D,
-// where the flattened loop is as fast or faster (cylinder: -1 % to -3 %)
+// where the flattened loop is as fast or faster (cylinder: -1 % to -3 %;
+// again -3 % / -4 % for 64 / 256 with FP64-accurate cells)
 template <int DIM>
 constexpr int kLaneNtcMax = DIM == 3 ? 256 : 0;
 // Cells above lane_sum_max<Acc> particles are summed by the whole warp.
@@ -867,22 +884,100 @@ constexpr int kLaneNtcMax = DIM == 3 ? 256 : 0;
 // costs more than the lanes a dense cell leaves idle.)
 template <class Acc>
 constexpr int lane_sum_max = Acc::kExact ? kLaneSumMaxExact : kLaneSumMax;
+// Parts split per cell for state type T (0: one lane per cell).
+template <class T>
+constexpr int kSplitOf = sizeof(T) == 4 ? kSplitLanes : 0;
+
+// The part of the per-cell sums a lane of the batch serves: owner lanes
+// (lane < G) part 0 of their own cell, helper lanes a later part of
+// another cell.  c = -1: none.  own_parts / h0: for an owner lane, its
+// cell's part count and the helper lane of part 1.
+struct LanePart {
+  int c, b, e;
+  int own_parts, h0;
+};
+
+// The lanes' parts of a batch of G cells (cells with Ni > kLaneSumMax: one
+// part, summed by the warp path); helper lanes read their (cell, part) from
+// the table.  Called by the whole warp.
+template <class TabT>
+__device__ __forceinline__ LanePart lane_parts(TabT* ct, int G, bool own, int offi, int Ni, int split) {
+  const int lane = threadIdx.x & 31;
+  LanePart lp;
+  lp.c = -1;
+  lp.b = lp.e = 0;
+  lp.own_parts = 1;
+  lp.h0 = 0;
+  int L = own ? cell_lanes(Ni, split) : 1;
+  int hs = L - 1;  // inclusive scan of the helpers over the cells
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, hs, o);
+    if (lane >= o) hs += y;
+  }
+  int nhelp = __shfl_sync(kFull, hs, 31);
+  hs -= L - 1;  // exclusive
+  if (G + nhelp > 32) {  // (the batch plan never makes such a batch)
+    L = 1;
+    hs = 0;
+    nhelp = 0;
+  }
+  if (own) {
+    const int h = (Ni + L - 1) / L;
+    lp.c = lane;
+    lp.b = offi;
+    lp.e = offi + (h < Ni ? h : Ni);
+    lp.own_parts = L;
+    lp.h0 = G + hs;
+    for (int p = 1; p < L; ++p) ct->hpart[hs + p - 1] = (uint16_t)((lane << 8) | p);
+  }
+  __syncwarp();
+  if (lane >= G && lane - G < nhelp) {
+    const int hp = ct->hpart[lane - G];
+    const int c = hp >> 8, p = hp & 255;
+    const int o0 = ct->off[c], n = ct->off[c + 1] - o0;
+    const int Lc = cell_lanes(n, split);
+    const int h = (n + Lc - 1) / Lc;
+    lp.c = c;
+    lp.b = o0 + p * h;
+    lp.e = o0 + ((p + 1) * h < n ? (p + 1) * h : n);
+  }
+  return lp;
+}
+
 // kLo: the terms come with exact low parts (else lo is ignored).
 template <class Acc, int K, bool kLo = false, class F>
-__device__ __forceinline__ void cell_sums_acc(bool own, int offi, int Ni, Acc (&out)[K], F f) {
+__device__ __forceinline__ void cell_sums_acc(const LanePart& lp, bool own, int offi, int Ni, Acc (&out)[K], F f) {
   using Tm = typename Acc::term;
   const int lane = threadIdx.x & 31;
   const bool small = own && Ni <= lane_sum_max<Acc>;
 #pragma unroll
   for (int k = 0; k < K; ++k) out[k].init();
-  if (small) {
-    for (int s = offi; s < offi + Ni; ++s) {
+  // this lane's part: its own small cell, or a helper's part of a small
+  // cell that takes part in this call
+  const int cp = lp.c >= 0 ? lp.c : lane;
+  const bool on = __shfl_sync(kFull, small, cp) && lp.c >= 0;
+  if (on) {
+    for (int s = lp.b; s < lp.e; ++s) {
       Tm v[K], lo[K];
-      f(s, lane, v, lo);
+      f(s, lp.c, v, lo);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if constexpr (kLo) out[k].add(v[k], lo[k]);
         else out[k].add1(v[k]);
+      }
+    }
+  }
+  // the owner adds parts 1.. in part order
+  if (__any_sync(kFull, small && lp.own_parts > 1)) {
+#pragma unroll
+    for (int p = 1; p < kMaxParts; ++p) {
+      const bool take = small && p < lp.own_parts;
+      const int src = take ? lp.h0 + p - 1 : lane;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const Acc o = out[k].shfl_from(src);
+        if (take) out[k].combine(o);
       }
     }
   }
@@ -916,9 +1011,10 @@ __device__ __forceinline__ void cell_sums_acc(bool own, int offi, int Ni, Acc (&
 }
 
 template <class Acc, int K, bool kLo = false, class F>
-__device__ __forceinline__ void cell_sums(bool own, int offi, int Ni, typename Acc::result (&out)[K], F f) {
+__device__ __forceinline__ void cell_sums(const LanePart& lp, bool own, int offi, int Ni,
+                                          typename Acc::result (&out)[K], F f) {
   Acc acc[K];
-  cell_sums_acc<Acc, K, kLo>(own, offi, Ni, acc, f);
+  cell_sums_acc<Acc, K, kLo>(lp, own, offi, Ni, acc, f);
 #pragma unroll
   for (int k = 0; k < K; ++k) out[k] = acc[k].get();
 }
@@ -1286,6 +1382,8 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   }
   if (lane == 0) ct->off[G] = M;
   __syncwarp();
+  // the lanes' parts of the per-cell sums (split cells: FP32 state only)
+  const LanePart lp = lane_parts(ct, G, own, offi, Ni, kSplitOf<T>);
   // ---- 1. source indices, cell of each slot, stable order within cells
   // (the index copies run while the cell of each slot is written)
 #pragma unroll 4
@@ -1475,7 +1573,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   if (__any_sync(kFull, two_pass)) {
     A r1[3];
     Acc a1[3];
-    cell_sums_acc<Acc, 3>(two_pass, offi, Ni, a1, [&](int s, int c, T* v, T* lo) {
+    cell_sums_acc<Acc, 3>(lp, two_pass, offi, Ni, a1, [&](int s, int c, T* v, T* lo) {
       v[0] = svx[s];
       v[1] = svy[s];
       v[2] = svz[s];
@@ -1506,7 +1604,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
     // only; sum |C|^2 C, needed by the Shakhov cells alone, after Step 4)
     constexpr int K2 = kMixed ? 1 : 4;
     A r2[K2];
-    cell_sums<Acc, K2>(two_pass, offi, Ni, r2, [&](int s, int c, T* v, T* lo) {
+    cell_sums<Acc, K2>(lp, two_pass, offi, Ni, r2, [&](int s, int c, T* v, T* lo) {
       T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
       if constexpr (kMixed) {
         C0 -= ct->Kl[0][c];
@@ -1578,7 +1676,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
     const bool qsh = own && cm.shk;
     if (__any_sync(kFull, qsh)) {
       A r3[3];
-      cell_sums<Acc, 3>(qsh, offi, Ni, r3, [&](int s, int c, T* v, T* lo) {
+      cell_sums<Acc, 3>(lp, qsh, offi, Ni, r3, [&](int s, int c, T* v, T* lo) {
         const T C0 = (svx[s] - ct->Up[0][c]) - ct->Kl[0][c];
         const T C1 = (svy[s] - ct->Up[1][c]) - ct->Kl[1][c];
         const T C2 = (svz[s] - ct->Up[2][c]) - ct->Kl[2][c];
@@ -1907,7 +2005,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
     if constexpr (!kMixed) {
       // the U_p pass, then T_p about U_p (the oracle's order)
       A r1[3];
-      cell_sums<Acc, 3>(rown, offi, Ni, r1, [&](int s, int c, T* v, T* lo) {
+      cell_sums<Acc, 3>(lp, rown, offi, Ni, r1, [&](int s, int c, T* v, T* lo) {
         v[0] = svx[s];
         v[1] = svy[s];
         v[2] = svz[s];
@@ -1920,7 +2018,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       }
       __syncwarp();
       A r2[1];
-      cell_sums<Acc, 1>(rown, offi, Ni, r2, [&](int s, int c, T* v, T* lo) {
+      cell_sums<Acc, 1>(lp, rown, offi, Ni, r2, [&](int s, int c, T* v, T* lo) {
         const T C0 = svx[s] - ct->Up[0][c], C1 = svy[s] - ct->Up[1][c], C2 = svz[s] - ct->Up[2][c];
         v[0] = C0 * C0 + C1 * C1 + C2 * C2;
         lo[0] = 0;
@@ -1950,7 +2048,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
       // The map is then applied as c' = c f + K, K = U - U_p f, with f and
       // K as FP32 pairs.
       A r[6];
-      cell_sums<Acc, 6, true>(rown, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
+      cell_sums<Acc, 6, true>(lp, rown, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
         const T x[3] = {svx[s], svy[s], svz[s]};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -1999,7 +2097,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
         // they are rounded to FP32) summed in FP64, against the targets
         const bool chk = rown && ct->f[lane] > (T)0;
         double r3[4];
-        cell_sums<PlainSum<double>, 4>(chk, offi, Ni, r3, [&](int s, int c, double* v, double* lo) {
+        cell_sums<PlainSum<double>, 4>(lp, chk, offi, Ni, r3, [&](int s, int c, double* v, double* lo) {
           const T x[3] = {svx[s], svy[s], svz[s]};
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
@@ -2033,7 +2131,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
         // record mode, FP64 mode: the rescaled velocities summed in FP64
         const bool chk = rown && ct->f[lane] > (T)0;
         double r3[4];
-        cell_sums<PlainSum<double>, 4>(chk, offi, Ni, r3, [&](int s, int c, double* v, double* lo) {
+        cell_sums<PlainSum<double>, 4>(lp, chk, offi, Ni, r3, [&](int s, int c, double* v, double* lo) {
           v[0] = svx[s];
           v[1] = svy[s];
           v[2] = svz[s];
@@ -2061,7 +2159,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
     A r[3];
     // (mixed precision: the FP32 squares, each rounded as the FP32 state
     // itself is, summed without loss; exact squares cost 1.6 %)
-    cell_sums<Acc, 3>(need_sq, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
+    cell_sums<Acc, 3>(lp, need_sq, offi, Ni, r, [&](int s, int c, T* v, T* lo) {
       const T x0 = svx[s], x1 = svy[s], x2 = svz[s];
       v[0] = x0 * x0;
       v[1] = x1 * x1;

@@ -9,6 +9,20 @@ namespace sp {
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // key of a removed particle
 constexpr int kMaxBounce = 16;               // wall events per particle per step
 constexpr int kMaxCross = 4096;              // face crossings per particle per step (O-grid)
+// Per-cell sums in the collision kernel: a cell of at most kLaneSumMax
+// particles is summed by lanes of its batch's warp, above it by the whole
+// warp.  With an FP32 state such a cell takes ceil(N / kSplitLanes) lanes
+// (at most kMaxParts), each summing a contiguous part; the batch plan keeps
+// the lanes of a batch within 32.  FP64 mode: one lane per cell (the
+// oracle's summation order).  (Developed cylinder, 864 x 2: split 32 +2.5 %
+// over no split; 16 / 24 / 48 / 64 and 8 parts were slower than 32 -- more
+// lanes per cell leave fewer cells per batch.)
+constexpr int kLaneSumMax = 256;
+constexpr int kSplitLanes = 32;
+constexpr int kMaxParts = 4;
+__host__ __device__ constexpr int cell_lanes(int n, int split) {
+  return (split > 0 && n <= kLaneSumMax) ? (n <= split ? 1 : (n + split - 1) / split > kMaxParts ? kMaxParts : (n + split - 1) / split) : 1;
+}
 constexpr int kSurfFields = 7;  // wall tallies per surface element
 constexpr int64_t kNcolCap = int64_t(1) << 24;
 constexpr int kBatchClasses = 9;             // batch lists by predicted cost (most expensive first)
@@ -201,7 +215,7 @@ const KernelSet& kernels_f32c();
 
 // Precision-independent kernels (sp_common.cu).
 void launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, cudaStream_t s);
-void launch_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, uint2* batches, uint32_t* nbatch,
+void launch_plan(const uint32_t* start, const uint8_t* cost, int64_t NC, int cap, int split, uint2* batches, uint32_t* nbatch,
                  uint32_t* big_list, uint32_t* big_count, cudaStream_t s);
 void launch_scatter(const uint32_t* key, const uint32_t* start, uint32_t* count, uint32_t* perm,
                     const uint32_t* Mtot, int64_t cap, cudaStream_t s);
