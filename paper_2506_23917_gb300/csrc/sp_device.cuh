@@ -953,31 +953,47 @@ __device__ __forceinline__ void cell_sums_acc(const LanePart& lp, bool own, int 
   const bool small = own && Ni <= lane_sum_max<Acc>;
 #pragma unroll
   for (int k = 0; k < K; ++k) out[k].init();
-  // this lane's part: its own small cell, or a helper's part of a small
-  // cell that takes part in this call
-  const int cp = lp.c >= 0 ? lp.c : lane;
-  const bool on = __shfl_sync(kFull, small, cp) && lp.c >= 0;
-  if (on) {
-    for (int s = lp.b; s < lp.e; ++s) {
-      Tm v[K], lo[K];
-      f(s, lp.c, v, lo);
+  if constexpr (sizeof(Tm) == 8) {
+    // FP64 terms (FP64 mode; the FP32 mode's FP64 record sums): one lane
+    // per cell, in slot order
+    if (small) {
+      for (int s = offi; s < offi + Ni; ++s) {
+        Tm v[K], lo[K];
+        f(s, lane, v, lo);
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if constexpr (kLo) out[k].add(v[k], lo[k]);
-        else out[k].add1(v[k]);
+        for (int k = 0; k < K; ++k) {
+          if constexpr (kLo) out[k].add(v[k], lo[k]);
+          else out[k].add1(v[k]);
+        }
       }
     }
-  }
-  // the owner adds parts 1.. in part order
-  if (__any_sync(kFull, small && lp.own_parts > 1)) {
+  } else {
+    // this lane's part: its own small cell, or a helper's part of a small
+    // cell that takes part in this call
+    const int cp = lp.c >= 0 ? lp.c : lane;
+    const bool on = __shfl_sync(kFull, small, cp) && lp.c >= 0;
+    if (on) {
+      for (int s = lp.b; s < lp.e; ++s) {
+        Tm v[K], lo[K];
+        f(s, lp.c, v, lo);
 #pragma unroll
-    for (int p = 1; p < kMaxParts; ++p) {
-      const bool take = small && p < lp.own_parts;
-      const int src = take ? lp.h0 + p - 1 : lane;
+        for (int k = 0; k < K; ++k) {
+          if constexpr (kLo) out[k].add(v[k], lo[k]);
+          else out[k].add1(v[k]);
+        }
+      }
+    }
+    // the owner adds parts 1.. in part order
+    if (__any_sync(kFull, small && lp.own_parts > 1)) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const Acc o = out[k].shfl_from(src);
-        if (take) out[k].combine(o);
+      for (int p = 1; p < kMaxParts; ++p) {
+        const bool take = small && p < lp.own_parts;
+        const int src = take ? lp.h0 + p - 1 : lane;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const Acc o = out[k].shfl_from(src);
+          if (take) out[k].combine(o);
+        }
       }
     }
   }
