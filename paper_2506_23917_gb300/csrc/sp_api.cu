@@ -545,7 +545,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     cudaEventRecord(c->join_ev, c->side);
     n += 4;
   }
-  launch_plan(c->start, c->cost, c->NC, c->sched_cap, c->prec == SP_FP64 ? 0 : kSplitLanes, c->batches, c->nbatch, c->big_list, c->big_count,
+  launch_plan(c->start, c->cost, c->NC, c->sched_cap, (c->prec != SP_FP64 && c->dim == 2) ? kSplitLanes : 0, c->batches, c->nbatch, c->big_list, c->big_count,
               c->stream); ++n;
   if (branch) {
     // the big-cell launch (cells disjoint from the batches') is a branch

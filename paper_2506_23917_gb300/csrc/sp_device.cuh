@@ -884,9 +884,11 @@ constexpr int kLaneNtcMax = DIM == 3 ? 256 : 0;
 // costs more than the lanes a dense cell leaves idle.)
 template <class Acc>
 constexpr int lane_sum_max = Acc::kExact ? kLaneSumMaxExact : kLaneSumMax;
-// Parts split per cell for state type T (0: one lane per cell).
-template <class T>
-constexpr int kSplitOf = sizeof(T) == 4 ? kSplitLanes : 0;
+// Parts split per cell for state type T (0: one lane per cell): 2-D FP32
+// state only (in 1-D and 3-D the fewer cells per batch cost more than the
+// shorter loops gain: the sphere 1.55e10 -> 1.24e10, the 1-D batch -4 %).
+template <class T, int DIM>
+constexpr int kSplitOf = (sizeof(T) == 4 && DIM == 2) ? kSplitLanes : 0;
 
 // The part of the per-cell sums a lane of the batch serves: owner lanes
 // (lane < G) part 0 of their own cell, helper lanes a later part of
@@ -1399,7 +1401,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   if (lane == 0) ct->off[G] = M;
   __syncwarp();
   // the lanes' parts of the per-cell sums (split cells: FP32 state only)
-  const LanePart lp = lane_parts(ct, G, own, offi, Ni, kSplitOf<T>);
+  const LanePart lp = lane_parts(ct, G, own, offi, Ni, kSplitOf<T, DIM>);
   // ---- 1. source indices, cell of each slot, stable order within cells
   // (the index copies run while the cell of each slot is written)
 #pragma unroll 4

@@ -11,7 +11,7 @@ constexpr int kMaxBounce = 16;               // wall events per particle per ste
 constexpr int kMaxCross = 4096;              // face crossings per particle per step (O-grid)
 // Per-cell sums in the collision kernel: a cell of at most kLaneSumMax
 // particles is summed by lanes of its batch's warp, above it by the whole
-// warp.  With an FP32 state such a cell takes ceil(N / kSplitLanes) lanes
+// warp.  With an FP32 state in 2-D such a cell takes ceil(N / kSplitLanes) lanes
 // (at most kMaxParts), each summing a contiguous part; the batch plan keeps
 // the lanes of a batch within 32.  FP64 mode: one lane per cell (the
 // oracle's summation order).  (Developed cylinder, 864 x 2: split 32 +2.5 %
