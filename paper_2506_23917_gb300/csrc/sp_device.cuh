@@ -893,71 +893,82 @@ constexpr int kSplitOf = (sizeof(T) == 4 && DIM == 2) ? kSplitLanes : 0;
 // The part of the per-cell sums a lane of the batch serves: owner lanes
 // (lane < G) part 0 of their own cell, helper lanes a later part of
 // another cell.  c = -1: none.  own_parts / h0: for an owner lane, its
-// cell's part count and the helper lane of part 1.
+// cell's part count and the helper lane of part 1.  kSplit = 0: no parts
+// (an empty record; every cell is summed by its own lane).
+template <int kSplit>
 struct LanePart {
+  static constexpr int split = kSplit;
   int c, b, e;
   int own_parts, h0;
+};
+template <>
+struct LanePart<0> {
+  static constexpr int split = 0;
 };
 
 // The lanes' parts of a batch of G cells (cells with Ni > kLaneSumMax: one
 // part, summed by the warp path); helper lanes read their (cell, part) from
 // the table.  Called by the whole warp.
-template <class TabT>
-__device__ __forceinline__ LanePart lane_parts(TabT* ct, int G, bool own, int offi, int Ni, int split) {
-  const int lane = threadIdx.x & 31;
-  LanePart lp;
-  lp.c = -1;
-  lp.b = lp.e = 0;
-  lp.own_parts = 1;
-  lp.h0 = 0;
-  int L = own ? cell_lanes(Ni, split) : 1;
-  int hs = L - 1;  // inclusive scan of the helpers over the cells
+template <int split, class TabT>
+__device__ __forceinline__ LanePart<split> lane_parts(TabT* ct, int G, bool own, int offi, int Ni) {
+  LanePart<split> lp;
+  if constexpr (split == 0) {
+    return lp;
+  } else {
+    const int lane = threadIdx.x & 31;
+    lp.c = -1;
+    lp.b = lp.e = 0;
+    lp.own_parts = 1;
+    lp.h0 = 0;
+    int L = own ? cell_lanes(Ni, split) : 1;
+    int hs = L - 1;  // inclusive scan of the helpers over the cells
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, hs, o);
-    if (lane >= o) hs += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, hs, o);
+      if (lane >= o) hs += y;
+    }
+    int nhelp = __shfl_sync(kFull, hs, 31);
+    hs -= L - 1;  // exclusive
+    if (G + nhelp > 32) {  // (the batch plan never makes such a batch)
+      L = 1;
+      hs = 0;
+      nhelp = 0;
+    }
+    if (own) {
+      const int h = (Ni + L - 1) / L;
+      lp.c = lane;
+      lp.b = offi;
+      lp.e = offi + (h < Ni ? h : Ni);
+      lp.own_parts = L;
+      lp.h0 = G + hs;
+      for (int p = 1; p < L; ++p) ct->hpart[hs + p - 1] = (uint16_t)((lane << 8) | p);
+    }
+    __syncwarp();
+    if (lane >= G && lane - G < nhelp) {
+      const int hp = ct->hpart[lane - G];
+      const int c = hp >> 8, p = hp & 255;
+      const int o0 = ct->off[c], n = ct->off[c + 1] - o0;
+      const int Lc = cell_lanes(n, split);
+      const int h = (n + Lc - 1) / Lc;
+      lp.c = c;
+      lp.b = o0 + p * h;
+      lp.e = o0 + ((p + 1) * h < n ? (p + 1) * h : n);
+    }
+    return lp;
   }
-  int nhelp = __shfl_sync(kFull, hs, 31);
-  hs -= L - 1;  // exclusive
-  if (G + nhelp > 32) {  // (the batch plan never makes such a batch)
-    L = 1;
-    hs = 0;
-    nhelp = 0;
-  }
-  if (own) {
-    const int h = (Ni + L - 1) / L;
-    lp.c = lane;
-    lp.b = offi;
-    lp.e = offi + (h < Ni ? h : Ni);
-    lp.own_parts = L;
-    lp.h0 = G + hs;
-    for (int p = 1; p < L; ++p) ct->hpart[hs + p - 1] = (uint16_t)((lane << 8) | p);
-  }
-  __syncwarp();
-  if (lane >= G && lane - G < nhelp) {
-    const int hp = ct->hpart[lane - G];
-    const int c = hp >> 8, p = hp & 255;
-    const int o0 = ct->off[c], n = ct->off[c + 1] - o0;
-    const int Lc = cell_lanes(n, split);
-    const int h = (n + Lc - 1) / Lc;
-    lp.c = c;
-    lp.b = o0 + p * h;
-    lp.e = o0 + ((p + 1) * h < n ? (p + 1) * h : n);
-  }
-  return lp;
 }
 
 // kLo: the terms come with exact low parts (else lo is ignored).
-template <class Acc, int K, bool kLo = false, class F>
-__device__ __forceinline__ void cell_sums_acc(const LanePart& lp, bool own, int offi, int Ni, Acc (&out)[K], F f) {
+template <class Acc, int K, bool kLo = false, class LP, class F>
+__device__ __forceinline__ void cell_sums_acc(const LP& lp, bool own, int offi, int Ni, Acc (&out)[K], F f) {
   using Tm = typename Acc::term;
   const int lane = threadIdx.x & 31;
   const bool small = own && Ni <= lane_sum_max<Acc>;
 #pragma unroll
   for (int k = 0; k < K; ++k) out[k].init();
-  if constexpr (sizeof(Tm) == 8) {
-    // FP64 terms (FP64 mode; the FP32 mode's FP64 record sums): one lane
-    // per cell, in slot order
+  if constexpr (sizeof(Tm) == 8 || LP::split == 0) {
+    // FP64 terms (FP64 mode; the FP32 mode's FP64 record sums), or no
+    // split parts: one lane per cell, in slot order
     if (small) {
       for (int s = offi; s < offi + Ni; ++s) {
         Tm v[K], lo[K];
@@ -1028,8 +1039,8 @@ __device__ __forceinline__ void cell_sums_acc(const LanePart& lp, bool own, int 
   __syncwarp();
 }
 
-template <class Acc, int K, bool kLo = false, class F>
-__device__ __forceinline__ void cell_sums(const LanePart& lp, bool own, int offi, int Ni,
+template <class Acc, int K, bool kLo = false, class LP, class F>
+__device__ __forceinline__ void cell_sums(const LP& lp, bool own, int offi, int Ni,
                                           typename Acc::result (&out)[K], F f) {
   Acc acc[K];
   cell_sums_acc<Acc, K, kLo>(lp, own, offi, Ni, acc, f);
@@ -1401,7 +1412,7 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   if (lane == 0) ct->off[G] = M;
   __syncwarp();
   // the lanes' parts of the per-cell sums (split cells: FP32 state only)
-  const LanePart lp = lane_parts(ct, G, own, offi, Ni, kSplitOf<T, DIM>);
+  const auto lp = lane_parts<kSplitOf<T, DIM>>(ct, G, own, offi, Ni);
   // ---- 1. source indices, cell of each slot, stable order within cells
   // (the index copies run while the cell of each slot is written)
 #pragma unroll 4
