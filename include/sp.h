@@ -197,7 +197,13 @@ sp_status sp_step(sp_ctx* ctx, int n_steps);
  * In reproducible runs (FP64, or sp_set_reproducible on) kind 0 sums each
  * cell in source order, so the fields are bit-identical from run to run;
  * it puts the cells' particles in that order on the device first, which is
- * the order the next step would restore anyway (no later result changes). */
+ * the order the next step would restore anyway (no later result changes).
+ * With an FP32 state, kind 0 forms the per-cell quotients as products of
+ * reciprocals (a few ulps from the FP64 mode's quotients).  When out is
+ * page-locked host memory mapped for the device (cudaHostAlloc,
+ * cudaHostRegister) and n_fields = SP_NFIELDS, the kernel writes the
+ * fields into it directly; otherwise they are copied from a device buffer.
+ * The call returns when out holds the fields. */
 sp_status sp_moments(sp_ctx* ctx, int inst, int kind, double* out, int n_fields);
 
 /* Current particles of instance inst in sorted order (host FP64, SoA).

@@ -1156,6 +1156,22 @@ sp_status sp_moments(sp_ctx* c, int inst, int kind, double* out, int n_fields) {
   const int64_t nc = P.ncells;
   const int nf = std::min(n_fields, (int)SP_NFIELDS);
   if (kind == 0) {
+    // page-locked host memory the device can address: the fields kernel
+    // writes its rows straight into it (the link transfer overlaps the
+    // FP64 work); otherwise a device buffer and one copy
+    cudaPointerAttributes pa;
+    double* direct = nullptr;
+    if (nf == SP_NFIELDS && cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer)
+      direct = (double*)pa.devicePointer;
+    cudaGetLastError();  // (a pointer unknown to CUDA leaves an error to clear)
+    if (direct) {
+      if (c->stable) launch_order_cells(c->start, c->NC, c->perm, c->stream);
+      StepArgs a = make_step_args(c, c->cur);
+      c->K->moments(a, P.cell_off, P.cell_off + nc, direct, c->stream);
+      CK(cudaStreamSynchronize(c->stream));
+      return check_errors(c);
+    }
     if (nc > c->mom_cells) {  // one device buffer, grown on demand
       CK(cudaStreamSynchronize(c->stream));
       if (c->mom) CK(cudaFree(c->mom));

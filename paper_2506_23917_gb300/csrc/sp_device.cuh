@@ -3309,7 +3309,8 @@ __global__ void k_keys_mesh(const T* x0, const T* x1, int64_t M, const uint32_t*
 // slot order, in two kernels.  k_moment_sums: a half-warp (16 lanes) per
 // cell; lanes stride over the cell's slots, a butterfly combines them, and
 // the first lane writes the cell's sums to sums[7][nc]: sum c (3), then
-// sum |C|^2 and sum |C|^2 C (3) about the mean.  The sums use the
+// sum |C|^2 and, when the fields are wanted (kQ), sum |C|^2 C (3) about
+// the mean.  The sums use the
 // collision kernel's accumulators (FP64 values in FP64 mode, FP32 terms
 // carried without loss in FP32 mode, plain FP32 in the all-FP32 mode).
 // With an FP32 state a sum is stored as its FP32 pair (s, e) in the 8-byte
@@ -3319,8 +3320,8 @@ __global__ void k_keys_mesh(const T* x0, const T* x1, int64_t M, const uint32_t*
 // time there.  k_moment_cells: one thread per cell forms the FP64 values and
 // scalars (U, n, T, q, tau, dt_c, the split ratio) from them on full warps,
 // and writes the fields to out [12][nc] or, with out == nullptr, takes the
-// minimum dt_c into dt_min.
-template <class T, class A>
+// minimum dt_c into dt_min (a warp minimum, then one atomic per warp).
+template <class T, class A, bool kQ>
 __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) {
   using Acc = CellAcc<T, A>;
   constexpr bool kMixed = mixed_prec<T, A>();
@@ -3369,9 +3370,11 @@ __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) 
         }
       }
     }
-    Acc r[4];
+    // sum |C|^2, and with kQ sum |C|^2 C (the heat flux; not needed for dt_c)
+    constexpr int K2 = kQ ? 4 : 1;
+    Acc r[K2];
 #pragma unroll
-    for (int d = 0; d < 4; ++d) r[d].init();
+    for (int d = 0; d < K2; ++d) r[d].init();
     if (N >= 2) {
       for (int s = lane; s < N; s += 16) {
         const uint32_t o = a.perm[s0 + s];
@@ -3383,15 +3386,17 @@ __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) 
         }
         const T c2 = C0 * C0 + C1 * C1 + C2 * C2;
         r[0].add1(c2);
-        r[1].add1(c2 * C0);
-        r[2].add1(c2 * C1);
-        r[3].add1(c2 * C2);
+        if constexpr (kQ) {
+          r[1].add1(c2 * C0);
+          r[2].add1(c2 * C1);
+          r[3].add1(c2 * C2);
+        }
       }
     }
 #pragma unroll
     for (int m = 8; m > 0; m >>= 1)
 #pragma unroll
-      for (int d = 0; d < 4; ++d) r[d].combine(r[d].shfl_xor(m));
+      for (int d = 0; d < K2; ++d) r[d].combine(r[d].shfl_xor(m));
     if (lane == 0 && valid) {
       const int64_t i = k - c0;
       if constexpr (kPair) {
@@ -3399,12 +3404,12 @@ __global__ void k_moment_sums(StepArgs a, int64_t c0, int64_t c1, double* sums) 
 #pragma unroll
         for (int d = 0; d < 3; ++d) sp2[d * nc + i] = acc_pair(sx[d]);
 #pragma unroll
-        for (int d = 0; d < 4; ++d) sp2[(3 + d) * nc + i] = acc_pair(r[d]);
+        for (int d = 0; d < K2; ++d) sp2[(3 + d) * nc + i] = acc_pair(r[d]);
       } else {
 #pragma unroll
         for (int d = 0; d < 3; ++d) sums[d * nc + i] = (double)sx[d].get();
 #pragma unroll
-        for (int d = 0; d < 4; ++d) sums[(3 + d) * nc + i] = (double)r[d].get();
+        for (int d = 0; d < K2; ++d) sums[(3 + d) * nc + i] = (double)r[d].get();
       }
     }
   }
@@ -3420,58 +3425,118 @@ __device__ __forceinline__ double moment_sum(const double* sums, int64_t idx) {
   }
 }
 
+// FP64 state (kPair false): the oracle's arithmetic, operation for
+// operation (FP64 runs reproduce its Delta t and fields bit for bit).  FP32
+// state: the same quantities with the divisions taken as products of
+// reciprocals (1/k from the table, 1/V, 1/L) and the viscosity power as
+// tau = tau_k exp((omega - 1) ln T) / n: a few ulps from the quotient forms,
+// at a third of the FP64 instructions.
 template <bool kPair>
 __global__ void k_moment_cells(StepArgs a, int64_t c0, int64_t c1, const double* sums, double* out) {
   const int64_t nc = c1 - c0;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nc) return;
-  const int64_t k = c0 + i;
-  const int N = (int)(a.start[k + 1] - a.start[k]);
-  const InstParams& P = a.P[a.cell_inst[k]];
-  const double Lk = a.Lc ? a.Lc[k] : P.Lmin;
+  const bool valid = i < nc;
+  const int64_t k = c0 + (valid ? i : 0);
+  const int N = valid ? (int)(a.start[k + 1] - a.start[k]) : 0;
+  const uint32_t inst = a.cell_inst[k];
+  const InstParams& P = a.P[inst];
   CellMoments m;
   m.U[0] = m.U[1] = m.U[2] = 0;
-  if (N > 0) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) m.U[d] = moment_sum<kPair>(sums, d * nc + i) / N;
-  }
-  m.n = N > 0 ? (double)N * P.Fn / a.vol[k] : 0.0;
-  m.T = 0; m.q[0] = m.q[1] = m.q[2] = 0;
+  m.n = 0;
+  m.T = 0;
+  m.q[0] = m.q[1] = m.q[2] = 0;
   m.tau = __longlong_as_double(0x7FF0000000000000ll);
   m.dtc = m.tau;
-  if (N >= 2) {
-    m.T = moment_sum<kPair>(sums, 3 * nc + i) / (3.0 * P.R * (double)(N - 1));
-    if (N >= 3 && out) {
-      const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
+  if constexpr (kPair) {
+    const double iL = a.iLc ? a.iLc[k] : P.inv_Lmin;
+    const auto rcp = [&](int j) { return j <= kHugeCell ? a.rcp[j] : 1.0 / (double)j; };
+    if (N > 0) {
+      const double rN = rcp(N);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) m.q[d] = f * moment_sum<kPair>(sums, (4 + d) * nc + i);
+      for (int d = 0; d < 3; ++d) m.U[d] = moment_sum<true>(sums, d * nc + i) * rN;
+      m.n = (double)N * P.Fn * a.ivol[k];
     }
-    const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
-    if (m.T > 0) {
-      if (out) {  // tau is an output field only (dt_c does not need it)
-        const double p = m.n * P.m * P.R * m.T;
-        m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
+    if (N >= 2) {
+      m.T = moment_sum<true>(sums, 3 * nc + i) * P.inv3R * rcp(N - 1);
+      if (N >= 3 && out) {
+        const double f = 0.5 * (double)N * rcp(N - 1) * rcp(N - 2);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) m.q[d] = f * moment_sum<true>(sums, (4 + d) * nc + i);
       }
-      m.dtc = Lk / (umag + sqrt(P.gamma * P.R * m.T));
-    } else if (umag > 0) {
-      m.dtc = Lk / umag;
+      const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
+      double idtc = umag * iL;  // 1 / dt_c
+      if (m.T > 0) {
+        idtc = (umag + sqrt(P.gamma * P.R * m.T)) * iL;
+        if (out) m.tau = P.tau_k * exp((P.omega - 1.0) * log(m.T)) / m.n;
+      }
+      if (idtc > 0) m.dtc = 1.0 / idtc;
+      if (out) {
+        double ratio = 1.0;
+        if (P.mode == 2) ratio = 0.0;
+        else if (P.mode != 1 && m.T > 0 && m.dtc > m.tau) ratio = m.tau * idtc;
+        out[11 * nc + i] = ratio;
+      }
+    } else if (out && valid) {
+      out[11 * nc + i] = P.mode == 2 ? 0.0 : 1.0;
     }
+  } else {
+    const double Lk = a.Lc ? a.Lc[k] : P.Lmin;
+    if (N > 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) m.U[d] = moment_sum<false>(sums, d * nc + i) / N;
+    }
+    m.n = N > 0 ? (double)N * P.Fn / a.vol[k] : 0.0;
+    if (N >= 2) {
+      m.T = moment_sum<false>(sums, 3 * nc + i) / (3.0 * P.R * (double)(N - 1));
+      if (N >= 3 && out) {
+        const double f = 0.5 * (double)N / ((double)(N - 1) * (double)(N - 2));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) m.q[d] = f * moment_sum<false>(sums, (4 + d) * nc + i);
+      }
+      const double umag = sqrt(m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2]);
+      if (m.T > 0) {
+        if (out) {  // tau is an output field only (dt_c does not need it)
+          const double p = m.n * P.m * P.R * m.T;
+          m.tau = P.mu_ref * pow(m.T / P.T_ref, P.omega) / p;
+        }
+        m.dtc = Lk / (umag + sqrt(P.gamma * P.R * m.T));
+      } else if (umag > 0) {
+        m.dtc = Lk / umag;
+      }
+    }
+    if (out && valid) out[11 * nc + i] = dsmc_ratio(P, N, m);
   }
   if (out) {
-    out[0 * nc + i] = (double)N;
-    out[1 * nc + i] = m.n;
-    out[2 * nc + i] = m.U[0];
-    out[3 * nc + i] = m.U[1];
-    out[4 * nc + i] = m.U[2];
-    out[5 * nc + i] = m.T;
-    out[6 * nc + i] = m.q[0];
-    out[7 * nc + i] = m.q[1];
-    out[8 * nc + i] = m.q[2];
-    out[9 * nc + i] = m.tau;
-    out[10 * nc + i] = m.dtc;
-    out[11 * nc + i] = dsmc_ratio(P, N, m);
-  } else if (N >= 2 && m.dtc < __longlong_as_double(0x7FF0000000000000ll)) {
-    atomicMin(&a.dt_min[a.cell_inst[k]], (unsigned long long)__double_as_longlong(m.dtc));
+    if (valid) {
+      out[0 * nc + i] = (double)N;
+      out[1 * nc + i] = m.n;
+      out[2 * nc + i] = m.U[0];
+      out[3 * nc + i] = m.U[1];
+      out[4 * nc + i] = m.U[2];
+      out[5 * nc + i] = m.T;
+      out[6 * nc + i] = m.q[0];
+      out[7 * nc + i] = m.q[1];
+      out[8 * nc + i] = m.q[2];
+      out[9 * nc + i] = m.tau;
+      out[10 * nc + i] = m.dtc;
+    }
+  } else {
+    // minimum dt_c per instance: a warp minimum where the warp's cells share
+    // an instance (dt_c > 0, so the bit patterns order as the values), then
+    // one atomic per warp
+    unsigned long long v = (N >= 2 && valid) ? (unsigned long long)__double_as_longlong(m.dtc)
+                                             : 0x7FF0000000000000ull;
+    const uint32_t inst0 = __shfl_sync(kFull, inst, 0);
+    if (__all_sync(kFull, !valid || inst == inst0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+        v = w < v ? w : v;
+      }
+      if ((threadIdx.x & 31) == 0 && v < 0x7FF0000000000000ull) atomicMin(&a.dt_min[inst0], v);
+    } else if (v < 0x7FF0000000000000ull) {
+      atomicMin(&a.dt_min[inst], v);
+    }
   }
 }
 

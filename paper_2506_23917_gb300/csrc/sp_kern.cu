@@ -80,7 +80,8 @@ void moments(const StepArgs& a, int64_t c0, int64_t c1, double* out, cudaStream_
   if (nc <= 0) return;
   int64_t g = (nc + 15) / 16;  // a half-warp per cell, 16 cells per block, grid-stride
   if (g > 65535) g = 65535;
-  k_moment_sums<T, A><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, a.msum);
+  if (out) k_moment_sums<T, A, true><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, a.msum);
+  else k_moment_sums<T, A, false><<<(unsigned)g, 256, 0, s>>>(a, c0, c1, a.msum);
   k_moment_cells<sizeof(T) == 4><<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(a, c0, c1, a.msum, out);
 }
 

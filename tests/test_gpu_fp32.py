@@ -196,3 +196,74 @@ def test_fp32_o_grid_time_averages_match_fp64(sp):
     cfg, regions = W.ogrid_box(nr=24, nt=48, r_out=3.0, growth=1.05, ppc=600.0, Kn=0.05)
     pos, vel = W.fill_regions(cfg, regions, 3)
     _compare(sp, cfg, pos, vel, warm=300, nbatch=20, per=200, reproducible=False)
+
+
+def _fp32_states():
+    """(name, cfg, pos, vel, steps): a channel with a cut-cell body, the same
+    channel at ~3 particles per cell (cells of 0, 1, 2, 3 particles), and a
+    tube whose cells hold 20000 / 6000 / 1500 / 300 particles (counts past
+    the 1/k table)."""
+    cfg, regions = W.box2d(nx=24, ny=12, ppc=40.0)
+    pos, vel = W.fill_regions(cfg, regions, 3)
+    yield "channel", cfg, pos, vel, 20
+    cfg, regions = W.box2d(nx=24, ny=12, ppc=3.0)
+    pos, vel = W.fill_regions(cfg, regions, 4)
+    yield "sparse", cfg, pos, vel, 5
+    cfg, pos, vel = W.huge_cells()
+    yield "huge", cfg, pos, vel, 2
+
+
+@pytest.mark.parametrize("case", ["channel", "sparse", "huge"])
+def test_fp32_instantaneous_moments_match_oracle_on_the_same_state(sp, case):
+    """sp_moments of an FP32 state (FP32-pair sums, FP64 fields from
+    reciprocal products, tau from tau_k exp((omega-1) ln T) / n) against the
+    oracle's FP64 moments of the same particles widened to FP64.  n and U
+    carry only the rounding of the pair sums (relative 1e-10 of the thermal
+    speed at 20000 particles a cell); T, q, tau, dt_c and the ratio the FP32
+    rounding of the thermal velocities (relative 1e-6).  The write into
+    mapped page-locked memory gives the bits of the device-buffer copy."""
+    import torch
+    import oracle
+
+    name, cfg, pos, vel, steps = next(c for c in _fp32_states() if c[0] == case)
+    s = sp.Sim(cfg, sp.FP32, capacity=4 * vel.shape[1] + 1000)
+    s.set_particles(0, pos, vel)
+    s.step(steps)
+    s.sync()
+    p, v, _ = s.particles(0)
+    m = s.moments(0, 0)
+    pinned = torch.zeros((len(sp.FIELDS), s.ncells[0]), dtype=torch.float64).pin_memory()
+    s.moments_into(0, 0, pinned.data_ptr())
+    np.testing.assert_array_equal(pinned.numpy(), m)
+    s.close()
+    o = oracle.Oracle(cfg)
+    o.set_particles(p, v)
+    mo = o.moments(0)
+    np.testing.assert_array_equal(m[0], mo[0])  # N
+    if case == "sparse":
+        assert {0, 1, 2, 3} <= set(np.unique(mo[0]).astype(int))
+    if case == "huge":
+        assert mo[0].max() > 1024
+    vs = np.sqrt(np.max(mo[5][np.isfinite(mo[5])]) * cfg["R"])  # thermal speed scale
+
+    def near(f, rtol, atol=0.0, what=""):
+        a, b = m[f], mo[f]
+        fin = np.isfinite(b)
+        np.testing.assert_array_equal(np.isfinite(a), fin, err_msg=what)
+        bad = np.abs(a[fin] - b[fin]) > rtol * np.abs(b[fin]) + atol
+        assert not bad.any(), (what, np.flatnonzero(bad)[:5], a[fin][bad][:5], b[fin][bad][:5])
+
+    near(1, 1e-13, what="n")
+    for d in range(3):
+        near(2 + d, 1e-10, 1e-10 * vs, what=f"U{d}")
+    near(5, 1e-6, what="T")
+    qs = max(np.max(np.abs(mo[6:9])), 1e-300)
+    for d in range(3):
+        near(6 + d, 1e-5, 1e-6 * qs, what=f"q{d}")
+    near(9, 1e-6, what="tau")
+    near(10, 1e-6, what="dt_c")
+    # the ratio: tau / dt_c below 1, else 1 (a cell at the switch may flip)
+    fin = np.isfinite(mo[9]) & np.isfinite(mo[10])
+    edge = fin & (np.abs(mo[9] / np.where(fin, mo[10], 1.0) - 1) < 1e-5)
+    ok = ~edge
+    np.testing.assert_allclose(m[11][ok], mo[11][ok], rtol=1e-6, atol=0)
