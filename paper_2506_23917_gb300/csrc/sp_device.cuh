@@ -565,6 +565,24 @@ __device__ __forceinline__ bool mesh_walk(const InstParams& P, const T* mface, d
       return false;
     }
     const T* f = (f0 != nullptr && kl == k0) ? f0 : mface + 12 * (P.cell_off + kl);
+    if constexpr (sizeof(T) == 4) {
+      // FP32 state: the flight that ends inside the cell (t_e >= trem on
+      // every face it approaches, i.e. s_e >= trem (n_e . v)) is settled
+      // without the four divisions; the FP64 state keeps the quotient
+      // test of the oracle (the two can differ only at a tie)
+      bool stay = true;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const T nvv = f[3 * e] * v[0] + f[3 * e + 1] * v[1];
+        const T se = f[3 * e + 2] - (f[3 * e] * x[0] + f[3 * e + 1] * x[1]);
+        stay = stay && !(nvv > (T)0 && se < trem * nvv);
+      }
+      if (stay) {
+        x[0] += v[0] * trem;
+        x[1] += v[1] * trem;
+        return false;
+      }
+    }
     T tmin = tinf<T>();
     int fm = -1;
 #pragma unroll
