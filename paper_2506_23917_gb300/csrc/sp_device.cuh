@@ -2192,15 +2192,30 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
   // ---- 8. time-averaged sums (Step 5).  Both collision sub-steps conserve
   // each cell's momentum (the DSMC pair rule and the rescale to U), so the
   // momentum sums are those of Step 3 up to rounding; the per-component
-  // squares need a pass over the post-collision velocities, except for the
-  // rescaled cells of the mixed mode (exact from the rescale's sums).
-  const bool need_sq = own && sample && Ni > 0 && !(kMixed && nres_i > 0);
+  // squares need a pass over the post-collision velocities.  Mixed mode:
+  // only sum |c|^2 is kept, in the first square's slot (the averaged T
+  // needs no more): a rescaled cell's comes exact from the rescale's sums,
+  // and a cell without a rescale had DSMC collisions alone, which conserve
+  // its energy, so its sum is sum |C|^2 + |sum c|^2 / N of Step 3.
+  const bool need_sq = !kMixed && own && sample && Ni > 0;
   const A a0 = m0, a1 = m1, a2 = m2;
   A b0 = bsq[0], b1 = bsq[1], b2 = bsq[2];
+  if constexpr (kMixed) {
+    if (own && sample && Ni > 0) {
+      if (nres_i > 0) {
+        b0 = b0 + b1 + b2;
+      } else {
+        const A iN = Ni <= kHugeCell ? a.rcp[Ni] : (A)1 / (A)Ni;
+        b0 = mS2 + (m0 * m0 + m1 * m1 + m2 * m2) * iN;
+      }
+      b1 = b2 = 0;
+    }
+  }
+  constexpr unsigned kSampSlots = kMixed ? 0x9Fu : 0xFFu;  // mixed: slots 5, 6 unused
   double sv[8];  // the accumulators, requested before the sums
   if (own && sample) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) sv[k] = a.samp[k * NC + kc];
+    for (int k = 0; k < 8; ++k) sv[k] = (kSampSlots >> k & 1u) ? a.samp[k * NC + kc] : 0.0;
   }
   if (__any_sync(kFull, need_sq)) {
     A r[3];
@@ -2228,8 +2243,10 @@ __device__ void process_batch(const StepArgs& a, int64_t k0, int G, CellTab<T, A
         S[2 * NC + kc] = sv[2] + (double)a1;
         S[3 * NC + kc] = sv[3] + (double)a2;
         S[4 * NC + kc] = sv[4] + (double)b0;
-        S[5 * NC + kc] = sv[5] + (double)b1;
-        S[6 * NC + kc] = sv[6] + (double)b2;
+        if constexpr (!kMixed) {
+          S[5 * NC + kc] = sv[5] + (double)b1;
+          S[6 * NC + kc] = sv[6] + (double)b2;
+        }
       }
       S[7 * NC + kc] = sv[7] + ratio;
     }

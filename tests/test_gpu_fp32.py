@@ -267,3 +267,31 @@ def test_fp32_instantaneous_moments_match_oracle_on_the_same_state(sp, case):
     edge = fin & (np.abs(mo[9] / np.where(fin, mo[10], 1.0) - 1) < 1e-5)
     ok = ~edge
     np.testing.assert_allclose(m[11][ok], mo[11][ok], rtol=1e-6, atol=0)
+
+
+def test_fp32_sampled_energy_is_the_post_collision_energy(sp):
+    """Step 5 in the FP32 mode keeps sum |c|^2 of each cell from what the
+    collision sub-steps conserve (a rescaled cell: the rescale's FP64 sums;
+    a cell with DSMC collisions alone: its Step 3 energy).  In a closed tube
+    the free flight that follows keeps every speed (specular walls), so
+    after one sampled step the sum over cells of N (3 R T + |U|^2) from the
+    averaged fields equals sum |c|^2 of the particles then, to the FP32
+    rounding of the collided velocities.  Sod tube: continuum cells on the
+    left resample, rarefied cells on the right collide only."""
+    cfg, regions = W.sod(ncell=100, ppc_left=200.0, lam_left=1e-3, n_steady=0)
+    pos, vel = W.fill_regions(cfg, regions, 11)
+    s = sp.Sim(cfg, sp.FP32, capacity=2 * vel.shape[1])
+    s.set_particles(0, pos, vel)
+    s.set_record(True)
+    s.step(1)
+    s.sync()
+    cell4, _, _ = s.record(0)
+    assert (cell4[2] > 0).sum() > 10  # rescaled cells
+    assert ((cell4[2] == 0) & (cell4[1] > 0)).sum() > 10  # DSMC-only cells with collisions
+    m = s.moments(0, 1)
+    _, v, _ = s.particles(0)
+    s.close()
+    N, U, T = m[0], m[2:5], m[5]
+    sampled = float(np.sum(N * (3.0 * cfg["R"] * T + np.sum(U ** 2, axis=0))))
+    state = float(np.sum(v.astype(np.float64) ** 2))
+    assert abs(sampled / state - 1) < 1e-5, (sampled, state)
