@@ -496,7 +496,8 @@ def main():
         sim.set_reproducible(False)
 
     # --- roofline of the dominant kernel (collision + free flight), measured
-    # with CUDA events around each kernel group on the library's stream
+    # by CUDA event nodes around each kernel group of the step graph (the
+    # graph the timed steps run), on the library's stream
     prof = sim.step_profiled(args.profile_steps)
     sim.sync()
     Mp = sim.count(0)
@@ -506,7 +507,6 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = bytes_collide / (collide_ms * 1e-3) / 1e9
     src_hash = kernel_source_hash()
-    # the committed ncu figure covers the FP32 cylinder only
     # the committed ncu figures cover the FP32 cylinder only
     prof_pp = collide_profile(src_hash) if (args.config == "cylinder" and prec == sp.FP32) else {}
     tpp = prof_pp.get("bytes_per_particle")

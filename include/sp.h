@@ -276,11 +276,12 @@ sp_status sp_surface_coefficients(const sp_config* cfg, const double* tallies, d
  * thread block each), [2] bounce cap, [3] AR cap, [4] NTC candidate cap.
  * Clears nothing. */
 sp_status sp_errors(sp_ctx* ctx, int64_t* out5);
-/* Advance n_steps steps launched one kernel at a time (no CUDA graph) with
- * CUDA events around the kernel groups; ms[0..min(n_slots,4)) receives the
- * summed device time of (0) the collision + free-flight kernels, (1) the
- * reservoir injection, (2) the histogram scan and bookkeeping, (3) the
- * scatter.  Synchronises after every step (for measurement only). */
+/* Advance n_steps steps, each as the step graph of sp_step with CUDA event
+ * nodes at the boundaries of its kernel groups; ms[0..min(n_slots,4))
+ * receives the summed device time of (0) the batch plan and the collision +
+ * free-flight kernels, (1) what of the reservoir injection (a branch beside
+ * them) is left when they end, (2) the histogram scan and bookkeeping,
+ * (3) the scatter.  Synchronises after every step (for measurement only). */
 sp_status sp_step_profiled(sp_ctx* ctx, int n_steps, double* ms, int n_slots);
 /* Within-cell order of the particles.  on = 1 (default): every step restores
  * the source order inside each cell (a stable counting sort overall), so a

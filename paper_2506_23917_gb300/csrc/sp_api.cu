@@ -83,6 +83,8 @@ struct sp_ctx {
   int64_t step_host = 0;
   bool uploaded = false, dirty = false, record = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t pgraph[2] = {nullptr, nullptr};  // the same steps with timing events
+  cudaEvent_t pev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool graph_ok = false;
   cudaStream_t side = nullptr;       // capture-time branches of the step graph (injection,
   cudaStream_t side2 = nullptr;      // big-cell launch, huge-cell launch)
@@ -525,16 +527,22 @@ bool apply_schedule(sp_ctx* c, int cap, int warps) {
 // Enqueue one step reading buffer `par` and writing buffer 1 - par.  With
 // ev != nullptr, events ev[0..4] bracket the four kernel groups (collide,
 // inject, scan + bookkeeping, scatter).
-int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = false) {
+// ev: timing events at the boundaries of the kernel groups (ext: recorded
+// as event nodes of a captured graph, which the host can time).
+int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = false, bool ext = false) {
   int n = 0;
   const StepArgs a = make_step_args(c, par);
-  if (ev) cudaEventRecord(ev[0], c->stream);
+  const auto rec = [&](int k) {
+    if (ext) cudaEventRecordWithFlags(ev[k], c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ev[k], c->stream);
+  };
+  if (ev) rec(0);
   // The reservoir injection reads nothing the collision kernel writes (the
   // previous step's particle count and Delta t; its particles go after the
   // current ones, its histogram counts are atomics), so in the step graph
   // it is a branch that runs beside the collision kernel, in the issue
   // slots and SMs that kernel leaves free; the cell scan joins the two.
-  const bool fork = branch && !ev && c->n_ghost > 0;
+  const bool fork = branch && (!ev || ext) && c->n_ghost > 0;
   if (fork) {
     cudaEventRecord(c->fork_ev, c->stream);
     cudaStreamWaitEvent(c->side, c->fork_ev, 0);
@@ -566,7 +574,7 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     launch_collide_p(c, a, true, kBigGridPerSm * c->nsm, c->stream); ++n;
     c->K->collide_huge(c->dim, a, kBigGridPerSm * c->nsm, c->stream); ++n;
   }
-  if (ev) cudaEventRecord(ev[1], c->stream);
+  if (ev) rec(1);
   if (fork) {
     cudaStreamWaitEvent(c->stream, c->join_ev, 0);
   } else if (c->n_ghost > 0) {
@@ -576,23 +584,28 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     c->K->inject(c->dim, ia, 1, c->stream);
     n += 4;
   }
-  if (ev) cudaEventRecord(ev[2], c->stream);
+  if (ev) rec(2);
   launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream); n += 2;
   launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
                        c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->nbatch,
                        c->surf_time, c->cyc, c->stream); ++n;
-  if (ev) cudaEventRecord(ev[3], c->stream);
+  if (ev) rec(3);
   launch_scatter(c->key, c->start, c->count, c->perm, c->Mtot, c->cap, c->stream); ++n;
-  if (ev) cudaEventRecord(ev[4], c->stream);
+  if (ev) rec(4);
   return n;
 }
 
 void destroy_graphs(sp_ctx* c) {
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 2; ++i) {
     if (c->graph[i]) {
       cudaGraphExecDestroy(c->graph[i]);
       c->graph[i] = nullptr;
     }
+    if (c->pgraph[i]) {
+      cudaGraphExecDestroy(c->pgraph[i]);
+      c->pgraph[i] = nullptr;
+    }
+  }
   c->graph_ok = false;
 }
 
@@ -608,25 +621,30 @@ sp_status build_graphs(sp_ctx* c) {
     CK(cudaStreamCreateWithFlags(&c->side3, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->fork3_ev, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->join3_ev, cudaEventDisableTiming));
+    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&c->pev[k]));
   }
-  for (int par = 0; par < 2; ++par) {
-    cudaStream_t cs;
-    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaStream_t saved = c->stream;
-    c->stream = cs;
-    cudaGraph_t g;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      c->launches = enqueue_step(c, par, nullptr, true);
-      e = cudaStreamEndCapture(cs, &g);
+  // per parity: the step graph, and the same graph with timing events at
+  // the kernel groups' boundaries (sp_step_profiled)
+  for (int prof = 0; prof < 2; ++prof)
+    for (int par = 0; par < 2; ++par) {
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaStream_t saved = c->stream;
+      c->stream = cs;
+      cudaGraph_t g;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const int n = enqueue_step(c, par, prof ? c->pev : nullptr, true, prof != 0);
+        if (!prof) c->launches = n;
+        e = cudaStreamEndCapture(cs, &g);
+      }
+      c->stream = saved;
+      cudaStreamDestroy(cs);
+      CK(e);
+      e = cudaGraphInstantiate(prof ? &c->pgraph[par] : &c->graph[par], g, 0);
+      cudaGraphDestroy(g);
+      CK(e);
     }
-    c->stream = saved;
-    cudaStreamDestroy(cs);
-    CK(e);
-    e = cudaGraphInstantiate(&c->graph[par], g, 0);
-    cudaGraphDestroy(g);
-    CK(e);
-  }
   c->graph_ok = true;
   return SP_OK;
 }
@@ -1020,21 +1038,22 @@ sp_status sp_step_profiled(sp_ctx* c, int n_steps, double* ms, int n_slots) {
   if (!c || n_steps < 0 || !ms || n_slots < 1) return SP_ERR_ARG;
   sp_status s = ensure_ready(c);
   if (s != SP_OK) return s;
-  cudaEvent_t ev[5];
-  for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
+  if (!c->graph_ok) {
+    s = build_graphs(c);
+    if (s != SP_OK) return s;
+  }
   double acc[4] = {0, 0, 0, 0};
   for (int it = 0; it < n_steps; ++it) {
-    enqueue_step(c, c->cur, ev);
-    CK(cudaEventSynchronize(ev[4]));
+    CK(cudaGraphLaunch(c->pgraph[c->cur], c->stream));
+    CK(cudaEventSynchronize(c->pev[4]));
     for (int k = 0; k < 4; ++k) {
       float t = 0;
-      CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      CK(cudaEventElapsedTime(&t, c->pev[k], c->pev[k + 1]));
       acc[k] += t;
     }
     c->cur ^= 1;
     c->step_host += 1;
   }
-  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
   for (int k = 0; k < n_slots && k < 4; ++k) ms[k] = acc[k];
   CK(cudaGetLastError());
   return SP_OK;
@@ -1438,6 +1457,7 @@ sp_status sp_free(sp_ctx* c) {
     cudaStreamDestroy(c->side3);
     cudaEventDestroy(c->fork3_ev);
     cudaEventDestroy(c->join3_ev);
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(c->pev[k]);
   }
   for (int b = 0; b < 2; ++b)
     for (int d = 0; d < 3; ++d) {
