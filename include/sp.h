@@ -298,9 +298,11 @@ sp_status sp_set_reproducible(sp_ctx* ctx, int on);
 sp_status sp_set_schedule(sp_ctx* ctx, int cap, int warps);
 /* Autotuner: for each candidate schedule (warps in 2, 4, 8; cap in 128,
  * 256, 384, 512, 768, 1024 and, per block size, the largest cap at each
- * number of resident blocks per SM; those that fit) advance one untimed step and then steps_per_trial ordinary
- * steps while timing the collision kernel with CUDA events; time the three
- * fastest once more the same way and keep the one with the least total.  The
+ * number of resident blocks per SM; those that fit) advance one untimed
+ * step and then steps_per_trial ordinary steps, each as the step graph with
+ * CUDA event nodes around the plan and collision launches, and sum their
+ * times; time the three fastest once more the same way and keep the one
+ * with the least total.  The
  * trial steps are part of the run (results do not depend on the schedule);
  * call it once the flow is developed.  *cap_out / *warps_out (may be NULL)
  * receive the choice. */

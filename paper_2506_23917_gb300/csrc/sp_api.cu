@@ -524,25 +524,24 @@ bool apply_schedule(sp_ctx* c, int cap, int warps) {
   return true;
 }
 
-// Enqueue one step reading buffer `par` and writing buffer 1 - par.  With
-// ev != nullptr, events ev[0..4] bracket the four kernel groups (collide,
-// inject, scan + bookkeeping, scatter).
-// ev: timing events at the boundaries of the kernel groups (ext: recorded
-// as event nodes of a captured graph, which the host can time).
-int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = false, bool ext = false) {
+// Enqueue one step reading buffer `par` and writing buffer 1 - par, for
+// capture into a step graph.  With ev != nullptr, event-record nodes
+// ev[0..4] bracket the four kernel groups (the plan and collision
+// launches; what is left of the injection branch when they end; the scan
+// and bookkeeping; the scatter), so that the host can time them.
+int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr) {
   int n = 0;
   const StepArgs a = make_step_args(c, par);
   const auto rec = [&](int k) {
-    if (ext) cudaEventRecordWithFlags(ev[k], c->stream, cudaEventRecordExternal);
-    else cudaEventRecord(ev[k], c->stream);
+    if (ev) cudaEventRecordWithFlags(ev[k], c->stream, cudaEventRecordExternal);
   };
-  if (ev) rec(0);
+  rec(0);
   // The reservoir injection reads nothing the collision kernel writes (the
   // previous step's particle count and Delta t; its particles go after the
   // current ones, its histogram counts are atomics), so in the step graph
   // it is a branch that runs beside the collision kernel, in the issue
   // slots and SMs that kernel leaves free; the cell scan joins the two.
-  const bool fork = branch && (!ev || ext) && c->n_ghost > 0;
+  const bool fork = c->n_ghost > 0;
   if (fork) {
     cudaEventRecord(c->fork_ev, c->stream);
     cudaStreamWaitEvent(c->side, c->fork_ev, 0);
@@ -553,45 +552,32 @@ int enqueue_step(sp_ctx* c, int par, cudaEvent_t* ev = nullptr, bool branch = fa
     cudaEventRecord(c->join_ev, c->side);
     n += 4;
   }
-  launch_plan(c->start, c->cost, c->NC, c->sched_cap, (c->prec != SP_FP64 && c->dim == 2) ? kSplitLanes : 0, c->batches, c->nbatch, c->big_list, c->big_count,
-              c->stream); ++n;
-  if (branch) {
-    // the big-cell launch (cells disjoint from the batches') is a branch
-    // beside the main launch: its blocks start as SMs free up at the end of
-    // the main launch instead of after all of it
-    cudaEventRecord(c->fork2_ev, c->stream);
-    cudaStreamWaitEvent(c->side2, c->fork2_ev, 0);
-    cudaStreamWaitEvent(c->side3, c->fork2_ev, 0);
-    launch_collide_p(c, a, true, kBigGridPerSm * c->nsm, c->side2); ++n;
-    cudaEventRecord(c->join2_ev, c->side2);
-    c->K->collide_huge(c->dim, a, kBigGridPerSm * c->nsm, c->side3); ++n;
-    cudaEventRecord(c->join3_ev, c->side3);
-    launch_collide_p(c, a, false, small_grid(c), c->stream); ++n;
-    cudaStreamWaitEvent(c->stream, c->join2_ev, 0);
-    cudaStreamWaitEvent(c->stream, c->join3_ev, 0);
-  } else {
-    launch_collide_p(c, a, false, small_grid(c), c->stream); ++n;
-    launch_collide_p(c, a, true, kBigGridPerSm * c->nsm, c->stream); ++n;
-    c->K->collide_huge(c->dim, a, kBigGridPerSm * c->nsm, c->stream); ++n;
-  }
-  if (ev) rec(1);
-  if (fork) {
-    cudaStreamWaitEvent(c->stream, c->join_ev, 0);
-  } else if (c->n_ghost > 0) {
-    const InjectArgs ia = make_inject_args(c, par);
-    c->K->inject(c->dim, ia, 0, c->stream);
-    launch_scan(c->gcount, c->goff, c->n_ghost, c->gscan_part, c->stream);
-    c->K->inject(c->dim, ia, 1, c->stream);
-    n += 4;
-  }
-  if (ev) rec(2);
+  launch_plan(c->start, c->cost, c->NC, c->sched_cap, (c->prec != SP_FP64 && c->dim == 2) ? kSplitLanes : 0,
+              c->batches, c->nbatch, c->big_list, c->big_count, c->stream);
+  ++n;
+  // the big-cell launch (cells disjoint from the batches') is a branch
+  // beside the main launch: its blocks start as SMs free up at the end of
+  // the main launch instead of after all of it
+  cudaEventRecord(c->fork2_ev, c->stream);
+  cudaStreamWaitEvent(c->side2, c->fork2_ev, 0);
+  cudaStreamWaitEvent(c->side3, c->fork2_ev, 0);
+  launch_collide_p(c, a, true, kBigGridPerSm * c->nsm, c->side2); ++n;
+  cudaEventRecord(c->join2_ev, c->side2);
+  c->K->collide_huge(c->dim, a, kBigGridPerSm * c->nsm, c->side3); ++n;
+  cudaEventRecord(c->join3_ev, c->side3);
+  launch_collide_p(c, a, false, small_grid(c), c->stream); ++n;
+  cudaStreamWaitEvent(c->stream, c->join2_ev, 0);
+  cudaStreamWaitEvent(c->stream, c->join3_ev, 0);
+  rec(1);
+  if (fork) cudaStreamWaitEvent(c->stream, c->join_ev, 0);
+  rec(2);
   launch_scan(c->count, c->start, c->NC, c->scan_part, c->stream); n += 2;
   launch_step_finalize(c->dP, c->n_inst, c->dt_cur, c->dt_min, c->step_d, c->Mcur, c->Mtot, c->start,
                        c->NC, c->goff, c->gcount, c->n_ghost, c->big_count, c->ticket, c->nbatch,
                        c->surf_time, c->cyc, c->stream); ++n;
-  if (ev) rec(3);
+  rec(3);
   launch_scatter(c->key, c->start, c->count, c->perm, c->Mtot, c->cap, c->stream); ++n;
-  if (ev) rec(4);
+  rec(4);
   return n;
 }
 
@@ -634,7 +620,7 @@ sp_status build_graphs(sp_ctx* c) {
       cudaGraph_t g;
       cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        const int n = enqueue_step(c, par, prof ? c->pev : nullptr, true, prof != 0);
+        const int n = enqueue_step(c, par, prof ? c->pev : nullptr);
         if (!prof) c->launches = n;
         e = cudaStreamEndCapture(cs, &g);
       }
@@ -1083,18 +1069,18 @@ sp_status sp_autotune(sp_ctx* c, int steps_per_trial, int* cap_out, int* warps_o
   static const int caps[] = {128, 256, 384, 512, 768, 1024};
   static const int warps[] = {2, 4, 8};
   const int cap0 = c->sched_cap, w0 = c->sched_warps;
-  cudaEvent_t ev[5];
-  for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
-  // collision-kernel time of steps_per_trial steps, after one untimed step
-  // (the batch partition changes with the schedule, and the heavy-batch
-  // flags of the old one are stale)
+  // collision-group time of steps_per_trial steps of the step graph (its
+  // copy with timing events), after one untimed step (the batch partition
+  // changes with the schedule, and the cost bytes of the old one are stale)
   auto trial = [&](int ci, int wi, float* tot) -> sp_status {
     *tot = 0;
+    sp_status bs = build_graphs(c);
+    if (bs != SP_OK) return bs;
     for (int it = 0; it <= steps_per_trial; ++it) {
-      enqueue_step(c, c->cur, ev);
-      CK(cudaEventSynchronize(ev[4]));
+      CK(cudaGraphLaunch(c->pgraph[c->cur], c->stream));
+      CK(cudaEventSynchronize(c->pev[4]));
       float t = 0;
-      CK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+      CK(cudaEventElapsedTime(&t, c->pev[0], c->pev[1]));
       if (it > 0) *tot += t;
       c->cur ^= 1;
       c->step_host += 1;
@@ -1145,7 +1131,6 @@ sp_status sp_autotune(sp_ctx* c, int steps_per_trial, int* cap_out, int* warps_o
       best_cap = k.cap;
       best_w = k.warps;
     }
-  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
   if (!apply_schedule(c, best_cap, best_w)) apply_schedule(c, cap0, w0);
   destroy_graphs(c);
   if (cap_out) *cap_out = c->sched_cap;
