@@ -302,10 +302,9 @@ sp_status sp_set_schedule(sp_ctx* ctx, int cap, int warps);
  * step and then steps_per_trial ordinary steps, each as the step graph with
  * CUDA event nodes around the plan and collision launches, and sum their
  * times; time the three fastest once more the same way and keep the one
- * with the least total.  The
- * trial steps are part of the run (results do not depend on the schedule);
- * call it once the flow is developed.  *cap_out / *warps_out (may be NULL)
- * receive the choice. */
+ * with the least total.  The trial steps are part of the run (results do
+ * not depend on the schedule); call it once the flow is developed.
+ * *cap_out / *warps_out (may be NULL) receive the choice. */
 sp_status sp_autotune(sp_ctx* ctx, int steps_per_trial, int* cap_out, int* warps_out);
 /* Wait for the context's stream. */
 sp_status sp_sync(sp_ctx* ctx);
