@@ -121,7 +121,8 @@ def collide_profile(src_hash):
                 kv[k.strip()] = v.strip()
         if kv.get("source_sha256") != src_hash:
             return {}
-        return {k: float(v) for k, v in kv.items() if k in ("bytes_per_particle", "inst_per_particle")}
+        return {k: float(v) for k, v in kv.items()
+                if k in ("bytes_per_particle", "inst_per_particle", "threads_per_inst")}
     except Exception:
         return {}
 
@@ -529,7 +530,8 @@ def main():
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     clk_mhz = clk.get("sm_mhz") or 2070.0
     issue_peak = nsm * 4 * clk_mhz * 1e6
-    roofline["issue"] = {"inst_per_particle": ipp, "unit": "warp-inst/s", "peak": issue_peak,
+    roofline["issue"] = {"inst_per_particle": ipp, "threads_per_inst": prof_pp.get("threads_per_inst"),
+                         "unit": "warp-inst/s", "peak": issue_peak,
                          "achieved": (ipp * Mp / (collide_ms * 1e-3)) if ipp else None,
                          "frac": (ipp * Mp / (collide_ms * 1e-3) / issue_peak) if ipp else None,
                          "source": "ncu smsp__inst_executed.sum of the committed profile" if ipp else
